@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds no arithmetic of the multigrid/IRK method itself: it builds
+the coarsest input mesh (a structured triangulation of the unit square), the
+analytic manufactured solution and its forcing (plain calculus, evaluated at
+points the caller supplies), and reproducible pseudo-random numbers from the
+published SplitMix64 generator.  Both sides consume these arrays; neither side
+derives anything from the other.
+"""
+import numpy as np
+
+__all__ = ["square_mesh", "mms_velocity", "mms_pressure", "mms_forcing",
+           "splitmix64", "uniform01", "normal", "random_vector"]
+
+
+def square_mesh(n):
+    """Unit square, n x n squares, each cut by its (1,-1) diagonal into 2 triangles.
+
+    Vertex (i, j) at (i/n, j/n) has id i + (n+1) j.  Square (i, j) gives the
+    triangles [(i,j), (i+1,j), (i,j+1)] and [(i+1,j), (i+1,j+1), (i,j+1)].
+    Returns (coords float64 [nv,2], cells int64 [nc,3], bnd uint8 [nv]) with
+    bnd = 1 on every boundary vertex (the whole boundary is no-slip).
+    """
+    n = int(n)
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    ii, jj = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy")
+    coords = np.stack([ii.ravel() / n, jj.ravel() / n], axis=1).astype(np.float64)
+    vid = lambda i, j: i + (n + 1) * j
+    cells = []
+    for j in range(n):
+        for i in range(n):
+            cells.append([vid(i, j), vid(i + 1, j), vid(i, j + 1)])
+            cells.append([vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)])
+    cells = np.asarray(cells, dtype=np.int64)
+    bi, bj = ii.ravel(), jj.ravel()
+    bnd = ((bi == 0) | (bi == n) | (bj == 0) | (bj == n)).astype(np.uint8)
+    return coords, cells, bnd
+
+
+# ---------------------------------------------------------------------------
+# Manufactured solution u = g(t) curl(psi), psi = sin^2(pi x) sin^2(pi y),
+# p = g(t) sin(2 pi x) cos(2 pi y).  All derivatives are written out by hand.
+# g = 1 (steady) or g = exp(-t).
+# ---------------------------------------------------------------------------
+
+def _g(t, kind):
+    if kind == "steady":
+        return 1.0, 0.0
+    if kind == "exp":
+        e = np.exp(-t)
+        return e, -e
+    raise ValueError(kind)
+
+
+def mms_velocity(x, y, t=0.0, kind="steady"):
+    """u = g(t) (d psi/dy, -d psi/dx); vanishes on the boundary of the unit square."""
+    g, _ = _g(t, kind)
+    sx, cx = np.sin(np.pi * x), np.cos(np.pi * x)
+    sy, cy = np.sin(np.pi * y), np.cos(np.pi * y)
+    ux = 2.0 * np.pi * sx * sx * sy * cy
+    uy = -2.0 * np.pi * sx * cx * sy * sy
+    return g * ux, g * uy
+
+
+def mms_pressure(x, y, t=0.0, kind="steady"):
+    """p = g(t) sin(2 pi x) cos(2 pi y); it has zero mean on the unit square."""
+    g, _ = _g(t, kind)
+    return g * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+
+
+def mms_forcing(x, y, t=0.0, nu=1.0, kind="steady"):
+    """f = g' u_s - nu g Lap(u_s) + g grad(p_s) for the fields above.
+
+    With ux_s = pi sin^2(pi x) sin(2 pi y): Lap ux_s = 2pi^3 cos(2pi x) sin(2pi y)
+    - 4 pi^3 sin^2(pi x) sin(2 pi y); uy_s = -pi sin(2 pi x) sin^2(pi y) gives
+    Lap uy_s = 4 pi^3 sin(2pi x) sin^2(pi y) - 2 pi^3 sin(2 pi x) cos(2 pi y).
+    """
+    g, dg = _g(t, kind)
+    pi = np.pi
+    s2x, c2x = np.sin(2 * pi * x), np.cos(2 * pi * x)
+    s2y, c2y = np.sin(2 * pi * y), np.cos(2 * pi * y)
+    sx2 = np.sin(pi * x) ** 2
+    sy2 = np.sin(pi * y) ** 2
+    ux = pi * sx2 * s2y
+    uy = -pi * s2x * sy2
+    lap_ux = 2 * pi ** 3 * c2x * s2y - 4 * pi ** 3 * sx2 * s2y
+    lap_uy = 4 * pi ** 3 * s2x * sy2 - 2 * pi ** 3 * s2x * c2y
+    dpx = 2 * pi * c2x * c2y
+    dpy = -2 * pi * s2x * s2y
+    fx = dg * ux - nu * g * lap_ux + g * dpx
+    fy = dg * uy - nu * g * lap_uy + g * dpy
+    return fx, fy
+
+
+# ---------------------------------------------------------------------------
+# SplitMix64 (Steele, Lea, Flood 2014): state += 0x9E3779B97F4A7C15, then the
+# published two multiply-xorshift rounds.  Vectorised over counters.
+# ---------------------------------------------------------------------------
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(seed, count, offset=0):
+    """Return `count` uint64 outputs of SplitMix64 started from `seed`."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed, count, offset=0):
+    """Doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, count, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed, count, offset=0):
+    """Standard normals by Box-Muller on pairs of uniform01 draws."""
+    m = (count + 1) // 2
+    u = uniform01(seed, 2 * m, offset)
+    u1 = 1.0 - u[0::2]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
+    return z[:count]
+
+
+def random_vector(seed, count):
+    """Seeded test vector with entries uniform in [-1, 1)."""
+    return 2.0 * uniform01(seed, count) - 1.0
