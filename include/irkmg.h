@@ -1,0 +1,208 @@
+/*
+ * irkmg — monolithic multigrid for fully implicit Runge–Kutta stage systems of
+ * incompressible (Stokes / Oseen) flow on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The method is that of Abu-Labdeh, MacLachlan & Farrell, "Monolithic multigrid
+ * for implicit Runge–Kutta discretizations of incompressible fluid flow"
+ * (arXiv:2202.07381):
+ *   - the stage system (Section 3.1, Kronecker form)
+ *       ( I_s ⊗ [[M,0],[0,0]] + dt·A ⊗ [[K,B],[Bᵀ,0]] ) k = F,
+ *     Taylor–Hood P2–P1 on triangles, K = nu·(P2 stiffness) [+ Oseen convection],
+ *     B the weak gradient from −<p, div v>;
+ *   - FGMRES as the outer Krylov method (Section 4);
+ *   - a geometric V-cycle with rediscretised coarse operators, I_s⊗P transfers,
+ *     restriction Pᵀ and a direct coarsest solve (Section 4.1);
+ *   - additive vertex-star Vanka relaxation with all s stages in every patch
+ *     (Section 4.2), damped or Chebyshev-accelerated (Section 5.1).
+ *
+ * Vector layout (every d_* vector of a level): stage-major, length
+ * N = s·(2·nf + nv); inside a stage the u_x block over the nf free
+ * (non-Dirichlet) P2 nodes, then the u_y block, then the pressure block over
+ * all nv vertices.  This is the ordering of Section 3.1 (stages consecutive,
+ * each (k_u, k_p) pair kept together).
+ *
+ * Numbering: mesh edges are the sorted vertex pairs in lexicographic order;
+ * P2 nodes are the vertices followed by the edge midpoints; free P2 nodes keep
+ * that order.  Refinement keeps coarse vertex ids and appends one vertex per
+ * coarse edge, so the P2 nodes of level l are the vertices of level l+1.
+ *
+ * Ownership: host arrays passed to a call are read during the call only.  All
+ * d_* pointers are caller-owned device pointers (e.g. the data pointer of a
+ * contiguous float64 CUDA tensor), read and written on the context's stream
+ * (irkmg_options.cuda_stream).  The context owns every device buffer it
+ * allocates (matrices, patch inverses, Krylov basis) and frees them in
+ * irkmg_destroy.
+ *
+ * Errors: every int-returning call returns one of the IRKMG_* codes below;
+ * nothing aborts, traps or throws across this interface.  irkmg_last_error()
+ * gives a one-line description of the most recent failure on the calling
+ * thread.
+ */
+#ifndef IRKMG_H
+#define IRKMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define IRKMG_OK 0
+#define IRKMG_EINVAL 1     /* bad sizes/arguments, inconsistent tableau, bad mesh  */
+#define IRKMG_ENOMEM 2     /* device or host allocation failed                      */
+#define IRKMG_ECUDA 3      /* a CUDA runtime call or kernel launch failed          */
+#define IRKMG_ESINGULAR 4  /* a patch or coarse pivot fell below 1e3·eps·max|A|    */
+#define IRKMG_ENOCONV 5    /* FGMRES hit maxit; the best iterate is written        */
+#define IRKMG_ETIMEOUT 6   /* a bounded device wait expired                        */
+#define IRKMG_ENOTIMPL 7   /* the requested form is not built                      */
+
+typedef struct irkmg_ctx irkmg_ctx;
+
+/* Coarsest mesh (Section 4.1: the hierarchy is its uniform refinements).
+ * Triangles only (dim = 2).  coords: nverts·2 doubles (x, y per vertex);
+ * cells: ncells·3 vertex ids; bnd_vertex: 1 on Dirichlet (no-slip) vertices.
+ * An edge is Dirichlet iff it lies on the boundary and both ends are flagged. */
+typedef struct {
+  int dim;
+  int64_t nverts, ncells;
+  const double *coords;
+  const int64_t *cells;
+  const uint8_t *bnd_vertex;
+} irkmg_mesh;
+
+/* Butcher tableau (Section 2): A row-major s×s, b and c of length s.
+ * irkmg_setup checks sum_j b_j = 1 and sum_j a_ij = c_i to 1e-12. */
+typedef struct {
+  int s;
+  const double *A, *b, *c;
+} irkmg_tableau;
+
+/* Solver options; irkmg_default_options fills the paper's 2D Stokes choices
+ * (Section 5.1): V(2,2), Chebyshev on [2, 8], FGMRES restart 30. */
+typedef struct {
+  int nlevels;             /* levels including the coarsest (>= 2)                  */
+  int nu_pre, nu_post;     /* relaxation steps before / after the coarse correction */
+  int smoother;            /* 0: damped additive Vanka (omega); 1: Chebyshev        */
+  double omega;            /* damping of smoother 0                                 */
+  double cheb_lo, cheb_hi; /* Chebyshev interval of smoother 1                      */
+  double rtol, atol;       /* stop when ||F - J k|| <= max(rtol ||F||, atol)        */
+  int restart, maxit;      /* FGMRES(restart), at most maxit iterations in total    */
+  int patch_precision;     /* 64: FP64 patch inverses; 32: FP32 inverses + applies  */
+  const double *wind;      /* host, finest-level Oseen wind at every P2 node,
+                              np2·2 doubles (x, y per node), or NULL for Stokes     */
+  void *cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream  */
+  int64_t timeout_spins;   /* bound for device-side waits (0 = library default)     */
+} irkmg_options;
+
+typedef struct {
+  int iters;               /* FGMRES iterations taken                               */
+  int status;              /* IRKMG_* of the solve                                  */
+  double r0, rfinal;       /* ||F - J k0||, final true residual norm                */
+  double t_setup, t_solve; /* seconds (host clock around synchronised work)         */
+  int64_t bad_index;       /* patch id (or coarse row) for IRKMG_ESINGULAR, else -1 */
+} irkmg_stats;
+
+typedef struct {
+  int64_t nv, ne, nc;      /* vertices, edges, cells of the level                   */
+  int64_t np2, nf;         /* P2 nodes, free P2 nodes                               */
+  int64_t m, N;            /* per-stage length 2 nf + nv, full length s·m           */
+  int64_t npatch, ncolours;/* Vanka patches (one per vertex), colours               */
+  int64_t max_patch_dofs;  /* largest patch size s·(2·nodes + 1)                    */
+  int64_t factor_bytes;    /* bytes of stored patch inverses on this level          */
+} irkmg_level_info;
+
+/* ---- set-up -------------------------------------------------------------- */
+
+/* Defaults described above.  Never fails. */
+void irkmg_default_options(irkmg_options *opt);
+
+/* Radau IIA(s) tableau into host arrays A[s*s], b[s], c[s] (Section 5: the
+ * standard RadauIIA family).  s in 1..3 from closed forms.  EINVAL otherwise. */
+int irkmg_radau_iia(int s, double *A, double *b, double *c);
+
+/* Build the hierarchy, assemble every level, build patch maps and colourings,
+ * factor (invert) every patch and the bordered coarsest system.  Host inputs
+ * are copied.  On failure *out is NULL. */
+int irkmg_setup(const irkmg_mesh *mesh, const irkmg_tableau *tab, double dt, double nu,
+                const irkmg_options *opt, irkmg_ctx **out);
+
+/* Re-assemble and re-factor for a new dt and nu (same mesh, tableau, wind). */
+int irkmg_update(irkmg_ctx *ctx, double dt, double nu);
+
+/* Sizes of level l (0 = coarsest, nlevels-1 = finest). */
+int irkmg_level_info_get(const irkmg_ctx *ctx, int level, irkmg_level_info *info);
+
+/* Host copies of set-up data of level l, for inspection and tests.
+ * irkmg_p2_coords: np2·2 doubles.  irkmg_free_nodes: nf int64 P2-node ids.
+ * irkmg_patch_map: ptr[npatch+1] and nodes[ptr[npatch]] (free-node ids,
+ * ascending per patch: the velocity nodes of the closure of the star of each
+ * vertex, Section 4.2).  irkmg_colouring: colour per vertex (greedy distance-2
+ * colouring in vertex-id order).  Pass NULL to query sizes through
+ * irkmg_level_info_get first. */
+int irkmg_p2_coords(const irkmg_ctx *ctx, int level, double *xy);
+int irkmg_free_nodes(const irkmg_ctx *ctx, int level, int64_t *ids);
+int irkmg_patch_map(const irkmg_ctx *ctx, int level, int64_t *ptr, int32_t *nodes);
+int irkmg_colouring(const irkmg_ctx *ctx, int level, int32_t *colour);
+
+/* ---- operators on level l (device vectors of length N_l) ---------------- */
+
+/* y = J x (transpose = 0) or y = Jᵀ x (transpose = 1), Section 3.1. */
+int irkmg_apply(irkmg_ctx *ctx, int level, const double *d_x, double *d_y, int transpose);
+
+/* c = sum_v R_vᵀ (R_v J R_vᵀ)^{-1} R_v r  (one additive Vanka correction,
+ * Section 4.2), with the stored patch inverses; transpose = 1 uses Jᵀ. */
+int irkmg_vanka_correction(irkmg_ctx *ctx, int level, const double *d_r, double *d_c,
+                           int transpose);
+
+/* nsteps relaxation steps on J x = F from the x given (in/out), with the
+ * smoother of the options (Sections 4.2, 5.1). */
+int irkmg_smooth(irkmg_ctx *ctx, int level, const double *d_F, double *d_x, int nsteps,
+                 int transpose);
+
+/* Transfers between level l (fine) and l-1: d_coarse = (I_s ⊗ P)ᵀ d_fine, and
+ * d_fine = (I_s ⊗ P) d_coarse (overwrites), Section 4.1. */
+int irkmg_restrict(irkmg_ctx *ctx, int level, const double *d_fine, double *d_coarse);
+int irkmg_prolong(irkmg_ctx *ctx, int level, const double *d_coarse, double *d_fine);
+
+/* Coarsest-level direct solve of the bordered system [[J, N], [Nᵀ, 0]] (N:
+ * one constant-pressure column per stage); the result has zero pressure sum
+ * in every stage. */
+int irkmg_coarse_solve(irkmg_ctx *ctx, const double *d_r, double *d_x, int transpose);
+
+/* ---- the solver ---------------------------------------------------------- */
+
+/* One V(nu_pre, nu_post) cycle on the finest level with zero initial guess. */
+int irkmg_vcycle(irkmg_ctx *ctx, const double *d_r, double *d_z, int transpose);
+
+/* FGMRES(restart) right-preconditioned by the V-cycle: J k = F on the finest
+ * level.  d_k holds the initial guess on entry and the solution on return.
+ * Each preconditioned vector has its per-stage pressure mean removed.
+ * stats may be NULL.  Returns ENOCONV (with the best iterate) at maxit. */
+int irkmg_solve(irkmg_ctx *ctx, const double *d_F, double *d_k, irkmg_stats *stats);
+
+/* The same for the transposed stage operator: Jᵀ lam = G (discrete adjoint;
+ * transposed Vanka patches, A -> Aᵀ). */
+int irkmg_adjoint_solve(irkmg_ctx *ctx, const double *d_G, double *d_lam, irkmg_stats *stats);
+
+/* ---- time stepping (Section 3.1) ----------------------------------------- */
+
+/* F_i = [ M f_i - K u^n - B p^n ; -Bᵀ u^n ] on the finest level.
+ * d_un: 2·nf (u_x then u_y on free nodes), d_pn: nv, d_f: s·2·np2 (stage,
+ * component, every P2 node: the interpolant of the forcing at t + c_i dt). */
+int irkmg_stage_rhs(irkmg_ctx *ctx, const double *d_un, const double *d_pn, const double *d_f,
+                    double *d_F);
+
+/* u^{n+1} = u^n + dt sum_j b_j k_j^u and likewise p (in place). */
+int irkmg_advance(irkmg_ctx *ctx, const double *d_k, double *d_un, double *d_pn);
+
+/* ---- teardown, diagnostics ------------------------------------------------ */
+void irkmg_destroy(irkmg_ctx *ctx);
+const char *irkmg_strerror(int status);
+const char *irkmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IRKMG_H */

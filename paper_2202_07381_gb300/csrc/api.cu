@@ -1,0 +1,706 @@
+// irkmg C ABI: set-up of the hierarchy, the V-cycle, the smoothers and FGMRES.
+//
+// Section 4: FGMRES right-preconditioned by a monolithic V-cycle whose
+// relaxation is the IRK-extended additive Vanka step (Section 4.2), damped or
+// Chebyshev-accelerated (Section 5.1), with I_s ⊗ P transfers, restriction Pᵀ
+// and a direct coarsest solve (Section 4.1).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "irkmg_internal.h"
+
+using namespace irkmg;
+
+struct irkmg_ctx : public Ctx {};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(IRKMG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+template <typename T>
+int dalloc(Ctx& C, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(IRKMG_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) +
+                                  " bytes failed: " + cudaGetErrorString(e));
+  }
+  C.allocs.push_back((void*)*p);
+  C.dev_bytes += (int64_t)(sizeof(T) * count);
+  return IRKMG_OK;
+}
+
+template <typename T>
+int upload(Ctx& C, T** p, const std::vector<T>& h) {
+  int rc = dalloc(C, p, h.size());
+  if (rc) return rc;
+  if (!h.empty()) CK(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return IRKMG_OK;
+}
+
+int upload_csr(Ctx& C, DevCSR& d, const HostCSR& h, int nvals) {
+  d.nrows = (int32_t)h.nrows;
+  d.nnz = h.nnz();
+  int rc;
+  if ((rc = upload(C, &d.ptr, h.ptr))) return rc;
+  if ((rc = upload(C, &d.col, h.col))) return rc;
+  for (int k = 0; k < nvals; ++k)
+    if ((rc = upload(C, &d.v[k], h.v[k]))) return rc;
+  return IRKMG_OK;
+}
+
+int refresh_csr_values(Ctx& C, DevCSR& d, const HostCSR& h, int nvals) {
+  (void)C;
+  for (int k = 0; k < nvals; ++k)
+    CK(cudaMemcpy(d.v[k], h.v[k].data(), sizeof(double) * h.v[k].size(), cudaMemcpyHostToDevice));
+  return IRKMG_OK;
+}
+
+int check_err(Ctx& C, const char* what, irkmg_stats* st = nullptr) {
+  int h[2] = {0, 0};
+  CK(cudaMemcpy(h, C.d_err, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[0] != 0) {
+    CK(cudaMemset(C.d_err, 0, sizeof(int) * 2));
+    if (st) st->bad_index = h[1];
+    return fail(h[0], std::string(what) + ": singular pivot at index " + std::to_string(h[1]));
+  }
+  return IRKMG_OK;
+}
+
+// --- patches: maps, colouring, ordering, inverses (Section 4.2) -----------
+int build_patches(Ctx& C, Level& L) {
+  const int maxnodes = 64;
+  int rc;
+  if ((rc = upload(C, &L.d_cells, L.mesh.cells))) return rc;
+  if ((rc = upload(C, &L.d_cell_edges, L.mesh.cell_edges))) return rc;
+  if ((rc = upload(C, &L.d_vc_ptr, L.mesh.vc_ptr))) return rc;
+  if ((rc = upload(C, &L.d_vc_idx, L.mesh.vc_idx))) return rc;
+  if ((rc = upload(C, &L.d_vv_ptr, L.mesh.vv_ptr))) return rc;
+  if ((rc = upload(C, &L.d_vv_idx, L.mesh.vv_idx))) return rc;
+  if ((rc = upload(C, &L.d_p2_to_free, L.mesh.p2_to_free))) return rc;
+  int32_t *d_tmp = nullptr, *d_cnt = nullptr;
+  CK(cudaMalloc(&d_tmp, sizeof(int32_t) * L.nv * maxnodes));
+  CK(cudaMalloc(&d_cnt, sizeof(int32_t) * (L.nv + 1)));
+  if ((rc = dalloc(C, &L.d_patch_ptr, L.nv + 1))) return rc;
+  CK(launch_patch_maps(L, C.stream, maxnodes, d_tmp, d_cnt));
+  std::vector<int32_t> cnt(L.nv);
+  CK(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * L.nv, cudaMemcpyDeviceToHost, C.stream));
+  CK(cudaStreamSynchronize(C.stream));
+  for (int64_t v = 0; v < L.nv; ++v)
+    if (cnt[v] < 0) {
+      cudaFree(d_tmp);
+      cudaFree(d_cnt);
+      return fail(IRKMG_EINVAL, "vertex star too large for the patch builder");
+    }
+  CK(launch_scan(d_cnt, L.d_patch_ptr, L.nv, C.stream));
+  L.h_patch_ptr.resize(L.nv + 1);
+  CK(cudaMemcpyAsync(L.h_patch_ptr.data(), L.d_patch_ptr, sizeof(int32_t) * (L.nv + 1),
+                     cudaMemcpyDeviceToHost, C.stream));
+  CK(cudaStreamSynchronize(C.stream));
+  if ((rc = dalloc(C, &L.d_patch_nodes, L.h_patch_ptr[L.nv]))) return rc;
+  CK(launch_compact_patches(L, C.stream, maxnodes, d_tmp, d_cnt));
+  L.h_patch_nodes.resize(L.h_patch_ptr[L.nv]);
+  CK(cudaMemcpyAsync(L.h_patch_nodes.data(), L.d_patch_nodes,
+                     sizeof(int32_t) * L.h_patch_nodes.size(), cudaMemcpyDeviceToHost, C.stream));
+  // colouring: Jones–Plassmann rounds until every vertex is coloured
+  if ((rc = dalloc(C, &L.d_colour, L.nv))) return rc;
+  CK(cudaMemsetAsync(L.d_colour, 0xff, sizeof(int32_t) * L.nv, C.stream));
+  int* d_flags = d_cnt;  // reuse: [0] remaining, [1] overflow
+  int h_flags[2] = {1, 0};
+  int64_t rounds = 0;
+  while (h_flags[0] > 0) {
+    CK(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2, C.stream));
+    for (int k = 0; k < 8; ++k) {
+      if (k == 7) CK(cudaMemsetAsync(d_flags, 0, sizeof(int), C.stream));
+      CK(launch_colour_round(L, C.stream, d_flags, d_flags + 1));
+    }
+    CK(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, C.stream));
+    CK(cudaStreamSynchronize(C.stream));
+    rounds += 8;
+    if (h_flags[1]) return fail(IRKMG_EINVAL, "colouring needs more than 256 colours");
+    if (rounds > 8 * (L.nv + 8)) return fail(IRKMG_ETIMEOUT, "colouring did not finish");
+  }
+  cudaFree(d_tmp);
+  cudaFree(d_cnt);
+  L.h_colour.resize(L.nv);
+  CK(cudaMemcpy(L.h_colour.data(), L.d_colour, sizeof(int32_t) * L.nv, cudaMemcpyDeviceToHost));
+  // order patches by (colour, vertex id); factor offsets in that order
+  L.ncolours = 0;
+  for (int32_t c : L.h_colour) L.ncolours = std::max(L.ncolours, c + 1);
+  std::vector<int64_t> start(L.ncolours + 1, 0);
+  for (int32_t c : L.h_colour) start[c + 1]++;
+  for (int c = 0; c < L.ncolours; ++c) start[c + 1] += start[c];
+  std::vector<int32_t> order(L.nv);
+  {
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t v = 0; v < L.nv; ++v) order[fill[L.h_colour[v]]++] = (int32_t)v;
+  }
+  L.colour_start = start;
+  std::vector<int64_t> off(L.nv + 1, 0);
+  L.max_np = 0;
+  for (int64_t i = 0; i < L.nv; ++i) {
+    const int32_t v = order[i];
+    const int64_t np = (int64_t)C.s * (2 * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
+    L.max_np = std::max<int>(L.max_np, (int)np);
+    // keep every patch inverse 16-byte aligned
+    const int64_t elems = np * np;
+    const int64_t align = (C.opt.patch_precision == 64) ? 2 : 4;
+    off[i + 1] = off[i] + (elems + align - 1) / align * align;
+  }
+  if (L.max_np > 160)
+    return fail(IRKMG_ENOTIMPL, "patches above 160 DoFs need the blocked patch factorisation");
+  L.fac_elems = off[L.nv];
+  if ((rc = upload(C, &L.d_order, order))) return rc;
+  off.pop_back();
+  if ((rc = upload(C, &L.d_fac_off, off))) return rc;
+  const size_t esz = C.opt.patch_precision == 64 ? 8 : 4;
+  void* fac = nullptr;
+  cudaError_t e = cudaMalloc(&fac, esz * std::max<int64_t>(L.fac_elems, 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IRKMG_ENOMEM, "patch inverses: " + std::to_string(esz * L.fac_elems) + " bytes");
+  }
+  C.allocs.push_back(fac);
+  C.dev_bytes += esz * L.fac_elems;
+  L.d_fac = fac;
+  return IRKMG_OK;
+}
+
+int factor_level(Ctx& C, Level& L) {
+  CK(launch_patch_invert(C, L, C.opt.patch_precision));
+  return IRKMG_OK;
+}
+
+int factor_coarse(Ctx& C) {
+  CK(launch_coarse_build(C, C.d_coarse_inv));
+  CK(coarse_invert(C, C.d_coarse_inv, C.nb));
+  return IRKMG_OK;
+}
+
+int assemble_all(Ctx& C) {
+  const int nl = (int)C.L.size();
+  std::vector<std::vector<double>> winds(nl);
+  if (!C.wind.empty()) {
+    winds[nl - 1] = C.wind;
+    for (int l = nl - 2; l >= 0; --l)
+      winds[l].assign(winds[l + 1].begin(), winds[l + 1].begin() + 2 * C.L[l].np2);
+  }
+  for (int l = 0; l < nl; ++l)
+    assemble_level(C.L[l].mesh, C.nu, winds[l].empty() ? nullptr : winds[l].data(), C.L[l].hops);
+  return IRKMG_OK;
+}
+
+int factor_all(Ctx& C) {
+  int rc;
+  for (size_t l = 1; l < C.L.size(); ++l)
+    if ((rc = factor_level(C, C.L[l]))) return rc;
+  if ((rc = factor_coarse(C))) return rc;
+  CK(cudaStreamSynchronize(C.stream));
+  return check_err(C, "factorisation");
+}
+
+// --- smoothers and V-cycle -------------------------------------------------
+int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr) {
+  for (int c = 0; c < L.ncolours; ++c) CK(launch_vanka(C, L, c, r, out, scale, tr));
+  return IRKMG_OK;
+}
+
+// nsteps relaxation steps on J x = b from x (x == 0 on entry if zero_init).
+int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_init, int tr) {
+  if (nsteps <= 0) {
+    if (zero_init) CK(launch_fill(x, 0.0, L.N, C.stream));
+    return IRKMG_OK;
+  }
+  int rc;
+  if (C.opt.smoother == 0) {
+    if (zero_init) CK(launch_fill(x, 0.0, L.N, C.stream));
+    for (int k = 0; k < nsteps; ++k) {
+      const double* res = b;
+      if (!(zero_init && k == 0)) {
+        CK(launch_residual(C, L, b, x, L.t, tr));
+        res = L.t;
+      }
+      if ((rc = vanka_all(C, L, res, x, C.opt.omega, tr))) return rc;
+    }
+    return IRKMG_OK;
+  }
+  const double theta = 0.5 * (C.opt.cheb_hi + C.opt.cheb_lo);
+  const double delta = 0.5 * (C.opt.cheb_hi - C.opt.cheb_lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const double* res = b;
+  if (!zero_init) {
+    CK(launch_residual(C, L, b, x, L.t, tr));
+    res = L.t;
+  }
+  CK(launch_fill(L.d, 0.0, L.N, C.stream));
+  if ((rc = vanka_all(C, L, res, L.d, 1.0 / theta, tr))) return rc;
+  if (zero_init)
+    CK(cudaMemcpyAsync(x, L.d, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, C.stream));
+  else
+    CK(launch_axpby(x, L.d, 1.0, 1.0, L.N, C.stream));
+  for (int k = 1; k < nsteps; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    CK(launch_residual(C, L, b, x, L.t, tr));
+    CK(launch_axpby(L.d, L.d, rho_new * rho, 0.0, L.N, C.stream));
+    if ((rc = vanka_all(C, L, L.t, L.d, 2.0 * rho_new / delta, tr))) return rc;
+    CK(launch_axpby(x, L.d, 1.0, 1.0, L.N, C.stream));
+    rho = rho_new;
+  }
+  return IRKMG_OK;
+}
+
+int vcycle_level(Ctx& C, int l, const double* b, double* z, int tr) {
+  if (l == 0) {
+    CK(launch_coarse_apply(C, b, z, tr));
+    return IRKMG_OK;
+  }
+  Level& L = C.L[l];
+  Level& Lc = C.L[l - 1];
+  int rc;
+  if ((rc = smooth(C, L, b, z, C.opt.nu_pre, true, tr))) return rc;
+  CK(launch_residual(C, L, b, z, L.t, tr));
+  CK(launch_restrict(C, L, L.t, Lc.r));
+  if ((rc = vcycle_level(C, l - 1, Lc.r, Lc.z, tr))) return rc;
+  CK(launch_prolong(C, L, Lc.z, z, 1));
+  return smooth(C, L, b, z, C.opt.nu_post, false, tr);
+}
+
+// --- FGMRES (Section 4) -----------------------------------------------------
+int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
+  Level& L = C.L.back();
+  const int64_t n = L.N;
+  const int m = C.opt.restart;
+  const double t0 = now();
+  double* V = C.d_V;
+  double* Z = C.d_Z;
+  double* w = C.d_w;
+  double* hd = C.d_h;       // device: [0..m] h1, [64..] h2, [128] norm
+  double* hh = C.h_h;       // pinned host mirror
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+  auto norm = [&](const double* v, double* out) -> int {
+    CK(launch_multidot(v, 0, 1, v, n, C.d_part, hd + 192, C.stream));
+    CK(cudaMemcpyAsync(hh + 192, hd + 192, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
+    CK(cudaStreamSynchronize(C.stream));
+    *out = std::sqrt(hh[192]);
+    return IRKMG_OK;
+  };
+  int rc;
+  double bnorm;
+  if ((rc = norm(F, &bnorm))) return rc;
+  const double target = std::max(C.opt.rtol * bnorm, C.opt.atol);
+  CK(launch_residual(C, L, F, x, V, tr));
+  double beta;
+  if ((rc = norm(V, &beta))) return rc;
+  if (st) {
+    st->r0 = beta;
+    st->iters = 0;
+  }
+  int its = 0;
+  while (beta > target && its < C.opt.maxit) {
+    CK(launch_axpby(V, V, 1.0 / beta, 0.0, n, C.stream));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (int64_t)j * n;
+      double* zj = Z + (int64_t)j * n;
+      if ((rc = vcycle_level(C, (int)C.L.size() - 1, vj, zj, tr))) return rc;
+      CK(launch_pressure_mean_remove(C, L, zj));
+      CK(launch_residual(C, L, nullptr, zj, w, tr));
+      // classical Gram–Schmidt, twice
+      CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd, C.stream));
+      CK(launch_multiaxpy(w, V, n, j + 1, hd, -1.0, n, C.stream));
+      CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd + 64, C.stream));
+      CK(launch_multiaxpy(w, V, n, j + 1, hd + 64, -1.0, n, C.stream));
+      CK(launch_multidot(w, 0, 1, w, n, C.d_part, hd + 128, C.stream));
+      CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 129, cudaMemcpyDeviceToHost, C.stream));
+      CK(cudaStreamSynchronize(C.stream));
+      double* Hj = &H[(size_t)j * (m + 1)];  // column j, length m+1
+      for (int i = 0; i <= j; ++i) Hj[i] = hh[i] + hh[64 + i];
+      const double hn = std::sqrt(hh[128]);
+      Hj[j + 1] = hn;
+      if (hn > 0.0) CK(launch_axpby(V + (int64_t)(j + 1) * n, w, 1.0 / hn, 0.0, n, C.stream));
+      for (int i = 0; i < j; ++i) {
+        const double a = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+        Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+        Hj[i] = a;
+      }
+      const double den = std::hypot(Hj[j], Hj[j + 1]);
+      cs[j] = Hj[j] / den;
+      sn[j] = Hj[j + 1] / den;
+      Hj[j] = den;
+      Hj[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= target || its >= C.opt.maxit || hn == 0.0) break;
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < jdone; ++k) s -= H[(size_t)k * (m + 1) + i] * y[k];
+      y[i] = s / H[(size_t)i * (m + 1) + i];
+    }
+    std::copy(y.begin(), y.begin() + jdone, hh + 256);
+    CK(cudaMemcpyAsync(hd + 256, hh + 256, sizeof(double) * jdone, cudaMemcpyHostToDevice,
+                       C.stream));
+    CK(launch_multiaxpy(x, Z, n, jdone, hd + 256, 1.0, n, C.stream));
+    CK(launch_residual(C, L, F, x, V, tr));
+    if ((rc = norm(V, &beta))) return rc;
+  }
+  if (st) {
+    st->iters = its;
+    st->rfinal = beta;
+    st->t_solve = now() - t0;
+    st->status = beta <= target ? IRKMG_OK : IRKMG_ENOCONV;
+    st->bad_index = -1;
+  }
+  if (beta > target) return fail(IRKMG_ENOCONV, "FGMRES reached maxit");
+  return IRKMG_OK;
+}
+
+int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double nu,
+             const irkmg_options* o) {
+  if (!mesh || !tab || !o) return fail(IRKMG_EINVAL, "null argument");
+  if (mesh->dim != 2) return fail(IRKMG_ENOTIMPL, "only dim = 2 (triangles) is built");
+  if (!mesh->coords || !mesh->cells || !mesh->bnd_vertex) return fail(IRKMG_EINVAL, "mesh arrays");
+  if (tab->s < 1 || tab->s > 3 || !tab->A || !tab->b || !tab->c)
+    return fail(IRKMG_EINVAL, "tableau: 1 <= s <= 3 and A, b, c required");
+  double sb = 0.0;
+  for (int j = 0; j < tab->s; ++j) sb += tab->b[j];
+  if (std::fabs(sb - 1.0) > 1e-12) return fail(IRKMG_EINVAL, "tableau: sum b != 1");
+  for (int i = 0; i < tab->s; ++i) {
+    double sa = 0.0;
+    for (int j = 0; j < tab->s; ++j) sa += tab->A[i * tab->s + j];
+    if (std::fabs(sa - tab->c[i]) > 1e-12) return fail(IRKMG_EINVAL, "tableau: row sum != c");
+  }
+  if (!(dt > 0.0) || !(nu > 0.0)) return fail(IRKMG_EINVAL, "dt and nu must be positive");
+  if (o->nlevels < 2 || o->nlevels > 12) return fail(IRKMG_EINVAL, "nlevels in [2, 12]");
+  if (o->nu_pre < 0 || o->nu_post < 0) return fail(IRKMG_EINVAL, "negative sweep count");
+  if (o->smoother != 0 && o->smoother != 1) return fail(IRKMG_EINVAL, "smoother is 0 or 1");
+  if (o->smoother == 1 && !(o->cheb_hi > o->cheb_lo && o->cheb_lo > 0.0))
+    return fail(IRKMG_EINVAL, "Chebyshev interval needs 0 < lo < hi");
+  if (o->restart < 1 || o->restart > 60) return fail(IRKMG_EINVAL, "restart in [1, 60]");
+  if (o->maxit < 1) return fail(IRKMG_EINVAL, "maxit >= 1");
+  if (o->patch_precision != 64 && o->patch_precision != 32)
+    return fail(IRKMG_EINVAL, "patch_precision is 64 or 32");
+  return IRKMG_OK;
+}
+
+int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt,
+               double nu, const irkmg_options* opt) {
+  const double t0 = now();
+  C->opt = *opt;
+  C->s = tab->s;
+  std::memcpy(C->A, tab->A, sizeof(double) * tab->s * tab->s);
+  std::memcpy(C->b, tab->b, sizeof(double) * tab->s);
+  std::memcpy(C->c, tab->c, sizeof(double) * tab->s);
+  C->dt = dt;
+  C->nu = nu;
+  C->stream = (cudaStream_t)opt->cuda_stream;
+  int rc;
+  const int nl = opt->nlevels;
+  C->L.resize(nl);
+  std::string why = build_mesh(mesh->coords, mesh->cells, mesh->bnd_vertex, mesh->nverts,
+                               mesh->ncells, C->L[0].mesh);
+  if (!why.empty()) return fail(IRKMG_EINVAL, why);
+  for (int l = 1; l < nl; ++l) {
+    if (C->L[l - 1].mesh.np2 > (1LL << 30)) return fail(IRKMG_EINVAL, "hierarchy too large");
+    refine_mesh(C->L[l - 1].mesh, C->L[l].mesh);
+  }
+  if (opt->wind) C->wind.assign(opt->wind, opt->wind + 2 * C->L[nl - 1].mesh.np2);
+  for (int l = 0; l < nl; ++l) {
+    Level& L = C->L[l];
+    L.nv = L.mesh.nv;
+    L.nf = L.mesh.nf;
+    L.np2 = L.mesh.np2;
+    L.m = 2 * L.nf + L.nv;
+    L.N = C->s * L.m;
+  }
+  if ((rc = assemble_all(*C))) return rc;
+  CK(cudaMalloc(&C->d_err, sizeof(int) * 2));
+  C->allocs.push_back(C->d_err);
+  CK(cudaMemset(C->d_err, 0, sizeof(int) * 2));
+  for (int l = 0; l < nl; ++l) {
+    Level& L = C->L[l];
+    if ((rc = upload_csr(*C, L.vel, L.hops.vel, 3))) return rc;
+    if ((rc = upload_csr(*C, L.b, L.hops.b, 2))) return rc;
+    if ((rc = upload_csr(*C, L.bt, L.hops.bt, 2))) return rc;
+    if (l == nl - 1 && (rc = upload_csr(*C, L.mall, L.hops.mall, 1))) return rc;
+    if ((rc = dalloc(*C, &L.r, L.N))) return rc;
+    if ((rc = dalloc(*C, &L.z, L.N))) return rc;
+    if ((rc = dalloc(*C, &L.t, L.N))) return rc;
+    if ((rc = dalloc(*C, &L.d, L.N))) return rc;
+    if (l > 0) {
+      HostCSR Pu, Pp;
+      build_prolongation(C->L[l - 1].mesh, L.mesh, Pu, Pp);
+      if ((rc = upload_csr(*C, L.pu, Pu, 1))) return rc;
+      if ((rc = upload_csr(*C, L.put, transpose_csr(Pu, 1), 1))) return rc;
+      if ((rc = upload_csr(*C, L.pp, Pp, 1))) return rc;
+      if ((rc = upload_csr(*C, L.ppt, transpose_csr(Pp, 1), 1))) return rc;
+      if ((rc = build_patches(*C, L))) return rc;
+    }
+  }
+  C->nb = C->L[0].N + C->s;
+  if (C->nb > 20000) return fail(IRKMG_EINVAL, "coarsest level too large for the dense solve");
+  if ((rc = dalloc(*C, &C->d_coarse_inv, (size_t)C->nb * C->nb))) return rc;
+  if ((rc = dalloc(*C, &C->d_coarse_perm, C->nb))) return rc;
+  const int64_t n = C->L.back().N;
+  const int m = opt->restart;
+  if ((rc = dalloc(*C, &C->d_V, (size_t)(m + 1) * n))) return rc;
+  if ((rc = dalloc(*C, &C->d_Z, (size_t)m * n))) return rc;
+  if ((rc = dalloc(*C, &C->d_w, n))) return rc;
+  if ((rc = dalloc(*C, &C->d_part, (size_t)kMultidotBlocks * 64))) return rc;
+  if ((rc = dalloc(*C, &C->d_h, 512))) return rc;
+  CK(cudaMallocHost(&C->h_h, sizeof(double) * 512));
+  if ((rc = factor_all(*C))) return rc;
+  (void)t0;
+  return IRKMG_OK;
+}
+
+bool level_ok(const irkmg_ctx* ctx, int level) {
+  return ctx && level >= 0 && level < (int)ctx->L.size();
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void irkmg_default_options(irkmg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->nlevels = 3;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->smoother = 1;
+  o->omega = 0.5;
+  o->cheb_lo = 2.0;
+  o->cheb_hi = 8.0;
+  o->rtol = 1e-10;
+  o->atol = 1e-30;
+  o->restart = 30;
+  o->maxit = 200;
+  o->patch_precision = 64;
+  o->wind = nullptr;
+  o->cuda_stream = nullptr;
+  o->timeout_spins = 0;
+}
+
+int irkmg_radau_iia(int s, double* A, double* b, double* c) {
+  if (!A || !b || !c) return fail(IRKMG_EINVAL, "null output");
+  int rc = radau_iia(s, A, b, c);
+  if (rc) return fail(rc, "Radau IIA closed forms exist here for s = 1, 2, 3");
+  return IRKMG_OK;
+}
+
+int irkmg_setup(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double nu,
+                const irkmg_options* opt, irkmg_ctx** out) {
+  if (!out) return fail(IRKMG_EINVAL, "null out");
+  *out = nullptr;
+  int rc = validate(mesh, tab, dt, nu, opt);
+  if (rc) return rc;
+  irkmg_ctx* C = new (std::nothrow) irkmg_ctx();
+  if (!C) return fail(IRKMG_ENOMEM, "context");
+  rc = setup_impl(C, mesh, tab, dt, nu, opt);
+  if (rc) {
+    std::string msg = g_last_error;
+    irkmg_destroy(C);
+    g_last_error = msg;
+    return rc;
+  }
+  *out = C;
+  return IRKMG_OK;
+}
+
+int irkmg_update(irkmg_ctx* C, double dt, double nu) {
+  if (!C || !(dt > 0.0) || !(nu > 0.0)) return fail(IRKMG_EINVAL, "bad update");
+  CK(C->stream ? cudaStreamSynchronize(C->stream) : cudaDeviceSynchronize());
+  C->dt = dt;
+  C->nu = nu;
+  int rc;
+  if ((rc = assemble_all(*C))) return rc;
+  for (size_t l = 0; l < C->L.size(); ++l) {
+    Level& L = C->L[l];
+    if ((rc = refresh_csr_values(*C, L.vel, L.hops.vel, 3))) return rc;
+    if ((rc = refresh_csr_values(*C, L.b, L.hops.b, 2))) return rc;
+    if ((rc = refresh_csr_values(*C, L.bt, L.hops.bt, 2))) return rc;
+    if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.mall, L.hops.mall, 1))) return rc;
+  }
+  return factor_all(*C);
+}
+
+int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) {
+  if (!level_ok(C, level) || !info) return fail(IRKMG_EINVAL, "bad level");
+  const Level& L = C->L[level];
+  info->nv = L.nv;
+  info->ne = L.mesh.ne;
+  info->nc = L.mesh.nc;
+  info->np2 = L.np2;
+  info->nf = L.nf;
+  info->m = L.m;
+  info->N = L.N;
+  info->npatch = level > 0 ? L.nv : 0;
+  info->ncolours = L.ncolours;
+  info->max_patch_dofs = L.max_np;
+  info->factor_bytes = L.fac_elems * (C->opt.patch_precision == 64 ? 8 : 4);
+  return IRKMG_OK;
+}
+
+int irkmg_p2_coords(const irkmg_ctx* C, int level, double* xy) {
+  if (!level_ok(C, level) || !xy) return fail(IRKMG_EINVAL, "bad level");
+  const HostMesh& m = C->L[level].mesh;
+  std::copy(m.xy.begin(), m.xy.end(), xy);
+  for (int64_t e = 0; e < m.ne; ++e) {
+    const int32_t a = m.edges[2 * e], b = m.edges[2 * e + 1];
+    xy[2 * (m.nv + e)] = 0.5 * (m.xy[2 * a] + m.xy[2 * b]);
+    xy[2 * (m.nv + e) + 1] = 0.5 * (m.xy[2 * a + 1] + m.xy[2 * b + 1]);
+  }
+  return IRKMG_OK;
+}
+
+int irkmg_free_nodes(const irkmg_ctx* C, int level, int64_t* ids) {
+  if (!level_ok(C, level) || !ids) return fail(IRKMG_EINVAL, "bad level");
+  const HostMesh& m = C->L[level].mesh;
+  for (int64_t i = 0; i < m.nf; ++i) ids[i] = m.free_to_p2[i];
+  return IRKMG_OK;
+}
+
+int irkmg_patch_map(const irkmg_ctx* C, int level, int64_t* ptr, int32_t* nodes) {
+  if (!level_ok(C, level) || level == 0 || !ptr || !nodes)
+    return fail(IRKMG_EINVAL, "bad level (patches exist on levels >= 1)");
+  const Level& L = C->L[level];
+  for (int64_t v = 0; v <= L.nv; ++v) ptr[v] = L.h_patch_ptr[v];
+  std::copy(L.h_patch_nodes.begin(), L.h_patch_nodes.end(), nodes);
+  return IRKMG_OK;
+}
+
+int irkmg_colouring(const irkmg_ctx* C, int level, int32_t* colour) {
+  if (!level_ok(C, level) || level == 0 || !colour)
+    return fail(IRKMG_EINVAL, "bad level (patches exist on levels >= 1)");
+  const Level& L = C->L[level];
+  std::copy(L.h_colour.begin(), L.h_colour.end(), colour);
+  return IRKMG_OK;
+}
+
+int irkmg_apply(irkmg_ctx* C, int level, const double* x, double* y, int transpose) {
+  if (!level_ok(C, level) || !x || !y) return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_residual(*C, C->L[level], nullptr, x, y, transpose ? 1 : 0));
+  return IRKMG_OK;
+}
+
+int irkmg_vanka_correction(irkmg_ctx* C, int level, const double* r, double* c, int transpose) {
+  if (!level_ok(C, level) || level == 0 || !r || !c) return fail(IRKMG_EINVAL, "bad arguments");
+  Level& L = C->L[level];
+  CK(launch_fill(c, 0.0, L.N, C->stream));
+  return vanka_all(*C, L, r, c, 1.0, transpose ? 1 : 0);
+}
+
+int irkmg_smooth(irkmg_ctx* C, int level, const double* F, double* x, int nsteps, int transpose) {
+  if (!level_ok(C, level) || level == 0 || !F || !x || nsteps < 0)
+    return fail(IRKMG_EINVAL, "bad arguments");
+  return smooth(*C, C->L[level], F, x, nsteps, false, transpose ? 1 : 0);
+}
+
+int irkmg_restrict(irkmg_ctx* C, int level, const double* fine, double* coarse) {
+  if (!level_ok(C, level) || level == 0 || !fine || !coarse)
+    return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_restrict(*C, C->L[level], fine, coarse));
+  return IRKMG_OK;
+}
+
+int irkmg_prolong(irkmg_ctx* C, int level, const double* coarse, double* fine) {
+  if (!level_ok(C, level) || level == 0 || !fine || !coarse)
+    return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_prolong(*C, C->L[level], coarse, fine, 0));
+  return IRKMG_OK;
+}
+
+int irkmg_coarse_solve(irkmg_ctx* C, const double* r, double* x, int transpose) {
+  if (!C || !r || !x) return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_coarse_apply(*C, r, x, transpose ? 1 : 0));
+  return IRKMG_OK;
+}
+
+int irkmg_vcycle(irkmg_ctx* C, const double* r, double* z, int transpose) {
+  if (!C || !r || !z) return fail(IRKMG_EINVAL, "bad arguments");
+  return vcycle_level(*C, (int)C->L.size() - 1, r, z, transpose ? 1 : 0);
+}
+
+int irkmg_solve(irkmg_ctx* C, const double* F, double* k, irkmg_stats* st) {
+  if (!C || !F || !k) return fail(IRKMG_EINVAL, "bad arguments");
+  return fgmres(*C, F, k, st, 0);
+}
+
+int irkmg_adjoint_solve(irkmg_ctx* C, const double* G, double* lam, irkmg_stats* st) {
+  if (!C || !G || !lam) return fail(IRKMG_EINVAL, "bad arguments");
+  return fgmres(*C, G, lam, st, 1);
+}
+
+int irkmg_stage_rhs(irkmg_ctx* C, const double* un, const double* pn, const double* f,
+                    double* F) {
+  if (!C || !un || !pn || !f || !F) return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_stage_rhs(*C, un, pn, f, F));
+  return IRKMG_OK;
+}
+
+int irkmg_advance(irkmg_ctx* C, const double* k, double* un, double* pn) {
+  if (!C || !k || !un || !pn) return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_advance(*C, k, un, pn));
+  return IRKMG_OK;
+}
+
+void irkmg_destroy(irkmg_ctx* C) {
+  if (!C) return;
+  if (C->stream) cudaStreamSynchronize(C->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : C->allocs) cudaFree(p);
+  if (C->h_h) cudaFreeHost(C->h_h);
+  delete C;
+}
+
+const char* irkmg_strerror(int s) {
+  switch (s) {
+    case IRKMG_OK: return "ok";
+    case IRKMG_EINVAL: return "invalid argument";
+    case IRKMG_ENOMEM: return "out of memory";
+    case IRKMG_ECUDA: return "CUDA error";
+    case IRKMG_ESINGULAR: return "singular patch or coarse pivot";
+    case IRKMG_ENOCONV: return "FGMRES did not converge";
+    case IRKMG_ETIMEOUT: return "bounded device wait expired";
+    case IRKMG_ENOTIMPL: return "not implemented";
+    default: return "unknown status";
+  }
+}
+
+const char* irkmg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations of the irkmg library (host set-up structures, device
+// level data and kernel launchers).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/irkmg.h"
+
+namespace irkmg {
+
+// ---------------------------------------------------------------------------
+// Host-side mesh level (Section 4.1: uniform refinements of a coarsest mesh;
+// Section 3.1: Taylor–Hood P2–P1 numbering).
+// ---------------------------------------------------------------------------
+struct HostMesh {
+  int64_t nv = 0, nc = 0, ne = 0, np2 = 0, nf = 0;
+  std::vector<double> xy;           // nv*2
+  std::vector<int32_t> cells;       // nc*3
+  std::vector<uint8_t> bnd;         // nv, Dirichlet vertex flags
+  std::vector<int32_t> edges;       // ne*2, sorted pairs, lexicographic
+  std::vector<int32_t> cell_edges;  // nc*3, local edges (0,1), (1,2), (0,2)
+  std::vector<uint8_t> edge_dir;    // ne, Dirichlet edge flags
+  std::vector<int32_t> p2_to_free;  // np2, -1 on Dirichlet nodes
+  std::vector<int32_t> free_to_p2;  // nf
+  std::vector<int32_t> vc_ptr, vc_idx;  // vertex -> cells (ascending)
+  std::vector<int32_t> vv_ptr, vv_idx;  // vertex -> vertices through edges (ascending)
+};
+
+// Returns an empty string on success, else the reason.
+std::string build_mesh(const double* xy, const int64_t* cells, const uint8_t* bnd, int64_t nv,
+                       int64_t nc, HostMesh& out);
+void refine_mesh(const HostMesh& c, HostMesh& f);
+// Edge id of the sorted pair (a, b), or -1.
+int64_t find_edge(const HostMesh& m, int32_t a, int32_t b);
+
+struct HostCSR {
+  int64_t nrows = 0, ncols = 0;
+  std::vector<int32_t> ptr, col;
+  std::vector<double> v[3];
+  int64_t nnz() const { return (int64_t)col.size(); }
+};
+
+// Transfer between coarse level c and its red refinement f (Section 4.1:
+// canonical P2 / P1 interpolation, free nodes only).
+void build_prolongation(const HostMesh& c, const HostMesh& f, HostCSR& Pu, HostCSR& Pp);
+HostCSR transpose_csr(const HostCSR& A, int nvals);
+
+// Assembled free-DoF operators of one level (Section 3.1).
+struct HostOps {
+  HostCSR vel;   // nf x nf: v[0] = M, v[1] = nu K (+ C), v[2] = transpose of v[1]
+  HostCSR mall;  // nf x np2: v[0] = M with every column (for M f)
+  HostCSR b;     // nf x nv : v[0] = B_x, v[1] = B_y   (B = -int psi_q d phi_a / dx_d)
+  HostCSR bt;    // nv x nf : v[0] = B_x^T, v[1] = B_y^T
+};
+// wind: np2*2 nodal values or nullptr
+void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& ops);
+
+// Radau IIA closed forms.
+int radau_iia(int s, double* A, double* b, double* c);
+
+// ---------------------------------------------------------------------------
+// Device data.
+// ---------------------------------------------------------------------------
+struct DevCSR {
+  int32_t nrows = 0;
+  int64_t nnz = 0;
+  int32_t* ptr = nullptr;
+  int32_t* col = nullptr;
+  double* v[3] = {nullptr, nullptr, nullptr};
+};
+
+struct Level {
+  HostMesh mesh;
+  int64_t nf = 0, nv = 0, np2 = 0, m = 0, N = 0;
+  HostOps hops;
+  DevCSR vel, b, bt, mall;
+  // transfer from level-1 into this level (l > 0)
+  DevCSR pu, put, pp, ppt;
+  // topology for patch construction
+  int32_t *d_cells = nullptr, *d_cell_edges = nullptr, *d_vc_ptr = nullptr, *d_vc_idx = nullptr;
+  int32_t *d_vv_ptr = nullptr, *d_vv_idx = nullptr, *d_p2_to_free = nullptr;
+  // patches (Section 4.2)
+  int32_t *d_patch_ptr = nullptr, *d_patch_nodes = nullptr;
+  std::vector<int32_t> h_patch_ptr, h_patch_nodes, h_colour;
+  int32_t* d_colour = nullptr;
+  int ncolours = 0;
+  std::vector<int64_t> colour_start;   // into the colour-ordered patch list
+  int32_t* d_order = nullptr;          // patches sorted by (colour, id)
+  int64_t* d_fac_off = nullptr;        // element offset of each ordered patch's inverse
+  void* d_fac = nullptr;
+  int64_t fac_elems = 0;
+  int max_np = 0;
+  // work vectors (length N)
+  double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
+};
+
+struct Ctx {
+  int s = 0;
+  double A[9] = {0}, AT[9] = {0}, b[3] = {0}, c[3] = {0};
+  double dt = 0, nu = 1;
+  irkmg_options opt{};
+  cudaStream_t stream = nullptr;
+  std::vector<double> wind;  // finest-level nodal wind (empty for Stokes)
+  std::vector<Level> L;
+  std::vector<void*> allocs;
+  // coarse bordered inverse, row-major n_b x n_b
+  double* d_coarse_inv = nullptr;
+  int64_t nb = 0;
+  int32_t* d_coarse_perm = nullptr;
+  // FGMRES storage (finest level)
+  double *d_V = nullptr, *d_Z = nullptr, *d_w = nullptr, *d_part = nullptr, *d_h = nullptr;
+  double* h_h = nullptr;  // pinned
+  int restart_alloc = 0;
+  int* d_err = nullptr;   // device error word: [0] status, [1] index
+  int64_t dev_bytes = 0;
+};
+
+// Launchers (all on ctx stream).  Each returns cudaGetLastError().
+cudaError_t launch_patch_maps(Level& L, cudaStream_t st, int maxnodes, int32_t* d_tmp,
+                              int32_t* d_cnt);
+cudaError_t launch_compact_patches(Level& L, cudaStream_t st, int maxnodes, const int32_t* d_tmp,
+                                   const int32_t* d_cnt);
+cudaError_t launch_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+cudaError_t launch_colour_round(Level& L, cudaStream_t st, int* d_remaining, int* d_overflow);
+cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision);
+cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
+                         int transpose);
+cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, double* r,
+                            int transpose);
+cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coarse);
+cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine, int add);
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n,
+                         cudaStream_t st);  // y = a*x + b*y
+cudaError_t launch_fill(double* y, double v, int64_t n, cudaStream_t st);
+cudaError_t launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
+                            double* part, double* out, cudaStream_t st);
+cudaError_t launch_multiaxpy(double* w, const double* V, int64_t ldv, int k, const double* h,
+                             double sign, int64_t n, cudaStream_t st);  // w += sign * V h
+cudaError_t launch_pressure_mean_remove(Ctx& C, Level& L, double* x);
+cudaError_t launch_stage_rhs(Ctx& C, const double* un, const double* pn, const double* f,
+                             double* F);
+cudaError_t launch_advance(Ctx& C, const double* k, double* un, double* pn);
+cudaError_t launch_coarse_build(Ctx& C, double* dense);
+cudaError_t coarse_invert(Ctx& C, double* dense, int64_t n);
+cudaError_t launch_coarse_apply(Ctx& C, const double* r, double* x, int transpose);
+
+constexpr int kMultidotBlocks = 304;  // 2 x 152 SMs; fixed for a deterministic sum order
+
+}  // namespace irkmg

@@ -1,0 +1,451 @@
+// Stage operator, transfers, stage right-hand side / update and the vector
+// kernels of FGMRES.
+//
+//   stage residual (Section 3.1):  r = F - J x,
+//     J = I_s ⊗ [[M,0],[0,0]] + dt A ⊗ [[K,B],[Bᵀ,0]],
+//   evaluated row by row: one pass over the scalar P2 pattern (M and K share
+//   it) and the B / Bᵀ rows gathers every stage and both velocity components
+//   of a neighbour at once, and the s×s stage mixing is applied per row.
+//   Jᵀ swaps A for Aᵀ and K for Kᵀ (the B blocks are unchanged).
+//   transfers (Section 4.1): I_s ⊗ diag(P_u, P_u, P_p) and its transpose.
+//   reductions are two-pass with a fixed block count, so sums are bitwise
+//   reproducible run to run.
+#include "irkmg_internal.h"
+
+namespace irkmg {
+
+struct OpParams {
+  int64_t nf, nv, m;
+  double mix[9];  // dt * A (or dt * Aᵀ), row-major 3x3
+  const int32_t *vptr, *vcol;
+  const double *M, *K;
+  const int32_t *bptr, *bcol;
+  const double *Bx, *By;
+  const int32_t *btptr, *btcol;
+  const double *BTx, *BTy;
+};
+
+template <int S>
+__global__ void __launch_bounds__(256) k_residual(OpParams P, const double* __restrict__ F,
+                                                  const double* __restrict__ x,
+                                                  double* __restrict__ r) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nf = P.nf, m = P.m;
+  if (row < nf) {
+    double am[S][2], ak[S][2];
+#pragma unroll
+    for (int t = 0; t < S; ++t) am[t][0] = am[t][1] = ak[t][0] = ak[t][1] = 0.0;
+    const int32_t p1 = P.vptr[row + 1];
+    for (int32_t p = P.vptr[row]; p < p1; ++p) {
+      const int32_t j = P.vcol[p];
+      const double mv = P.M[p], kv = P.K[p];
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        const double xx = x[t * m + j], xy = x[t * m + nf + j];
+        am[t][0] = fma(mv, xx, am[t][0]);
+        am[t][1] = fma(mv, xy, am[t][1]);
+        ak[t][0] = fma(kv, xx, ak[t][0]);
+        ak[t][1] = fma(kv, xy, ak[t][1]);
+      }
+    }
+    const int32_t q1 = P.bptr[row + 1];
+    for (int32_t p = P.bptr[row]; p < q1; ++p) {
+      const int32_t vtx = P.bcol[p];
+      const double bx = P.Bx[p], by = P.By[p];
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        const double pv = x[t * m + 2 * nf + vtx];
+        ak[t][0] = fma(bx, pv, ak[t][0]);
+        ak[t][1] = fma(by, pv, ak[t][1]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double yx = am[i][0], yy = am[i][1];
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        yx = fma(P.mix[i * 3 + t], ak[t][0], yx);
+        yy = fma(P.mix[i * 3 + t], ak[t][1], yy);
+      }
+      const int64_t gx = i * m + row, gy = i * m + nf + row;
+      if (F) {
+        r[gx] = F[gx] - yx;
+        r[gy] = F[gy] - yy;
+      } else {
+        r[gx] = yx;
+        r[gy] = yy;
+      }
+    }
+  } else if (row < nf + P.nv) {
+    const int64_t v = row - nf;
+    double ap[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) ap[t] = 0.0;
+    const int32_t p1 = P.btptr[v + 1];
+    for (int32_t p = P.btptr[v]; p < p1; ++p) {
+      const int32_t j = P.btcol[p];
+      const double bx = P.BTx[p], by = P.BTy[p];
+#pragma unroll
+      for (int t = 0; t < S; ++t) ap[t] = fma(bx, x[t * m + j], fma(by, x[t * m + nf + j], ap[t]));
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double y = 0.0;
+#pragma unroll
+      for (int t = 0; t < S; ++t) y = fma(P.mix[i * 3 + t], ap[t], y);
+      const int64_t g = i * m + 2 * nf + v;
+      r[g] = F ? F[g] - y : y;
+    }
+  }
+}
+
+static OpParams op_params(Ctx& C, Level& L, int transpose) {
+  OpParams P;
+  P.nf = L.nf;
+  P.nv = L.nv;
+  P.m = L.m;
+  for (int i = 0; i < 9; ++i) P.mix[i] = 0.0;
+  for (int i = 0; i < C.s; ++i)
+    for (int j = 0; j < C.s; ++j)
+      P.mix[i * 3 + j] = C.dt * (transpose ? C.A[j * C.s + i] : C.A[i * C.s + j]);
+  P.vptr = L.vel.ptr;
+  P.vcol = L.vel.col;
+  P.M = L.vel.v[0];
+  P.K = transpose ? L.vel.v[2] : L.vel.v[1];
+  P.bptr = L.b.ptr;
+  P.bcol = L.b.col;
+  P.Bx = L.b.v[0];
+  P.By = L.b.v[1];
+  P.btptr = L.bt.ptr;
+  P.btcol = L.bt.col;
+  P.BTx = L.bt.v[0];
+  P.BTy = L.bt.v[1];
+  return P;
+}
+
+cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, double* r,
+                            int transpose) {
+  OpParams P = op_params(C, L, transpose);
+  const int64_t rows = L.nf + L.nv;
+  const unsigned grid = (unsigned)((rows + 255) / 256);
+  switch (C.s) {
+    case 1: k_residual<1><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+    case 2: k_residual<2><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+    default: k_residual<3><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Transfers.  Rows: nf free P2 nodes (both components, every stage), then nv
+// vertices (pressure, every stage).
+// ---------------------------------------------------------------------------
+struct XferParams {
+  int s;
+  int64_t nf_out, nv_out, m_out, nf_in, m_in;
+  const int32_t *uptr, *ucol;
+  const double* uw;
+  const int32_t *pptr, *pcol;
+  const double* pw;
+};
+
+__global__ void k_transfer(XferParams P, const double* __restrict__ in, double* __restrict__ out,
+                           int add) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < P.nf_out) {
+    double acc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int32_t p = P.uptr[row]; p < P.uptr[row + 1]; ++p) {
+      const int32_t j = P.ucol[p];
+      const double w = P.uw[p];
+      for (int t = 0; t < P.s; ++t) {
+        acc[t][0] = fma(w, in[t * P.m_in + j], acc[t][0]);
+        acc[t][1] = fma(w, in[t * P.m_in + P.nf_in + j], acc[t][1]);
+      }
+    }
+    for (int t = 0; t < P.s; ++t) {
+      const int64_t gx = t * P.m_out + row, gy = t * P.m_out + P.nf_out + row;
+      out[gx] = add ? out[gx] + acc[t][0] : acc[t][0];
+      out[gy] = add ? out[gy] + acc[t][1] : acc[t][1];
+    }
+  } else if (row < P.nf_out + P.nv_out) {
+    const int64_t v = row - P.nf_out;
+    double acc[3] = {0, 0, 0};
+    for (int32_t p = P.pptr[v]; p < P.pptr[v + 1]; ++p) {
+      const int32_t j = P.pcol[p];
+      const double w = P.pw[p];
+      for (int t = 0; t < P.s; ++t) acc[t] = fma(w, in[t * P.m_in + 2 * P.nf_in + j], acc[t]);
+    }
+    for (int t = 0; t < P.s; ++t) {
+      const int64_t g = t * P.m_out + 2 * P.nf_out + v;
+      out[g] = add ? out[g] + acc[t] : acc[t];
+    }
+  }
+}
+
+cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coarse) {
+  Level& Lc = *(&Lf - 1);
+  XferParams P;
+  P.s = C.s;
+  P.nf_out = Lc.nf;
+  P.nv_out = Lc.nv;
+  P.m_out = Lc.m;
+  P.nf_in = Lf.nf;
+  P.m_in = Lf.m;
+  P.uptr = Lf.put.ptr;
+  P.ucol = Lf.put.col;
+  P.uw = Lf.put.v[0];
+  P.pptr = Lf.ppt.ptr;
+  P.pcol = Lf.ppt.col;
+  P.pw = Lf.ppt.v[0];
+  const int64_t rows = Lc.nf + Lc.nv;
+  k_transfer<<<(unsigned)((rows + 255) / 256), 256, 0, C.stream>>>(P, fine, coarse, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine, int add) {
+  Level& Lc = *(&Lf - 1);
+  XferParams P;
+  P.s = C.s;
+  P.nf_out = Lf.nf;
+  P.nv_out = Lf.nv;
+  P.m_out = Lf.m;
+  P.nf_in = Lc.nf;
+  P.m_in = Lc.m;
+  P.uptr = Lf.pu.ptr;
+  P.ucol = Lf.pu.col;
+  P.uw = Lf.pu.v[0];
+  P.pptr = Lf.pp.ptr;
+  P.pcol = Lf.pp.col;
+  P.pw = Lf.pp.v[0];
+  const int64_t rows = Lf.nf + Lf.nv;
+  k_transfer<<<(unsigned)((rows + 255) / 256), 256, 0, C.stream>>>(P, coarse, fine, add);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Vector kernels
+// ---------------------------------------------------------------------------
+__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b,
+                        int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
+}
+
+__global__ void k_fill(double* __restrict__ y, double v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = v;
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n,
+                         cudaStream_t st) {
+  k_axpby<<<grid_for(n), 256, 0, st>>>(y, x, a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* y, double v, int64_t n, cudaStream_t st) {
+  k_fill<<<grid_for(n), 256, 0, st>>>(y, v, n);
+  return cudaGetLastError();
+}
+
+// part[b*k + j] = partial sum over block b's contiguous chunk of V_j . w
+__global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict__ V, int64_t ldv,
+                                                       int k, const double* __restrict__ w,
+                                                       int64_t n, double* __restrict__ part) {
+  __shared__ double red[4][256];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = min(n, b0 + chunk);
+  for (int j0 = 0; j0 < k; j0 += 4) {
+    double acc[4] = {0, 0, 0, 0};
+    const int nj = min(4, k - j0);
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nj) acc[q] = fma(V[(int64_t)(j0 + q) * ldv + i], wi, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < (unsigned)o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x < (unsigned)nj) part[(int64_t)blockIdx.x * k + j0 + threadIdx.x] = red[threadIdx.x][0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_multidot_final(const double* __restrict__ part, int nblocks, int k,
+                                 double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * k + j];
+  out[j] = s;
+}
+
+cudaError_t launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
+                            double* part, double* out, cudaStream_t st) {
+  k_multidot_part<<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
+  k_multidot_final<<<1, 64, 0, st>>>(part, kMultidotBlocks, k, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int k,
+                            const double* __restrict__ h, double sign, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(h[j], V[(int64_t)j * ldv + i], acc);
+    w[i] = fma(sign, acc, w[i]);
+  }
+}
+
+cudaError_t launch_multiaxpy(double* w, const double* V, int64_t ldv, int k, const double* h,
+                             double sign, int64_t n, cudaStream_t st) {
+  k_multiaxpy<<<grid_for(n), 256, 0, st>>>(w, V, ldv, k, h, sign, n);
+  return cudaGetLastError();
+}
+
+// Per-stage pressure mean removal: block t sums stage t's pressure block in a
+// fixed order, then subtracts the mean.
+__global__ void __launch_bounds__(1024) k_pressure_mean(double* x, int64_t m, int64_t off,
+                                                        int64_t nv) {
+  __shared__ double red[1024];
+  double* p = x + blockIdx.x * m + off;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) s += p[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (threadIdx.x < (unsigned)o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double mean = red[0] / (double)nv;
+  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) p[i] -= mean;
+}
+
+cudaError_t launch_pressure_mean_remove(Ctx& C, Level& L, double* x) {
+  k_pressure_mean<<<C.s, 1024, 0, C.stream>>>(x, L.m, 2 * L.nf, L.nv);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Stage right-hand side and update (Section 3.1)
+// ---------------------------------------------------------------------------
+struct RhsParams {
+  int s;
+  int64_t nf, nv, np2, m;
+  const int32_t *aptr, *acol;
+  const double* Mall;
+  const int32_t *vptr, *vcol;
+  const double* K;
+  const int32_t *bptr, *bcol;
+  const double *Bx, *By;
+  const int32_t *btptr, *btcol;
+  const double *BTx, *BTy;
+};
+
+__global__ void k_stage_rhs(RhsParams P, const double* __restrict__ un, const double* __restrict__ pn,
+                            const double* __restrict__ f, double* __restrict__ F) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nf = P.nf;
+  if (row < nf) {
+    double kx = 0.0, ky = 0.0;
+    for (int32_t p = P.vptr[row]; p < P.vptr[row + 1]; ++p) {
+      const int32_t j = P.vcol[p];
+      kx = fma(P.K[p], un[j], kx);
+      ky = fma(P.K[p], un[nf + j], ky);
+    }
+    for (int32_t p = P.bptr[row]; p < P.bptr[row + 1]; ++p) {
+      const double pv = pn[P.bcol[p]];
+      kx = fma(P.Bx[p], pv, kx);
+      ky = fma(P.By[p], pv, ky);
+    }
+    for (int t = 0; t < P.s; ++t) {
+      double mx = 0.0, my = 0.0;
+      const double* fx = f + (int64_t)t * 2 * P.np2;
+      const double* fy = fx + P.np2;
+      for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) {
+        const int32_t j = P.acol[p];
+        mx = fma(P.Mall[p], fx[j], mx);
+        my = fma(P.Mall[p], fy[j], my);
+      }
+      F[t * P.m + row] = mx - kx;
+      F[t * P.m + nf + row] = my - ky;
+    }
+  } else if (row < nf + P.nv) {
+    const int64_t v = row - nf;
+    double a = 0.0;
+    for (int32_t p = P.btptr[v]; p < P.btptr[v + 1]; ++p) {
+      const int32_t j = P.btcol[p];
+      a = fma(P.BTx[p], un[j], fma(P.BTy[p], un[nf + j], a));
+    }
+    for (int t = 0; t < P.s; ++t) F[t * P.m + 2 * nf + v] = -a;
+  }
+}
+
+cudaError_t launch_stage_rhs(Ctx& C, const double* un, const double* pn, const double* f,
+                             double* F) {
+  Level& L = C.L.back();
+  RhsParams P;
+  P.s = C.s;
+  P.nf = L.nf;
+  P.nv = L.nv;
+  P.np2 = L.np2;
+  P.m = L.m;
+  P.aptr = L.mall.ptr;
+  P.acol = L.mall.col;
+  P.Mall = L.mall.v[0];
+  P.vptr = L.vel.ptr;
+  P.vcol = L.vel.col;
+  P.K = L.vel.v[1];
+  P.bptr = L.b.ptr;
+  P.bcol = L.b.col;
+  P.Bx = L.b.v[0];
+  P.By = L.b.v[1];
+  P.btptr = L.bt.ptr;
+  P.btcol = L.bt.col;
+  P.BTx = L.bt.v[0];
+  P.BTy = L.bt.v[1];
+  const int64_t rows = L.nf + L.nv;
+  k_stage_rhs<<<(unsigned)((rows + 255) / 256), 256, 0, C.stream>>>(P, un, pn, f, F);
+  return cudaGetLastError();
+}
+
+__global__ void k_advance(int s, int64_t nu_, int64_t np_, int64_t m, double b0, double b1,
+                          double b2, const double* __restrict__ k, double* __restrict__ un,
+                          double* __restrict__ pn) {
+  const double bw[3] = {b0, b1, b2};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu_ + np_;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int t = 0; t < s; ++t) acc = fma(bw[t], k[t * m + i], acc);
+    if (i < nu_)
+      un[i] += acc;
+    else
+      pn[i - nu_] += acc;
+  }
+}
+
+cudaError_t launch_advance(Ctx& C, const double* k, double* un, double* pn) {
+  Level& L = C.L.back();
+  double bw[3] = {0, 0, 0};
+  for (int t = 0; t < C.s; ++t) bw[t] = C.dt * C.b[t];
+  k_advance<<<grid_for(L.m), 256, 0, C.stream>>>(C.s, 2 * L.nf, L.nv, L.m, bw[0], bw[1], bw[2], k,
+                                                 un, pn);
+  return cudaGetLastError();
+}
+
+}  // namespace irkmg

@@ -1,0 +1,543 @@
+// Vertex-star Vanka patches on the GPU (Section 4.2, Fig. 1 left):
+//   * patch maps: for every vertex v, the free P2 nodes in the closure of the
+//     cells around v (ascending);  the patch S_v is, per stage, the u_x and
+//     u_y DoFs of those nodes and the single pressure DoF of v;
+//   * distance-2 colouring (patches of one colour share no DoF), computed by
+//     Jones–Plassmann rounds with priority = -vertex id, which reproduces the
+//     sequential greedy colouring in vertex order exactly;
+//   * gather of A_v = R_v J R_vᵀ from the assembled level operators and its
+//     explicit inverse by Gauss–Jordan elimination with partial pivoting;
+//   * the additive correction  out += scale · R_vᵀ A_v⁻¹ R_v r, one launch per
+//     colour, so the scatter needs no atomics and is deterministic.
+#include <cfloat>
+#include <cstdio>
+
+#include "irkmg_internal.h"
+
+namespace irkmg {
+
+constexpr int kMaxStar = 24;        // cells around a vertex handled by the map kernel
+constexpr int kMaxPatchNodes = 64;  // free P2 nodes per patch (2D interior: 19)
+
+// ---------------------------------------------------------------------------
+// Patch maps
+// ---------------------------------------------------------------------------
+__global__ void k_patch_maps(int32_t nv, const int32_t* __restrict__ cells,
+                             const int32_t* __restrict__ cell_edges,
+                             const int32_t* __restrict__ vc_ptr, const int32_t* __restrict__ vc_idx,
+                             const int32_t* __restrict__ p2_to_free, int32_t maxnodes,
+                             int32_t* __restrict__ tmp, int32_t* __restrict__ cnt) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  int32_t buf[6 * kMaxStar];
+  int n = 0;
+  const int32_t b0 = vc_ptr[v], b1 = vc_ptr[v + 1];
+  if (b1 - b0 > kMaxStar) {
+    cnt[v] = -1;
+    return;
+  }
+  for (int32_t p = b0; p < b1; ++p) {
+    const int32_t c = vc_idx[p];
+    for (int a = 0; a < 3; ++a) {
+      int32_t f = p2_to_free[cells[3 * c + a]];
+      if (f >= 0) buf[n++] = f;
+    }
+    for (int a = 0; a < 3; ++a) {
+      int32_t f = p2_to_free[nv + cell_edges[3 * c + a]];
+      if (f >= 0) buf[n++] = f;
+    }
+  }
+  // insertion sort + unique (free numbering preserves P2 order)
+  for (int i = 1; i < n; ++i) {
+    int32_t x = buf[i];
+    int j = i - 1;
+    while (j >= 0 && buf[j] > x) {
+      buf[j + 1] = buf[j];
+      --j;
+    }
+    buf[j + 1] = x;
+  }
+  int u = 0;
+  for (int i = 0; i < n; ++i)
+    if (u == 0 || buf[i] != buf[u - 1]) buf[u++] = buf[i];
+  if (u > maxnodes) {
+    cnt[v] = -1;
+    return;
+  }
+  for (int i = 0; i < u; ++i) tmp[(int64_t)v * maxnodes + i] = buf[i];
+  cnt[v] = u;
+}
+
+__global__ void k_compact_patches(int32_t nv, int32_t maxnodes, const int32_t* __restrict__ tmp,
+                                  const int32_t* __restrict__ ptr, int32_t* __restrict__ nodes) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const int32_t b = ptr[v], e = ptr[v + 1];
+  for (int32_t i = 0; i < e - b; ++i) nodes[b + i] = tmp[(int64_t)v * maxnodes + i];
+}
+
+// Exclusive scan of n counts into n+1 offsets (single block; set-up only).
+__global__ void k_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n) {
+  __shared__ int32_t s[1024];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += 1024) {
+    int64_t i = base + threadIdx.x;
+    int32_t x = (i < n) ? in[i] : 0;
+    s[threadIdx.x] = x;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      int32_t y = (threadIdx.x >= (unsigned)off) ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (i < n) out[i] = carry + s[threadIdx.x] - x;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+cudaError_t launch_patch_maps(Level& L, cudaStream_t st, int maxnodes, int32_t* d_tmp,
+                              int32_t* d_cnt) {
+  int32_t nv = (int32_t)L.nv;
+  k_patch_maps<<<(nv + 127) / 128, 128, 0, st>>>(nv, L.d_cells, L.d_cell_edges, L.d_vc_ptr,
+                                                  L.d_vc_idx, L.d_p2_to_free, maxnodes, d_tmp,
+                                                  d_cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_patches(Level& L, cudaStream_t st, int maxnodes, const int32_t* d_tmp,
+                                   const int32_t* d_cnt) {
+  (void)d_cnt;
+  int32_t nv = (int32_t)L.nv;
+  k_compact_patches<<<(nv + 127) / 128, 128, 0, st>>>(nv, maxnodes, d_tmp, L.d_patch_ptr,
+                                                       L.d_patch_nodes);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Distance-2 colouring, one Jones–Plassmann round.  A vertex is coloured once
+// every lower-id vertex within graph distance 2 is coloured; it takes the
+// smallest colour none of them uses.  Colours are written once, so reading a
+// neighbour coloured in the same round is harmless.
+// ---------------------------------------------------------------------------
+constexpr int kMaxColours = 256;
+
+__global__ void k_colour_round(int32_t nv, const int32_t* __restrict__ vv_ptr,
+                               const int32_t* __restrict__ vv_idx, int32_t* colour,
+                               int* remaining, int* overflow) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  volatile int32_t* col = colour;
+  if (col[v] >= 0) return;
+  uint64_t mask[kMaxColours / 64] = {0, 0, 0, 0};
+  bool ready = true;
+  for (int32_t p = vv_ptr[v]; p < vv_ptr[v + 1] && ready; ++p) {
+    const int32_t x = vv_idx[p];
+    if (x < v) {
+      int32_t cx = col[x];
+      if (cx < 0) {
+        ready = false;
+        break;
+      }
+      mask[cx >> 6] |= 1ull << (cx & 63);
+    }
+    for (int32_t q = vv_ptr[x]; q < vv_ptr[x + 1]; ++q) {
+      const int32_t y = vv_idx[q];
+      if (y >= v) continue;
+      int32_t cy = col[y];
+      if (cy < 0) {
+        ready = false;
+        break;
+      }
+      mask[cy >> 6] |= 1ull << (cy & 63);
+    }
+  }
+  if (!ready) {
+    atomicAdd(remaining, 1);
+    return;
+  }
+  int c = 0;
+  while (c < kMaxColours && (mask[c >> 6] >> (c & 63)) & 1ull) ++c;
+  if (c >= kMaxColours) {
+    atomicExch(overflow, 1);
+    c = kMaxColours - 1;
+  }
+  col[v] = c;
+}
+
+cudaError_t launch_colour_round(Level& L, cudaStream_t st, int* d_remaining, int* d_overflow) {
+  int32_t nv = (int32_t)L.nv;
+  k_colour_round<<<(nv + 127) / 128, 128, 0, st>>>(nv, L.d_vv_ptr, L.d_vv_idx, L.d_colour,
+                                                    d_remaining, d_overflow);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Patch gather + explicit inverse (one CTA per patch, FP64 in shared memory).
+// Local order of S_v inside a stage: u_x of the L nodes, u_y of the L nodes,
+// p_v; stages consecutive.  Block entries (Section 3.1 Kronecker form):
+//   velocity-velocity  delta_tu M_ab + dt a_tu K_ab   (same component)
+//   velocity-pressure  dt a_tu B^d_{a v}
+//   pressure-velocity  dt a_tu B^d_{b v}              (row of Bᵀ)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int csr_find(const int32_t* __restrict__ col, int32_t b, int32_t e,
+                                        int32_t key) {
+  while (b < e) {
+    int32_t mid = (b + e) >> 1;
+    int32_t c = col[mid];
+    if (c < key)
+      b = mid + 1;
+    else
+      e = mid;
+  }
+  return b;  // caller checks col[b] == key
+}
+
+struct InvParams {
+  int s;
+  double A[9];
+  double dt;
+  int64_t nf;
+  const int32_t *patch_ptr, *patch_nodes, *order;
+  const int64_t* fac_off;
+  const int32_t *vptr, *vcol;
+  const double *M, *K;
+  const int32_t *bptr, *bcol;
+  const double *Bx, *By;
+  int* err;  // [0] status, [1] patch id
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatch, T* fac) {
+  extern __shared__ double smem[];
+  __shared__ int32_t nodes[kMaxPatchNodes];
+  __shared__ int32_t s_perm[3 * (2 * kMaxPatchNodes + 1)];
+  __shared__ double colk[3 * (2 * kMaxPatchNodes + 1)];
+  __shared__ double red_v[256];
+  __shared__ int red_i[256];
+  __shared__ double s_maxabs;
+  const int64_t pi = blockIdx.x;
+  if (pi >= npatch) return;
+  const int32_t v = P.order[pi];
+  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+  const int q = 2 * L + 1, np = P.s * q;
+  double* A = smem;  // row-major np x np
+  for (int i = threadIdx.x; i < L; i += blockDim.x) nodes[i] = P.patch_nodes[nb + i];
+  for (int i = threadIdx.x; i < np * np; i += blockDim.x) A[i] = 0.0;
+  __syncthreads();
+  // velocity-velocity blocks
+  for (int idx = threadIdx.x; idx < L * L; idx += blockDim.x) {
+    const int a = idx / L, b = idx % L;
+    const int32_t ra = nodes[a], cb = nodes[b];
+    const int32_t p0 = P.vptr[ra], p1 = P.vptr[ra + 1];
+    const int32_t pos = csr_find(P.vcol, p0, p1, cb);
+    double mab = 0.0, kab = 0.0;
+    if (pos < p1 && P.vcol[pos] == cb) {
+      mab = P.M[pos];
+      kab = P.K[pos];
+    }
+    for (int t = 0; t < P.s; ++t)
+      for (int u = 0; u < P.s; ++u) {
+        const double val = (t == u ? mab : 0.0) + P.dt * P.A[t * 3 + u] * kab;
+        for (int d = 0; d < 2; ++d) A[(t * q + d * L + a) * np + (u * q + d * L + b)] = val;
+      }
+  }
+  // velocity-pressure and pressure-velocity blocks
+  for (int a = threadIdx.x; a < L; a += blockDim.x) {
+    const int32_t ra = nodes[a];
+    const int32_t p0 = P.bptr[ra], p1 = P.bptr[ra + 1];
+    const int32_t pos = csr_find(P.bcol, p0, p1, v);
+    double bx = 0.0, by = 0.0;
+    if (pos < p1 && P.bcol[pos] == v) {
+      bx = P.Bx[pos];
+      by = P.By[pos];
+    }
+    for (int t = 0; t < P.s; ++t)
+      for (int u = 0; u < P.s; ++u) {
+        const double f = P.dt * P.A[t * 3 + u];
+        A[(t * q + a) * np + (u * q + 2 * L)] = f * bx;
+        A[(t * q + L + a) * np + (u * q + 2 * L)] = f * by;
+        A[(t * q + 2 * L) * np + (u * q + a)] = f * bx;
+        A[(t * q + 2 * L) * np + (u * q + L + a)] = f * by;
+      }
+  }
+  __syncthreads();
+  // max |A| for the singularity threshold
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < np * np; i += blockDim.x) mx = fmax(mx, fabs(A[i]));
+  red_v[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < (unsigned)o) red_v[threadIdx.x] = fmax(red_v[threadIdx.x], red_v[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s_maxabs = red_v[0];
+  __syncthreads();
+  const double thresh = 1e3 * DBL_EPSILON * s_maxabs;
+  // Gauss–Jordan with partial pivoting (first largest |.|), in place
+  for (int k = 0; k < np; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < np; i += blockDim.x) {
+      double a = fabs(A[i * np + k]);
+      if (a > best) {
+        best = a;
+        bi = i;
+      }
+    }
+    red_v[threadIdx.x] = best;
+    red_i[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < (unsigned)o) {
+        double a = red_v[threadIdx.x + o];
+        int ia = red_i[threadIdx.x + o];
+        if (a > red_v[threadIdx.x] || (a == red_v[threadIdx.x] && ia < red_i[threadIdx.x])) {
+          red_v[threadIdx.x] = a;
+          red_i[threadIdx.x] = ia;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = red_i[0];
+    const double pabs = red_v[0];
+    if (threadIdx.x == 0) s_perm[k] = p;
+    if (p != k)
+      for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        double x = A[k * np + j];
+        A[k * np + j] = A[p * np + j];
+        A[p * np + j] = x;
+      }
+    __syncthreads();
+    if (!(pabs > thresh)) {
+      if (threadIdx.x == 0 && atomicCAS(&P.err[0], 0, IRKMG_ESINGULAR) == 0) P.err[1] = v;
+    }
+    for (int i = threadIdx.x; i < np; i += blockDim.x) colk[i] = A[i * np + k];
+    __syncthreads();
+    const double pinv = (pabs > 0.0) ? 1.0 / colk[k] : 0.0;
+    for (int j = threadIdx.x; j < np; j += blockDim.x)
+      A[k * np + j] = (j == k ? 1.0 : A[k * np + j]) * pinv;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
+      const int i = idx / np, j = idx - i * np;
+      if (i == k) continue;
+      A[idx] = (j == k ? 0.0 : A[idx]) - colk[i] * A[k * np + j];
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, in reverse order
+  for (int k = np - 1; k >= 0; --k) {
+    const int p = s_perm[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        double x = A[i * np + k];
+        A[i * np + k] = A[i * np + p];
+        A[i * np + p] = x;
+      }
+    __syncthreads();
+  }
+  // store column-major: X[j*np + i] = Ainv[i][j]
+  T* X = fac + P.fac_off[pi];
+  for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
+    const int j = idx / np, i = idx - j * np;
+    X[idx] = (T)A[i * np + j];
+  }
+}
+
+cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
+  InvParams P;
+  P.s = C.s;
+  for (int i = 0; i < 9; ++i) P.A[i] = 0.0;
+  for (int i = 0; i < C.s; ++i)
+    for (int j = 0; j < C.s; ++j) P.A[i * 3 + j] = C.A[i * C.s + j];
+  P.dt = C.dt;
+  P.nf = L.nf;
+  P.patch_ptr = L.d_patch_ptr;
+  P.patch_nodes = L.d_patch_nodes;
+  P.order = L.d_order;
+  P.fac_off = L.d_fac_off;
+  P.vptr = L.vel.ptr;
+  P.vcol = L.vel.col;
+  P.M = L.vel.v[0];
+  P.K = L.vel.v[1];
+  P.bptr = L.b.ptr;
+  P.bcol = L.b.col;
+  P.Bx = L.b.v[0];
+  P.By = L.b.v[1];
+  P.err = C.d_err;
+  const size_t smem = (size_t)L.max_np * L.max_np * sizeof(double);
+  if (precision == 64) {
+    cudaFuncSetAttribute(k_patch_invert<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_invert<double><<<(unsigned)L.nv, 256, smem, C.stream>>>(P, L.nv, (double*)L.d_fac);
+  } else {
+    cudaFuncSetAttribute(k_patch_invert<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_invert<float><<<(unsigned)L.nv, 256, smem, C.stream>>>(P, L.nv, (float*)L.d_fac);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Vanka apply for one colour: warp per patch.  y = A_v⁻¹ r|_{S_v} as a dense
+// column-major mat-vec (lanes over rows, one column per step, fully coalesced
+// loads of the stored inverse), then out[S_v] += scale · y.  Patches of one
+// colour share no DoF, so the read-modify-write needs no atomics.
+// transpose = 1 applies (A_v⁻¹)ᵀ = (A_vᵀ)⁻¹, the patch inverse of Jᵀ.
+// ---------------------------------------------------------------------------
+constexpr int kApplyWarps = 8;
+constexpr int kMaxNp = 160;
+
+struct ApplyParams {
+  int s;
+  int64_t nf, m;
+  const int32_t *patch_ptr, *patch_nodes, *order;
+  const int64_t* fac_off;
+  const double* r;
+  double* out;
+  double scale;
+  int64_t first, count;  // ordered-patch range of this colour
+};
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kApplyWarps * 32) k_vanka_apply(ApplyParams P, const T* __restrict__ fac) {
+  __shared__ T s_r[kApplyWarps][kMaxNp];
+  __shared__ int32_t s_g[kApplyWarps][kMaxNp];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kApplyWarps + warp;
+  if (w >= P.count) return;
+  const int64_t pi = P.first + w;
+  const int32_t v = P.order[pi];
+  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+  const int q = 2 * L + 1, np = P.s * q;
+  for (int i = lane; i < np; i += 32) {
+    const int t = i / q, k = i - t * q;
+    int64_t g;
+    if (k < L)
+      g = t * P.m + P.patch_nodes[nb + k];
+    else if (k < 2 * L)
+      g = t * P.m + P.nf + P.patch_nodes[nb + k - L];
+    else
+      g = t * P.m + 2 * P.nf + v;
+    s_g[warp][i] = (int32_t)g;
+    s_r[warp][i] = (T)P.r[g];
+  }
+  __syncwarp();
+  const T* X = fac + P.fac_off[pi];
+  T y[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) y[k] = (T)0;
+#pragma unroll 4
+  for (int j = 0; j < np; ++j) {
+    const T rj = s_r[warp][j];
+    const T* col = X + (int64_t)j * np;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = lane + 32 * k;
+      if (i < np) y[k] = fma(col[i], rj, y[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = lane + 32 * k;
+    if (i < np) {
+      const int32_t g = s_g[warp][i];
+      P.out[g] += P.scale * (double)y[k];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyWarps * 32) k_vanka_apply_t(ApplyParams P, const T* __restrict__ fac) {
+  __shared__ T s_r[kApplyWarps][kMaxNp];
+  __shared__ int32_t s_g[kApplyWarps][kMaxNp];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kApplyWarps + warp;
+  if (w >= P.count) return;
+  const int64_t pi = P.first + w;
+  const int32_t v = P.order[pi];
+  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+  const int q = 2 * L + 1, np = P.s * q;
+  for (int i = lane; i < np; i += 32) {
+    const int t = i / q, k = i - t * q;
+    int64_t g;
+    if (k < L)
+      g = t * P.m + P.patch_nodes[nb + k];
+    else if (k < 2 * L)
+      g = t * P.m + P.nf + P.patch_nodes[nb + k - L];
+    else
+      g = t * P.m + 2 * P.nf + v;
+    s_g[warp][i] = (int32_t)g;
+    s_r[warp][i] = (T)P.r[g];
+  }
+  __syncwarp();
+  const T* X = fac + P.fac_off[pi];
+  // (Xᵀ r)_i = sum_j X[i*np + j] r_j : column i of the column-major X is contiguous
+  for (int i = 0; i < np; ++i) {
+    T acc = (T)0;
+    for (int j = lane; j < np; j += 32) acc = fma(X[(int64_t)i * np + j], s_r[warp][j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == (i & 31)) P.out[s_g[warp][i]] += P.scale * (double)acc;
+  }
+}
+
+cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
+                         int transpose) {
+  ApplyParams P;
+  P.s = C.s;
+  P.nf = L.nf;
+  P.m = L.m;
+  P.patch_ptr = L.d_patch_ptr;
+  P.patch_nodes = L.d_patch_nodes;
+  P.order = L.d_order;
+  P.fac_off = L.d_fac_off;
+  P.r = r;
+  P.out = out;
+  P.scale = scale;
+  P.first = L.colour_start[colour];
+  P.count = L.colour_start[colour + 1] - P.first;
+  if (P.count <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((P.count + kApplyWarps - 1) / kApplyWarps);
+  const int prec = C.opt.patch_precision;
+  if (transpose) {
+    if (prec == 64)
+      k_vanka_apply_t<double><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, (const double*)L.d_fac);
+    else
+      k_vanka_apply_t<float><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, (const float*)L.d_fac);
+    return cudaGetLastError();
+  }
+  const int R = (L.max_np + 31) / 32;
+  if (prec == 64) {
+    const double* f = (const double*)L.d_fac;
+    switch (R) {
+      case 1: k_vanka_apply<double, 1><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      case 2: k_vanka_apply<double, 2><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      case 3: k_vanka_apply<double, 3><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      case 4: k_vanka_apply<double, 4><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      default: k_vanka_apply<double, 5><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+    }
+  } else {
+    const float* f = (const float*)L.d_fac;
+    switch (R) {
+      case 1: k_vanka_apply<float, 1><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      case 2: k_vanka_apply<float, 2><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      case 3: k_vanka_apply<float, 3><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      case 4: k_vanka_apply<float, 4><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+      default: k_vanka_apply<float, 5><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, f); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace irkmg

@@ -1,0 +1,319 @@
+"""ctypes binding of the irkmg C ABI (include/irkmg.h); argument marshalling only.
+
+Device vectors are passed as contiguous float64 CUDA tensors (their data
+pointers); host arrays as numpy arrays.  Every call checks the returned status
+and raises IrkmgError with the library's message on failure.  There is no
+fallback: if libirkmg.so is missing the first call raises.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IRKMG_OK, IRKMG_EINVAL, IRKMG_ENOMEM, IRKMG_ECUDA = 0, 1, 2, 3
+IRKMG_ESINGULAR, IRKMG_ENOCONV, IRKMG_ETIMEOUT, IRKMG_ENOTIMPL = 4, 5, 6, 7
+
+
+class IrkmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"irkmg status {status}: {msg}")
+        self.status = status
+
+
+class Mesh(ct.Structure):
+    _fields_ = [("dim", ct.c_int), ("nverts", ct.c_int64), ("ncells", ct.c_int64),
+                ("coords", ct.POINTER(ct.c_double)), ("cells", ct.POINTER(ct.c_int64)),
+                ("bnd_vertex", ct.POINTER(ct.c_uint8))]
+
+
+class Tableau(ct.Structure):
+    _fields_ = [("s", ct.c_int), ("A", ct.POINTER(ct.c_double)), ("b", ct.POINTER(ct.c_double)),
+                ("c", ct.POINTER(ct.c_double))]
+
+
+class Options(ct.Structure):
+    _fields_ = [("nlevels", ct.c_int), ("nu_pre", ct.c_int), ("nu_post", ct.c_int),
+                ("smoother", ct.c_int), ("omega", ct.c_double), ("cheb_lo", ct.c_double),
+                ("cheb_hi", ct.c_double), ("rtol", ct.c_double), ("atol", ct.c_double),
+                ("restart", ct.c_int), ("maxit", ct.c_int), ("patch_precision", ct.c_int),
+                ("wind", ct.POINTER(ct.c_double)), ("cuda_stream", ct.c_void_p),
+                ("timeout_spins", ct.c_int64)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("status", ct.c_int), ("r0", ct.c_double),
+                ("rfinal", ct.c_double), ("t_setup", ct.c_double), ("t_solve", ct.c_double),
+                ("bad_index", ct.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LevelInfo(ct.Structure):
+    _fields_ = [(k, ct.c_int64) for k in ("nv", "ne", "nc", "np2", "nf", "m", "N", "npatch",
+                                          "ncolours", "max_patch_dofs", "factor_bytes")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ct.c_void_p
+_SIGS = {
+    "irkmg_default_options": (None, [ct.POINTER(Options)]),
+    "irkmg_radau_iia": (ct.c_int, [ct.c_int, _P, _P, _P]),
+    "irkmg_setup": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(Tableau), ct.c_double, ct.c_double,
+                               ct.POINTER(Options), ct.POINTER(_P)]),
+    "irkmg_update": (ct.c_int, [_P, ct.c_double, ct.c_double]),
+    "irkmg_level_info_get": (ct.c_int, [_P, ct.c_int, ct.POINTER(LevelInfo)]),
+    "irkmg_p2_coords": (ct.c_int, [_P, ct.c_int, _P]),
+    "irkmg_free_nodes": (ct.c_int, [_P, ct.c_int, _P]),
+    "irkmg_patch_map": (ct.c_int, [_P, ct.c_int, _P, _P]),
+    "irkmg_colouring": (ct.c_int, [_P, ct.c_int, _P]),
+    "irkmg_apply": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
+    "irkmg_vanka_correction": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
+    "irkmg_smooth": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int, ct.c_int]),
+    "irkmg_restrict": (ct.c_int, [_P, ct.c_int, _P, _P]),
+    "irkmg_prolong": (ct.c_int, [_P, ct.c_int, _P, _P]),
+    "irkmg_coarse_solve": (ct.c_int, [_P, _P, _P, ct.c_int]),
+    "irkmg_vcycle": (ct.c_int, [_P, _P, _P, ct.c_int]),
+    "irkmg_solve": (ct.c_int, [_P, _P, _P, ct.POINTER(Stats)]),
+    "irkmg_adjoint_solve": (ct.c_int, [_P, _P, _P, ct.POINTER(Stats)]),
+    "irkmg_stage_rhs": (ct.c_int, [_P, _P, _P, _P, _P]),
+    "irkmg_advance": (ct.c_int, [_P, _P, _P, _P]),
+    "irkmg_destroy": (None, [_P]),
+    "irkmg_strerror": (ct.c_char_p, [ct.c_int]),
+    "irkmg_last_error": (ct.c_char_p, []),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded libirkmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2202_07381_gb300.build.build()")
+        L = ct.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != IRKMG_OK:
+        raise IrkmgError(rc, lib().irkmg_last_error().decode())
+    return rc
+
+
+def _dptr(t, n=None, name="vector"):
+    """Data pointer of a contiguous float64 CUDA tensor (length n if given)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError(f"{name}: need a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name}: expected {n} entries, got {t.numel()}")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ct.POINTER(np.ctypeslib.as_ctypes_type(dtype)))
+
+
+def irkmg_default_options():
+    o = Options()
+    lib().irkmg_default_options(ct.byref(o))
+    return o
+
+
+def irkmg_radau_iia(s):
+    A, b, c = np.zeros(s * s), np.zeros(s), np.zeros(s)
+    _check(lib().irkmg_radau_iia(s, A.ctypes.data, b.ctypes.data, c.ctypes.data))
+    return A.reshape(s, s), b, c
+
+
+class Context:
+    """Owns an irkmg_ctx; sizes per level are cached in .levels."""
+
+    def __init__(self, handle, s, keep):
+        self.handle = handle
+        self.s = s
+        self._keep = keep
+        self.levels = []
+        k = 0
+        while True:
+            info = LevelInfo()
+            if lib().irkmg_level_info_get(handle, k, ct.byref(info)) != IRKMG_OK:
+                break
+            self.levels.append(info.as_dict())
+            k += 1
+        self.nlevels = len(self.levels)
+
+    @property
+    def finest(self):
+        return self.levels[-1]
+
+    def N(self, level=-1):
+        return self.levels[level]["N"]
+
+    def close(self):
+        if self.handle:
+            lib().irkmg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def irkmg_setup(coords, cells, bnd, A, b, c, dt, nu, options=None, wind=None, stream=None):
+    """Build a context.  coords [nv,2], cells [nc,3], bnd [nv] (host arrays)."""
+    o = options if options is not None else irkmg_default_options()
+    xy, pxy = _hptr(coords, np.float64)
+    cl, pcl = _hptr(cells, np.int64)
+    bd, pbd = _hptr(bnd, np.uint8)
+    mesh = Mesh(2, xy.shape[0], cl.shape[0], pxy, pcl, pbd)
+    s = int(np.asarray(b).size)
+    Aa, pA = _hptr(A, np.float64)
+    ba, pb = _hptr(b, np.float64)
+    ca, pc = _hptr(c, np.float64)
+    tab = Tableau(s, pA, pb, pc)
+    keep = [xy, cl, bd, Aa, ba, ca]
+    if wind is not None:
+        w, pw = _hptr(wind, np.float64)
+        o.wind = pw
+        keep.append(w)
+    if stream is not None:
+        o.cuda_stream = ct.c_void_p(stream)
+    h = ct.c_void_p()
+    _check(lib().irkmg_setup(ct.byref(mesh), ct.byref(tab), float(dt), float(nu), ct.byref(o),
+                             ct.byref(h)))
+    return Context(h, s, keep)
+
+
+def irkmg_update(ctx, dt, nu):
+    _check(lib().irkmg_update(ctx.handle, float(dt), float(nu)))
+
+
+def irkmg_p2_coords(ctx, level=-1):
+    level %= ctx.nlevels
+    out = np.zeros((ctx.levels[level]["np2"], 2))
+    _check(lib().irkmg_p2_coords(ctx.handle, level, out.ctypes.data))
+    return out
+
+
+def irkmg_free_nodes(ctx, level=-1):
+    level %= ctx.nlevels
+    out = np.zeros(ctx.levels[level]["nf"], dtype=np.int64)
+    _check(lib().irkmg_free_nodes(ctx.handle, level, out.ctypes.data))
+    return out
+
+
+def irkmg_patch_map(ctx, level=-1):
+    level %= ctx.nlevels
+    nv = ctx.levels[level]["nv"]
+    ptr = np.zeros(nv + 1, dtype=np.int64)
+    nodes = np.zeros(64 * nv, dtype=np.int32)
+    _check(lib().irkmg_patch_map(ctx.handle, level, ptr.ctypes.data, nodes.ctypes.data))
+    return ptr, nodes[: ptr[-1]].copy()
+
+
+def irkmg_colouring(ctx, level=-1):
+    level %= ctx.nlevels
+    out = np.zeros(ctx.levels[level]["nv"], dtype=np.int32)
+    _check(lib().irkmg_colouring(ctx.handle, level, out.ctypes.data))
+    return out
+
+
+def irkmg_apply(ctx, x, y, level=-1, transpose=False):
+    level %= ctx.nlevels
+    n = ctx.N(level)
+    _check(lib().irkmg_apply(ctx.handle, level, _dptr(x, n, "x"), _dptr(y, n, "y"), int(transpose)))
+
+
+def irkmg_vanka_correction(ctx, r, c, level=-1, transpose=False):
+    level %= ctx.nlevels
+    n = ctx.N(level)
+    _check(lib().irkmg_vanka_correction(ctx.handle, level, _dptr(r, n, "r"), _dptr(c, n, "c"),
+                                        int(transpose)))
+
+
+def irkmg_smooth(ctx, F, x, nsteps, level=-1, transpose=False):
+    level %= ctx.nlevels
+    n = ctx.N(level)
+    _check(lib().irkmg_smooth(ctx.handle, level, _dptr(F, n, "F"), _dptr(x, n, "x"), int(nsteps),
+                              int(transpose)))
+
+
+def irkmg_restrict(ctx, fine, coarse, level=-1):
+    level %= ctx.nlevels
+    _check(lib().irkmg_restrict(ctx.handle, level, _dptr(fine, ctx.N(level), "fine"),
+                                _dptr(coarse, ctx.N(level - 1), "coarse")))
+
+
+def irkmg_prolong(ctx, coarse, fine, level=-1):
+    level %= ctx.nlevels
+    _check(lib().irkmg_prolong(ctx.handle, level, _dptr(coarse, ctx.N(level - 1), "coarse"),
+                               _dptr(fine, ctx.N(level), "fine")))
+
+
+def irkmg_coarse_solve(ctx, r, x, transpose=False):
+    n = ctx.N(0)
+    _check(lib().irkmg_coarse_solve(ctx.handle, _dptr(r, n, "r"), _dptr(x, n, "x"), int(transpose)))
+
+
+def irkmg_vcycle(ctx, r, z, transpose=False):
+    n = ctx.N()
+    _check(lib().irkmg_vcycle(ctx.handle, _dptr(r, n, "r"), _dptr(z, n, "z"), int(transpose)))
+
+
+def _solve(fn, ctx, F, k, raise_on_noconv):
+    st = Stats()
+    n = ctx.N()
+    rc = fn(ctx.handle, _dptr(F, n, "F"), _dptr(k, n, "k"), ct.byref(st))
+    if rc == IRKMG_ENOCONV and not raise_on_noconv:
+        return st.as_dict()
+    _check(rc)
+    return st.as_dict()
+
+
+def irkmg_solve(ctx, F, k, raise_on_noconv=False):
+    """FGMRES + V-cycle solve of J k = F (k: initial guess in, solution out)."""
+    return _solve(lib().irkmg_solve, ctx, F, k, raise_on_noconv)
+
+
+def irkmg_adjoint_solve(ctx, G, lam, raise_on_noconv=False):
+    return _solve(lib().irkmg_adjoint_solve, ctx, G, lam, raise_on_noconv)
+
+
+def irkmg_stage_rhs(ctx, un, pn, f, F):
+    L = ctx.finest
+    _check(lib().irkmg_stage_rhs(ctx.handle, _dptr(un, 2 * L["nf"], "un"), _dptr(pn, L["nv"], "pn"),
+                                 _dptr(f, ctx.s * 2 * L["np2"], "f"), _dptr(F, L["N"], "F")))
+
+
+def irkmg_advance(ctx, k, un, pn):
+    L = ctx.finest
+    _check(lib().irkmg_advance(ctx.handle, _dptr(k, L["N"], "k"), _dptr(un, 2 * L["nf"], "un"),
+                               _dptr(pn, L["nv"], "pn")))
+
+
+def irkmg_destroy(ctx):
+    ctx.close()
+
+
+def irkmg_strerror(status):
+    return lib().irkmg_strerror(int(status)).decode()
