@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: time of one fully implicit Radau IIA stage solve to a 1e-10
+relative residual, and the HBM throughput of the Vanka apply and the stage
+operator against the measured peak.
+
+Workload (default): 2D Stokes, Radau IIA(3), dt = 1/64, nu = 1, manufactured
+solution u = curl(sin^2(pi x) sin^2(pi y)), p = sin(2 pi x) cos(2 pi y), on the
+512 x 512 two-triangle-per-square mesh reached from an 8 x 8 coarsest mesh by
+6 uniform refinements (7 levels), Taylor-Hood P2-P1: 7,068,681 coupled DoFs
+over 3 stages, 263,169 vertex-star patches of up to 117 DoFs.  FGMRES(30)
+right-preconditioned by V(2,2) Chebyshev [2, 8] additive Vanka.
+
+A step is one implicit RK time step through the C ABI: stage right-hand side,
+the FGMRES + V-cycle solve from a zero guess to ||F - J k|| <= 1e-10 ||F||,
+and the update of (u, p).  The patch inverses and the coarse inverse are built
+once in set-up (dt and nu are fixed) and reused every step; set-up time is
+reported separately as setup_s.
+
+--impl reference times the oracle (plain FP64 CPU restatement) on a bounded
+sample of the same workload.
+"""
+import os
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "IRK stage solve time to 1e-10 resid; Vanka apply+SpMV HBM GB/s vs peak"
+UNIT = "s/solve"
+FALLBACK_HBM = 6800.0
+
+# DRAM traffic per launch of the finest-level Vanka kernel from an ncu capture,
+# keyed by the hash of the kernel source it was taken with (None until taken).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_2202_07381_gb300", "csrc", "k_patch.cu"), "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def workload(args):
+    if args.small:
+        return dict(name="2D Stokes RadauIIA(2) 8x8 (3 levels), dt=1/8", n0=2, levels=3, s=2,
+                    dt=1 / 8, nu=1.0, n=8)
+    return dict(name="2D Stokes RadauIIA(3) 512x512 (7 levels from 8x8), dt=1/64", n0=8,
+                levels=7, s=3, dt=1 / 64, nu=1.0, n=512)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, n_sample):
+    """Time the oracle's FGMRES + V-cycle solve of the same problem on an
+    n_sample x n_sample mesh; returns (seconds per solve at the sample size,
+    seconds scaled to the workload by the DoF ratio, description)."""
+    from oracle import fgmres, mg, problem, tableau
+    A, b, c = tableau.radau_iia(wl["s"])
+    levels = int(round(np.log2(n_sample / wl["n0"]))) + 1
+    H = mg.Hierarchy(*synth.square_mesh(wl["n0"]), levels, A, wl["dt"], nu=wl["nu"])
+    F, _, _ = problem.mms_rhs(H, c)
+    t0 = time.perf_counter()
+    _, its, _ = fgmres.fgmres(H.finest.J, F, H.vcycle, rtol=1e-10, project=H.project_pressure)
+    dt = time.perf_counter() - t0
+    n_full = wl["s"] * (2 * (2 * wl["n"] - 1) ** 2 + (wl["n"] + 1) ** 2)
+    scaled = dt * n_full / H.finest.N
+    desc = (f"oracle solve at {n_sample}x{n_sample} ({levels} levels, N={H.finest.N}, {its} FGMRES "
+            f"iterations, {dt:.2f} s, 1 thread), scaled by N ratio {n_full}/{H.finest.N}")
+    return dt, scaled, desc
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    n_sample = 8 if args.small else 64
+    vals, desc = [], ""
+    for _ in range(max(1, args.warmup)):
+        oracle_sample(wl, n_sample)
+        if not args.small:
+            break
+    for _ in range(args.steps):
+        _, scaled, desc = oracle_sample(wl, n_sample)
+        vals.append(scaled)
+    v = float(np.mean(vals))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["name"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def make_context(irkmg, wl, precision, stream):
+    A, b, c = irkmg.irkmg_radau_iia(wl["s"])
+    o = irkmg.irkmg_default_options()
+    o.nlevels = wl["levels"]
+    o.patch_precision = precision
+    o.rtol = 1e-10
+    o.maxit = 300
+    t0 = time.perf_counter()
+    ctx = irkmg.irkmg_setup(*synth.square_mesh(wl["n0"]), A, b, c, wl["dt"], wl["nu"], o,
+                            stream=stream)
+    return ctx, time.perf_counter() - t0, c
+
+
+def initial_data(irkmg, ctx, wl, c):
+    xy = irkmg.irkmg_p2_coords(ctx)
+    free = irkmg.irkmg_free_nodes(ctx)
+    nv = ctx.finest["nv"]
+    ux, uy = synth.mms_velocity(xy[free, 0], xy[free, 1])
+    u0 = np.concatenate([ux, uy])
+    p0 = synth.mms_pressure(xy[:nv, 0], xy[:nv, 1])
+    p0 = p0 - p0.mean()
+    fx, fy = synth.mms_forcing(xy[:, 0], xy[:, 1], nu=wl["nu"])
+    f = np.concatenate([np.concatenate([fx, fy]) for _ in c])   # steady: same at every c_i
+    return u0, p0, f
+
+
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+    from paper_2202_07381_gb300 import irkmg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    prec = 32 if args.form == "fp32" else 64
+    ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream)
+    u0, p0, f = initial_data(irkmg, ctx, wl, c)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    u, p, fd = T(u0), T(p0), T(f)
+    N = ctx.finest["N"]
+    F = torch.zeros(N, dtype=torch.float64, device=dev)
+    k = torch.zeros_like(F)
+    stats = []
+
+    def step():
+        irkmg.irkmg_stage_rhs(ctx, u, p, fd, F)
+        k.zero_()
+        st = irkmg.irkmg_solve(ctx, F, k)
+        irkmg.irkmg_advance(ctx, k, u, p)
+        stats.append(st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats.clear()
+    barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+    irkmg.irkmg_trace_enable(ctx, True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        time.sleep(0.25)
+    ms = e0.elapsed_time(e1)
+    trace = irkmg.irkmg_trace_read(ctx)
+    irkmg.irkmg_trace_enable(ctx, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = [s_["iters"] for s_ in stats]
+    resid = [s_["rfinal"] / max(s_["r0"], 1e-300) for s_ in stats]
+    assert all(s_["status"] == 0 for s_ in stats), stats
+
+    # end to end: host state in pinned memory, copies inside the timed region
+    hu = torch.tensor(u0, dtype=torch.float64).pin_memory()
+    hp = torch.tensor(p0, dtype=torch.float64).pin_memory()
+    hf = torch.tensor(f, dtype=torch.float64).pin_memory()
+    h2d = (hu.numel() + hp.numel() + hf.numel()) * 8
+    d2h = (hu.numel() + hp.numel()) * 8
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u.copy_(hu, non_blocking=True)
+        p.copy_(hp, non_blocking=True)
+        fd.copy_(hf, non_blocking=True)
+        irkmg.irkmg_stage_rhs(ctx, u, p, fd, F)
+        k.zero_()
+        irkmg.irkmg_solve(ctx, F, k)
+        irkmg.irkmg_advance(ctx, k, u, p)
+        hu.copy_(u, non_blocking=True)
+        hp.copy_(p, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    result = None
+    if rank == 0:
+        hbm, hbm_kind = peaks()
+        van_gbs = trace["vanka_bytes"] / (trace["vanka_ms"] * 1e-3) / 1e9 if trace["vanka_ms"] else None
+        op_gbs = trace["op_bytes"] / (trace["op_ms"] * 1e-3) / 1e9 if trace["op_ms"] else None
+        nvl = max(trace["vanka_launches"], 1)
+        h = kernel_source_hash()
+        traffic = NCU_TRAFFIC.get(h)
+        value = ms * 1e-3 / (args.steps * world)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 64 else "f64+f32patch", "data": "synthetic",
+            "config": {"workload": wl["name"], "N": N, "patches_finest": ctx.finest["nv"],
+                       "patch_precision": prec, "smoother": "Chebyshev[2,8] V(2,2)",
+                       "fgmres_restart": 30, "rtol": 1e-10,
+                       "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
+                             % (ctx.finest["factor_bytes"] / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iters_per_solve": iters, "rel_residual": max(resid), "setup_s": setup_s,
+            "roofline": {"bound": "hbm", "kernel": "k_vanka_apply (finest level)",
+                         "achieved": van_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": van_gbs / hbm if van_gbs else None, "traffic": traffic,
+                         "peak_source": f"{hbm_kind} hbm_gbs",
+                         "launches": trace["vanka_launches"],
+                         "bytes_per_launch": trace["vanka_bytes"] / nvl,
+                         "avg_launch_ms": trace["vanka_ms"] / nvl, "kernel_src": h},
+            "roofline_spmv": {"bound": "hbm", "kernel": "k_residual (finest level)",
+                              "achieved": op_gbs, "peak": hbm, "unit": "GB/s",
+                              "frac": op_gbs / hbm if op_gbs else None,
+                              "launches": trace["op_launches"],
+                              "avg_launch_ms": trace["op_ms"] / max(trace["op_launches"], 1)},
+            "gpu_launches": trace["launches"],
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_s / (args.steps * world), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        }
+    ctx.close()
+    return result
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--small", action="store_true", help="8x8 mesh (quick check)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = workload(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, wl, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            n_sample = 8 if args.small else 64
+            _, scaled, desc = oracle_sample(wl, n_sample)
+            res["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -197,6 +197,29 @@ int irkmg_stage_rhs(irkmg_ctx *ctx, const double *d_un, const double *d_pn, cons
 /* u^{n+1} = u^n + dt sum_j b_j k_j^u and likewise p (in place). */
 int irkmg_advance(irkmg_ctx *ctx, const double *d_k, double *d_un, double *d_pn);
 
+/* ---- tracing ---------------------------------------------------------------- */
+
+/* Kernel accounting since the last irkmg_trace_enable.  `launches` counts every
+ * kernel the library issued.  With tracing on, each finest-level Vanka colour
+ * launch and each finest-level stage-operator launch is bracketed by CUDA events
+ * on the context stream; *_ms is their summed device time and *_bytes their
+ * algorithmic bytes: per Vanka sweep, sum over patches of n_p^2·w + 4·n_p plus
+ * 24·N for reading r and updating the target (split over the colour launches
+ * in proportion to their inverse bytes); per operator application,
+ * nnz(vel)·20 + (nnz(B) + nnz(Bᵀ))·20 + 24·N bytes. */
+typedef struct {
+  int64_t launches;
+  int64_t vanka_launches;
+  double vanka_ms, vanka_bytes;
+  int64_t op_launches;
+  double op_ms, op_bytes;
+} irkmg_trace;
+
+/* Reset the counters; on = 1 also starts event timing.  Never fails on a valid ctx. */
+int irkmg_trace_enable(irkmg_ctx *ctx, int on);
+/* Synchronise the context stream and return the totals (resets the event pool). */
+int irkmg_trace_read(irkmg_ctx *ctx, irkmg_trace *out);
+
 /* ---- teardown, diagnostics ------------------------------------------------ */
 void irkmg_destroy(irkmg_ctx *ctx);
 const char *irkmg_strerror(int status);

@@ -92,6 +92,55 @@ int check_err(Ctx& C, const char* what, irkmg_stats* st = nullptr) {
   return IRKMG_OK;
 }
 
+// --- tracing -----------------------------------------------------------------
+// Returns the start/stop event pair to record around one traced launch.
+int trace_pair(Ctx& C, int cls, double bytes, cudaEvent_t* a, cudaEvent_t* b) {
+  if (C.ev_used + 2 > C.ev.size()) {
+    for (int k = 0; k < 256; ++k) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      C.ev.push_back(e);
+    }
+  }
+  *a = C.ev[C.ev_used];
+  *b = C.ev[C.ev_used + 1];
+  C.ev_used += 2;
+  C.ev_class.push_back(cls);
+  C.ev_bytes.push_back(bytes);
+  return IRKMG_OK;
+}
+
+// Stage operator (r = F - J x, or y = J x when F is null), counted and traced.
+int op(Ctx& C, Level& L, const double* F, const double* x, double* r, int tr) {
+  const bool timed = C.trace_on && &L == &C.L.back();
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (timed) {
+    int rc = trace_pair(C, 1, L.op_bytes - (F ? 0.0 : 8.0 * L.N), &a, &b);
+    if (rc) return rc;
+    CK(cudaEventRecord(a, C.stream));
+  }
+  CK(launch_residual(C, L, F, x, r, tr));
+  C.launches++;
+  if (timed) CK(cudaEventRecord(b, C.stream));
+  return IRKMG_OK;
+}
+
+void level_trace_bytes(Ctx& C, Level& L) {
+  const double w = C.opt.patch_precision == 64 ? 8.0 : 4.0;
+  L.colour_bytes.assign(L.ncolours, 0.0);
+  double total = 0.0;
+  std::vector<double> inv(L.ncolours, 0.0);
+  for (int64_t v = 0; v < L.nv; ++v) {
+    const double np = (double)C.s * (2 * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
+    inv[L.h_colour[v]] += np * np * w;
+    total += np * np * w + 4.0 * np;
+  }
+  double invsum = 0.0;
+  for (double x : inv) invsum += x;
+  const double sweep = total + 24.0 * (double)L.N;
+  for (int c = 0; c < L.ncolours; ++c) L.colour_bytes[c] = sweep * inv[c] / invsum;
+}
+
 // --- patches: maps, colouring, ordering, inverses (Section 4.2) -----------
 int build_patches(Ctx& C, Level& L) {
   const int maxnodes = 64;
@@ -226,7 +275,18 @@ int factor_all(Ctx& C) {
 
 // --- smoothers and V-cycle -------------------------------------------------
 int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr) {
-  for (int c = 0; c < L.ncolours; ++c) CK(launch_vanka(C, L, c, r, out, scale, tr));
+  const bool timed = C.trace_on && &L == &C.L.back();
+  for (int c = 0; c < L.ncolours; ++c) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) {
+      int rc = trace_pair(C, 0, L.colour_bytes[c], &a, &b);
+      if (rc) return rc;
+      CK(cudaEventRecord(a, C.stream));
+    }
+    CK(launch_vanka(C, L, c, r, out, scale, tr));
+    C.launches++;
+    if (timed) CK(cudaEventRecord(b, C.stream));
+  }
   return IRKMG_OK;
 }
 
@@ -234,15 +294,19 @@ int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int 
 int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_init, int tr) {
   if (nsteps <= 0) {
     if (zero_init) CK(launch_fill(x, 0.0, L.N, C.stream));
+    C.launches += zero_init ? 1 : 0;
     return IRKMG_OK;
   }
   int rc;
   if (C.opt.smoother == 0) {
-    if (zero_init) CK(launch_fill(x, 0.0, L.N, C.stream));
+    if (zero_init) {
+      CK(launch_fill(x, 0.0, L.N, C.stream));
+      C.launches++;
+    }
     for (int k = 0; k < nsteps; ++k) {
       const double* res = b;
       if (!(zero_init && k == 0)) {
-        CK(launch_residual(C, L, b, x, L.t, tr));
+        { int rc_ = op(C, L, b, x, L.t, tr); if (rc_) return rc_; }
         res = L.t;
       }
       if ((rc = vanka_all(C, L, res, x, C.opt.omega, tr))) return rc;
@@ -255,21 +319,25 @@ int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_i
   double rho = 1.0 / sigma;
   const double* res = b;
   if (!zero_init) {
-    CK(launch_residual(C, L, b, x, L.t, tr));
+    { int rc_ = op(C, L, b, x, L.t, tr); if (rc_) return rc_; }
     res = L.t;
   }
   CK(launch_fill(L.d, 0.0, L.N, C.stream));
+  C.launches++;
   if ((rc = vanka_all(C, L, res, L.d, 1.0 / theta, tr))) return rc;
-  if (zero_init)
+  if (zero_init) {
     CK(cudaMemcpyAsync(x, L.d, sizeof(double) * L.N, cudaMemcpyDeviceToDevice, C.stream));
-  else
+  } else {
     CK(launch_axpby(x, L.d, 1.0, 1.0, L.N, C.stream));
+    C.launches++;
+  }
   for (int k = 1; k < nsteps; ++k) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    CK(launch_residual(C, L, b, x, L.t, tr));
+    { int rc_ = op(C, L, b, x, L.t, tr); if (rc_) return rc_; }
     CK(launch_axpby(L.d, L.d, rho_new * rho, 0.0, L.N, C.stream));
     if ((rc = vanka_all(C, L, L.t, L.d, 2.0 * rho_new / delta, tr))) return rc;
     CK(launch_axpby(x, L.d, 1.0, 1.0, L.N, C.stream));
+    C.launches += 2;
     rho = rho_new;
   }
   return IRKMG_OK;
@@ -278,16 +346,18 @@ int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_i
 int vcycle_level(Ctx& C, int l, const double* b, double* z, int tr) {
   if (l == 0) {
     CK(launch_coarse_apply(C, b, z, tr));
+    C.launches++;
     return IRKMG_OK;
   }
   Level& L = C.L[l];
   Level& Lc = C.L[l - 1];
   int rc;
   if ((rc = smooth(C, L, b, z, C.opt.nu_pre, true, tr))) return rc;
-  CK(launch_residual(C, L, b, z, L.t, tr));
+  { int rc_ = op(C, L, b, z, L.t, tr); if (rc_) return rc_; }
   CK(launch_restrict(C, L, L.t, Lc.r));
   if ((rc = vcycle_level(C, l - 1, Lc.r, Lc.z, tr))) return rc;
   CK(launch_prolong(C, L, Lc.z, z, 1));
+  C.launches += 2;
   return smooth(C, L, b, z, C.opt.nu_post, false, tr);
 }
 
@@ -305,6 +375,7 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
   auto norm = [&](const double* v, double* out) -> int {
     CK(launch_multidot(v, 0, 1, v, n, C.d_part, hd + 192, C.stream));
+    C.launches += 2;
     CK(cudaMemcpyAsync(hh + 192, hd + 192, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
     CK(cudaStreamSynchronize(C.stream));
     *out = std::sqrt(hh[192]);
@@ -314,7 +385,7 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
   double bnorm;
   if ((rc = norm(F, &bnorm))) return rc;
   const double target = std::max(C.opt.rtol * bnorm, C.opt.atol);
-  CK(launch_residual(C, L, F, x, V, tr));
+  if ((rc = op(C, L, F, x, V, tr))) return rc;
   double beta;
   if ((rc = norm(V, &beta))) return rc;
   if (st) {
@@ -324,6 +395,7 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
   int its = 0;
   while (beta > target && its < C.opt.maxit) {
     CK(launch_axpby(V, V, 1.0 / beta, 0.0, n, C.stream));
+    C.launches++;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jdone = 0;
@@ -332,20 +404,25 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
       double* zj = Z + (int64_t)j * n;
       if ((rc = vcycle_level(C, (int)C.L.size() - 1, vj, zj, tr))) return rc;
       CK(launch_pressure_mean_remove(C, L, zj));
-      CK(launch_residual(C, L, nullptr, zj, w, tr));
+      C.launches++;
+      if ((rc = op(C, L, nullptr, zj, w, tr))) return rc;
       // classical Gram–Schmidt, twice
       CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd, C.stream));
       CK(launch_multiaxpy(w, V, n, j + 1, hd, -1.0, n, C.stream));
       CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd + 64, C.stream));
       CK(launch_multiaxpy(w, V, n, j + 1, hd + 64, -1.0, n, C.stream));
       CK(launch_multidot(w, 0, 1, w, n, C.d_part, hd + 128, C.stream));
+      C.launches += 10;
       CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 129, cudaMemcpyDeviceToHost, C.stream));
       CK(cudaStreamSynchronize(C.stream));
       double* Hj = &H[(size_t)j * (m + 1)];  // column j, length m+1
       for (int i = 0; i <= j; ++i) Hj[i] = hh[i] + hh[64 + i];
       const double hn = std::sqrt(hh[128]);
       Hj[j + 1] = hn;
-      if (hn > 0.0) CK(launch_axpby(V + (int64_t)(j + 1) * n, w, 1.0 / hn, 0.0, n, C.stream));
+      if (hn > 0.0) {
+        CK(launch_axpby(V + (int64_t)(j + 1) * n, w, 1.0 / hn, 0.0, n, C.stream));
+        C.launches++;
+      }
       for (int i = 0; i < j; ++i) {
         const double a = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
         Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
@@ -371,7 +448,8 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
     CK(cudaMemcpyAsync(hd + 256, hh + 256, sizeof(double) * jdone, cudaMemcpyHostToDevice,
                        C.stream));
     CK(launch_multiaxpy(x, Z, n, jdone, hd + 256, 1.0, n, C.stream));
-    CK(launch_residual(C, L, F, x, V, tr));
+    C.launches++;
+    if ((rc = op(C, L, F, x, V, tr))) return rc;
     if ((rc = norm(V, &beta))) return rc;
   }
   if (st) {
@@ -465,7 +543,9 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
       if ((rc = upload_csr(*C, L.pp, Pp, 1))) return rc;
       if ((rc = upload_csr(*C, L.ppt, transpose_csr(Pp, 1), 1))) return rc;
       if ((rc = build_patches(*C, L))) return rc;
+      level_trace_bytes(*C, L);
     }
+    L.op_bytes = 20.0 * (double)L.vel.nnz + 20.0 * (double)(L.b.nnz + L.bt.nnz) + 24.0 * (double)L.N;
   }
   C->nb = C->L[0].N + C->s;
   if (C->nb > 20000) return fail(IRKMG_EINVAL, "coarsest level too large for the dense solve");
@@ -613,14 +693,14 @@ int irkmg_colouring(const irkmg_ctx* C, int level, int32_t* colour) {
 
 int irkmg_apply(irkmg_ctx* C, int level, const double* x, double* y, int transpose) {
   if (!level_ok(C, level) || !x || !y) return fail(IRKMG_EINVAL, "bad arguments");
-  CK(launch_residual(*C, C->L[level], nullptr, x, y, transpose ? 1 : 0));
-  return IRKMG_OK;
+  return op(*C, C->L[level], nullptr, x, y, transpose ? 1 : 0);
 }
 
 int irkmg_vanka_correction(irkmg_ctx* C, int level, const double* r, double* c, int transpose) {
   if (!level_ok(C, level) || level == 0 || !r || !c) return fail(IRKMG_EINVAL, "bad arguments");
   Level& L = C->L[level];
   CK(launch_fill(c, 0.0, L.N, C->stream));
+  C->launches++;
   return vanka_all(*C, L, r, c, 1.0, transpose ? 1 : 0);
 }
 
@@ -669,12 +749,48 @@ int irkmg_stage_rhs(irkmg_ctx* C, const double* un, const double* pn, const doub
                     double* F) {
   if (!C || !un || !pn || !f || !F) return fail(IRKMG_EINVAL, "bad arguments");
   CK(launch_stage_rhs(*C, un, pn, f, F));
+  C->launches++;
   return IRKMG_OK;
 }
 
 int irkmg_advance(irkmg_ctx* C, const double* k, double* un, double* pn) {
   if (!C || !k || !un || !pn) return fail(IRKMG_EINVAL, "bad arguments");
   CK(launch_advance(*C, k, un, pn));
+  C->launches++;
+  return IRKMG_OK;
+}
+
+int irkmg_trace_enable(irkmg_ctx* C, int on) {
+  if (!C) return fail(IRKMG_EINVAL, "null ctx");
+  C->launches = 0;
+  C->trace_on = on != 0;
+  C->ev_used = 0;
+  C->ev_class.clear();
+  C->ev_bytes.clear();
+  return IRKMG_OK;
+}
+
+int irkmg_trace_read(irkmg_ctx* C, irkmg_trace* out) {
+  if (!C || !out) return fail(IRKMG_EINVAL, "null argument");
+  CK(C->stream ? cudaStreamSynchronize(C->stream) : cudaDeviceSynchronize());
+  std::memset(out, 0, sizeof(*out));
+  out->launches = C->launches;
+  for (size_t k = 0; k < C->ev_class.size(); ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, C->ev[2 * k], C->ev[2 * k + 1]));
+    if (C->ev_class[k] == 0) {
+      out->vanka_launches++;
+      out->vanka_ms += ms;
+      out->vanka_bytes += C->ev_bytes[k];
+    } else {
+      out->op_launches++;
+      out->op_ms += ms;
+      out->op_bytes += C->ev_bytes[k];
+    }
+  }
+  C->ev_used = 0;
+  C->ev_class.clear();
+  C->ev_bytes.clear();
   return IRKMG_OK;
 }
 
@@ -682,6 +798,7 @@ void irkmg_destroy(irkmg_ctx* C) {
   if (!C) return;
   if (C->stream) cudaStreamSynchronize(C->stream);
   else cudaDeviceSynchronize();
+  for (cudaEvent_t e : C->ev) cudaEventDestroy(e);
   for (void* p : C->allocs) cudaFree(p);
   if (C->h_h) cudaFreeHost(C->h_h);
   delete C;

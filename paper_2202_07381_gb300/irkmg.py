@@ -59,6 +59,15 @@ class LevelInfo(ct.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Trace(ct.Structure):
+    _fields_ = [("launches", ct.c_int64), ("vanka_launches", ct.c_int64), ("vanka_ms", ct.c_double),
+                ("vanka_bytes", ct.c_double), ("op_launches", ct.c_int64), ("op_ms", ct.c_double),
+                ("op_bytes", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _P = ct.c_void_p
 _SIGS = {
@@ -83,6 +92,8 @@ _SIGS = {
     "irkmg_adjoint_solve": (ct.c_int, [_P, _P, _P, ct.POINTER(Stats)]),
     "irkmg_stage_rhs": (ct.c_int, [_P, _P, _P, _P, _P]),
     "irkmg_advance": (ct.c_int, [_P, _P, _P, _P]),
+    "irkmg_trace_enable": (ct.c_int, [_P, ct.c_int]),
+    "irkmg_trace_read": (ct.c_int, [_P, ct.POINTER(Trace)]),
     "irkmg_destroy": (None, [_P]),
     "irkmg_strerror": (ct.c_char_p, [ct.c_int]),
     "irkmg_last_error": (ct.c_char_p, []),
@@ -309,6 +320,16 @@ def irkmg_advance(ctx, k, un, pn):
     L = ctx.finest
     _check(lib().irkmg_advance(ctx.handle, _dptr(k, L["N"], "k"), _dptr(un, 2 * L["nf"], "un"),
                                _dptr(pn, L["nv"], "pn")))
+
+
+def irkmg_trace_enable(ctx, on=True):
+    _check(lib().irkmg_trace_enable(ctx.handle, int(on)))
+
+
+def irkmg_trace_read(ctx):
+    t = Trace()
+    _check(lib().irkmg_trace_read(ctx.handle, ct.byref(t)))
+    return t.as_dict()
 
 
 def irkmg_destroy(ctx):
