@@ -10,11 +10,14 @@ solution u = curl(sin^2(pi x) sin^2(pi y)), p = sin(2 pi x) cos(2 pi y), on the
 over 3 stages, 263,169 vertex-star patches of up to 117 DoFs.  FGMRES(30)
 right-preconditioned by V(2,2) Chebyshev [2, 8] additive Vanka.
 
-A step is one implicit RK time step through the C ABI: stage right-hand side,
-the FGMRES + V-cycle solve from a zero guess to ||F - J k|| <= 1e-10 ||F||,
-and the update of (u, p).  The patch inverses and the coarse inverse are built
-once in set-up (dt and nu are fixed) and reused every step; set-up time is
-reported separately as setup_s.
+A step is one implicit RK time step through the C ABI from the interpolated
+initial state (u^0, p^0) at t = 0: stage right-hand side, the FGMRES + V-cycle
+solve from a zero guess to ||F - J k|| <= 1e-10 ||F||, and the update to
+(u^1, p^1).  Every step repeats the same first step, so every step does the
+same work (with the steady manufactured solution, stepping on would drive F
+towards zero and a relative 1e-10 below rounding).  The patch inverses and the
+coarse inverse are built once in set-up (dt and nu fixed) and reused every
+step; set-up time is reported separately as setup_s.
 
 --impl reference times the oracle (plain FP64 CPU restatement) on a bounded
 sample of the same workload.
@@ -205,6 +208,7 @@ def run_ours(args, wl, rank, world, local_rank):
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
+    u1, p1 = torch.empty_like(u), torch.empty_like(p)
     N = ctx.finest["N"]
     F = torch.zeros(N, dtype=torch.float64, device=dev)
     k = torch.zeros_like(F)
@@ -214,7 +218,9 @@ def run_ours(args, wl, rank, world, local_rank):
         irkmg.irkmg_stage_rhs(ctx, u, p, fd, F)
         k.zero_()
         st = irkmg.irkmg_solve(ctx, F, k)
-        irkmg.irkmg_advance(ctx, k, u, p)
+        u1.copy_(u)
+        p1.copy_(p)
+        irkmg.irkmg_advance(ctx, k, u1, p1)
         stats.append(st)
 
     for _ in range(args.warmup):
@@ -249,8 +255,9 @@ def run_ours(args, wl, rank, world, local_rank):
     hu = torch.tensor(u0, dtype=torch.float64).pin_memory()
     hp = torch.tensor(p0, dtype=torch.float64).pin_memory()
     hf = torch.tensor(f, dtype=torch.float64).pin_memory()
+    hu1, hp1 = torch.empty_like(hu).pin_memory(), torch.empty_like(hp).pin_memory()
     h2d = (hu.numel() + hp.numel() + hf.numel()) * 8
-    d2h = (hu.numel() + hp.numel()) * 8
+    d2h = (hu1.numel() + hp1.numel()) * 8
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -261,9 +268,11 @@ def run_ours(args, wl, rank, world, local_rank):
         irkmg.irkmg_stage_rhs(ctx, u, p, fd, F)
         k.zero_()
         irkmg.irkmg_solve(ctx, F, k)
-        irkmg.irkmg_advance(ctx, k, u, p)
-        hu.copy_(u, non_blocking=True)
-        hp.copy_(p, non_blocking=True)
+        u1.copy_(u)
+        p1.copy_(p)
+        irkmg.irkmg_advance(ctx, k, u1, p1)
+        hu1.copy_(u1, non_blocking=True)
+        hp1.copy_(p1, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
