@@ -69,8 +69,12 @@ def workload(args):
     if args.small:
         return dict(name="2D Stokes RadauIIA(2) 8x8 (3 levels), dt=1/8", n0=2, levels=3, s=2,
                     dt=1 / 8, nu=1.0, n=8)
-    return dict(name="2D Stokes RadauIIA(3) 512x512 (7 levels from 8x8), dt=1/64", n0=8,
-                levels=7, s=3, dt=1 / 64, nu=1.0, n=512)
+    n = args.n
+    levels = int(round(np.log2(n / 8))) + 1
+    if n < 16 or 8 * 2 ** (levels - 1) != n:
+        raise SystemExit("--n must be 8 * 2^k with k >= 1")
+    return dict(name=f"2D Stokes RadauIIA(3) {n}x{n} ({levels} levels from 8x8), dt=1/64", n0=8,
+                levels=levels, s=3, dt=1 / 64, nu=1.0, n=n)
 
 
 class ClockSampler:
@@ -331,6 +335,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--small", action="store_true", help="8x8 mesh (quick check)")
+    ap.add_argument("--n", type=int, default=512, help="finest mesh n x n (8 * 2^k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = workload(args)
@@ -347,7 +352,7 @@ def main():
     res = run_ours(args, wl, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            n_sample = 8 if args.small else 64
+            n_sample = 8 if args.small else min(64, wl["n"])
             _, scaled, desc = oracle_sample(wl, n_sample)
             res["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
                                    "sample": desc}
