@@ -161,6 +161,25 @@ int irkmg_vanka_correction(irkmg_ctx *ctx, int level, const double *d_r, double 
 int irkmg_smooth(irkmg_ctx *ctx, int level, const double *d_F, double *d_x, int nsteps,
                  int transpose);
 
+/* The same relaxation as irkmg_smooth, with no device allocation anywhere on
+ * its path.  The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc when they relax a vector — for example code whose
+ * device memory is entirely reserved by another framework's caching
+ * allocator, or a time loop that must not pay the device-wide synchronisation
+ * an allocation can imply.  Its two work vectors (residual and Chebyshev
+ * direction) live in one file-scope static device array of
+ * 2 × 524,288 doubles (8 MB, held by every GPU that loads the library until
+ * the process exits), so the level must have N <= 524,288 (e.g. 128×128 with
+ * s = 3); larger levels are rejected with IRKMG_EINVAL and no work is done.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the array: calls that overlap on the GPU (other
+ * streams, other contexts, other threads) race and must be serialised by the
+ * caller.  The array keeps the last call's contents; every value a call reads
+ * from it is written (or cleared) first by that same call. */
+int irkmg_smooth_noalloc(irkmg_ctx *ctx, int level, const double *d_F, double *d_x, int nsteps,
+                         int transpose);
+
 /* Transfers between level l (fine) and l-1: d_coarse = (I_s ⊗ P)ᵀ d_fine, and
  * d_fine = (I_s ⊗ P) d_coarse (overwrites), Section 4.1. */
 int irkmg_restrict(irkmg_ctx *ctx, int level, const double *d_fine, double *d_coarse);

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -568,6 +569,66 @@ bool level_ok(const irkmg_ctx* ctx, int level) {
   return ctx && level >= 0 && level < (int)ctx->L.size();
 }
 
+// --- relaxation without device allocation -----------------------------------
+// Work vectors for irkmg_smooth_noalloc: [0, kNoallocMaxN) holds the residual,
+// [kNoallocMaxN, 2 kNoallocMaxN) the Chebyshev direction.  Host code cannot
+// use the symbol as an address; the device address is looked up once per
+// device and cached.
+constexpr int64_t kNoallocMaxN = 1 << 19;
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoallocMaxN];
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+int noalloc_scratch(double** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(IRKMG_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return IRKMG_OK;
+}
+
+// nsteps relaxation steps on J x = b from x, with the residual in t and the
+// Chebyshev direction in d (both caller-provided, length >= L.N).
+int smooth_in(Ctx& C, Level& L, const double* b, double* x, int nsteps, int tr, double* t,
+              double* d) {
+  if (nsteps <= 0) return IRKMG_OK;
+  int rc;
+  if (C.opt.smoother == 0) {
+    for (int k = 0; k < nsteps; ++k) {
+      if ((rc = op(C, L, b, x, t, tr))) return rc;
+      if ((rc = vanka_all(C, L, t, x, C.opt.omega, tr))) return rc;
+    }
+    return IRKMG_OK;
+  }
+  const double theta = 0.5 * (C.opt.cheb_hi + C.opt.cheb_lo);
+  const double delta = 0.5 * (C.opt.cheb_hi - C.opt.cheb_lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if ((rc = op(C, L, b, x, t, tr))) return rc;
+  CK(launch_fill(d, 0.0, L.N, C.stream));
+  C.launches++;
+  if ((rc = vanka_all(C, L, t, d, 1.0 / theta, tr))) return rc;
+  CK(launch_axpby(x, d, 1.0, 1.0, L.N, C.stream));
+  C.launches++;
+  for (int k = 1; k < nsteps; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    if ((rc = op(C, L, b, x, t, tr))) return rc;
+    CK(launch_axpby(d, d, rho_new * rho, 0.0, L.N, C.stream));
+    if ((rc = vanka_all(C, L, t, d, 2.0 * rho_new / delta, tr))) return rc;
+    CK(launch_axpby(x, d, 1.0, 1.0, L.N, C.stream));
+    C.launches += 2;
+    rho = rho_new;
+  }
+  return IRKMG_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -708,6 +769,21 @@ int irkmg_smooth(irkmg_ctx* C, int level, const double* F, double* x, int nsteps
   if (!level_ok(C, level) || level == 0 || !F || !x || nsteps < 0)
     return fail(IRKMG_EINVAL, "bad arguments");
   return smooth(*C, C->L[level], F, x, nsteps, false, transpose ? 1 : 0);
+}
+
+int irkmg_smooth_noalloc(irkmg_ctx* C, int level, const double* F, double* x, int nsteps,
+                         int transpose) {
+  if (!level_ok(C, level) || level == 0 || !F || !x || nsteps < 0)
+    return fail(IRKMG_EINVAL, "bad arguments");
+  Level& L = C->L[level];
+  if (L.N > kNoallocMaxN)
+    return fail(IRKMG_EINVAL, "level has " + std::to_string(L.N) +
+                                  " unknowns; the static work array holds at most " +
+                                  std::to_string(kNoallocMaxN));
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  return smooth_in(*C, L, F, x, nsteps, transpose ? 1 : 0, scratch, scratch + kNoallocMaxN);
 }
 
 int irkmg_restrict(irkmg_ctx* C, int level, const double* fine, double* coarse) {

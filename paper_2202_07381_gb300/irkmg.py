@@ -84,6 +84,7 @@ _SIGS = {
     "irkmg_apply": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
     "irkmg_vanka_correction": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
     "irkmg_smooth": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int, ct.c_int]),
+    "irkmg_smooth_noalloc": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int, ct.c_int]),
     "irkmg_restrict": (ct.c_int, [_P, ct.c_int, _P, _P]),
     "irkmg_prolong": (ct.c_int, [_P, ct.c_int, _P, _P]),
     "irkmg_coarse_solve": (ct.c_int, [_P, _P, _P, ct.c_int]),
@@ -267,6 +268,15 @@ def irkmg_smooth(ctx, F, x, nsteps, level=-1, transpose=False):
     n = ctx.N(level)
     _check(lib().irkmg_smooth(ctx.handle, level, _dptr(F, n, "F"), _dptr(x, n, "x"), int(nsteps),
                               int(transpose)))
+
+
+def irkmg_smooth_noalloc(ctx, F, x, nsteps, level=-1, transpose=False):
+    """irkmg_smooth with its work vectors in the library's static device array
+    (no device allocation; levels with N <= 524,288)."""
+    level %= ctx.nlevels
+    n = ctx.N(level)
+    _check(lib().irkmg_smooth_noalloc(ctx.handle, level, _dptr(F, n, "F"), _dptr(x, n, "x"),
+                                      int(nsteps), int(transpose)))
 
 
 def irkmg_restrict(ctx, fine, coarse, level=-1):
