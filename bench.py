@@ -45,6 +45,9 @@ import synth  # noqa: E402
 METRIC = "IRK stage solve time to 1e-10 resid; Vanka apply+SpMV HBM GB/s vs peak"
 UNIT = "s/solve"
 FALLBACK_HBM = 6800.0
+# FP64 ALU peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz
+# (nominal 1.25 TFLOP/s; the project's FMA probe measured 1.251).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM traffic per launch of the finest-level Vanka kernel from an ncu capture,
 # keyed by the hash of the kernel source it was taken with (None until taken).
@@ -174,9 +177,10 @@ def run_reference(args, wl, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def make_context(irkmg, wl, precision, stream):
+def make_context(irkmg, wl, precision, stream, apply_variant=0):
     A, b, c = irkmg.irkmg_radau_iia(wl["s"])
     o = irkmg.irkmg_default_options()
+    o.apply_variant = apply_variant
     o.nlevels = wl["levels"]
     o.patch_precision = precision
     o.rtol = 1e-10
@@ -208,7 +212,7 @@ def run_ours(args, wl, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     prec = 32 if args.form == "fp32" else 64
-    ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream)
+    ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream, args.apply)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -292,8 +296,26 @@ def run_ours(args, wl, rank, world, local_rank):
         op_gbs = trace["op_bytes"] / (trace["op_ms"] * 1e-3) / 1e9 if trace["op_ms"] else None
         nvl = max(trace["vanka_launches"], 1)
         h = kernel_source_hash()
+        kname = "k_vanka_apply_staged" if args.apply == 0 else "k_vanka_apply"
         traffic = NCU_TRAFFIC.get(h)
         value = ms * 1e-3 / (args.steps * world)
+        van_tf = trace["vanka_flops"] / (trace["vanka_ms"] * 1e-3) / 1e12 if trace["vanka_ms"] else None
+        common = {"kernel": kname + " (finest level)", "traffic": traffic,
+                  "launches": trace["vanka_launches"], "bytes_per_launch": trace["vanka_bytes"] / nvl,
+                  "flops_per_launch": trace["vanka_flops"] / nvl,
+                  "avg_launch_ms": trace["vanka_ms"] / nvl, "kernel_src": h,
+                  "hbm_gbs": van_gbs, "hbm_frac": van_gbs / hbm if van_gbs else None,
+                  "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
+        if prec == 64:
+            # FP64 on GB300 runs at 1/62 of FP32: a dense FP64 mat-vec (2 flop per
+            # 8-byte entry) is bound by the FP64 pipe, not by HBM
+            roofline = {"bound": "alu", "achieved": van_tf, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": van_tf / FP64_PEAK_TFLOPS if van_tf else None,
+                        "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz", **common}
+        else:
+            roofline = {"bound": "hbm", "achieved": van_gbs, "peak": hbm, "unit": "GB/s",
+                        "frac": van_gbs / hbm if van_gbs else None,
+                        "peak_source": f"{hbm_kind} hbm_gbs", **common}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
@@ -306,13 +328,7 @@ def run_ours(args, wl, rank, world, local_rank):
                              % (ctx.finest["factor_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iters_per_solve": iters, "rel_residual": max(resid), "setup_s": setup_s,
-            "roofline": {"bound": "hbm", "kernel": "k_vanka_apply (finest level)",
-                         "achieved": van_gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": van_gbs / hbm if van_gbs else None, "traffic": traffic,
-                         "peak_source": f"{hbm_kind} hbm_gbs",
-                         "launches": trace["vanka_launches"],
-                         "bytes_per_launch": trace["vanka_bytes"] / nvl,
-                         "avg_launch_ms": trace["vanka_ms"] / nvl, "kernel_src": h},
+            "roofline": roofline,
             "roofline_spmv": {"bound": "hbm", "kernel": "k_residual (finest level)",
                               "achieved": op_gbs, "peak": hbm, "unit": "GB/s",
                               "frac": op_gbs / hbm if op_gbs else None,
@@ -337,6 +353,8 @@ def main():
     ap.add_argument("--small", action="store_true", help="8x8 mesh (quick check)")
     ap.add_argument("--n", type=int, default=512, help="finest mesh n x n (8 * 2^k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply", type=int, default=0, choices=[0, 1],
+                    help="Vanka apply kernel: 0 TMA-staged, 1 warp-per-patch")
     args = ap.parse_args()
     wl = workload(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -93,7 +93,11 @@ typedef struct {
   const double *wind;      /* host, finest-level Oseen wind at every P2 node,
                               np2·2 doubles (x, y per node), or NULL for Stokes     */
   void *cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream  */
-  int64_t timeout_spins;   /* bound for device-side waits (0 = library default)     */
+  int64_t timeout_spins;   /* bound on polls of one device-side wait (0 = 2^26); an
+                              expired wait makes the call return IRKMG_ETIMEOUT     */
+  int apply_variant;       /* Vanka apply kernel: 0 = TMA-staged (patch inverses
+                              streamed to shared memory by cp.async.bulk) when two
+                              stages fit, else 1; 1 = warp-per-patch mat-vec        */
 } irkmg_options;
 
 typedef struct {
@@ -232,6 +236,7 @@ typedef struct {
   double vanka_ms, vanka_bytes;
   int64_t op_launches;
   double op_ms, op_bytes;
+  double vanka_flops;      /* 2·n_p^2 per patch applied in the timed Vanka launches */
 } irkmg_trace;
 
 /* Reset the counters; on = 1 also starts event timing.  Never fails on a valid ctx. */

@@ -95,7 +95,8 @@ int check_err(Ctx& C, const char* what, irkmg_stats* st = nullptr) {
 
 // --- tracing -----------------------------------------------------------------
 // Returns the start/stop event pair to record around one traced launch.
-int trace_pair(Ctx& C, int cls, double bytes, cudaEvent_t* a, cudaEvent_t* b) {
+int trace_pair(Ctx& C, int cls, double bytes, cudaEvent_t* a, cudaEvent_t* b,
+               double flops = 0.0) {
   if (C.ev_used + 2 > C.ev.size()) {
     for (int k = 0; k < 256; ++k) {
       cudaEvent_t e;
@@ -108,6 +109,7 @@ int trace_pair(Ctx& C, int cls, double bytes, cudaEvent_t* a, cudaEvent_t* b) {
   C.ev_used += 2;
   C.ev_class.push_back(cls);
   C.ev_bytes.push_back(bytes);
+  C.ev_flops.push_back(flops);
   return IRKMG_OK;
 }
 
@@ -129,11 +131,13 @@ int op(Ctx& C, Level& L, const double* F, const double* x, double* r, int tr) {
 void level_trace_bytes(Ctx& C, Level& L) {
   const double w = C.opt.patch_precision == 64 ? 8.0 : 4.0;
   L.colour_bytes.assign(L.ncolours, 0.0);
+  L.colour_flops.assign(L.ncolours, 0.0);
   double total = 0.0;
   std::vector<double> inv(L.ncolours, 0.0);
   for (int64_t v = 0; v < L.nv; ++v) {
     const double np = (double)C.s * (2 * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
     inv[L.h_colour[v]] += np * np * w;
+    L.colour_flops[L.h_colour[v]] += 2.0 * np * np;
     total += np * np * w + 4.0 * np;
   }
   double invsum = 0.0;
@@ -280,7 +284,7 @@ int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int 
   for (int c = 0; c < L.ncolours; ++c) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (timed) {
-      int rc = trace_pair(C, 0, L.colour_bytes[c], &a, &b);
+      int rc = trace_pair(C, 0, L.colour_bytes[c], &a, &b, L.colour_flops[c]);
       if (rc) return rc;
       CK(cudaEventRecord(a, C.stream));
     }
@@ -415,7 +419,14 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
       CK(launch_multidot(w, 0, 1, w, n, C.d_part, hd + 128, C.stream));
       C.launches += 10;
       CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 129, cudaMemcpyDeviceToHost, C.stream));
+      CK(cudaMemcpyAsync(C.h_err, C.d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, C.stream));
       CK(cudaStreamSynchronize(C.stream));
+      if (C.h_err[0] != 0) {
+        const int code = C.h_err[0];
+        CK(cudaMemsetAsync(C.d_err, 0, sizeof(int) * 2, C.stream));
+        if (st) st->status = code;
+        return fail(code, "a bounded device-side wait expired during the V-cycle");
+      }
       double* Hj = &H[(size_t)j * (m + 1)];  // column j, length m+1
       for (int i = 0; i <= j; ++i) Hj[i] = hh[i] + hh[64 + i];
       const double hn = std::sqrt(hh[128]);
@@ -489,6 +500,9 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
   if (o->maxit < 1) return fail(IRKMG_EINVAL, "maxit >= 1");
   if (o->patch_precision != 64 && o->patch_precision != 32)
     return fail(IRKMG_EINVAL, "patch_precision is 64 or 32");
+  if (o->apply_variant != 0 && o->apply_variant != 1)
+    return fail(IRKMG_EINVAL, "apply_variant is 0 or 1");
+  if (o->timeout_spins < 0) return fail(IRKMG_EINVAL, "timeout_spins >= 0");
   return IRKMG_OK;
 }
 
@@ -560,6 +574,7 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   if ((rc = dalloc(*C, &C->d_part, (size_t)kMultidotBlocks * 64))) return rc;
   if ((rc = dalloc(*C, &C->d_h, 512))) return rc;
   CK(cudaMallocHost(&C->h_h, sizeof(double) * 512));
+  CK(cudaMallocHost(&C->h_err, sizeof(int) * 2));
   if ((rc = factor_all(*C))) return rc;
   (void)t0;
   return IRKMG_OK;
@@ -654,6 +669,7 @@ void irkmg_default_options(irkmg_options* o) {
   o->wind = nullptr;
   o->cuda_stream = nullptr;
   o->timeout_spins = 0;
+  o->apply_variant = 0;
 }
 
 int irkmg_radau_iia(int s, double* A, double* b, double* c) {
@@ -843,6 +859,7 @@ int irkmg_trace_enable(irkmg_ctx* C, int on) {
   C->ev_used = 0;
   C->ev_class.clear();
   C->ev_bytes.clear();
+  C->ev_flops.clear();
   return IRKMG_OK;
 }
 
@@ -858,6 +875,7 @@ int irkmg_trace_read(irkmg_ctx* C, irkmg_trace* out) {
       out->vanka_launches++;
       out->vanka_ms += ms;
       out->vanka_bytes += C->ev_bytes[k];
+      out->vanka_flops += C->ev_flops[k];
     } else {
       out->op_launches++;
       out->op_ms += ms;
@@ -867,6 +885,7 @@ int irkmg_trace_read(irkmg_ctx* C, irkmg_trace* out) {
   C->ev_used = 0;
   C->ev_class.clear();
   C->ev_bytes.clear();
+  C->ev_flops.clear();
   return IRKMG_OK;
 }
 
@@ -877,6 +896,7 @@ void irkmg_destroy(irkmg_ctx* C) {
   for (cudaEvent_t e : C->ev) cudaEventDestroy(e);
   for (void* p : C->allocs) cudaFree(p);
   if (C->h_h) cudaFreeHost(C->h_h);
+  if (C->h_err) cudaFreeHost(C->h_err);
   delete C;
 }
 

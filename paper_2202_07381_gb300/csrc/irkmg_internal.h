@@ -97,7 +97,7 @@ struct Level {
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
   // algorithmic bytes for tracing
-  std::vector<double> colour_bytes;
+  std::vector<double> colour_bytes, colour_flops;
   double op_bytes = 0.0;
 };
 
@@ -120,12 +120,13 @@ struct Ctx {
   int restart_alloc = 0;
   int* d_err = nullptr;   // device error word: [0] status, [1] index
   int64_t dev_bytes = 0;
+  int* h_err = nullptr;    // pinned mirror of d_err
   // tracing
   int64_t launches = 0;
   bool trace_on = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;       // 0 vanka, 1 operator (one per event pair)
-  std::vector<double> ev_bytes;
+  std::vector<double> ev_bytes, ev_flops;
   size_t ev_used = 0;
 };
 

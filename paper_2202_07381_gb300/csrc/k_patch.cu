@@ -492,6 +492,195 @@ __global__ void __launch_bounds__(kApplyWarps * 32) k_vanka_apply_t(ApplyParams 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-staged Vanka apply (persistent over the patches of one colour).
+// One CTA of kStagedThreads threads works on one patch at a time (thread i owns
+// row i, and row i + kStagedThreads when n_p > kStagedThreads).  Each patch
+// inverse is one contiguous 16-byte-aligned block, streamed into a ring of
+// shared-memory stages by the TMA unit (cp.async.bulk, completion on an
+// mbarrier); while the CTA computes patch k from shared memory the copies of
+// the next stages are in flight, and their residual entries are gathered by
+// plain loads.  Every mbarrier wait is bounded: on expiry the CTA records
+// IRKMG_ETIMEOUT, waits (bounded) for its own copies still in flight, and
+// returns.
+// ---------------------------------------------------------------------------
+constexpr int kStagedThreads = 256;
+constexpr int kMaxStages = 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bounded wait on a stage barrier; false if the bound expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t spins) {
+  for (int64_t k = 0; k < spins; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+struct StagedParams {
+  ApplyParams a;
+  int stages;
+  uint32_t stage_bytes;
+  int64_t spins;
+  int* err;
+};
+
+// Thread t works on row (t mod 128) [and that row + 128 when n_p > 128] over
+// column half (t / 128); the two halves are added through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kStagedThreads) k_vanka_apply_staged(StagedParams S, const T* __restrict__ fac) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ __align__(8) uint64_t bar[kMaxStages];
+  __shared__ T s_r[kMaxStages][kMaxNp];
+  __shared__ int32_t s_g[kMaxStages][kMaxNp];
+  __shared__ T s_part[2][128];
+  __shared__ int s_np[kMaxStages];
+  __shared__ int s_abort;
+  const ApplyParams& P = S.a;
+  const int tid = threadIdx.x;
+  const int row = tid & 127, half = tid >> 7;
+  const int64_t nmine = (P.count > blockIdx.x) ? (P.count - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (tid == 0) {
+    for (int st = 0; st < S.stages; ++st) mbar_init(&bar[st], 1);
+    s_abort = 0;
+  }
+  fence_proxy_async();
+  __syncthreads();
+
+  // Issue the copy of this CTA's k-th patch into stage st and gather its
+  // residual entries and target indices.
+  auto load = [&](int64_t k, int st) {
+    const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+    const int32_t v = P.order[pi];
+    const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+    const int q = 2 * L + 1, np = P.s * q;
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)(((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15);
+      mbar_expect_tx(&bar[st], bytes);
+      bulk_g2s(dyn + (size_t)st * S.stage_bytes, fac + P.fac_off[pi], bytes, &bar[st]);
+      s_np[st] = np;
+    }
+    for (int i = tid; i < np; i += kStagedThreads) {
+      const int t = i / q, kk = i - t * q;
+      int64_t g;
+      if (kk < L)
+        g = t * P.m + P.patch_nodes[nb + kk];
+      else if (kk < 2 * L)
+        g = t * P.m + P.nf + P.patch_nodes[nb + kk - L];
+      else
+        g = t * P.m + 2 * P.nf + v;
+      s_g[st][i] = (int32_t)g;
+      s_r[st][i] = (T)P.r[g];
+    }
+  };
+
+  const int64_t pre = nmine < S.stages ? nmine : S.stages;
+  for (int64_t k = 0; k < pre; ++k) load(k, (int)k);
+  __syncthreads();
+
+  for (int64_t k = 0; k < nmine; ++k) {
+    const int st = (int)(k % S.stages);
+    const uint32_t parity = (uint32_t)((k / S.stages) & 1);
+    if (!mbar_wait_bounded(&bar[st], parity, S.spins)) {
+      s_abort = 1;
+      atomicCAS(&S.err[0], 0, IRKMG_ETIMEOUT);
+    }
+    __syncthreads();
+    if (s_abort) {
+      // wait (bounded) for every copy this CTA still has in flight, then leave
+      for (int64_t j = k; j < nmine && j < k + S.stages; ++j)
+        mbar_wait_bounded(&bar[j % S.stages], (uint32_t)((j / S.stages) & 1), S.spins);
+      return;
+    }
+    const int np = s_np[st];
+    const T* X = reinterpret_cast<const T*>(dyn + (size_t)st * S.stage_bytes);
+    const T* rr = s_r[st];
+    const int jb = half ? (np >> 1) : 0, je = half ? np : (np >> 1);
+    const int r1 = row + 128;
+    T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;
+    if (r1 < np) {
+      int j = jb;
+      for (; j + 1 < je; j += 2) {
+        const T x0 = rr[j], x1 = rr[j + 1];
+        a0 = fma(X[j * np + row], x0, a0);
+        b0 = fma(X[(j + 1) * np + row], x1, b0);
+        a1 = fma(X[j * np + r1], x0, a1);
+        b1 = fma(X[(j + 1) * np + r1], x1, b1);
+      }
+      if (j < je) {
+        a0 = fma(X[j * np + row], rr[j], a0);
+        a1 = fma(X[j * np + r1], rr[j], a1);
+      }
+    } else if (row < np) {
+      int j = jb;
+#pragma unroll 4
+      for (; j + 1 < je; j += 2) {
+        a0 = fma(X[j * np + row], rr[j], a0);
+        b0 = fma(X[(j + 1) * np + row], rr[j + 1], b0);
+      }
+      if (j < je) a0 = fma(X[j * np + row], rr[j], a0);
+    }
+    if (half) {
+      s_part[0][row] = a0 + b0;
+      s_part[1][row] = a1 + b1;
+    }
+    __syncthreads();
+    if (!half) {
+      if (row < np) P.out[s_g[st][row]] += P.scale * (double)(a0 + b0 + s_part[0][row]);
+      if (r1 < np) P.out[s_g[st][r1]] += P.scale * (double)(a1 + b1 + s_part[1][row]);
+    }
+    fence_proxy_async();
+    __syncthreads();  // stage st and s_part fully consumed
+    if (k + S.stages < nmine) load(k + S.stages, st);
+  }
+}
+
+// Returns false when the staged kernel cannot hold two stages of this level.
+bool staged_config(int max_np, int prec, int* stages, uint32_t* stage_bytes) {
+  const size_t w = prec == 64 ? 8 : 4;
+  const size_t static_b = kMaxStages * (kMaxNp * (w + 4) + 16) + 2 * 128 * w + 64;
+  const size_t limit = 227 * 1024 - static_b;
+  size_t sb = ((size_t)max_np * max_np * w + 127) & ~(size_t)127;
+  int st = (int)(limit / sb);
+  if (st > kMaxStages) st = kMaxStages;
+  if (st < 2 || max_np > kMaxNp) return false;
+  *stages = st;
+  *stage_bytes = (uint32_t)sb;
+  return true;
+}
+
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose) {
   ApplyParams P;
@@ -508,8 +697,33 @@ cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* 
   P.first = L.colour_start[colour];
   P.count = L.colour_start[colour + 1] - P.first;
   if (P.count <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((P.count + kApplyWarps - 1) / kApplyWarps);
   const int prec = C.opt.patch_precision;
+  int stages = 0;
+  uint32_t stage_bytes = 0;
+  if (!transpose && C.opt.apply_variant == 0 &&
+      staged_config(L.max_np, prec, &stages, &stage_bytes)) {
+    StagedParams S;
+    S.a = P;
+    S.stages = stages;
+    S.stage_bytes = stage_bytes;
+    S.spins = C.opt.timeout_spins > 0 ? C.opt.timeout_spins : (int64_t)1 << 26;
+    S.err = C.d_err;
+    const int64_t ctas = P.count < 152 ? P.count : 152;
+    const size_t smem = (size_t)stages * stage_bytes;
+    if (prec == 64) {
+      cudaFuncSetAttribute(k_vanka_apply_staged<double>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_vanka_apply_staged<double><<<(unsigned)ctas, kStagedThreads, smem, C.stream>>>(
+          S, (const double*)L.d_fac);
+    } else {
+      cudaFuncSetAttribute(k_vanka_apply_staged<float>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_vanka_apply_staged<float><<<(unsigned)ctas, kStagedThreads, smem, C.stream>>>(
+          S, (const float*)L.d_fac);
+    }
+    return cudaGetLastError();
+  }
+  const unsigned grid = (unsigned)((P.count + kApplyWarps - 1) / kApplyWarps);
   if (transpose) {
     if (prec == 64)
       k_vanka_apply_t<double><<<grid, kApplyWarps * 32, 0, C.stream>>>(P, (const double*)L.d_fac);

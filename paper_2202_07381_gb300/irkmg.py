@@ -39,7 +39,7 @@ class Options(ct.Structure):
                 ("cheb_hi", ct.c_double), ("rtol", ct.c_double), ("atol", ct.c_double),
                 ("restart", ct.c_int), ("maxit", ct.c_int), ("patch_precision", ct.c_int),
                 ("wind", ct.POINTER(ct.c_double)), ("cuda_stream", ct.c_void_p),
-                ("timeout_spins", ct.c_int64)]
+                ("timeout_spins", ct.c_int64), ("apply_variant", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -62,7 +62,7 @@ class LevelInfo(ct.Structure):
 class Trace(ct.Structure):
     _fields_ = [("launches", ct.c_int64), ("vanka_launches", ct.c_int64), ("vanka_ms", ct.c_double),
                 ("vanka_bytes", ct.c_double), ("op_launches", ct.c_int64), ("op_ms", ct.c_double),
-                ("op_bytes", ct.c_double)]
+                ("op_bytes", ct.c_double), ("vanka_flops", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
