@@ -93,8 +93,9 @@ typedef struct {
   const double *wind;      /* host, finest-level Oseen wind at every P2 node,
                               np2·2 doubles (x, y per node), or NULL for Stokes     */
   void *cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream  */
-  int64_t timeout_spins;   /* bound on polls of one device-side wait (0 = 2^26); an
-                              expired wait makes the call return IRKMG_ETIMEOUT     */
+  int64_t timeout_spins;   /* bound on polls of one device-side wait (0 = 2^26; each
+                              wait also gives up after 2 s); an expired wait makes
+                              FGMRES return IRKMG_ETIMEOUT                          */
   int apply_variant;       /* Vanka apply kernel: 0 = TMA-staged (patch inverses
                               streamed to shared memory by cp.async.bulk) when two
                               stages fit, else 1; 1 = warp-per-patch mat-vec        */

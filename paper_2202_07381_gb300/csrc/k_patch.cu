@@ -542,10 +542,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// Bounded wait on a stage barrier; false if the bound expired.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on a stage barrier: at most `spins` polls and at most 2 s of
+// wall time; false if either bound expired.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t spins) {
-  for (int64_t k = 0; k < spins; ++k)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int64_t k = 0; k < spins; ++k) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((k & 255) == 255 && global_ns() - t0 > 2000000000ull) return false;
+  }
   return false;
 }
 
