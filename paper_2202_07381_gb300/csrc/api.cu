@@ -215,21 +215,26 @@ int build_patches(Ctx& C, Level& L) {
     for (int64_t v = 0; v < L.nv; ++v) order[fill[L.h_colour[v]]++] = (int32_t)v;
   }
   L.colour_start = start;
+  // Each ordered patch owns one 16-byte-aligned block: its n_p x n_p inverse
+  // (column-major, padded to 16 bytes) followed by its n_p global DoF indices
+  // (int32, padded to 16 bytes), so one bulk copy brings both.
   std::vector<int64_t> off(L.nv + 1, 0);
+  std::vector<int32_t> npv(L.nv);
   L.max_np = 0;
+  const int64_t w = C.opt.patch_precision == 64 ? 8 : 4;
   for (int64_t i = 0; i < L.nv; ++i) {
     const int32_t v = order[i];
     const int64_t np = (int64_t)C.s * (2 * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
     L.max_np = std::max<int>(L.max_np, (int)np);
-    // keep every patch inverse 16-byte aligned
-    const int64_t elems = np * np;
-    const int64_t align = (C.opt.patch_precision == 64) ? 2 : 4;
-    off[i + 1] = off[i] + (elems + align - 1) / align * align;
+    npv[i] = (int32_t)np;
+    const int64_t xbytes = (np * np * w + 15) / 16 * 16, gbytes = (np * 4 + 15) / 16 * 16;
+    off[i + 1] = off[i] + (xbytes + gbytes) / w;
   }
   if (L.max_np > 160)
     return fail(IRKMG_ENOTIMPL, "patches above 160 DoFs need the blocked patch factorisation");
   L.fac_elems = off[L.nv];
   if ((rc = upload(C, &L.d_order, order))) return rc;
+  if ((rc = upload(C, &L.d_np, npv))) return rc;
   off.pop_back();
   if ((rc = upload(C, &L.d_fac_off, off))) return rc;
   const size_t esz = C.opt.patch_precision == 64 ? 8 : 4;
@@ -242,6 +247,7 @@ int build_patches(Ctx& C, Level& L) {
   C.allocs.push_back(fac);
   C.dev_bytes += esz * L.fac_elems;
   L.d_fac = fac;
+  CK(launch_patch_gidx(C, L));
   return IRKMG_OK;
 }
 

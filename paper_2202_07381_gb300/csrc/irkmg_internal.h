@@ -90,7 +90,8 @@ struct Level {
   int ncolours = 0;
   std::vector<int64_t> colour_start;   // into the colour-ordered patch list
   int32_t* d_order = nullptr;          // patches sorted by (colour, id)
-  int64_t* d_fac_off = nullptr;        // element offset of each ordered patch's inverse
+  int64_t* d_fac_off = nullptr;        // element offset of each ordered patch's block
+  int32_t* d_np = nullptr;             // n_p of each ordered patch
   void* d_fac = nullptr;
   int64_t fac_elems = 0;
   int max_np = 0;
@@ -138,6 +139,7 @@ cudaError_t launch_compact_patches(Level& L, cudaStream_t st, int maxnodes, cons
 cudaError_t launch_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
 cudaError_t launch_colour_round(Level& L, cudaStream_t st, int* d_remaining, int* d_overflow);
 cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision);
+cudaError_t launch_patch_gidx(Ctx& C, Level& L);
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose);
 cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, double* r,

@@ -9,6 +9,7 @@
 //     explicit inverse by Gauss–Jordan elimination with partial pivoting;
 //   * the additive correction  out += scale · R_vᵀ A_v⁻¹ R_v r, one launch per
 //     colour, so the scatter needs no atomics and is deterministic.
+#include <algorithm>
 #include <cfloat>
 #include <cstdio>
 
@@ -388,6 +389,47 @@ cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
   return cudaGetLastError();
 }
 
+// Global DoF index list of every ordered patch, stored after its inverse.
+template <typename T>
+__global__ void k_patch_gidx(int s, int64_t nf, int64_t m, int64_t npatch,
+                             const int32_t* __restrict__ patch_ptr,
+                             const int32_t* __restrict__ patch_nodes,
+                             const int32_t* __restrict__ order, const int64_t* __restrict__ fac_off,
+                             T* fac) {
+  const int64_t pi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (pi >= npatch) return;
+  const int32_t v = order[pi];
+  const int32_t nb = patch_ptr[v], L = patch_ptr[v + 1] - nb;
+  const int q = 2 * L + 1, np = s * q;
+  const int64_t xbytes = ((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15;
+  int32_t* g = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(fac + fac_off[pi]) + xbytes);
+  for (int i = lane; i < np; i += 32) {
+    const int t = i / q, k = i - t * q;
+    int64_t gi;
+    if (k < L)
+      gi = t * m + patch_nodes[nb + k];
+    else if (k < 2 * L)
+      gi = t * m + nf + patch_nodes[nb + k - L];
+    else
+      gi = t * m + 2 * nf + v;
+    g[i] = (int32_t)gi;
+  }
+}
+
+cudaError_t launch_patch_gidx(Ctx& C, Level& L) {
+  const unsigned grid = (unsigned)((L.nv * 32 + 255) / 256);
+  if (C.opt.patch_precision == 64)
+    k_patch_gidx<double><<<grid, 256, 0, C.stream>>>(C.s, L.nf, L.m, L.nv, L.d_patch_ptr,
+                                                     L.d_patch_nodes, L.d_order, L.d_fac_off,
+                                                     (double*)L.d_fac);
+  else
+    k_patch_gidx<float><<<grid, 256, 0, C.stream>>>(C.s, L.nf, L.m, L.nv, L.d_patch_ptr,
+                                                    L.d_patch_nodes, L.d_order, L.d_fac_off,
+                                                    (float*)L.d_fac);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Vanka apply for one colour: warp per patch.  y = A_v⁻¹ r|_{S_v} as a dense
 // column-major mat-vec (lanes over rows, one column per step, fully coalesced
@@ -401,7 +443,7 @@ constexpr int kMaxNp = 160;
 struct ApplyParams {
   int s;
   int64_t nf, m;
-  const int32_t *patch_ptr, *patch_nodes, *order;
+  const int32_t *patch_ptr, *patch_nodes, *order, *np;
   const int64_t* fac_off;
   const double* r;
   double* out;
@@ -562,23 +604,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 struct StagedParams {
   ApplyParams a;
   int stages;
-  uint32_t stage_bytes;
+  uint32_t stage_bytes;  // bytes per stage (largest patch block, rounded to 128)
+  uint32_t rpart_off;    // offset of the gathered residual / partial sums in dynamic smem
   int64_t spins;
   int* err;
 };
 
-// Thread t works on row (t mod 128) [and that row + 128 when n_p > 128] over
-// column half (t / 128); the two halves are added through shared memory.
+// One CTA works on one patch at a time.  Thread t owns row (t mod 128) [and
+// that row + 128 when n_p > 128] over column half (t / 128); the halves are
+// added through shared memory.  The patch block (inverse + index list) arrives
+// by one bulk copy; the residual entries are gathered through the index list.
 template <typename T>
 __global__ void __launch_bounds__(kStagedThreads) k_vanka_apply_staged(StagedParams S, const T* __restrict__ fac) {
   extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ __align__(8) uint64_t bar[kMaxStages];
-  __shared__ T s_r[kMaxStages][kMaxNp];
-  __shared__ int32_t s_g[kMaxStages][kMaxNp];
-  __shared__ T s_part[2][128];
-  __shared__ int s_np[kMaxStages];
   __shared__ int s_abort;
   const ApplyParams& P = S.a;
+  T* s_r = reinterpret_cast<T*>(dyn + S.rpart_off);
+  T* s_part = s_r + kMaxNp;  // [2][128]
   const int tid = threadIdx.x;
   const int row = tid & 127, half = tid >> 7;
   const int64_t nmine = (P.count > blockIdx.x) ? (P.count - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -589,40 +632,27 @@ __global__ void __launch_bounds__(kStagedThreads) k_vanka_apply_staged(StagedPar
   fence_proxy_async();
   __syncthreads();
 
-  // Issue the copy of this CTA's k-th patch into stage st and gather its
-  // residual entries and target indices.
-  auto load = [&](int64_t k, int st) {
-    const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
-    const int32_t v = P.order[pi];
-    const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
-    const int q = 2 * L + 1, np = P.s * q;
-    if (tid == 0) {
-      const uint32_t bytes = (uint32_t)(((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15);
-      mbar_expect_tx(&bar[st], bytes);
-      bulk_g2s(dyn + (size_t)st * S.stage_bytes, fac + P.fac_off[pi], bytes, &bar[st]);
-      s_np[st] = np;
-    }
-    for (int i = tid; i < np; i += kStagedThreads) {
-      const int t = i / q, kk = i - t * q;
-      int64_t g;
-      if (kk < L)
-        g = t * P.m + P.patch_nodes[nb + kk];
-      else if (kk < 2 * L)
-        g = t * P.m + P.nf + P.patch_nodes[nb + kk - L];
-      else
-        g = t * P.m + 2 * P.nf + v;
-      s_g[st][i] = (int32_t)g;
-      s_r[st][i] = (T)P.r[g];
-    }
+  auto block_bytes = [](int np) -> uint32_t {
+    return (uint32_t)((((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15) +
+                      (((int64_t)np * 4 + 15) & ~(int64_t)15));
   };
-
-  const int64_t pre = nmine < S.stages ? nmine : S.stages;
-  for (int64_t k = 0; k < pre; ++k) load(k, (int)k);
-  __syncthreads();
+  // thread 0: start the bulk copy of this CTA's k-th patch block into stage st
+  auto issue = [&](int64_t k, int st) {
+    const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+    const uint32_t bytes = block_bytes(P.np[pi]);
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_g2s(dyn + (size_t)st * S.stage_bytes, fac + P.fac_off[pi], bytes, &bar[st]);
+  };
+  if (tid == 0) {
+    const int64_t pre = nmine < S.stages ? nmine : S.stages;
+    for (int64_t k = 0; k < pre; ++k) issue(k, (int)k);
+  }
 
   for (int64_t k = 0; k < nmine; ++k) {
     const int st = (int)(k % S.stages);
     const uint32_t parity = (uint32_t)((k / S.stages) & 1);
+    const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+    const int np = P.np[pi];
     if (!mbar_wait_bounded(&bar[st], parity, S.spins)) {
       s_abort = 1;
       atomicCAS(&S.err[0], 0, IRKMG_ETIMEOUT);
@@ -634,61 +664,82 @@ __global__ void __launch_bounds__(kStagedThreads) k_vanka_apply_staged(StagedPar
         mbar_wait_bounded(&bar[j % S.stages], (uint32_t)((j / S.stages) & 1), S.spins);
       return;
     }
-    const int np = s_np[st];
-    const T* X = reinterpret_cast<const T*>(dyn + (size_t)st * S.stage_bytes);
-    const T* rr = s_r[st];
+    const unsigned char* stage = dyn + (size_t)st * S.stage_bytes;
+    const T* X = reinterpret_cast<const T*>(stage);
+    const int32_t* G = reinterpret_cast<const int32_t*>(
+        stage + (((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15));
+    for (int i = tid; i < np; i += kStagedThreads) s_r[i] = (T)P.r[G[i]];
+    __syncthreads();
     const int jb = half ? (np >> 1) : 0, je = half ? np : (np >> 1);
     const int r1 = row + 128;
     T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;
     if (r1 < np) {
       int j = jb;
       for (; j + 1 < je; j += 2) {
-        const T x0 = rr[j], x1 = rr[j + 1];
+        const T x0 = s_r[j], x1 = s_r[j + 1];
         a0 = fma(X[j * np + row], x0, a0);
         b0 = fma(X[(j + 1) * np + row], x1, b0);
         a1 = fma(X[j * np + r1], x0, a1);
         b1 = fma(X[(j + 1) * np + r1], x1, b1);
       }
       if (j < je) {
-        a0 = fma(X[j * np + row], rr[j], a0);
-        a1 = fma(X[j * np + r1], rr[j], a1);
+        a0 = fma(X[j * np + row], s_r[j], a0);
+        a1 = fma(X[j * np + r1], s_r[j], a1);
       }
     } else if (row < np) {
       int j = jb;
 #pragma unroll 4
       for (; j + 1 < je; j += 2) {
-        a0 = fma(X[j * np + row], rr[j], a0);
-        b0 = fma(X[(j + 1) * np + row], rr[j + 1], b0);
+        a0 = fma(X[j * np + row], s_r[j], a0);
+        b0 = fma(X[(j + 1) * np + row], s_r[j + 1], b0);
       }
-      if (j < je) a0 = fma(X[j * np + row], rr[j], a0);
+      if (j < je) a0 = fma(X[j * np + row], s_r[j], a0);
     }
     if (half) {
-      s_part[0][row] = a0 + b0;
-      s_part[1][row] = a1 + b1;
+      s_part[row] = a0 + b0;
+      if (r1 < np) s_part[128 + row] = a1 + b1;
     }
     __syncthreads();
     if (!half) {
-      if (row < np) P.out[s_g[st][row]] += P.scale * (double)(a0 + b0 + s_part[0][row]);
-      if (r1 < np) P.out[s_g[st][r1]] += P.scale * (double)(a1 + b1 + s_part[1][row]);
+      if (row < np) P.out[G[row]] += P.scale * (double)(a0 + b0 + s_part[row]);
+      if (r1 < np) P.out[G[r1]] += P.scale * (double)(a1 + b1 + s_part[128 + row]);
     }
     fence_proxy_async();
-    __syncthreads();  // stage st and s_part fully consumed
-    if (k + S.stages < nmine) load(k + S.stages, st);
+    __syncthreads();  // stage st, s_r and s_part fully consumed
+    if (tid == 0 && k + S.stages < nmine) issue(k + S.stages, st);
   }
 }
 
-// Returns false when the staged kernel cannot hold two stages of this level.
-bool staged_config(int max_np, int prec, int* stages, uint32_t* stage_bytes) {
+// Launch shape of the staged apply for a level: two CTAs per SM when one
+// stage each fits, else one CTA with two or more stages; false when neither
+// fits (the warp-per-patch kernel is used then).
+struct StagedShape {
+  int stages, ctas_per_sm;
+  uint32_t stage_bytes, rpart_off, dyn_bytes;
+};
+bool staged_config(int max_np, int prec, StagedShape* out) {
+  if (max_np > kMaxNp) return false;
   const size_t w = prec == 64 ? 8 : 4;
-  const size_t static_b = kMaxStages * (kMaxNp * (w + 4) + 16) + 2 * 128 * w + 64;
-  const size_t limit = 227 * 1024 - static_b;
-  size_t sb = ((size_t)max_np * max_np * w + 127) & ~(size_t)127;
-  int st = (int)(limit / sb);
-  if (st > kMaxStages) st = kMaxStages;
-  if (st < 2 || max_np > kMaxNp) return false;
-  *stages = st;
-  *stage_bytes = (uint32_t)sb;
-  return true;
+  const size_t blk = ((((size_t)max_np * max_np * w + 15) & ~(size_t)15) +
+                      (((size_t)max_np * 4 + 15) & ~(size_t)15));
+  const size_t sb = (blk + 127) & ~(size_t)127;
+  const size_t extra = (kMaxNp + 256) * w;  // gathered residual + partial sums
+  const size_t static_b = 128;  // barriers + abort flag (ptxas: 128 bytes)
+  const size_t per_sm = 233472, reserved = 1024, per_block = 232448;
+  for (int ctas = 2; ctas >= 1; --ctas) {
+    const size_t budget = std::min(per_sm / ctas - reserved, per_block) - static_b - extra;
+    int st = (int)(budget / sb);
+    if (st > kMaxStages) st = kMaxStages;
+    if (st >= (ctas == 2 ? 1 : 2)) {
+      out->stages = st;
+      out->ctas_per_sm = ctas;
+      out->stage_bytes = (uint32_t)sb;
+      out->rpart_off = (uint32_t)(st * sb);
+      out->dyn_bytes = (uint32_t)(st * sb + extra);
+      return true;
+    }
+  }
+  return false;
 }
 
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
@@ -700,6 +751,7 @@ cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* 
   P.patch_ptr = L.d_patch_ptr;
   P.patch_nodes = L.d_patch_nodes;
   P.order = L.d_order;
+  P.np = L.d_np;
   P.fac_off = L.d_fac_off;
   P.r = r;
   P.out = out;
@@ -708,18 +760,18 @@ cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* 
   P.count = L.colour_start[colour + 1] - P.first;
   if (P.count <= 0) return cudaSuccess;
   const int prec = C.opt.patch_precision;
-  int stages = 0;
-  uint32_t stage_bytes = 0;
-  if (!transpose && C.opt.apply_variant == 0 &&
-      staged_config(L.max_np, prec, &stages, &stage_bytes)) {
+  StagedShape shp;
+  if (!transpose && C.opt.apply_variant == 0 && staged_config(L.max_np, prec, &shp)) {
     StagedParams S;
     S.a = P;
-    S.stages = stages;
-    S.stage_bytes = stage_bytes;
+    S.stages = shp.stages;
+    S.stage_bytes = shp.stage_bytes;
+    S.rpart_off = shp.rpart_off;
     S.spins = C.opt.timeout_spins > 0 ? C.opt.timeout_spins : (int64_t)1 << 26;
     S.err = C.d_err;
-    const int64_t ctas = P.count < 152 ? P.count : 152;
-    const size_t smem = (size_t)stages * stage_bytes;
+    const int64_t cap = 152 * shp.ctas_per_sm;
+    const int64_t ctas = P.count < cap ? P.count : cap;
+    const size_t smem = shp.dyn_bytes;
     if (prec == 64) {
       cudaFuncSetAttribute(k_vanka_apply_staged<double>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
