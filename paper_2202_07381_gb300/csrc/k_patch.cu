@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kApplyWarps * 32) k_vanka_apply(ApplyParams P,
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int i = lane + 32 * k;
-      if (i < np) y[k] = fma(col[i], rj, y[k]);
+      if (i < np) y[k] = fma(__ldcs(col + i), rj, y[k]);  // read once: evict-first
     }
   }
 #pragma unroll
@@ -572,11 +572,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// L2 policy for data read exactly once per sweep (the patch inverses): evict
+// first, so the stream does not push the residual and target vectors out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t pol) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], "
+      "%2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
 }
 // Orders this thread's earlier generic-proxy shared-memory accesses before
@@ -636,12 +644,13 @@ __global__ void __launch_bounds__(kStagedThreads) k_vanka_apply_staged(StagedPar
     return (uint32_t)((((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15) +
                       (((int64_t)np * 4 + 15) & ~(int64_t)15));
   };
+  const uint64_t pol = l2_evict_first_policy();
   // thread 0: start the bulk copy of this CTA's k-th patch block into stage st
   auto issue = [&](int64_t k, int st) {
     const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
     const uint32_t bytes = block_bytes(P.np[pi]);
     mbar_expect_tx(&bar[st], bytes);
-    bulk_g2s(dyn + (size_t)st * S.stage_bytes, fac + P.fac_off[pi], bytes, &bar[st]);
+    bulk_g2s(dyn + (size_t)st * S.stage_bytes, fac + P.fac_off[pi], bytes, &bar[st], pol);
   };
   if (tid == 0) {
     const int64_t pre = nmine < S.stages ? nmine : S.stages;
