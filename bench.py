@@ -296,7 +296,7 @@ def run_ours(args, wl, rank, world, local_rank):
         op_gbs = trace["op_bytes"] / (trace["op_ms"] * 1e-3) / 1e9 if trace["op_ms"] else None
         nvl = max(trace["vanka_launches"], 1)
         h = kernel_source_hash()
-        kname = "k_vanka_apply_staged" if args.apply == 0 else "k_vanka_apply"
+        kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply"}[ctx.finest["apply_kernel"]]
         traffic = NCU_TRAFFIC.get(h)
         value = ms * 1e-3 / (args.steps * world)
         van_tf = trace["vanka_flops"] / (trace["vanka_ms"] * 1e-3) / 1e12 if trace["vanka_ms"] else None
@@ -324,6 +324,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "config": {"workload": wl["name"], "N": N, "patches_finest": ctx.finest["nv"],
                        "patch_precision": prec, "smoother": "Chebyshev[2,8] V(2,2)",
                        "fgmres_restart": 30, "rtol": 1e-10,
+                       "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
                              % (ctx.finest["factor_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -353,8 +354,8 @@ def main():
     ap.add_argument("--small", action="store_true", help="8x8 mesh (quick check)")
     ap.add_argument("--n", type=int, default=512, help="finest mesh n x n (8 * 2^k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--apply", type=int, default=0, choices=[0, 1],
-                    help="Vanka apply kernel: 0 TMA-staged, 1 warp-per-patch")
+    ap.add_argument("--apply", type=int, default=0, choices=[0, 1, 2],
+                    help="Vanka apply kernel: 0 autotuned per level, 1 TMA-staged, 2 warp-per-patch")
     args = ap.parse_args()
     wl = workload(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))

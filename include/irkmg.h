@@ -96,9 +96,11 @@ typedef struct {
   int64_t timeout_spins;   /* bound on polls of one device-side wait (0 = 2^26; each
                               wait also gives up after 2 s); an expired wait makes
                               FGMRES return IRKMG_ETIMEOUT                          */
-  int apply_variant;       /* Vanka apply kernel: 0 = TMA-staged (patch inverses
-                              streamed to shared memory by cp.async.bulk) when two
-                              stages fit, else 1; 1 = warp-per-patch mat-vec        */
+  int apply_variant;       /* Vanka apply kernel per level: 0 = autotuned at set-up
+                              (both kernels timed once per level, the faster kept);
+                              1 = TMA-staged (patch blocks streamed to shared memory
+                              by cp.async.bulk) wherever it fits; 2 = warp-per-patch
+                              mat-vec everywhere                                    */
 } irkmg_options;
 
 typedef struct {
@@ -115,7 +117,9 @@ typedef struct {
   int64_t m, N;            /* per-stage length 2 nf + nv, full length s·m           */
   int64_t npatch, ncolours;/* Vanka patches (one per vertex), colours               */
   int64_t max_patch_dofs;  /* largest patch size s·(2·nodes + 1)                    */
-  int64_t factor_bytes;    /* bytes of stored patch inverses on this level          */
+  int64_t factor_bytes;    /* bytes of stored patch blocks (inverse + index list)   */
+  int64_t apply_kernel;    /* Vanka apply kernel in use: 1 TMA-staged, 2 warp-per-patch */
+  double apply_ms[2];      /* autotuner: one sweep with kernel 1 / kernel 2 (0 if untimed) */
 } irkmg_level_info;
 
 /* ---- set-up -------------------------------------------------------------- */

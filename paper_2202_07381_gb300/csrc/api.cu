@@ -284,6 +284,57 @@ int factor_all(Ctx& C) {
   return check_err(C, "factorisation");
 }
 
+int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr);
+
+// Choose the Vanka apply kernel of every level: the option forces one, or
+// (apply_variant 0) both are timed on one sweep of the level (after a warm-up
+// sweep) with CUDA events on the context stream and the faster is kept.
+int tune_apply(Ctx& C) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  const bool saved = C.trace_on;
+  C.trace_on = false;
+  int rc = IRKMG_OK;
+  for (size_t l = 1; l < C.L.size() && rc == IRKMG_OK; ++l) {
+    Level& L = C.L[l];
+    const bool fits = vanka_staged_fits(C, L);
+    if (C.opt.apply_variant == 1 || C.opt.apply_variant == 2) {
+      L.apply_kernel = (C.opt.apply_variant == 1 && fits) ? 1 : 2;
+      continue;
+    }
+    if (!fits) {
+      L.apply_kernel = 2;
+      continue;
+    }
+    cudaError_t e = cudaMemsetAsync(L.t, 0, sizeof(double) * L.N, C.stream);
+    if (e != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e)); break; }
+    for (int kern = 1; kern <= 2 && rc == IRKMG_OK; ++kern) {
+      L.apply_kernel = kern;
+      float best = 1e30f;
+      for (int rep = 0; rep < 3 && rc == IRKMG_OK; ++rep) {
+        cudaEventRecord(a, C.stream);
+        rc = vanka_all(C, L, L.t, L.d, 1.0, 0);
+        cudaEventRecord(b, C.stream);
+        cudaError_t e2 = cudaEventSynchronize(b);
+        if (e2 != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e2)); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best) best = ms;   // rep 0 is the warm-up
+      }
+      L.apply_ms[kern] = best;
+    }
+    L.apply_kernel = (L.apply_ms[1] <= L.apply_ms[2]) ? 1 : 2;
+  }
+  C.trace_on = saved;
+  C.launches = 0;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(C.stream));
+  return check_err(C, "apply autotuning");
+}
+
 // --- smoothers and V-cycle -------------------------------------------------
 int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr) {
   const bool timed = C.trace_on && &L == &C.L.back();
@@ -506,8 +557,8 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
   if (o->maxit < 1) return fail(IRKMG_EINVAL, "maxit >= 1");
   if (o->patch_precision != 64 && o->patch_precision != 32)
     return fail(IRKMG_EINVAL, "patch_precision is 64 or 32");
-  if (o->apply_variant != 0 && o->apply_variant != 1)
-    return fail(IRKMG_EINVAL, "apply_variant is 0 or 1");
+  if (o->apply_variant < 0 || o->apply_variant > 2)
+    return fail(IRKMG_EINVAL, "apply_variant is 0, 1 or 2");
   if (o->timeout_spins < 0) return fail(IRKMG_EINVAL, "timeout_spins >= 0");
   return IRKMG_OK;
 }
@@ -582,6 +633,7 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   CK(cudaMallocHost(&C->h_h, sizeof(double) * 512));
   CK(cudaMallocHost(&C->h_err, sizeof(int) * 2));
   if ((rc = factor_all(*C))) return rc;
+  if ((rc = tune_apply(*C))) return rc;
   (void)t0;
   return IRKMG_OK;
 }
@@ -735,6 +787,9 @@ int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) 
   info->ncolours = L.ncolours;
   info->max_patch_dofs = L.max_np;
   info->factor_bytes = L.fac_elems * (C->opt.patch_precision == 64 ? 8 : 4);
+  info->apply_kernel = level > 0 ? L.apply_kernel : 0;
+  info->apply_ms[0] = L.apply_ms[1];
+  info->apply_ms[1] = L.apply_ms[2];
   return IRKMG_OK;
 }
 

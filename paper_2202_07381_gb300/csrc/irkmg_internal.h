@@ -95,6 +95,8 @@ struct Level {
   void* d_fac = nullptr;
   int64_t fac_elems = 0;
   int max_np = 0;
+  int apply_kernel = 1;                // 1 staged, 2 warp-per-patch (chosen at set-up)
+  float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
   // algorithmic bytes for tracing
@@ -142,6 +144,7 @@ cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision);
 cudaError_t launch_patch_gidx(Ctx& C, Level& L);
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose);
+bool vanka_staged_fits(Ctx& C, Level& L);
 cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, double* r,
                             int transpose);
 cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coarse);

@@ -751,6 +751,11 @@ bool staged_config(int max_np, int prec, StagedShape* out) {
   return false;
 }
 
+bool vanka_staged_fits(Ctx& C, Level& L) {
+  StagedShape shp;
+  return staged_config(L.max_np, C.opt.patch_precision, &shp);
+}
+
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose) {
   ApplyParams P;
@@ -770,7 +775,7 @@ cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* 
   if (P.count <= 0) return cudaSuccess;
   const int prec = C.opt.patch_precision;
   StagedShape shp;
-  if (!transpose && C.opt.apply_variant == 0 && staged_config(L.max_np, prec, &shp)) {
+  if (!transpose && L.apply_kernel == 1 && staged_config(L.max_np, prec, &shp)) {
     StagedParams S;
     S.a = P;
     S.stages = shp.stages;

@@ -53,10 +53,13 @@ class Stats(ct.Structure):
 
 class LevelInfo(ct.Structure):
     _fields_ = [(k, ct.c_int64) for k in ("nv", "ne", "nc", "np2", "nf", "m", "N", "npatch",
-                                          "ncolours", "max_patch_dofs", "factor_bytes")]
+                                          "ncolours", "max_patch_dofs", "factor_bytes",
+                                          "apply_kernel")] + [("apply_ms", ct.c_double * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "apply_ms"}
+        d["apply_ms"] = list(self.apply_ms)
+        return d
 
 
 class Trace(ct.Structure):

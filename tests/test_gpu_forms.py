@@ -25,3 +25,40 @@ def test_fp32_patches_reach_fp64_solution(n0, nl, s, dt):
     assert rel(H.project_pressure(host(k)), H.project_pressure(x_ref)) < 1e-8
     assert st["iters"] <= its_ref + 3
     ctx.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2], ids=["tma_staged", "warp_per_patch"])
+@pytest.mark.parametrize("n0,nl,s,dt", [(2, 5, 2, 1 / 8), (2, 4, 3, 1 / 64)])
+def test_both_apply_kernels_match_oracle(variant, n0, nl, s, dt):
+    """Each Vanka apply kernel, forced on every level, against the oracle: one
+    correction per level and one V-cycle (1e-12)."""
+    irkmg = need_gpu()
+    import synth
+    H = oracle_hierarchy(n0, nl, s, dt)
+    ctx = gpu_context(irkmg, n0, nl, s, dt, apply_variant=variant)
+    try:
+        for l in range(1, nl):
+            assert ctx.levels[l]["apply_kernel"] == variant
+            L = H.levels[l]
+            r = synth.random_vector(300 + l, L.N)
+            c = dev(np.zeros(L.N))
+            irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l)
+            assert rel(host(c), L.vanka.correction(r)) < 1e-12
+        r = synth.random_vector(399, H.finest.N)
+        z = dev(np.zeros(H.finest.N))
+        irkmg.irkmg_vcycle(ctx, dev(r), z)
+        assert rel(host(z), H.vcycle(r)) < 1e-12
+    finally:
+        ctx.close()
+
+
+def test_autotuner_records_both_timings():
+    irkmg = need_gpu()
+    ctx = gpu_context(irkmg, 2, 5, 2, 1 / 8)
+    try:
+        for lv in ctx.levels[1:]:
+            assert lv["apply_kernel"] in (1, 2)
+            assert all(t > 0 for t in lv["apply_ms"])
+            assert lv["apply_kernel"] == (1 if lv["apply_ms"][0] <= lv["apply_ms"][1] else 2)
+    finally:
+        ctx.close()
