@@ -75,6 +75,63 @@ int upload_csr(Ctx& C, DevCSR& d, const HostCSR& h, int nvals) {
   return IRKMG_OK;
 }
 
+// SELL-32 copy of a host CSR (see DevSELL).
+struct HostSELL {
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> v[3];
+};
+
+HostSELL to_sell(const HostCSR& A, int nvals) {
+  HostSELL S;
+  const int64_t n = A.nrows, ns = (n + 31) / 32;
+  S.ptr.assign(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int32_t w = 0;
+    for (int64_t r = sl * 32; r < std::min(n, sl * 32 + 32); ++r)
+      w = std::max(w, A.ptr[r + 1] - A.ptr[r]);
+    S.ptr[sl + 1] = S.ptr[sl] + 32 * (int64_t)w;
+  }
+  S.col.assign(S.ptr[ns], 0);
+  for (int k = 0; k < nvals; ++k) S.v[k].assign(S.ptr[ns], 0.0);
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t base = S.ptr[r / 32] + r % 32;
+    const int64_t w = (S.ptr[r / 32 + 1] - S.ptr[r / 32]) / 32;
+    const int32_t len = A.ptr[r + 1] - A.ptr[r];
+    const int32_t pad = len > 0 ? A.col[A.ptr[r + 1] - 1] : 0;
+    for (int64_t k = 0; k < w; ++k) {
+      const int64_t dst = base + 32 * k;
+      if (k < len) {
+        S.col[dst] = A.col[A.ptr[r] + k];
+        for (int q = 0; q < nvals; ++q) S.v[q][dst] = A.v[q][A.ptr[r] + k];
+      } else {
+        S.col[dst] = pad;
+      }
+    }
+  }
+  return S;
+}
+
+int upload_sell(Ctx& C, DevSELL& d, const HostCSR& h, int nvals) {
+  HostSELL S = to_sell(h, nvals);
+  d.nrows = (int32_t)h.nrows;
+  d.stored = (int64_t)S.col.size();
+  int rc;
+  if ((rc = upload(C, &d.ptr, S.ptr))) return rc;
+  if ((rc = upload(C, &d.col, S.col))) return rc;
+  for (int k = 0; k < nvals; ++k)
+    if ((rc = upload(C, &d.v[k], S.v[k]))) return rc;
+  return IRKMG_OK;
+}
+
+int refresh_sell_values(Ctx& C, DevSELL& d, const HostCSR& h, int nvals) {
+  (void)C;
+  HostSELL S = to_sell(h, nvals);
+  for (int k = 0; k < nvals; ++k)
+    CK(cudaMemcpy(d.v[k], S.v[k].data(), sizeof(double) * S.v[k].size(), cudaMemcpyHostToDevice));
+  return IRKMG_OK;
+}
+
 int refresh_csr_values(Ctx& C, DevCSR& d, const HostCSR& h, int nvals) {
   (void)C;
   for (int k = 0; k < nvals; ++k)
@@ -602,6 +659,9 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
     if ((rc = upload_csr(*C, L.vel, L.hops.vel, 3))) return rc;
     if ((rc = upload_csr(*C, L.b, L.hops.b, 2))) return rc;
     if ((rc = upload_csr(*C, L.bt, L.hops.bt, 2))) return rc;
+    if ((rc = upload_sell(*C, L.svel, L.hops.vel, 3))) return rc;
+    if ((rc = upload_sell(*C, L.sb, L.hops.b, 2))) return rc;
+    if ((rc = upload_sell(*C, L.sbt, L.hops.bt, 2))) return rc;
     if (l == nl - 1 && (rc = upload_csr(*C, L.mall, L.hops.mall, 1))) return rc;
     if ((rc = dalloc(*C, &L.r, L.N))) return rc;
     if ((rc = dalloc(*C, &L.z, L.N))) return rc;
@@ -768,6 +828,9 @@ int irkmg_update(irkmg_ctx* C, double dt, double nu) {
     if ((rc = refresh_csr_values(*C, L.vel, L.hops.vel, 3))) return rc;
     if ((rc = refresh_csr_values(*C, L.b, L.hops.b, 2))) return rc;
     if ((rc = refresh_csr_values(*C, L.bt, L.hops.bt, 2))) return rc;
+    if ((rc = refresh_sell_values(*C, L.svel, L.hops.vel, 3))) return rc;
+    if ((rc = refresh_sell_values(*C, L.sb, L.hops.b, 2))) return rc;
+    if ((rc = refresh_sell_values(*C, L.sbt, L.hops.bt, 2))) return rc;
     if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.mall, L.hops.mall, 1))) return rc;
   }
   return factor_all(*C);

@@ -73,11 +73,23 @@ struct DevCSR {
   double* v[3] = {nullptr, nullptr, nullptr};
 };
 
+// Sliced ELLPACK with slices of 32 rows: entry k of row r sits at
+// ptr[r/32] + 32 k + r%32 (column-major inside a slice), padded with zero
+// values on the row's own last column, so a warp reads every entry coalesced.
+struct DevSELL {
+  int32_t nrows = 0;
+  int64_t* ptr = nullptr;  // nslices + 1 offsets
+  int32_t* col = nullptr;
+  double* v[3] = {nullptr, nullptr, nullptr};
+  int64_t stored = 0;
+};
+
 struct Level {
   HostMesh mesh;
   int64_t nf = 0, nv = 0, np2 = 0, m = 0, N = 0;
   HostOps hops;
   DevCSR vel, b, bt, mall;
+  DevSELL svel, sb, sbt;  // SELL copies of vel, b and bt for the stage operator
   // transfer from level-1 into this level (l > 0)
   DevCSR pu, put, pp, ppt;
   // topology for patch construction

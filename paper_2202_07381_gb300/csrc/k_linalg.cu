@@ -3,9 +3,10 @@
 //
 //   stage residual (Section 3.1):  r = F - J x,
 //     J = I_s ⊗ [[M,0],[0,0]] + dt A ⊗ [[K,B],[Bᵀ,0]],
-//   evaluated row by row: one pass over the scalar P2 pattern (M and K share
-//   it) and the B / Bᵀ rows gathers every stage and both velocity components
-//   of a neighbour at once, and the s×s stage mixing is applied per row.
+//   evaluated row by row on SELL-32 copies of the operators: one pass over the
+//   scalar P2 pattern (M and K share it) and the B / Bᵀ rows gathers every
+//   stage and both velocity components of a neighbour at once, and the s×s
+//   stage mixing is applied per row.
 //   Jᵀ swaps A for Aᵀ and K for Kᵀ (the B blocks are unchanged).
 //   transfers (Section 4.1): I_s ⊗ diag(P_u, P_u, P_p) and its transpose.
 //   reductions are two-pass with a fixed block count, so sums are bitwise
@@ -16,6 +17,7 @@ namespace irkmg {
 
 struct OpParams {
   int64_t nf, nv, m;
+  int64_t nf_pad;  // velocity rows rounded up to a whole slice (SELL kernel)
   double mix[9];  // dt * A (or dt * Aᵀ), row-major 3x3
   const int32_t *vptr, *vcol;
   const double *M, *K;
@@ -23,22 +25,32 @@ struct OpParams {
   const double *Bx, *By;
   const int32_t *btptr, *btcol;
   const double *BTx, *BTy;
+  // SELL-32 copies
+  const int64_t *svp, *sbp, *sbtp;
+  const int32_t *svc, *sbc, *sbtc;
+  const double *sM, *sK, *sBx, *sBy, *sBTx, *sBTy;
 };
 
+// The stage operator on SELL-32 storage: threads [0, nf_pad) take velocity
+// rows, threads [nf_pad, nf_pad + nv) pressure rows, so every warp maps onto
+// one slice and all matrix reads are coalesced.
 template <int S>
-__global__ void __launch_bounds__(256) k_residual(OpParams P, const double* __restrict__ F,
-                                                  const double* __restrict__ x,
-                                                  double* __restrict__ r) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_residual_sell(OpParams P, const double* __restrict__ F,
+                                                       const double* __restrict__ x,
+                                                       double* __restrict__ r) {
+  const int64_t tidg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nf = P.nf, m = P.m;
-  if (row < nf) {
+  if (tidg < P.nf_pad) {
+    const int64_t row = tidg;
+    if (row >= nf) return;
     double am[S][2], ak[S][2];
 #pragma unroll
     for (int t = 0; t < S; ++t) am[t][0] = am[t][1] = ak[t][0] = ak[t][1] = 0.0;
-    const int32_t p1 = P.vptr[row + 1];
-    for (int32_t p = P.vptr[row]; p < p1; ++p) {
-      const int32_t j = P.vcol[p];
-      const double mv = P.M[p], kv = P.K[p];
+    const int64_t sl = row >> 5, lane = row & 31;
+    const int64_t b0 = P.svp[sl], b1 = P.svp[sl + 1];
+    for (int64_t e = b0 + lane; e < b1; e += 32) {
+      const int32_t j = P.svc[e];
+      const double mv = P.sM[e], kv = P.sK[e];
 #pragma unroll
       for (int t = 0; t < S; ++t) {
         const double xx = x[t * m + j], xy = x[t * m + nf + j];
@@ -48,10 +60,10 @@ __global__ void __launch_bounds__(256) k_residual(OpParams P, const double* __re
         ak[t][1] = fma(kv, xy, ak[t][1]);
       }
     }
-    const int32_t q1 = P.bptr[row + 1];
-    for (int32_t p = P.bptr[row]; p < q1; ++p) {
-      const int32_t vtx = P.bcol[p];
-      const double bx = P.Bx[p], by = P.By[p];
+    const int64_t c0 = P.sbp[sl], c1 = P.sbp[sl + 1];
+    for (int64_t e = c0 + lane; e < c1; e += 32) {
+      const int32_t vtx = P.sbc[e];
+      const double bx = P.sBx[e], by = P.sBy[e];
 #pragma unroll
       for (int t = 0; t < S; ++t) {
         const double pv = x[t * m + 2 * nf + vtx];
@@ -76,15 +88,17 @@ __global__ void __launch_bounds__(256) k_residual(OpParams P, const double* __re
         r[gy] = yy;
       }
     }
-  } else if (row < nf + P.nv) {
-    const int64_t v = row - nf;
+  } else {
+    const int64_t v = tidg - P.nf_pad;
+    if (v >= P.nv) return;
     double ap[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) ap[t] = 0.0;
-    const int32_t p1 = P.btptr[v + 1];
-    for (int32_t p = P.btptr[v]; p < p1; ++p) {
-      const int32_t j = P.btcol[p];
-      const double bx = P.BTx[p], by = P.BTy[p];
+    const int64_t sl = v >> 5, lane = v & 31;
+    const int64_t b0 = P.sbtp[sl], b1 = P.sbtp[sl + 1];
+    for (int64_t e = b0 + lane; e < b1; e += 32) {
+      const int32_t j = P.sbtc[e];
+      const double bx = P.sBTx[e], by = P.sBTy[e];
 #pragma unroll
       for (int t = 0; t < S; ++t) ap[t] = fma(bx, x[t * m + j], fma(by, x[t * m + nf + j], ap[t]));
     }
@@ -120,18 +134,31 @@ static OpParams op_params(Ctx& C, Level& L, int transpose) {
   P.btcol = L.bt.col;
   P.BTx = L.bt.v[0];
   P.BTy = L.bt.v[1];
+  P.nf_pad = (L.nf + 31) / 32 * 32;
+  P.svp = L.svel.ptr;
+  P.svc = L.svel.col;
+  P.sM = L.svel.v[0];
+  P.sK = transpose ? L.svel.v[2] : L.svel.v[1];
+  P.sbp = L.sb.ptr;
+  P.sbc = L.sb.col;
+  P.sBx = L.sb.v[0];
+  P.sBy = L.sb.v[1];
+  P.sbtp = L.sbt.ptr;
+  P.sbtc = L.sbt.col;
+  P.sBTx = L.sbt.v[0];
+  P.sBTy = L.sbt.v[1];
   return P;
 }
 
 cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, double* r,
                             int transpose) {
   OpParams P = op_params(C, L, transpose);
-  const int64_t rows = L.nf + L.nv;
+  const int64_t rows = P.nf_pad + L.nv;
   const unsigned grid = (unsigned)((rows + 255) / 256);
   switch (C.s) {
-    case 1: k_residual<1><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
-    case 2: k_residual<2><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
-    default: k_residual<3><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+    case 1: k_residual_sell<1><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+    case 2: k_residual_sell<2><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+    default: k_residual_sell<3><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
   }
   return cudaGetLastError();
 }
