@@ -225,6 +225,38 @@ int irkmg_stage_rhs(irkmg_ctx *ctx, const double *d_un, const double *d_pn, cons
 /* u^{n+1} = u^n + dt sum_j b_j k_j^u and likewise p (in place). */
 int irkmg_advance(irkmg_ctx *ctx, const double *d_k, double *d_un, double *d_pn);
 
+/* ---- forcing control and the discrete adjoint (differentiation of the
+ * Section 3.1 time stepping; the paper does not differentiate) ------------- */
+
+/* Velocity load of a per-cell constant forcing th: g = C th with
+ * C[a, c] = ∫_c φ_a on the finest level.  d_theta: 2·nc (x block, then y
+ * block, cell ids of the finest mesh); d_g: 2·nf (u_x block, then u_y). */
+int irkmg_forcing_load(irkmg_ctx *ctx, const double *d_theta, double *d_g);
+
+/* One implicit RK time step on the finest level (Section 3.1):
+ * F = irkmg_stage_rhs(u^n, p^n, f) plus d_g in every stage (d_g may be NULL),
+ * J k = F by FGMRES from a zero guess (stages written to d_k, length N), then
+ * u^n, p^n advanced in place to u^{n+1}, p^{n+1}.  Status as irkmg_solve. */
+int irkmg_step(irkmg_ctx *ctx, double *d_un, double *d_pn, const double *d_f, const double *d_g,
+               double *d_k, irkmg_stats *stats);
+
+/* Reverse of irkmg_step for the adjoint state (ub, pb) = dObj/d(u^{n+1}, p^{n+1})
+ * (in) -> dObj/d(u^n, p^n) (out, in place), given that step's stages d_k and
+ * start state d_un:  kb_j = dt b_j [ub; pb],  Jᵀ lam = kb (FGMRES with the
+ * transposed V-cycle),  ub -= sum_i (Kᵀ lam_i,u + B lam_i,p),
+ * pb -= sum_i Bᵀ lam_i,u.  It also accumulates the forcing gradient
+ * d_theta_bar += Cᵀ sum_i lam_i,u (2·nc, may be NULL) and, through K = nu·K1
+ * in both J and F, *d_nu += -(1/nu) sum_i lam_i,u · K (u^n + dt sum_j a_ij k_j,u)
+ * (host double, may be NULL). */
+int irkmg_adjoint_step(irkmg_ctx *ctx, double *d_ubar, double *d_pbar, const double *d_k,
+                       const double *d_un, double *d_theta_bar, double *d_nu, irkmg_stats *stats);
+
+/* Tracking objective on the finest level: *value = 1/2 eᵀ M2 e with
+ * e = u - u_target (free velocity DoFs, M2 = diag(M, M)); d_grad = M2 e
+ * (2·nf, may be NULL).  *value is a host double. */
+int irkmg_tracking(irkmg_ctx *ctx, const double *d_u, const double *d_utarget, double *d_grad,
+                   double *value);
+
 /* ---- tracing ---------------------------------------------------------------- */
 
 /* Kernel accounting since the last irkmg_trace_enable.  `launches` counts every

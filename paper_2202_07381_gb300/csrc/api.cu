@@ -679,6 +679,17 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
     }
     L.op_bytes = 20.0 * (double)L.vel.nnz + 20.0 * (double)(L.b.nnz + L.bt.nnz) + 24.0 * (double)L.N;
   }
+  {
+    Level& Lf = C->L[nl - 1];
+    HostCSR cl;
+    assemble_cell_load(Lf.mesh, cl);
+    if ((rc = upload_csr(*C, C->cload, cl, 1))) return rc;
+    if ((rc = upload_csr(*C, C->cloadt, transpose_csr(cl, 1), 1))) return rc;
+    if ((rc = dalloc(*C, &C->d_F, Lf.N))) return rc;
+    if ((rc = dalloc(*C, &C->d_kb, Lf.N))) return rc;
+    if ((rc = dalloc(*C, &C->d_lam, Lf.N))) return rc;
+    if ((rc = dalloc(*C, &C->d_scalar, 8))) return rc;
+  }
   C->nb = C->L[0].N + C->s;
   if (C->nb > 20000) return fail(IRKMG_EINVAL, "coarsest level too large for the dense solve");
   if ((rc = dalloc(*C, &C->d_coarse_inv, (size_t)C->nb * C->nb))) return rc;
@@ -973,6 +984,68 @@ int irkmg_advance(irkmg_ctx* C, const double* k, double* un, double* pn) {
   if (!C || !k || !un || !pn) return fail(IRKMG_EINVAL, "bad arguments");
   CK(launch_advance(*C, k, un, pn));
   C->launches++;
+  return IRKMG_OK;
+}
+
+int irkmg_forcing_load(irkmg_ctx* C, const double* theta, double* g) {
+  if (!C || !theta || !g) return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_cell_load(*C, theta, g));
+  C->launches++;
+  return IRKMG_OK;
+}
+
+int irkmg_step(irkmg_ctx* C, double* un, double* pn, const double* f, const double* g, double* k,
+               irkmg_stats* st) {
+  if (!C || !un || !pn || !f || !k) return fail(IRKMG_EINVAL, "bad arguments");
+  Level& L = C->L.back();
+  CK(launch_stage_rhs(*C, un, pn, f, C->d_F));
+  C->launches++;
+  if (g) {
+    CK(launch_add_to_stages(*C, g, C->d_F));
+    C->launches++;
+  }
+  CK(cudaMemsetAsync(k, 0, sizeof(double) * L.N, C->stream));
+  int rc = fgmres(*C, C->d_F, k, st, 0);
+  if (rc) return rc;
+  CK(launch_advance(*C, k, un, pn));
+  C->launches++;
+  return IRKMG_OK;
+}
+
+int irkmg_adjoint_step(irkmg_ctx* C, double* ub, double* pb, const double* k, const double* un,
+                       double* thb, double* dnu, irkmg_stats* st) {
+  if (!C || !ub || !pb || !k || !un) return fail(IRKMG_EINVAL, "bad arguments");
+  Level& L = C->L.back();
+  CK(launch_kbar(*C, ub, pb, C->d_kb));
+  CK(cudaMemsetAsync(C->d_lam, 0, sizeof(double) * L.N, C->stream));
+  C->launches++;
+  int rc = fgmres(*C, C->d_kb, C->d_lam, st, 1);
+  if (rc) return rc;
+  if (dnu) {
+    CK(launch_dnu(*C, C->d_lam, k, un, C->d_part, C->d_scalar));
+    C->launches += 2;
+  }
+  CK(launch_adjoint_update(*C, C->d_lam, ub, pb));
+  C->launches++;
+  if (thb) {
+    CK(launch_theta_bar(*C, C->d_lam, thb));
+    C->launches++;
+  }
+  if (dnu) {
+    double h = 0.0;
+    CK(cudaMemcpyAsync(&h, C->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    *dnu += h;
+  }
+  return IRKMG_OK;
+}
+
+int irkmg_tracking(irkmg_ctx* C, const double* u, const double* ut, double* grad, double* value) {
+  if (!C || !u || !ut || !value) return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_tracking(*C, u, ut, grad, C->d_part, C->d_scalar));
+  C->launches += 2;
+  CK(cudaMemcpyAsync(value, C->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+  CK(cudaStreamSynchronize(C->stream));
   return IRKMG_OK;
 }
 

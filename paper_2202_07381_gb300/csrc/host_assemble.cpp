@@ -196,4 +196,45 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
   ops.bt = transpose_csr(B, 2);
 }
 
+// Load of a per-cell constant (P0) forcing: C[a, c] = int_c phi_a for the free
+// P2 nodes a of cell c (the same for both velocity components).  P2 vertex
+// functions integrate to zero on a triangle, edge functions to |c|/3; the
+// degree-5 rule is exact for these quadratics.
+void assemble_cell_load(const HostMesh& m, HostCSR& C) {
+  const QuadRule q = radon7();
+  C = HostCSR();
+  C.nrows = m.nf;
+  C.ncols = m.nc;
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(m.nf);
+  for (int64_t c = 0; c < m.nc; ++c) {
+    const int32_t* t = &m.cells[3 * c];
+    const double x0 = m.xy[2 * t[0]], y0 = m.xy[2 * t[0] + 1];
+    const double d1x = m.xy[2 * t[1]] - x0, d1y = m.xy[2 * t[1] + 1] - y0;
+    const double d2x = m.xy[2 * t[2]] - x0, d2y = m.xy[2 * t[2] + 1] - y0;
+    const double area = 0.5 * std::fabs(d1x * d2y - d1y * d2x);
+    double gl[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    double w[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 7; ++k) {
+      double phi[6], g[6][2];
+      p2_eval(q.lam[k], gl, phi, g);
+      for (int a = 0; a < 6; ++a) w[a] += q.w[k] * area * phi[a];
+    }
+    for (int a = 0; a < 6; ++a) {
+      const int32_t node = a < 3 ? t[a] : (int32_t)(m.nv + m.cell_edges[3 * c + a - 3]);
+      const int32_t f = m.p2_to_free[node];
+      if (f < 0 || std::fabs(w[a]) <= 1e-12 * area) continue;  // vertex functions: zero
+      rows[f].push_back({(int32_t)c, w[a]});
+    }
+  }
+  C.ptr.assign(1, 0);
+  for (int64_t i = 0; i < m.nf; ++i) {
+    std::sort(rows[i].begin(), rows[i].end());
+    for (auto& pr : rows[i]) {
+      C.col.push_back(pr.first);
+      C.v[0].push_back(pr.second);
+    }
+    C.ptr.push_back((int32_t)C.col.size());
+  }
+}
+
 }  // namespace irkmg

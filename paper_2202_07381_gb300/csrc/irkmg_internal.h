@@ -59,6 +59,8 @@ struct HostOps {
 // wind: np2*2 nodal values or nullptr
 void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& ops);
 
+void assemble_cell_load(const HostMesh& m, HostCSR& C);
+
 // Radau IIA closed forms.
 int radau_iia(int s, double* A, double* b, double* c);
 
@@ -136,6 +138,9 @@ struct Ctx {
   int* d_err = nullptr;   // device error word: [0] status, [1] index
   int64_t dev_bytes = 0;
   int* h_err = nullptr;    // pinned mirror of d_err
+  // time stepping and adjoint (finest level)
+  DevCSR cload, cloadt;    // P0 cell load C (nf x nc) and its transpose
+  double *d_F = nullptr, *d_kb = nullptr, *d_lam = nullptr, *d_scalar = nullptr;
   // tracing
   int64_t launches = 0;
   bool trace_on = false;
@@ -175,6 +180,16 @@ cudaError_t launch_advance(Ctx& C, const double* k, double* un, double* pn);
 cudaError_t launch_coarse_build(Ctx& C, double* dense);
 cudaError_t coarse_invert(Ctx& C, double* dense, int64_t n);
 cudaError_t launch_coarse_apply(Ctx& C, const double* r, double* x, int transpose);
+
+cudaError_t launch_cell_load(Ctx& C, const double* theta, double* g);
+cudaError_t launch_add_to_stages(Ctx& C, const double* g, double* F);
+cudaError_t launch_kbar(Ctx& C, const double* ub, const double* pb, double* kb);
+cudaError_t launch_adjoint_update(Ctx& C, const double* lam, double* ub, double* pb);
+cudaError_t launch_theta_bar(Ctx& C, const double* lam, double* thb);
+cudaError_t launch_dnu(Ctx& C, const double* lam, const double* k, const double* un, double* part,
+                       double* out);
+cudaError_t launch_tracking(Ctx& C, const double* u, const double* ut, double* grad, double* part,
+                            double* out);
 
 constexpr int kMultidotBlocks = 304;  // 2 x 152 SMs; fixed for a deterministic sum order
 

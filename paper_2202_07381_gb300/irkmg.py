@@ -96,6 +96,11 @@ _SIGS = {
     "irkmg_adjoint_solve": (ct.c_int, [_P, _P, _P, ct.POINTER(Stats)]),
     "irkmg_stage_rhs": (ct.c_int, [_P, _P, _P, _P, _P]),
     "irkmg_advance": (ct.c_int, [_P, _P, _P, _P]),
+    "irkmg_forcing_load": (ct.c_int, [_P, _P, _P]),
+    "irkmg_step": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(Stats)]),
+    "irkmg_adjoint_step": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(ct.c_double),
+                                      ct.POINTER(Stats)]),
+    "irkmg_tracking": (ct.c_int, [_P, _P, _P, _P, ct.POINTER(ct.c_double)]),
     "irkmg_trace_enable": (ct.c_int, [_P, ct.c_int]),
     "irkmg_trace_read": (ct.c_int, [_P, ct.POINTER(Trace)]),
     "irkmg_destroy": (None, [_P]),
@@ -333,6 +338,44 @@ def irkmg_advance(ctx, k, un, pn):
     L = ctx.finest
     _check(lib().irkmg_advance(ctx.handle, _dptr(k, L["N"], "k"), _dptr(un, 2 * L["nf"], "un"),
                                _dptr(pn, L["nv"], "pn")))
+
+
+def irkmg_forcing_load(ctx, theta, g):
+    L = ctx.finest
+    _check(lib().irkmg_forcing_load(ctx.handle, _dptr(theta, 2 * L["nc"], "theta"),
+                                    _dptr(g, 2 * L["nf"], "g")))
+
+
+def irkmg_step(ctx, un, pn, f, g, k):
+    L = ctx.finest
+    st = Stats()
+    _check(lib().irkmg_step(ctx.handle, _dptr(un, 2 * L["nf"], "un"), _dptr(pn, L["nv"], "pn"),
+                            _dptr(f, ctx.s * 2 * L["np2"], "f"),
+                            _dptr(g, 2 * L["nf"], "g") if g is not None else None,
+                            _dptr(k, L["N"], "k"), ct.byref(st)))
+    return st.as_dict()
+
+
+def irkmg_adjoint_step(ctx, ubar, pbar, k, un, theta_bar=None, want_nu=True):
+    """Returns (stats, dObj/dnu contribution of this step or None)."""
+    L = ctx.finest
+    st = Stats()
+    dnu = ct.c_double(0.0)
+    _check(lib().irkmg_adjoint_step(
+        ctx.handle, _dptr(ubar, 2 * L["nf"], "ubar"), _dptr(pbar, L["nv"], "pbar"),
+        _dptr(k, L["N"], "k"), _dptr(un, 2 * L["nf"], "un"),
+        _dptr(theta_bar, 2 * L["nc"], "theta_bar") if theta_bar is not None else None,
+        ct.byref(dnu) if want_nu else None, ct.byref(st)))
+    return st.as_dict(), (dnu.value if want_nu else None)
+
+
+def irkmg_tracking(ctx, u, ut, grad=None):
+    L = ctx.finest
+    v = ct.c_double(0.0)
+    _check(lib().irkmg_tracking(ctx.handle, _dptr(u, 2 * L["nf"], "u"), _dptr(ut, 2 * L["nf"], "ut"),
+                                _dptr(grad, 2 * L["nf"], "grad") if grad is not None else None,
+                                ct.byref(v)))
+    return v.value
 
 
 def irkmg_trace_enable(ctx, on=True):
