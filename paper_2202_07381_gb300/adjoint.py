@@ -36,10 +36,10 @@ class TrackingProblem:
             self.nu = nu
 
     def _step(self, u, p, g, k):
-        st = irkmg.irkmg_step(self.ctx, u, p, self.f, g, k)
+        st = irkmg.irkmg_step(self.ctx, u, p, self.f, g, k, raise_on_noconv=False)
         self.stats.append(st)
         if st["status"] != 0:
-            raise irkmg.IrkmgError(st["status"], "stage solve did not converge")
+            raise irkmg.IrkmgError(st["status"], f"stage solve did not converge: {st}")
 
     def forward_states(self, g):
         """Run all steps; returns (u^N, p^N, checkpoints {n: (u^n, p^n)})."""

@@ -346,13 +346,17 @@ def irkmg_forcing_load(ctx, theta, g):
                                     _dptr(g, 2 * L["nf"], "g")))
 
 
-def irkmg_step(ctx, un, pn, f, g, k):
+def irkmg_step(ctx, un, pn, f, g, k, raise_on_noconv=True):
+    """One IRK step; returns the solve's stats (status ENOCONV is returned
+    instead of raised when raise_on_noconv is False)."""
     L = ctx.finest
     st = Stats()
-    _check(lib().irkmg_step(ctx.handle, _dptr(un, 2 * L["nf"], "un"), _dptr(pn, L["nv"], "pn"),
-                            _dptr(f, ctx.s * 2 * L["np2"], "f"),
-                            _dptr(g, 2 * L["nf"], "g") if g is not None else None,
-                            _dptr(k, L["N"], "k"), ct.byref(st)))
+    rc = lib().irkmg_step(ctx.handle, _dptr(un, 2 * L["nf"], "un"), _dptr(pn, L["nv"], "pn"),
+                          _dptr(f, ctx.s * 2 * L["np2"], "f"),
+                          _dptr(g, 2 * L["nf"], "g") if g is not None else None,
+                          _dptr(k, L["N"], "k"), ct.byref(st))
+    if not (rc == IRKMG_ENOCONV and not raise_on_noconv):
+        _check(rc)
     return st.as_dict()
 
 

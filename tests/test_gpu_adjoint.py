@@ -2,7 +2,8 @@
 torch.autograd): against the oracle's adjoint on the same problem (1e-9
 relative, with tight solver tolerances on the GPU), and against central finite
 differences of the GPU forward model (1e-5 relative) on the 128 x 128,
-8-step, dt = 1/32 configuration with checkpoints every 2 steps."""
+8-step, dt = 1/32 configuration with checkpoints every 2 steps (step 1 along a
+seeded N(0,1) direction for the forcing, 1e-6 for nu)."""
 import numpy as np
 import pytest
 
@@ -12,10 +13,12 @@ from tests.gpu_util import gpu_context, need_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _problem(irkmg, n0, nl, s, dt, nsteps, nu=1.0, rtol=1e-13):
+def _problem(irkmg, n0, nl, s, dt, nsteps, nu=1.0, rtol=1e-13, atol=1e-15):
     import torch
     from paper_2202_07381_gb300.adjoint import TrackingProblem
-    ctx = gpu_context(irkmg, n0, nl, s, dt, nu=nu, rtol=rtol, maxit=400)
+    # the residual of a solve cannot go below ~1e-16 in absolute terms, and F
+    # shrinks as the steps proceed, so the test stops at max(1e-13 |F|, 1e-15)
+    ctx = gpu_context(irkmg, n0, nl, s, dt, nu=nu, rtol=rtol, atol=atol, maxit=400)
     xy = irkmg.irkmg_p2_coords(ctx)
     free = irkmg.irkmg_free_nodes(ctx)
     nv = ctx.finest["nv"]
@@ -64,7 +67,10 @@ def test_adjoint_matches_finite_differences_128():
     J = tracking_objective(th, nu, prob)
     J.backward()
     d = torch.tensor(synth.normal(11, theta.size), dtype=torch.float64, device="cuda")
-    h = 1e-6 * max(1.0, float(np.abs(theta).max()))
+    # u^N is affine in theta, so the objective is exactly quadratic in theta and
+    # central differences carry no truncation error: a unit step keeps the
+    # difference far above the solver's rounding floor
+    h = 1.0
     with torch.no_grad():
         Jp = prob.objective(th + h * d, 1.0)
         Jm = prob.objective(th - h * d, 1.0)
