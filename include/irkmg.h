@@ -140,6 +140,13 @@ int irkmg_setup(const irkmg_mesh *mesh, const irkmg_tableau *tab, double dt, dou
 /* Re-assemble and re-factor for a new dt and nu (same mesh, tableau, wind). */
 int irkmg_update(irkmg_ctx *ctx, double dt, double nu);
 
+/* Replace the Oseen wind (host array, finest-level P2 nodes, np2·2 doubles,
+ * x and y per node; NULL returns to Stokes) and re-assemble and re-factor every
+ * level, as irkmg_update does; coarse levels take the wind at their own P2
+ * nodes (which are finest-level nodes).  This is the frozen-wind update of a
+ * Picard linearisation of Navier–Stokes (Section 3.2). */
+int irkmg_set_wind(irkmg_ctx *ctx, const double *wind);
+
 /* Sizes of level l (0 = coarsest, nlevels-1 = finest). */
 int irkmg_level_info_get(const irkmg_ctx *ctx, int level, irkmg_level_info *info);
 
@@ -224,6 +231,31 @@ int irkmg_stage_rhs(irkmg_ctx *ctx, const double *d_un, const double *d_pn, cons
 
 /* u^{n+1} = u^n + dt sum_j b_j k_j^u and likewise p (in place). */
 int irkmg_advance(irkmg_ctx *ctx, const double *d_k, double *d_un, double *d_pn);
+
+/* The stage right-hand side with u^n given at every P2 node (2·np2: u_x then
+ * u_y), so that boundary values of u^n enter (a moving lid, Section 3.1 with
+ * inhomogeneous Dirichlet data carried by u^n):
+ * F_i = [ M f_i - K u^n - B p^n ; -Bᵀ u^n ] with K (including any Oseen
+ * convection) and Bᵀ over every velocity column.  The stages themselves stay
+ * homogeneous on the boundary (the boundary data is steady). */
+int irkmg_stage_rhs_full(irkmg_ctx *ctx, const double *d_un_all, const double *d_pn,
+                         const double *d_f, double *d_F);
+
+/* ---- batched solves of independent stage systems --------------------------
+ * A batch groups contexts of any sizes, tableaux, dt, nu and winds.  Creating
+ * it gives every context its own non-blocking stream (restored by
+ * irkmg_batch_destroy; contexts stay owned by the caller and must outlive the
+ * batch).  irkmg_batch_solve runs FGMRES on all systems in lock step: each
+ * Arnoldi step of every unconverged system is issued on its stream (its
+ * V-cycle as one CUDA graph, captured on first use), then all are synchronised
+ * once and the small Hessenberg updates run on the host.  Results equal those
+ * of irkmg_solve on each system.  d_F[i], d_k[i] live on the device of
+ * system i's context; stats (may be NULL) has nsys entries. */
+typedef struct irkmg_batch irkmg_batch;
+int irkmg_batch_create(int nsys, irkmg_ctx *const *ctxs, irkmg_batch **out);
+int irkmg_batch_solve(irkmg_batch *batch, const double *const *d_F, double *const *d_k,
+                      irkmg_stats *stats);
+void irkmg_batch_destroy(irkmg_batch *batch);
 
 /* ---- forcing control and the discrete adjoint (differentiation of the
  * Section 3.1 time stepping; the paper does not differentiate) ------------- */

@@ -662,7 +662,8 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
     if ((rc = upload_sell(*C, L.svel, L.hops.vel, 3))) return rc;
     if ((rc = upload_sell(*C, L.sb, L.hops.b, 2))) return rc;
     if ((rc = upload_sell(*C, L.sbt, L.hops.bt, 2))) return rc;
-    if (l == nl - 1 && (rc = upload_csr(*C, L.mall, L.hops.mall, 1))) return rc;
+    if (l == nl - 1 && (rc = upload_csr(*C, L.mall, L.hops.mall, 2))) return rc;
+    if (l == nl - 1 && (rc = upload_csr(*C, L.btall, L.hops.btall, 2))) return rc;
     if ((rc = dalloc(*C, &L.r, L.N))) return rc;
     if ((rc = dalloc(*C, &L.z, L.N))) return rc;
     if ((rc = dalloc(*C, &L.t, L.N))) return rc;
@@ -773,6 +774,190 @@ int smooth_in(Ctx& C, Level& L, const double* b, double* x, int nsteps, int tr, 
   return IRKMG_OK;
 }
 
+// --- batched solves ----------------------------------------------------------
+// One V-cycle of C captured as a CUDA graph that reads d_gin and writes
+// d_gout; captured once, on the context's (non-default) stream.
+int capture_vcycle(Ctx& C) {
+  if (C.vgraph) return IRKMG_OK;
+  const int64_t n = C.L.back().N;
+  int rc;
+  if (!C.d_gin && (rc = dalloc(C, &C.d_gin, n))) return rc;
+  if (!C.d_gout && (rc = dalloc(C, &C.d_gout, n))) return rc;
+  const bool saved = C.trace_on;
+  C.trace_on = false;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(C.stream, cudaStreamCaptureModeThreadLocal));
+  rc = vcycle_level(C, (int)C.L.size() - 1, C.d_gin, C.d_gout, 0);
+  cudaError_t e = cudaStreamEndCapture(C.stream, &g);
+  C.trace_on = saved;
+  if (rc) {
+    if (e == cudaSuccess && g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CK(e);
+  e = cudaGraphInstantiate(&C.vgraph, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  return IRKMG_OK;
+}
+
+// Per-system state of the lock-step FGMRES (the same recurrences as fgmres()).
+struct FState {
+  Ctx* C = nullptr;
+  const double* F = nullptr;
+  double* x = nullptr;
+  irkmg_stats* st = nullptr;
+  int m = 0, j = 0, its = 0;
+  double bnorm = 0, beta = 0, target = 0, t0 = 0;
+  bool done = false, finishing = false;
+  std::vector<double> H, cs, sn, g, y;
+};
+
+int issue_norm(Ctx& C, const double* v, int slot) {
+  const int64_t n = C.L.back().N;
+  CK(launch_multidot(v, 0, 1, v, n, C.d_part, C.d_h + slot, C.stream));
+  CK(cudaMemcpyAsync(C.h_h + slot, C.d_h + slot, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
+  C.launches += 2;
+  return IRKMG_OK;
+}
+
+int batch_fgmres(std::vector<FState>& S) {
+  int rc;
+  for (FState& f : S) {  // initial residuals and norms
+    Ctx& C = *f.C;
+    const int64_t n = C.L.back().N;
+    f.m = C.opt.restart;
+    f.H.assign((size_t)(f.m + 1) * f.m, 0.0);
+    f.cs.assign(f.m, 0.0);
+    f.sn.assign(f.m, 0.0);
+    f.g.assign(f.m + 1, 0.0);
+    f.y.assign(f.m, 0.0);
+    f.t0 = now();
+    if ((rc = capture_vcycle(C))) return rc;
+    if ((rc = issue_norm(C, f.F, 192))) return rc;
+    if ((rc = op(C, C.L.back(), f.F, f.x, C.d_V, 0))) return rc;
+    if ((rc = issue_norm(C, C.d_V, 193))) return rc;
+    (void)n;
+  }
+  for (FState& f : S) {
+    CK(cudaStreamSynchronize(f.C->stream));
+    f.bnorm = std::sqrt(f.C->h_h[192]);
+    f.beta = std::sqrt(f.C->h_h[193]);
+    f.target = std::max(f.C->opt.rtol * f.bnorm, f.C->opt.atol);
+    if (f.st) f.st->r0 = f.beta;
+    f.done = !(f.beta > f.target && f.its < f.C->opt.maxit);
+    f.finishing = false;
+    f.j = -1;  // a new cycle starts
+  }
+  for (;;) {
+    bool any = false;
+    for (FState& f : S) {  // issue one Arnoldi step per active system
+      if (f.done) continue;
+      any = true;
+      Ctx& C = *f.C;
+      Level& L = C.L.back();
+      const int64_t n = L.N;
+      if (f.j < 0) {
+        CK(launch_axpby(C.d_V, C.d_V, 1.0 / f.beta, 0.0, n, C.stream));
+        C.launches++;
+        std::fill(f.g.begin(), f.g.end(), 0.0);
+        f.g[0] = f.beta;
+        f.j = 0;
+      }
+      double* vj = C.d_V + (int64_t)f.j * n;
+      double* zj = C.d_Z + (int64_t)f.j * n;
+      CK(cudaMemcpyAsync(C.d_gin, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.stream));
+      CK(cudaGraphLaunch(C.vgraph, C.stream));
+      CK(cudaMemcpyAsync(zj, C.d_gout, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.stream));
+      CK(launch_pressure_mean_remove(C, L, zj));
+      if ((rc = op(C, L, nullptr, zj, C.d_w, 0))) return rc;
+      CK(launch_multidot(C.d_V, n, f.j + 1, C.d_w, n, C.d_part, C.d_h, C.stream));
+      CK(launch_multiaxpy(C.d_w, C.d_V, n, f.j + 1, C.d_h, -1.0, n, C.stream));
+      CK(launch_multidot(C.d_V, n, f.j + 1, C.d_w, n, C.d_part, C.d_h + 64, C.stream));
+      CK(launch_multiaxpy(C.d_w, C.d_V, n, f.j + 1, C.d_h + 64, -1.0, n, C.stream));
+      CK(launch_multidot(C.d_w, 0, 1, C.d_w, n, C.d_part, C.d_h + 128, C.stream));
+      C.launches += 11;
+      CK(cudaMemcpyAsync(C.h_h, C.d_h, sizeof(double) * 129, cudaMemcpyDeviceToHost, C.stream));
+      CK(cudaMemcpyAsync(C.h_err, C.d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, C.stream));
+    }
+    if (!any) break;
+    for (FState& f : S) {  // Givens updates, cycle ends
+      if (f.done) continue;
+      Ctx& C = *f.C;
+      const int64_t n = C.L.back().N;
+      CK(cudaStreamSynchronize(C.stream));
+      if (C.h_err[0] != 0) {
+        const int code = C.h_err[0];
+        CK(cudaMemsetAsync(C.d_err, 0, sizeof(int) * 2, C.stream));
+        if (f.st) f.st->status = code;
+        return fail(code, "a bounded device-side wait expired during a batched V-cycle");
+      }
+      const int j = f.j, m = f.m;
+      double* Hj = &f.H[(size_t)j * (m + 1)];
+      for (int i = 0; i <= j; ++i) Hj[i] = C.h_h[i] + C.h_h[64 + i];
+      const double hn = std::sqrt(C.h_h[128]);
+      Hj[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = f.cs[i] * Hj[i] + f.sn[i] * Hj[i + 1];
+        Hj[i + 1] = -f.sn[i] * Hj[i] + f.cs[i] * Hj[i + 1];
+        Hj[i] = a;
+      }
+      const double den = std::hypot(Hj[j], Hj[j + 1]);
+      f.cs[j] = Hj[j] / den;
+      f.sn[j] = Hj[j + 1] / den;
+      Hj[j] = den;
+      Hj[j + 1] = 0.0;
+      f.g[j + 1] = -f.sn[j] * f.g[j];
+      f.g[j] = f.cs[j] * f.g[j];
+      ++f.its;
+      const bool end = std::fabs(f.g[j + 1]) <= f.target || f.its >= C.opt.maxit || hn == 0.0 ||
+                       j + 1 == m;
+      if (!end) {
+        CK(launch_axpby(C.d_V + (int64_t)(j + 1) * n, C.d_w, 1.0 / hn, 0.0, n, C.stream));
+        C.launches++;
+        f.j = j + 1;
+        continue;
+      }
+      const int jdone = j + 1;
+      for (int i = jdone - 1; i >= 0; --i) {
+        double sum = f.g[i];
+        for (int k = i + 1; k < jdone; ++k) sum -= f.H[(size_t)k * (m + 1) + i] * f.y[k];
+        f.y[i] = sum / f.H[(size_t)i * (m + 1) + i];
+      }
+      std::copy(f.y.begin(), f.y.begin() + jdone, C.h_h + 256);
+      CK(cudaMemcpyAsync(C.d_h + 256, C.h_h + 256, sizeof(double) * jdone, cudaMemcpyHostToDevice,
+                         C.stream));
+      CK(launch_multiaxpy(f.x, C.d_Z, n, jdone, C.d_h + 256, 1.0, n, C.stream));
+      C.launches++;
+      if ((rc = op(C, C.L.back(), f.F, f.x, C.d_V, 0))) return rc;
+      if ((rc = issue_norm(C, C.d_V, 193))) return rc;
+      f.finishing = true;
+    }
+    for (FState& f : S) {  // restarts: true residual decides
+      if (f.done || !f.finishing) continue;
+      CK(cudaStreamSynchronize(f.C->stream));
+      f.beta = std::sqrt(f.C->h_h[193]);
+      f.finishing = false;
+      f.j = -1;
+      if (!(f.beta > f.target && f.its < f.C->opt.maxit)) f.done = true;
+    }
+  }
+  int worst = IRKMG_OK;
+  for (FState& f : S) {
+    const int status = f.beta <= f.target ? IRKMG_OK : IRKMG_ENOCONV;
+    if (f.st) {
+      f.st->iters = f.its;
+      f.st->rfinal = f.beta;
+      f.st->t_solve = now() - f.t0;
+      f.st->status = status;
+      f.st->bad_index = -1;
+    }
+    if (status != IRKMG_OK) worst = status;
+  }
+  if (worst) return fail(worst, "FGMRES reached maxit in at least one system of the batch");
+  return IRKMG_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -842,9 +1027,20 @@ int irkmg_update(irkmg_ctx* C, double dt, double nu) {
     if ((rc = refresh_sell_values(*C, L.svel, L.hops.vel, 3))) return rc;
     if ((rc = refresh_sell_values(*C, L.sb, L.hops.b, 2))) return rc;
     if ((rc = refresh_sell_values(*C, L.sbt, L.hops.bt, 2))) return rc;
-    if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.mall, L.hops.mall, 1))) return rc;
+    if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.mall, L.hops.mall, 2))) return rc;
+    if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.btall, L.hops.btall, 2))) return rc;
   }
   return factor_all(*C);
+}
+
+int irkmg_set_wind(irkmg_ctx* C, const double* wind) {
+  if (!C) return fail(IRKMG_EINVAL, "null ctx");
+  CK(C->stream ? cudaStreamSynchronize(C->stream) : cudaDeviceSynchronize());
+  if (wind)
+    C->wind.assign(wind, wind + 2 * C->L.back().np2);
+  else
+    C->wind.clear();
+  return irkmg_update(C, C->dt, C->nu);
 }
 
 int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) {
@@ -1049,6 +1245,68 @@ int irkmg_tracking(irkmg_ctx* C, const double* u, const double* ut, double* grad
   return IRKMG_OK;
 }
 
+int irkmg_stage_rhs_full(irkmg_ctx* C, const double* un_all, const double* pn, const double* f,
+                         double* F) {
+  if (!C || !un_all || !pn || !f || !F) return fail(IRKMG_EINVAL, "bad arguments");
+  CK(launch_stage_rhs_full(*C, un_all, pn, f, F));
+  C->launches++;
+  return IRKMG_OK;
+}
+
+struct irkmg_batch {
+  std::vector<irkmg_ctx*> sys;
+  std::vector<cudaStream_t> own, saved;
+};
+
+int irkmg_batch_create(int nsys, irkmg_ctx* const* ctxs, irkmg_batch** out) {
+  if (!out || nsys < 1 || !ctxs) return fail(IRKMG_EINVAL, "bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < nsys; ++i)
+    for (int j = 0; j < i; ++j)
+      if (!ctxs[i] || ctxs[i] == ctxs[j]) return fail(IRKMG_EINVAL, "null or repeated context");
+  irkmg_batch* B = new (std::nothrow) irkmg_batch();
+  if (!B) return fail(IRKMG_ENOMEM, "batch");
+  for (int i = 0; i < nsys; ++i) {
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      irkmg_batch_destroy(B);
+      return fail(IRKMG_ECUDA, cudaGetErrorString(e));
+    }
+    // the context finishes pending work on its own stream before switching
+    ctxs[i]->stream ? cudaStreamSynchronize(ctxs[i]->stream) : cudaDeviceSynchronize();
+    B->sys.push_back(ctxs[i]);
+    B->own.push_back(st);
+    B->saved.push_back(ctxs[i]->stream);
+    ctxs[i]->stream = st;
+  }
+  *out = B;
+  return IRKMG_OK;
+}
+
+int irkmg_batch_solve(irkmg_batch* B, const double* const* F, double* const* k, irkmg_stats* st) {
+  if (!B || !F || !k) return fail(IRKMG_EINVAL, "bad arguments");
+  std::vector<FState> S(B->sys.size());
+  for (size_t i = 0; i < B->sys.size(); ++i) {
+    if (!F[i] || !k[i]) return fail(IRKMG_EINVAL, "null vector in batch");
+    S[i].C = B->sys[i];
+    S[i].F = F[i];
+    S[i].x = k[i];
+    S[i].st = st ? &st[i] : nullptr;
+  }
+  return batch_fgmres(S);
+}
+
+void irkmg_batch_destroy(irkmg_batch* B) {
+  if (!B) return;
+  for (size_t i = 0; i < B->own.size(); ++i) {
+    cudaStreamSynchronize(B->own[i]);
+    if (i < B->sys.size()) B->sys[i]->stream = B->saved[i];
+    cudaStreamDestroy(B->own[i]);
+  }
+  delete B;
+}
+
 int irkmg_trace_enable(irkmg_ctx* C, int on) {
   if (!C) return fail(IRKMG_EINVAL, "null ctx");
   C->launches = 0;
@@ -1091,6 +1349,7 @@ void irkmg_destroy(irkmg_ctx* C) {
   if (C->stream) cudaStreamSynchronize(C->stream);
   else cudaDeviceSynchronize();
   for (cudaEvent_t e : C->ev) cudaEventDestroy(e);
+  if (C->vgraph) cudaGraphExecDestroy(C->vgraph);
   for (void* p : C->allocs) cudaFree(p);
   if (C->h_h) cudaFreeHost(C->h_h);
   if (C->h_err) cudaFreeHost(C->h_err);

@@ -117,6 +117,9 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
   V.v[0].assign(V.col.size(), 0.0);
   V.v[1].assign(V.col.size(), 0.0);
   MA.v[0].assign(MA.col.size(), 0.0);
+  MA.v[1].assign(MA.col.size(), 0.0);
+  // B with every P2 row (Dirichlet rows too), for the lifted right-hand side
+  std::vector<std::vector<std::pair<int32_t, double>>> bfull_x(m.np2), bfull_y(m.np2);
   B.v[0].assign(B.col.size(), 0.0);
   B.v[1].assign(B.col.size(), 0.0);
 
@@ -166,12 +169,18 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
         }
       }
     }
+    for (int a = 0; a < 6; ++a)
+      for (int p = 0; p < 3; ++p) {
+        bfull_x[node[a]].push_back({t[p], Be[0][a][p]});
+        bfull_y[node[a]].push_back({t[p], Be[1][a][p]});
+      }
     for (int a = 0; a < 6; ++a) {
       const int32_t row = m.p2_to_free[node[a]];
       if (row < 0) continue;
       for (int b = 0; b < 6; ++b) {
         int64_t sa = slot(MA, row, node[b]);
         MA.v[0][sa] += Me[a][b];
+        MA.v[1][sa] += Ke[a][b];
         const int32_t cf = m.p2_to_free[node[b]];
         if (cf >= 0) {
           int64_t sv = slot(V, row, cf);
@@ -194,6 +203,32 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
       V.v[2][p] = V.v[1][st];
     }
   ops.bt = transpose_csr(B, 2);
+  // Bᵀ over every velocity column: vertex rows, P2-node columns, summed per pair
+  HostCSR Bf;
+  Bf.nrows = m.np2;
+  Bf.ncols = m.nv;
+  Bf.ptr.assign(1, 0);
+  for (int64_t n = 0; n < m.np2; ++n) {
+    std::vector<std::pair<int32_t, std::pair<double, double>>> e;
+    for (size_t k = 0; k < bfull_x[n].size(); ++k)
+      e.push_back({bfull_x[n][k].first, {bfull_x[n][k].second, bfull_y[n][k].second}});
+    std::stable_sort(e.begin(), e.end(),
+                     [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (size_t k = 0; k < e.size();) {
+      size_t j = k;
+      double sx = 0.0, sy = 0.0;
+      for (; j < e.size() && e[j].first == e[k].first; ++j) {
+        sx += e[j].second.first;
+        sy += e[j].second.second;
+      }
+      Bf.col.push_back(e[k].first);
+      Bf.v[0].push_back(sx);
+      Bf.v[1].push_back(sy);
+      k = j;
+    }
+    Bf.ptr.push_back((int32_t)Bf.col.size());
+  }
+  ops.btall = transpose_csr(Bf, 2);
 }
 
 // Load of a per-cell constant (P0) forcing: C[a, c] = int_c phi_a for the free

@@ -52,7 +52,8 @@ HostCSR transpose_csr(const HostCSR& A, int nvals);
 // Assembled free-DoF operators of one level (Section 3.1).
 struct HostOps {
   HostCSR vel;   // nf x nf: v[0] = M, v[1] = nu K (+ C), v[2] = transpose of v[1]
-  HostCSR mall;  // nf x np2: v[0] = M with every column (for M f)
+  HostCSR mall;  // nf x np2: v[0] = M, v[1] = nu K (+ C), with every column (for M f, K u)
+  HostCSR btall; // nv x np2: v[0] = B_x^T, v[1] = B_y^T with every velocity column
   HostCSR b;     // nf x nv : v[0] = B_x, v[1] = B_y   (B = -int psi_q d phi_a / dx_d)
   HostCSR bt;    // nv x nf : v[0] = B_x^T, v[1] = B_y^T
 };
@@ -90,7 +91,7 @@ struct Level {
   HostMesh mesh;
   int64_t nf = 0, nv = 0, np2 = 0, m = 0, N = 0;
   HostOps hops;
-  DevCSR vel, b, bt, mall;
+  DevCSR vel, b, bt, mall, btall;
   DevSELL svel, sb, sbt;  // SELL copies of vel, b and bt for the stage operator
   // transfer from level-1 into this level (l > 0)
   DevCSR pu, put, pp, ppt;
@@ -144,6 +145,9 @@ struct Ctx {
   // tracing
   int64_t launches = 0;
   bool trace_on = false;
+  // CUDA graph of one V-cycle from d_gin to d_gout (batched solves)
+  cudaGraphExec_t vgraph = nullptr;
+  double *d_gin = nullptr, *d_gout = nullptr;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;       // 0 vanka, 1 operator (one per event pair)
   std::vector<double> ev_bytes, ev_flops;
@@ -177,6 +181,8 @@ cudaError_t launch_pressure_mean_remove(Ctx& C, Level& L, double* x);
 cudaError_t launch_stage_rhs(Ctx& C, const double* un, const double* pn, const double* f,
                              double* F);
 cudaError_t launch_advance(Ctx& C, const double* k, double* un, double* pn);
+cudaError_t launch_stage_rhs_full(Ctx& C, const double* un_all, const double* pn, const double* f,
+                                  double* F);
 cudaError_t launch_coarse_build(Ctx& C, double* dense);
 cudaError_t coarse_invert(Ctx& C, double* dense, int64_t n);
 cudaError_t launch_coarse_apply(Ctx& C, const double* r, double* x, int transpose);

@@ -451,6 +451,81 @@ cudaError_t launch_stage_rhs(Ctx& C, const double* un, const double* pn, const d
   return cudaGetLastError();
 }
 
+// Stage right-hand side with u^n given at every P2 node (boundary values
+// included, e.g. a moving lid): F_i = [M f_i - K u^n - B p^n; -Bᵀ u^n] with K
+// and Bᵀ taken over every velocity column.
+__global__ void k_stage_rhs_full(RhsParams P, const int32_t* __restrict__ btaptr,
+                                 const int32_t* __restrict__ btacol,
+                                 const double* __restrict__ btax, const double* __restrict__ btay,
+                                 const double* __restrict__ Kall, const double* __restrict__ un,
+                                 const double* __restrict__ pn, const double* __restrict__ f,
+                                 double* __restrict__ F) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nf = P.nf, np2 = P.np2;
+  if (row < nf) {
+    double kx = 0.0, ky = 0.0;
+    for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) {
+      const int32_t j = P.acol[p];
+      kx = fma(Kall[p], un[j], kx);
+      ky = fma(Kall[p], un[np2 + j], ky);
+    }
+    for (int32_t p = P.bptr[row]; p < P.bptr[row + 1]; ++p) {
+      const double pv = pn[P.bcol[p]];
+      kx = fma(P.Bx[p], pv, kx);
+      ky = fma(P.By[p], pv, ky);
+    }
+    for (int t = 0; t < P.s; ++t) {
+      double mx = 0.0, my = 0.0;
+      const double* fx = f + (int64_t)t * 2 * np2;
+      const double* fy = fx + np2;
+      for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) {
+        const int32_t j = P.acol[p];
+        mx = fma(P.Mall[p], fx[j], mx);
+        my = fma(P.Mall[p], fy[j], my);
+      }
+      F[t * P.m + row] = mx - kx;
+      F[t * P.m + nf + row] = my - ky;
+    }
+  } else if (row < nf + P.nv) {
+    const int64_t v = row - nf;
+    double a = 0.0;
+    for (int32_t p = btaptr[v]; p < btaptr[v + 1]; ++p) {
+      const int32_t j = btacol[p];
+      a = fma(btax[p], un[j], fma(btay[p], un[np2 + j], a));
+    }
+    for (int t = 0; t < P.s; ++t) F[t * P.m + 2 * nf + v] = -a;
+  }
+}
+
+cudaError_t launch_stage_rhs_full(Ctx& C, const double* un_all, const double* pn, const double* f,
+                                  double* F) {
+  Level& L = C.L.back();
+  RhsParams P;
+  P.s = C.s;
+  P.nf = L.nf;
+  P.nv = L.nv;
+  P.np2 = L.np2;
+  P.m = L.m;
+  P.aptr = L.mall.ptr;
+  P.acol = L.mall.col;
+  P.Mall = L.mall.v[0];
+  P.vptr = L.vel.ptr;
+  P.vcol = L.vel.col;
+  P.K = L.vel.v[1];
+  P.bptr = L.b.ptr;
+  P.bcol = L.b.col;
+  P.Bx = L.b.v[0];
+  P.By = L.b.v[1];
+  P.btptr = L.bt.ptr;
+  P.btcol = L.bt.col;
+  P.BTx = L.bt.v[0];
+  P.BTy = L.bt.v[1];
+  const int64_t rows = L.nf + L.nv;
+  k_stage_rhs_full<<<(unsigned)((rows + 255) / 256), 256, 0, C.stream>>>(
+      P, L.btall.ptr, L.btall.col, L.btall.v[0], L.btall.v[1], L.mall.v[1], un_all, pn, f, F);
+  return cudaGetLastError();
+}
+
 __global__ void k_advance(int s, int64_t nu_, int64_t np_, int64_t m, double b0, double b1,
                           double b2, const double* __restrict__ k, double* __restrict__ un,
                           double* __restrict__ pn) {

@@ -79,6 +79,7 @@ _SIGS = {
     "irkmg_setup": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(Tableau), ct.c_double, ct.c_double,
                                ct.POINTER(Options), ct.POINTER(_P)]),
     "irkmg_update": (ct.c_int, [_P, ct.c_double, ct.c_double]),
+    "irkmg_set_wind": (ct.c_int, [_P, _P]),
     "irkmg_level_info_get": (ct.c_int, [_P, ct.c_int, ct.POINTER(LevelInfo)]),
     "irkmg_p2_coords": (ct.c_int, [_P, ct.c_int, _P]),
     "irkmg_free_nodes": (ct.c_int, [_P, ct.c_int, _P]),
@@ -96,6 +97,10 @@ _SIGS = {
     "irkmg_adjoint_solve": (ct.c_int, [_P, _P, _P, ct.POINTER(Stats)]),
     "irkmg_stage_rhs": (ct.c_int, [_P, _P, _P, _P, _P]),
     "irkmg_advance": (ct.c_int, [_P, _P, _P, _P]),
+    "irkmg_stage_rhs_full": (ct.c_int, [_P, _P, _P, _P, _P]),
+    "irkmg_batch_create": (ct.c_int, [ct.c_int, ct.POINTER(_P), ct.POINTER(_P)]),
+    "irkmg_batch_solve": (ct.c_int, [_P, ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(Stats)]),
+    "irkmg_batch_destroy": (None, [_P]),
     "irkmg_forcing_load": (ct.c_int, [_P, _P, _P]),
     "irkmg_step": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(Stats)]),
     "irkmg_adjoint_step": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(ct.c_double),
@@ -228,6 +233,18 @@ def irkmg_update(ctx, dt, nu):
     _check(lib().irkmg_update(ctx.handle, float(dt), float(nu)))
 
 
+def irkmg_set_wind(ctx, wind):
+    """wind: host array [np2, 2] at the finest P2 nodes, or None for Stokes."""
+    if wind is None:
+        _check(lib().irkmg_set_wind(ctx.handle, None))
+        return
+    w = np.ascontiguousarray(wind, dtype=np.float64)
+    if w.size != 2 * ctx.finest["np2"]:
+        raise ValueError("wind: expected np2 x 2 values")
+    ctx._keep.append(w)
+    _check(lib().irkmg_set_wind(ctx.handle, w.ctypes.data))
+
+
 def irkmg_p2_coords(ctx, level=-1):
     level %= ctx.nlevels
     out = np.zeros((ctx.levels[level]["np2"], 2))
@@ -338,6 +355,58 @@ def irkmg_advance(ctx, k, un, pn):
     L = ctx.finest
     _check(lib().irkmg_advance(ctx.handle, _dptr(k, L["N"], "k"), _dptr(un, 2 * L["nf"], "un"),
                                _dptr(pn, L["nv"], "pn")))
+
+
+def irkmg_stage_rhs_full(ctx, un_all, pn, f, F):
+    """Stage RHS with u^n at every P2 node (boundary values included)."""
+    L = ctx.finest
+    _check(lib().irkmg_stage_rhs_full(ctx.handle, _dptr(un_all, 2 * L["np2"], "un_all"),
+                                      _dptr(pn, L["nv"], "pn"), _dptr(f, ctx.s * 2 * L["np2"], "f"),
+                                      _dptr(F, L["N"], "F")))
+
+
+class Batch:
+    """Owns an irkmg_batch over caller-owned contexts (which must outlive it)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (_P * len(self.contexts))(*[c.handle for c in self.contexts])
+        h = _P()
+        _check(lib().irkmg_batch_create(len(self.contexts), arr, ct.byref(h)))
+        self.handle = h
+
+    def solve(self, Fs, ks, raise_on_noconv=False):
+        n = len(self.contexts)
+        F = (_P * n)(*[_dptr(F_, c.N(), "F").value for F_, c in zip(Fs, self.contexts)])
+        K = (_P * n)(*[_dptr(k_, c.N(), "k").value for k_, c in zip(ks, self.contexts)])
+        st = (Stats * n)()
+        rc = lib().irkmg_batch_solve(self.handle, F, K, st)
+        if not (rc == IRKMG_ENOCONV and not raise_on_noconv):
+            _check(rc)
+        return [x.as_dict() for x in st]
+
+    def close(self):
+        if self.handle:
+            lib().irkmg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def irkmg_batch_create(contexts):
+    return Batch(contexts)
+
+
+def irkmg_batch_solve(batch, Fs, ks, raise_on_noconv=False):
+    return batch.solve(Fs, ks, raise_on_noconv)
+
+
+def irkmg_batch_destroy(batch):
+    batch.close()
 
 
 def irkmg_forcing_load(ctx, theta, g):

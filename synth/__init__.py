@@ -10,7 +10,8 @@ derives anything from the other.
 import numpy as np
 
 __all__ = ["square_mesh", "mms_velocity", "mms_pressure", "mms_forcing",
-           "splitmix64", "uniform01", "normal", "random_vector"]
+           "splitmix64", "uniform01", "normal", "random_vector", "wind_coefficients",
+           "wind_field", "lid_velocity", "oseen_batch"]
 
 
 def square_mesh(n):
@@ -130,3 +131,47 @@ def normal(seed, count, offset=0):
 def random_vector(seed, count):
     """Seeded test vector with entries uniform in [-1, 1)."""
     return 2.0 * uniform01(seed, count) - 1.0
+
+
+# ---------------------------------------------------------------------------
+# Lid-driven cavity with a frozen wind (Oseen linearisation inputs)
+# ---------------------------------------------------------------------------
+def wind_coefficients(seed, kmax=4):
+    """a_kl ~ N(0,1)/(k^2+l^2), k, l = 1..kmax (row-major), from SplitMix64."""
+    z = normal(seed, kmax * kmax)
+    k = np.arange(1, kmax + 1)
+    return (z.reshape(kmax, kmax) / (k[:, None] ** 2 + k[None, :] ** 2))
+
+
+def wind_field(x, y, a):
+    """w = curl(psi), psi = sum a_kl sin(k pi x) sin(l pi y): w = (dpsi/dy, -dpsi/dx).
+    Divergence-free and tangential-free on the unit square boundary."""
+    kmax = a.shape[0]
+    wx = np.zeros_like(x, dtype=np.float64)
+    wy = np.zeros_like(x, dtype=np.float64)
+    for k in range(1, kmax + 1):
+        for l in range(1, kmax + 1):
+            c = a[k - 1, l - 1]
+            wx += c * l * np.pi * np.sin(k * np.pi * x) * np.cos(l * np.pi * y)
+            wy -= c * k * np.pi * np.cos(k * np.pi * x) * np.sin(l * np.pi * y)
+    return wx, wy
+
+
+def lid_velocity(x, y):
+    """u = (1, 0) on the lid y = 1 (corners excluded), 0 elsewhere."""
+    on = (y == 1.0) & (x > 0.0) & (x < 1.0)
+    return on.astype(np.float64), np.zeros_like(x, dtype=np.float64)
+
+
+def oseen_batch(seed, count, sizes=(32, 64, 128, 256)):
+    """Seeded description of a batch of independent Oseen stage systems:
+    per system the mesh size n (uniform over `sizes`), Re ~ U[100, 1000]
+    (nu = 1/Re), dt log-uniform in [1e-3, 1e-1] and a wind seed."""
+    u = uniform01(seed, 4 * count).reshape(count, 4)
+    out = []
+    for i in range(count):
+        n = sizes[min(int(u[i, 0] * len(sizes)), len(sizes) - 1)]
+        re = 100.0 + 900.0 * u[i, 1]
+        dt = 10.0 ** (-3.0 + 2.0 * u[i, 2])
+        out.append({"n": n, "nu": 1.0 / re, "dt": dt, "wind_seed": int(seed * 1000 + i)})
+    return out
