@@ -49,9 +49,14 @@ FALLBACK_HBM = 6800.0
 # (nominal 1.25 TFLOP/s; the project's FMA probe measured 1.251).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
-# DRAM traffic per launch of the finest-level Vanka kernel from an ncu capture,
-# keyed by the hash of the kernel source it was taken with (None until taken).
-NCU_TRAFFIC = {}
+# DRAM traffic of the finest-level Vanka kernel from an ncu capture, as the
+# ratio (dram__bytes_read + dram__bytes_write) / algorithmic bytes of the
+# captured launch, keyed by kernel and by the hash of the kernel source it was
+# taken with; reported as ratio x algorithmic bytes per launch, null once the
+# source has changed.  Captures: profiles/vanka_apply_128x128.md.
+NCU_TRAFFIC = {
+    ("k_vanka_apply", "c01e3c9fe148"): 0.97,
+}
 
 
 def kernel_source_hash():
@@ -392,10 +397,12 @@ def run_ours(args, wl, rank, world, local_rank):
         hbm, hbm_kind = peaks()
         van_gbs = trace["vanka_bytes"] / (trace["vanka_ms"] * 1e-3) / 1e9 if trace["vanka_ms"] else None
         op_gbs = trace["op_bytes"] / (trace["op_ms"] * 1e-3) / 1e9 if trace["op_ms"] else None
+        op_tf = trace["op_flops"] / (trace["op_ms"] * 1e-3) / 1e12 if trace["op_ms"] else None
         nvl = max(trace["vanka_launches"], 1)
         h = kernel_source_hash()
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply"}[ctx.finest["apply_kernel"]]
-        traffic = NCU_TRAFFIC.get(h)
+        ratio = NCU_TRAFFIC.get((kname, h))
+        traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
         value = ms * 1e-3 / (args.steps * world)
         van_tf = trace["vanka_flops"] / (trace["vanka_ms"] * 1e-3) / 1e12 if trace["vanka_ms"] else None
         common = {"kernel": kname + " (finest level)", "traffic": traffic,
@@ -428,9 +435,10 @@ def run_ours(args, wl, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iters_per_solve": iters, "rel_residual": max(resid), "setup_s": setup_s,
             "roofline": roofline,
-            "roofline_spmv": {"bound": "hbm", "kernel": "k_residual (finest level)",
-                              "achieved": op_gbs, "peak": hbm, "unit": "GB/s",
-                              "frac": op_gbs / hbm if op_gbs else None,
+            "roofline_spmv": {"bound": "alu", "kernel": "k_residual_sell (finest level)",
+                              "achieved": op_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": op_tf / FP64_PEAK_TFLOPS if op_tf else None,
+                              "hbm_gbs": op_gbs, "hbm_frac": op_gbs / hbm if op_gbs else None,
                               "launches": trace["op_launches"],
                               "avg_launch_ms": trace["op_ms"] / max(trace["op_launches"], 1)},
             "gpu_launches": trace["launches"],

@@ -306,6 +306,8 @@ typedef struct {
   int64_t op_launches;
   double op_ms, op_bytes;
   double vanka_flops;      /* 2·n_p^2 per patch applied in the timed Vanka launches */
+  double op_flops;         /* 2·(4s·nnz(vel) + 2s·(nnz(B) + nnz(Bᵀ)) + 2s²·n_f + s²·n_v)
+                              per timed operator launch                              */
 } irkmg_trace;
 
 /* Reset the counters; on = 1 also starts event timing.  Never fails on a valid ctx. */

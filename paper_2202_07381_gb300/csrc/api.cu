@@ -175,7 +175,7 @@ int op(Ctx& C, Level& L, const double* F, const double* x, double* r, int tr) {
   const bool timed = C.trace_on && &L == &C.L.back();
   cudaEvent_t a = nullptr, b = nullptr;
   if (timed) {
-    int rc = trace_pair(C, 1, L.op_bytes - (F ? 0.0 : 8.0 * L.N), &a, &b);
+    int rc = trace_pair(C, 1, L.op_bytes - (F ? 0.0 : 8.0 * L.N), &a, &b, L.op_flops);
     if (rc) return rc;
     CK(cudaEventRecord(a, C.stream));
   }
@@ -679,6 +679,11 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
       level_trace_bytes(*C, L);
     }
     L.op_bytes = 20.0 * (double)L.vel.nnz + 20.0 * (double)(L.b.nnz + L.bt.nnz) + 24.0 * (double)L.N;
+    {
+      const double s = (double)C->s;
+      L.op_flops = 2.0 * (4.0 * s * (double)L.vel.nnz + 2.0 * s * (double)(L.b.nnz + L.bt.nnz) +
+                          2.0 * s * s * (double)L.nf + s * s * (double)L.nv);
+    }
   }
   {
     Level& Lf = C->L[nl - 1];
@@ -1335,6 +1340,7 @@ int irkmg_trace_read(irkmg_ctx* C, irkmg_trace* out) {
       out->op_launches++;
       out->op_ms += ms;
       out->op_bytes += C->ev_bytes[k];
+      out->op_flops += C->ev_flops[k];
     }
   }
   C->ev_used = 0;

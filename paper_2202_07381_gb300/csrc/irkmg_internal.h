@@ -116,7 +116,7 @@ struct Level {
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
   // algorithmic bytes for tracing
   std::vector<double> colour_bytes, colour_flops;
-  double op_bytes = 0.0;
+  double op_bytes = 0.0, op_flops = 0.0;
 };
 
 struct Ctx {

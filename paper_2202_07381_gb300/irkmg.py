@@ -65,7 +65,7 @@ class LevelInfo(ct.Structure):
 class Trace(ct.Structure):
     _fields_ = [("launches", ct.c_int64), ("vanka_launches", ct.c_int64), ("vanka_ms", ct.c_double),
                 ("vanka_bytes", ct.c_double), ("op_launches", ct.c_int64), ("op_ms", ct.c_double),
-                ("op_bytes", ct.c_double), ("vanka_flops", ct.c_double)]
+                ("op_bytes", ct.c_double), ("vanka_flops", ct.c_double), ("op_flops", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
