@@ -51,11 +51,11 @@ class Hierarchy:
             L.mesh = m
             L.ops = fem.assemble(m, nu=nu, wind=winds[l])
             L.J = stage.stage_matrix(L.ops, self.A, dt)
-            L.m = 2 * m.nf + m.nv
+            L.m = m.dim * m.nf + m.nv
             L.N = self.s * L.m
             if l > 0:
                 Pu, Pp = transfer.prolongation(meshes[l - 1], m)
-                L.P = transfer.stage_prolongation(Pu, Pp, self.s)
+                L.P = transfer.stage_prolongation(Pu, Pp, self.s, m.dim)
                 if build_patches:
                     L.dofs = vanka.all_patch_dofs(m, self.s)
                     L.vanka = vanka.Vanka(L.J, L.dofs)
@@ -66,7 +66,7 @@ class Hierarchy:
         L = self.levels[0]
         Nmat = np.zeros((L.N, self.s))
         for t in range(self.s):
-            Nmat[t * L.m + 2 * L.mesh.nf: (t + 1) * L.m, t] = 1.0
+            Nmat[t * L.m + L.mesh.dim * L.mesh.nf: (t + 1) * L.m, t] = 1.0
         Jd = L.J.toarray()
         self.coarse_bordered = np.block([[Jd, Nmat], [Nmat.T, np.zeros((self.s, self.s))]])
 
@@ -104,7 +104,7 @@ class Hierarchy:
         L = self.levels[-1 if level is None else level]
         mask = np.zeros(L.N, dtype=bool)
         for t in range(self.s):
-            mask[t * L.m + 2 * L.mesh.nf: (t + 1) * L.m] = True
+            mask[t * L.m + L.mesh.dim * L.mesh.nf: (t + 1) * L.m] = True
         return mask
 
     def project_pressure(self, x, level=None):
@@ -113,6 +113,6 @@ class Hierarchy:
         L = self.levels[-1 if level is None else level]
         y = x.copy()
         for t in range(self.s):
-            sl = slice(t * L.m + 2 * L.mesh.nf, (t + 1) * L.m)
+            sl = slice(t * L.m + L.mesh.dim * L.mesh.nf, (t + 1) * L.m)
             y[sl] -= y[sl].mean()
         return y

@@ -12,16 +12,17 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def velocity_block(S):
-    """Scalar P2 block S applied to both velocity components."""
-    return sp.block_diag([S, S], format="csr")
+def velocity_block(S, dim=2):
+    """Scalar P2 block S applied to every velocity component."""
+    return sp.block_diag([S] * dim, format="csr")
 
 
 def single_stage_blocks(ops):
-    """Return (Mt, St): Mt = [[M2, 0], [0, 0]], St = [[K2, B], [B^T, 0]]
-    with M2 = diag(M, M), K2 = diag(K, K), as sparse matrices of size m x m."""
-    M2 = velocity_block(ops["M"])
-    K2 = velocity_block(ops["K"])
+    """Return (Mt, St): Mt = [[Md, 0], [0, 0]], St = [[Kd, B], [B^T, 0]]
+    with Md = diag(M, ..., M), Kd = diag(K, ..., K) (d copies), size m x m."""
+    dim = ops.get("dim", 2)
+    M2 = velocity_block(ops["M"], dim)
+    K2 = velocity_block(ops["K"], dim)
     B = ops["B"]
     nv = B.shape[1]
     Z = sp.csr_matrix((nv, nv))
@@ -40,18 +41,19 @@ def stage_matrix(ops, A, dt):
 def stage_rhs(ops, un, pn, f_all):
     """F_i = [M f_i - K u^n - B p^n; -B^T u^n].
 
-    un: free velocity [2 nf]; pn: [nv]; f_all: [s, 2, np2] forcing interpolant at
-    every P2 node (M f uses boundary columns too, since f need not vanish there).
+    un: free velocity [d nf]; pn: [nv]; f_all: [s, d, np2] forcing interpolant
+    at every P2 node (M f uses boundary columns too, since f need not vanish
+    there).
     """
-    nf = ops["M"].shape[0]
+    dim = ops.get("dim", 2)
     s = f_all.shape[0]
-    K2 = velocity_block(ops["K"])
+    K2 = velocity_block(ops["K"], dim)
     B = ops["B"]
     base_u = -(K2 @ un) - B @ pn
     base_p = -(B.T @ un)
     out = []
     for i in range(s):
-        mf = np.concatenate([ops["Mall"] @ f_all[i, 0], ops["Mall"] @ f_all[i, 1]])
+        mf = np.concatenate([ops["Mall"] @ f_all[i, c] for c in range(dim)])
         out.append(np.concatenate([mf + base_u, base_p]))
     return np.concatenate(out)
 

@@ -4,28 +4,30 @@ velocity component) and P_p the P1 interpolation; for s stages it is
 I_s (x) P, and restriction is its transpose.
 
 P_u[f, c] is the value of coarse P2 basis function c at fine node f, found by
-locating each fine node in its parent cell (child cell 4c+k has parent c) and
-evaluating the parent's six basis functions at the node's barycentric
-coordinates.  Only free (non-Dirichlet) nodes are kept: coarse Dirichlet basis
-functions carry zero coefficients.
+locating each fine node in its parent cell (child cell 4c+k, or 8c+k in 3D,
+has parent c) and evaluating the parent's P2 basis functions at the node's
+barycentric coordinates.  Only free (non-Dirichlet) nodes are kept: coarse
+Dirichlet basis functions carry zero coefficients.
 """
 import numpy as np
 import scipy.sparse as sp
 
 
 def _barycentric(coords_parent, pts):
-    x0, x1, x2 = coords_parent[:, 0], coords_parent[:, 1], coords_parent[:, 2]
-    d1, d2, r = x1 - x0, x2 - x0, pts - x0
-    det = d1[:, 0] * d2[:, 1] - d1[:, 1] * d2[:, 0]
-    l1 = (r[:, 0] * d2[:, 1] - r[:, 1] * d2[:, 0]) / det
-    l2 = (d1[:, 0] * r[:, 1] - d1[:, 1] * r[:, 0]) / det
-    return np.stack([1.0 - l1 - l2, l1, l2], axis=1)
+    """Barycentric coordinates of pts in the parent simplices (by solving
+    [x_1 - x_0 ... x_d - x_0] l = p - x_0)."""
+    d = pts.shape[1]
+    Jm = np.stack([coords_parent[:, i + 1] - coords_parent[:, 0] for i in range(d)], axis=2)
+    lam = np.linalg.solve(Jm, (pts - coords_parent[:, 0])[..., None])[..., 0]
+    return np.concatenate([1.0 - lam.sum(axis=1, keepdims=True), lam], axis=1)
 
 
 def _p2_values(lam):
-    l0, l1, l2 = lam[:, 0], lam[:, 1], lam[:, 2]
-    return np.stack([l0 * (2 * l0 - 1), l1 * (2 * l1 - 1), l2 * (2 * l2 - 1),
-                     4 * l0 * l1, 4 * l1 * l2, 4 * l0 * l2], axis=1)
+    from .mesh import LOCAL_EDGES
+    d = lam.shape[1] - 1
+    V = [lam[:, i] * (2 * lam[:, i] - 1) for i in range(d + 1)]
+    E = [4 * lam[:, a] * lam[:, b] for a, b in LOCAL_EDGES[d]]
+    return np.stack(V + E, axis=1)
 
 
 def _unique_entries(rows, cols, vals, shape):
@@ -46,24 +48,26 @@ def prolongation(coarse, fine):
 def prolongation_full(coarse, fine):
     """Interpolation between all P2 nodes (np2_fine x np2_coarse) and all
     vertices (P1)."""
-    parent = np.arange(fine.nc) // 4
-    pc = coarse.coords[coarse.cells[parent]]            # [ncf, 3, 2]
+    kids = 2 ** fine.dim
+    parent = np.arange(fine.nc) // kids
+    pc = coarse.coords[coarse.cells[parent]]            # [ncf, d+1, d]
+    nn = fine.cell_p2.shape[1]
     rows, cols, vals = [], [], []
-    for a in range(6):
+    for a in range(nn):
         fnode = fine.cell_p2[:, a]
         lam = _barycentric(pc, fine.p2_coords[fnode])
         phi = _p2_values(lam)
-        for b in range(6):
+        for b in range(nn):
             rows.append(fnode)
             cols.append(coarse.cell_p2[parent, b])
             vals.append(phi[:, b])
     P2 = _unique_entries(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals),
                          (fine.np2, coarse.np2))
     rows, cols, vals = [], [], []
-    for a in range(3):
+    for a in range(fine.dim + 1):
         fv = fine.cells[:, a]
         lam = _barycentric(pc, fine.coords[fv])
-        for b in range(3):
+        for b in range(fine.dim + 1):
             rows.append(fv)
             cols.append(coarse.cells[parent, b])
             vals.append(lam[:, b])
@@ -72,7 +76,7 @@ def prolongation_full(coarse, fine):
     return P2, Pp
 
 
-def stage_prolongation(Pu, Pp, s):
-    """I_s (x) diag(Pu, Pu, Pp)."""
-    one = sp.block_diag([Pu, Pu, Pp], format="csr")
+def stage_prolongation(Pu, Pp, s, dim=2):
+    """I_s (x) diag(Pu, ..., Pu, Pp) (dim copies of Pu)."""
+    one = sp.block_diag([Pu] * dim + [Pp], format="csr")
     return sp.kron(sp.identity(s), one, format="csr")

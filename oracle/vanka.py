@@ -3,7 +3,7 @@
 Patch S_v (one per mesh vertex v): every velocity degree of freedom in the
 closure of the cells touching v, plus the single pressure DoF at v, for every
 stage.  Order inside S_v: stage by stage; inside a stage the free velocity DoFs
-in ascending global index (all u_x, then all u_y), then p_v.
+in ascending global index (all u_x, then all u_y [, then all u_z]), then p_v.
 
 One relaxation step (the additive update of Section 4.2):
     k <- k + omega * sum_v R_v^T (R_v J R_v^T)^{-1} R_v (F - J k),
@@ -42,9 +42,9 @@ def patch_nodes(mesh):
 
 def patch_dofs(mesh, nodes_v, v, s):
     """Global stage-vector indices of S_v (see module docstring)."""
-    nf, nv = mesh.nf, mesh.nv
-    m = 2 * nf + nv
-    one = np.concatenate([nodes_v, nf + nodes_v, [2 * nf + v]])
+    nf, nv, d = mesh.nf, mesh.nv, mesh.dim
+    m = d * nf + nv
+    one = np.concatenate([c * nf + nodes_v for c in range(d)] + [[d * nf + v]])
     return np.concatenate([t * m + one for t in range(s)]).astype(np.int64)
 
 

@@ -9,7 +9,7 @@ derives anything from the other.
 """
 import numpy as np
 
-__all__ = ["square_mesh", "mms_velocity", "mms_pressure", "mms_forcing",
+__all__ = ["square_mesh", "cube_mesh", "mms3_velocity", "mms3_pressure", "mms3_forcing", "mms_velocity", "mms_pressure", "mms_forcing",
            "splitmix64", "uniform01", "normal", "random_vector", "wind_coefficients",
            "wind_field", "lid_velocity", "oseen_batch"]
 
@@ -175,3 +175,75 @@ def oseen_batch(seed, count, sizes=(32, 64, 128, 256)):
         dt = 10.0 ** (-3.0 + 2.0 * u[i, 2])
         out.append({"n": n, "nu": 1.0 / re, "dt": dt, "wind_seed": int(seed * 1000 + i)})
     return out
+
+
+# ---------------------------------------------------------------------------
+# 3D inputs: Kuhn (6-tetrahedra-per-cube) mesh of the unit cube and the
+# manufactured solution u = curl(psi (1,1,1)), psi = sin^2(pi x) sin^2(pi y)
+# sin^2(pi z), p = sin(2 pi x) cos(2 pi y) cos(2 pi z).
+# ---------------------------------------------------------------------------
+def cube_mesh(n):
+    """Unit cube, n^3 cubes, each cut into the 6 Kuhn tetrahedra: for every
+    permutation sigma of the axes (lexicographic order), the tetrahedron with
+    vertices 0, e_s1, e_s1 + e_s2, (1,1,1) (corner offsets of the cube).
+    Vertex (i,j,k) has id i + (n+1) (j + (n+1) k).  bnd = 1 on the boundary."""
+    import itertools
+    n = int(n)
+    r = np.arange(n + 1)
+    K, J, I = np.meshgrid(r, r, r, indexing="ij")
+    coords = np.stack([I.ravel() / n, J.ravel() / n, K.ravel() / n], axis=1).astype(np.float64)
+    vid = lambda i, j, k: i + (n + 1) * (j + (n + 1) * k)
+    cells = []
+    perms = list(itertools.permutations(range(3)))
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                base = np.array([i, j, k])
+                for sg in perms:
+                    p = base.copy()
+                    tet = [vid(*p)]
+                    for ax in sg:
+                        p = p.copy()
+                        p[ax] += 1
+                        tet.append(vid(*p))
+                    cells.append(tet)
+    cells = np.asarray(cells, dtype=np.int64)
+    bi, bj, bk = I.ravel(), J.ravel(), K.ravel()
+    bnd = ((bi == 0) | (bi == n) | (bj == 0) | (bj == n) | (bk == 0) | (bk == n)).astype(np.uint8)
+    return coords, cells, bnd
+
+
+def _s3(t):
+    """S = sin^2(pi t) and its first three derivatives."""
+    pi = np.pi
+    return (np.sin(pi * t) ** 2, pi * np.sin(2 * pi * t), 2 * pi ** 2 * np.cos(2 * pi * t),
+            -4 * pi ** 3 * np.sin(2 * pi * t))
+
+
+def mms3_velocity(x, y, z):
+    """u = (psi_y - psi_z, psi_z - psi_x, psi_x - psi_y); zero on the boundary."""
+    Sx, Sy, Sz = _s3(x), _s3(y), _s3(z)
+    px = Sx[1] * Sy[0] * Sz[0]
+    py = Sx[0] * Sy[1] * Sz[0]
+    pz = Sx[0] * Sy[0] * Sz[1]
+    return py - pz, pz - px, px - py
+
+
+def mms3_pressure(x, y, z):
+    return np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * np.cos(2 * np.pi * z)
+
+
+def mms3_forcing(x, y, z, nu=1.0):
+    """f = -nu Lap(u) + grad p with Lap(u) = curl(Lap(psi) (1,1,1))."""
+    Sx, Sy, Sz = _s3(x), _s3(y), _s3(z)
+    # d/dx, d/dy, d/dz of Lap(psi) = S''SS + SS''S + SSS''
+    Lx = Sx[3] * Sy[0] * Sz[0] + Sx[1] * Sy[2] * Sz[0] + Sx[1] * Sy[0] * Sz[2]
+    Ly = Sx[2] * Sy[1] * Sz[0] + Sx[0] * Sy[3] * Sz[0] + Sx[0] * Sy[1] * Sz[2]
+    Lz = Sx[2] * Sy[0] * Sz[1] + Sx[0] * Sy[2] * Sz[1] + Sx[0] * Sy[0] * Sz[3]
+    lap = (Ly - Lz, Lz - Lx, Lx - Ly)
+    pi = np.pi
+    s2x, c2x = np.sin(2 * pi * x), np.cos(2 * pi * x)
+    s2y, c2y = np.sin(2 * pi * y), np.cos(2 * pi * y)
+    s2z, c2z = np.sin(2 * pi * z), np.cos(2 * pi * z)
+    gp = (2 * pi * c2x * c2y * c2z, -2 * pi * s2x * s2y * c2z, -2 * pi * s2x * c2y * s2z)
+    return tuple(-nu * lap[d] + gp[d] for d in range(3))
