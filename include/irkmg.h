@@ -16,9 +16,9 @@
  *     (Section 4.2), damped or Chebyshev-accelerated (Section 5.1).
  *
  * Vector layout (every d_* vector of a level): stage-major, length
- * N = s·(2·nf + nv); inside a stage the u_x block over the nf free
- * (non-Dirichlet) P2 nodes, then the u_y block, then the pressure block over
- * all nv vertices.  This is the ordering of Section 3.1 (stages consecutive,
+ * N = s·(d·nf + nv); inside a stage the u_x block over the nf free
+ * (non-Dirichlet) P2 nodes, then the u_y block (then u_z in 3D), then the
+ * pressure block over all nv vertices.  This is the ordering of Section 3.1 (stages consecutive,
  * each (k_u, k_p) pair kept together).
  *
  * Numbering: mesh edges are the sorted vertex pairs in lexicographic order;
@@ -61,9 +61,13 @@ extern "C" {
 typedef struct irkmg_ctx irkmg_ctx;
 
 /* Coarsest mesh (Section 4.1: the hierarchy is its uniform refinements).
- * Triangles only (dim = 2).  coords: nverts·2 doubles (x, y per vertex);
- * cells: ncells·3 vertex ids; bnd_vertex: 1 on Dirichlet (no-slip) vertices.
- * An edge is Dirichlet iff it lies on the boundary and both ends are flagged. */
+ * dim = 2: triangles (red refinement); dim = 3: tetrahedra (Bey refinement).
+ * coords: nverts·dim doubles; cells: ncells·(dim+1) vertex ids; bnd_vertex: 1
+ * on Dirichlet (no-slip) vertices.  An edge is Dirichlet iff it lies on a
+ * boundary facet and both ends are flagged.  In 3D, vectors hold u_x, u_y and
+ * u_z blocks before the pressure block; patches above 160 DoFs are factored
+ * by blocked LU (their transposed solves, the Oseen wind and the adjoint
+ * entry points return IRKMG_ENOTIMPL in 3D). */
 typedef struct {
   int dim;
   int64_t nverts, ncells;
@@ -118,8 +122,10 @@ typedef struct {
   int64_t npatch, ncolours;/* Vanka patches (one per vertex), colours               */
   int64_t max_patch_dofs;  /* largest patch size s·(2·nodes + 1)                    */
   int64_t factor_bytes;    /* bytes of stored patch blocks (inverse + index list)   */
-  int64_t apply_kernel;    /* Vanka apply kernel in use: 1 TMA-staged, 2 warp-per-patch */
+  int64_t apply_kernel;    /* Vanka apply kernel in use: 1 TMA-staged, 2 warp-per-patch,
+                              3 blocked-LU solves (patches above 160 DoFs, 3D)       */
   double apply_ms[2];      /* autotuner: one sweep with kernel 1 / kernel 2 (0 if untimed) */
+  int64_t dim;             /* 2 or 3                                                */
 } irkmg_level_info;
 
 /* ---- set-up -------------------------------------------------------------- */

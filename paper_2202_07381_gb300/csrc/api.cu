@@ -205,7 +205,7 @@ void level_trace_bytes(Ctx& C, Level& L) {
 
 // --- patches: maps, colouring, ordering, inverses (Section 4.2) -----------
 int build_patches(Ctx& C, Level& L) {
-  const int maxnodes = 64;
+  const int maxnodes = 96;
   int rc;
   if ((rc = upload(C, &L.d_cells, L.mesh.cells))) return rc;
   if ((rc = upload(C, &L.d_cell_edges, L.mesh.cell_edges))) return rc;
@@ -275,20 +275,25 @@ int build_patches(Ctx& C, Level& L) {
   // Each ordered patch owns one 16-byte-aligned block: its n_p x n_p inverse
   // (column-major, padded to 16 bytes) followed by its n_p global DoF indices
   // (int32, padded to 16 bytes), so one bulk copy brings both.
+  // Large patches (3D) keep LU factors and pivots instead of an inverse.
   std::vector<int64_t> off(L.nv + 1, 0);
   std::vector<int32_t> npv(L.nv);
   L.max_np = 0;
   const int64_t w = C.opt.patch_precision == 64 ? 8 : 4;
   for (int64_t i = 0; i < L.nv; ++i) {
     const int32_t v = order[i];
-    const int64_t np = (int64_t)C.s * (2 * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
+    const int64_t np = (int64_t)C.s * (L.dim * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
     L.max_np = std::max<int>(L.max_np, (int)np);
     npv[i] = (int32_t)np;
-    const int64_t xbytes = (np * np * w + 15) / 16 * 16, gbytes = (np * 4 + 15) / 16 * 16;
-    off[i + 1] = off[i] + (xbytes + gbytes) / w;
   }
-  if (L.max_np > 160)
-    return fail(IRKMG_ENOTIMPL, "patches above 160 DoFs need the blocked patch factorisation");
+  if (L.max_np > kMaxBigNp)
+    return fail(IRKMG_ENOTIMPL, "patches above " + std::to_string(kMaxBigNp) + " DoFs");
+  L.big = L.max_np > kMaxSmallNp;
+  for (int64_t i = 0; i < L.nv; ++i) {
+    const int64_t np = npv[i];
+    const int64_t xbytes = (np * np * w + 15) / 16 * 16, gbytes = (np * 4 + 15) / 16 * 16;
+    off[i + 1] = off[i] + (xbytes + gbytes * (L.big ? 2 : 1)) / w;
+  }
   L.fac_elems = off[L.nv];
   if ((rc = upload(C, &L.d_order, order))) return rc;
   if ((rc = upload(C, &L.d_np, npv))) return rc;
@@ -309,7 +314,10 @@ int build_patches(Ctx& C, Level& L) {
 }
 
 int factor_level(Ctx& C, Level& L) {
-  CK(launch_patch_invert(C, L, C.opt.patch_precision));
+  if (L.big)
+    CK(launch_patch_lu_big(C, L));
+  else
+    CK(launch_patch_invert(C, L, C.opt.patch_precision));
   return IRKMG_OK;
 }
 
@@ -355,6 +363,10 @@ int tune_apply(Ctx& C) {
   int rc = IRKMG_OK;
   for (size_t l = 1; l < C.L.size() && rc == IRKMG_OK; ++l) {
     Level& L = C.L[l];
+    if (L.big) {
+      L.apply_kernel = 3;
+      continue;
+    }
     const bool fits = vanka_staged_fits(C, L);
     if (C.opt.apply_variant == 1 || C.opt.apply_variant == 2) {
       L.apply_kernel = (C.opt.apply_variant == 1 && fits) ? 1 : 2;
@@ -394,6 +406,8 @@ int tune_apply(Ctx& C) {
 
 // --- smoothers and V-cycle -------------------------------------------------
 int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr) {
+  if (L.big && tr)
+    return fail(IRKMG_ENOTIMPL, "transposed patch solves of LU-factored (3D) patches");
   const bool timed = C.trace_on && &L == &C.L.back();
   for (int c = 0; c < L.ncolours; ++c) {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -402,7 +416,10 @@ int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int 
       if (rc) return rc;
       CK(cudaEventRecord(a, C.stream));
     }
-    CK(launch_vanka(C, L, c, r, out, scale, tr));
+    if (L.big)
+      CK(launch_vanka_lu(C, L, c, r, out, scale));
+    else
+      CK(launch_vanka(C, L, c, r, out, scale, tr));
     C.launches++;
     if (timed) CK(cudaEventRecord(b, C.stream));
   }
@@ -592,7 +609,10 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
 int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double nu,
              const irkmg_options* o) {
   if (!mesh || !tab || !o) return fail(IRKMG_EINVAL, "null argument");
-  if (mesh->dim != 2) return fail(IRKMG_ENOTIMPL, "only dim = 2 (triangles) is built");
+  if (mesh->dim != 2 && mesh->dim != 3)
+    return fail(IRKMG_ENOTIMPL, "dim must be 2 (triangles) or 3 (tetrahedra)");
+  if (mesh->dim == 3 && o->wind)
+    return fail(IRKMG_ENOTIMPL, "the Oseen wind is built for 2D meshes only");
   if (!mesh->coords || !mesh->cells || !mesh->bnd_vertex) return fail(IRKMG_EINVAL, "mesh arrays");
   if (tab->s < 1 || tab->s > 3 || !tab->A || !tab->b || !tab->c)
     return fail(IRKMG_EINVAL, "tableau: 1 <= s <= 3 and A, b, c required");
@@ -634,8 +654,9 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   int rc;
   const int nl = opt->nlevels;
   C->L.resize(nl);
+  C->dim = mesh->dim;
   std::string why = build_mesh(mesh->coords, mesh->cells, mesh->bnd_vertex, mesh->nverts,
-                               mesh->ncells, C->L[0].mesh);
+                               mesh->ncells, mesh->dim, C->L[0].mesh);
   if (!why.empty()) return fail(IRKMG_EINVAL, why);
   for (int l = 1; l < nl; ++l) {
     if (C->L[l - 1].mesh.np2 > (1LL << 30)) return fail(IRKMG_EINVAL, "hierarchy too large");
@@ -644,10 +665,11 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   if (opt->wind) C->wind.assign(opt->wind, opt->wind + 2 * C->L[nl - 1].mesh.np2);
   for (int l = 0; l < nl; ++l) {
     Level& L = C->L[l];
+    L.dim = C->dim;
     L.nv = L.mesh.nv;
     L.nf = L.mesh.nf;
     L.np2 = L.mesh.np2;
-    L.m = 2 * L.nf + L.nv;
+    L.m = L.dim * L.nf + L.nv;
     L.N = C->s * L.m;
   }
   if ((rc = assemble_all(*C))) return rc;
@@ -657,13 +679,13 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   for (int l = 0; l < nl; ++l) {
     Level& L = C->L[l];
     if ((rc = upload_csr(*C, L.vel, L.hops.vel, 3))) return rc;
-    if ((rc = upload_csr(*C, L.b, L.hops.b, 2))) return rc;
-    if ((rc = upload_csr(*C, L.bt, L.hops.bt, 2))) return rc;
+    if ((rc = upload_csr(*C, L.b, L.hops.b, L.dim))) return rc;
+    if ((rc = upload_csr(*C, L.bt, L.hops.bt, L.dim))) return rc;
     if ((rc = upload_sell(*C, L.svel, L.hops.vel, 3))) return rc;
-    if ((rc = upload_sell(*C, L.sb, L.hops.b, 2))) return rc;
-    if ((rc = upload_sell(*C, L.sbt, L.hops.bt, 2))) return rc;
+    if ((rc = upload_sell(*C, L.sb, L.hops.b, L.dim))) return rc;
+    if ((rc = upload_sell(*C, L.sbt, L.hops.bt, L.dim))) return rc;
     if (l == nl - 1 && (rc = upload_csr(*C, L.mall, L.hops.mall, 2))) return rc;
-    if (l == nl - 1 && (rc = upload_csr(*C, L.btall, L.hops.btall, 2))) return rc;
+    if (l == nl - 1 && (rc = upload_csr(*C, L.btall, L.hops.btall, L.dim))) return rc;
     if ((rc = dalloc(*C, &L.r, L.N))) return rc;
     if ((rc = dalloc(*C, &L.z, L.N))) return rc;
     if ((rc = dalloc(*C, &L.t, L.N))) return rc;
@@ -1027,19 +1049,21 @@ int irkmg_update(irkmg_ctx* C, double dt, double nu) {
   for (size_t l = 0; l < C->L.size(); ++l) {
     Level& L = C->L[l];
     if ((rc = refresh_csr_values(*C, L.vel, L.hops.vel, 3))) return rc;
-    if ((rc = refresh_csr_values(*C, L.b, L.hops.b, 2))) return rc;
-    if ((rc = refresh_csr_values(*C, L.bt, L.hops.bt, 2))) return rc;
+    if ((rc = refresh_csr_values(*C, L.b, L.hops.b, L.dim))) return rc;
+    if ((rc = refresh_csr_values(*C, L.bt, L.hops.bt, L.dim))) return rc;
     if ((rc = refresh_sell_values(*C, L.svel, L.hops.vel, 3))) return rc;
-    if ((rc = refresh_sell_values(*C, L.sb, L.hops.b, 2))) return rc;
-    if ((rc = refresh_sell_values(*C, L.sbt, L.hops.bt, 2))) return rc;
+    if ((rc = refresh_sell_values(*C, L.sb, L.hops.b, L.dim))) return rc;
+    if ((rc = refresh_sell_values(*C, L.sbt, L.hops.bt, L.dim))) return rc;
     if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.mall, L.hops.mall, 2))) return rc;
-    if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.btall, L.hops.btall, 2))) return rc;
+    if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.btall, L.hops.btall, L.dim)))
+      return rc;
   }
   return factor_all(*C);
 }
 
 int irkmg_set_wind(irkmg_ctx* C, const double* wind) {
   if (!C) return fail(IRKMG_EINVAL, "null ctx");
+  if (C->dim != 2 && wind) return fail(IRKMG_ENOTIMPL, "the Oseen wind is built for 2D meshes only");
   CK(C->stream ? cudaStreamSynchronize(C->stream) : cudaDeviceSynchronize());
   if (wind)
     C->wind.assign(wind, wind + 2 * C->L.back().np2);
@@ -1063,6 +1087,7 @@ int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) 
   info->max_patch_dofs = L.max_np;
   info->factor_bytes = L.fac_elems * (C->opt.patch_precision == 64 ? 8 : 4);
   info->apply_kernel = level > 0 ? L.apply_kernel : 0;
+  info->dim = L.dim;
   info->apply_ms[0] = L.apply_ms[1];
   info->apply_ms[1] = L.apply_ms[2];
   return IRKMG_OK;
@@ -1071,11 +1096,11 @@ int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) 
 int irkmg_p2_coords(const irkmg_ctx* C, int level, double* xy) {
   if (!level_ok(C, level) || !xy) return fail(IRKMG_EINVAL, "bad level");
   const HostMesh& m = C->L[level].mesh;
+  const int d = m.dim;
   std::copy(m.xy.begin(), m.xy.end(), xy);
   for (int64_t e = 0; e < m.ne; ++e) {
     const int32_t a = m.edges[2 * e], b = m.edges[2 * e + 1];
-    xy[2 * (m.nv + e)] = 0.5 * (m.xy[2 * a] + m.xy[2 * b]);
-    xy[2 * (m.nv + e) + 1] = 0.5 * (m.xy[2 * a + 1] + m.xy[2 * b + 1]);
+    for (int k = 0; k < d; ++k) xy[d * (m.nv + e) + k] = 0.5 * (m.xy[d * a + k] + m.xy[d * b + k]);
   }
   return IRKMG_OK;
 }
@@ -1190,6 +1215,7 @@ int irkmg_advance(irkmg_ctx* C, const double* k, double* un, double* pn) {
 
 int irkmg_forcing_load(irkmg_ctx* C, const double* theta, double* g) {
   if (!C || !theta || !g) return fail(IRKMG_EINVAL, "bad arguments");
+  if (C->dim != 2) return fail(IRKMG_ENOTIMPL, "the adjoint form is built for 2D meshes");
   CK(launch_cell_load(*C, theta, g));
   C->launches++;
   return IRKMG_OK;
@@ -1216,6 +1242,7 @@ int irkmg_step(irkmg_ctx* C, double* un, double* pn, const double* f, const doub
 int irkmg_adjoint_step(irkmg_ctx* C, double* ub, double* pb, const double* k, const double* un,
                        double* thb, double* dnu, irkmg_stats* st) {
   if (!C || !ub || !pb || !k || !un) return fail(IRKMG_EINVAL, "bad arguments");
+  if (C->dim != 2) return fail(IRKMG_ENOTIMPL, "the adjoint form is built for 2D meshes");
   Level& L = C->L.back();
   CK(launch_kbar(*C, ub, pb, C->d_kb));
   CK(cudaMemsetAsync(C->d_lam, 0, sizeof(double) * L.N, C->stream));
@@ -1243,6 +1270,7 @@ int irkmg_adjoint_step(irkmg_ctx* C, double* ub, double* pb, const double* k, co
 
 int irkmg_tracking(irkmg_ctx* C, const double* u, const double* ut, double* grad, double* value) {
   if (!C || !u || !ut || !value) return fail(IRKMG_EINVAL, "bad arguments");
+  if (C->dim != 2) return fail(IRKMG_ENOTIMPL, "the adjoint form is built for 2D meshes");
   CK(launch_tracking(*C, u, ut, grad, C->d_part, C->d_scalar));
   C->launches += 2;
   CK(cudaMemcpyAsync(value, C->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, C->stream));

@@ -1,12 +1,14 @@
 // Host-side assembly of the Taylor–Hood P2–P1 operators of one level
 // (Section 3.1: M, K, B with B the weak gradient from -<p, div v>;
-// Section 3.2: Oseen convection <(w . grad) u, v> for a frozen wind w).
+// Section 3.2: Oseen convection <(w . grad) u, v> for a frozen wind w, 2D).
 //
-// Element integrals use the 7-point degree-5 rule of Radon (Stroud T2:5-1),
-// which integrates every integrand here exactly on affine triangles: the mass
-// matrix is degree 4, the stiffness degree 2, the gradient block degree 2 and
-// the convection block (P2 wind x grad P2 x P2) degree 5.
+// Element integrals are exact quadratures on affine simplices: the 7-point
+// degree-5 rule of Radon (Stroud T2:5-1) on triangles, and on tetrahedra the
+// collapsed (Duffy) product of 4-point Gauss–Legendre rules, exact for
+// degree 7 in each collapsed direction, hence for every integrand of degree
+// <= 5 here (mass degree 4, stiffness and gradient degree 2).
 #include <algorithm>
+#include <array>
 #include <cmath>
 
 #include "irkmg_internal.h"
@@ -16,8 +18,8 @@ namespace irkmg {
 namespace {
 
 struct QuadRule {
-  double lam[7][3];
-  double w[7];  // weights sum to 1 (multiply by the area)
+  std::vector<std::array<double, 4>> lam;  // barycentric coordinates
+  std::vector<double> w;                   // weights sum to 1 (multiply by the volume)
 };
 
 QuadRule radon7() {
@@ -25,33 +27,91 @@ QuadRule radon7() {
   const double r15 = std::sqrt(15.0);
   const double a1 = (6.0 - r15) / 21.0, a2 = (6.0 + r15) / 21.0;
   const double w1 = (155.0 - r15) / 1200.0, w2 = (155.0 + r15) / 1200.0;
-  q.lam[0][0] = q.lam[0][1] = q.lam[0][2] = 1.0 / 3.0;
-  q.w[0] = 9.0 / 40.0;
+  q.lam.push_back({1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 0.0});
+  q.w.push_back(9.0 / 40.0);
   const double as[2] = {a1, a2}, ws[2] = {w1, w2};
-  int k = 1;
   for (int g = 0; g < 2; ++g)
     for (int r = 0; r < 3; ++r) {
-      for (int j = 0; j < 3; ++j) q.lam[k][j] = (j == r) ? 1.0 - 2.0 * as[g] : as[g];
-      q.w[k] = ws[g];
-      ++k;
+      std::array<double, 4> l = {as[g], as[g], as[g], 0.0};
+      l[r] = 1.0 - 2.0 * as[g];
+      q.lam.push_back(l);
+      q.w.push_back(ws[g]);
     }
   return q;
 }
 
-// P2 basis on barycentrics: vertex i -> l_i (2 l_i - 1); edge (i, j) -> 4 l_i l_j,
-// local edges (0,1), (1,2), (0,2).  Gradients by the chain rule from grad l.
-const int kEdge[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+QuadRule duffy_tet() {
+  // 4-point Gauss–Legendre on [-1, 1]: nodes +-sqrt((3 -+ 2 sqrt(6/5)) / 7),
+  // weights (18 +- sqrt(30)) / 36, mapped to [0, 1]
+  const double s65 = std::sqrt(6.0 / 5.0), s30 = std::sqrt(30.0);
+  const double x1 = std::sqrt((3.0 - 2.0 * s65) / 7.0), x2 = std::sqrt((3.0 + 2.0 * s65) / 7.0);
+  const double w1 = (18.0 + s30) / 36.0, w2 = (18.0 - s30) / 36.0;
+  const double xs[4] = {-x2, -x1, x1, x2}, wsg[4] = {w2, w1, w1, w2};
+  QuadRule q;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < 4; ++k) {
+        const double u = 0.5 * (xs[i] + 1), v = 0.5 * (xs[j] + 1), t = 0.5 * (xs[k] + 1);
+        const double x = u, y = v * (1 - u), z = t * (1 - u) * (1 - v);
+        // reference volume 1/6: weights scaled by 6 to sum to one
+        const double wt = 6.0 * 0.125 * wsg[i] * wsg[j] * wsg[k] * (1 - u) * (1 - u) * (1 - v);
+        q.lam.push_back({1.0 - x - y - z, x, y, z});
+        q.w.push_back(wt);
+      }
+  return q;
+}
 
-inline void p2_eval(const double l[3], const double gl[3][2], double phi[6], double gphi[6][2]) {
-  for (int i = 0; i < 3; ++i) {
+// P2 basis on barycentrics: vertex i -> l_i (2 l_i - 1); edge (i, j) -> 4 l_i l_j
+// in the local edge order; gradients by the chain rule from grad l.
+inline void p2_eval(int d, const double* l, const double gl[4][3], double* phi,
+                    double gphi[10][3]) {
+  const int kv = d + 1, ke = d == 2 ? 3 : 6;
+  for (int i = 0; i < kv; ++i) {
     phi[i] = l[i] * (2.0 * l[i] - 1.0);
-    for (int d = 0; d < 2; ++d) gphi[i][d] = (4.0 * l[i] - 1.0) * gl[i][d];
+    for (int c = 0; c < d; ++c) gphi[i][c] = (4.0 * l[i] - 1.0) * gl[i][c];
   }
-  for (int e = 0; e < 3; ++e) {
-    int i = kEdge[e][0], j = kEdge[e][1];
-    phi[3 + e] = 4.0 * l[i] * l[j];
-    for (int d = 0; d < 2; ++d) gphi[3 + e][d] = 4.0 * (l[j] * gl[i][d] + l[i] * gl[j][d]);
+  for (int e = 0; e < ke; ++e) {
+    const int i = kLocalEdges[e][0], j = kLocalEdges[e][1];
+    phi[kv + e] = 4.0 * l[i] * l[j];
+    for (int c = 0; c < d; ++c) gphi[kv + e][c] = 4.0 * (l[j] * gl[i][c] + l[i] * gl[j][c]);
   }
+}
+
+// Volume and barycentric gradients of cell c.
+double cell_geometry(const HostMesh& m, int64_t c, double gl[4][3]) {
+  const int d = m.dim;
+  const int32_t* t = &m.cells[(d + 1) * c];
+  double J[3][3] = {{0}};
+  for (int i = 0; i < d; ++i)
+    for (int k = 0; k < d; ++k) J[k][i] = m.xy[d * t[i + 1] + k] - m.xy[d * t[0] + k];
+  if (d == 2) {
+    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    // rows of J^{-1} are grad l_1, grad l_2
+    gl[1][0] = J[1][1] / det;
+    gl[1][1] = -J[0][1] / det;
+    gl[2][0] = -J[1][0] / det;
+    gl[2][1] = J[0][0] / det;
+    gl[0][0] = -gl[1][0] - gl[2][0];
+    gl[0][1] = -gl[1][1] - gl[2][1];
+    return 0.5 * std::fabs(det);
+  }
+  const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) gl[i + 1][k] = inv[i][k];
+  for (int k = 0; k < 3; ++k) gl[0][k] = -gl[1][k] - gl[2][k] - gl[3][k];
+  return std::fabs(det) / 6.0;
 }
 
 // Find the slot of column `col` in row `row` of a CSR with sorted columns.
@@ -64,19 +124,21 @@ inline int64_t slot(const HostCSR& A, int64_t row, int32_t col) {
 }  // namespace
 
 void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& ops) {
-  const QuadRule q = radon7();
-  // node -> cells, then sparsity patterns by union over cells
-  std::vector<int32_t> nc_ptr(m.np2 + 1, 0), nc_idx(6 * m.nc);
+  const int d = m.dim, kv = m.nvc(), nn = m.nn();
+  const QuadRule q = d == 2 ? radon7() : duffy_tet();
+  const int nq = (int)q.w.size();
   auto cell_node = [&](int64_t c, int a) -> int32_t {
-    return a < 3 ? m.cells[3 * c + a] : (int32_t)(m.nv + m.cell_edges[3 * c + a - 3]);
+    return a < kv ? m.cells[kv * c + a] : (int32_t)(m.nv + m.cell_edges[m.nle() * c + a - kv]);
   };
+  // node -> cells, then sparsity patterns by union over cells
+  std::vector<int32_t> nc_ptr(m.np2 + 1, 0), nc_idx(nn * m.nc);
   for (int64_t c = 0; c < m.nc; ++c)
-    for (int a = 0; a < 6; ++a) nc_ptr[cell_node(c, a) + 1]++;
+    for (int a = 0; a < nn; ++a) nc_ptr[cell_node(c, a) + 1]++;
   for (int64_t n = 0; n < m.np2; ++n) nc_ptr[n + 1] += nc_ptr[n];
   {
     std::vector<int32_t> fill(nc_ptr.begin(), nc_ptr.end() - 1);
     for (int64_t c = 0; c < m.nc; ++c)
-      for (int a = 0; a < 6; ++a) nc_idx[fill[cell_node(c, a)]++] = (int32_t)c;
+      for (int a = 0; a < nn; ++a) nc_idx[fill[cell_node(c, a)]++] = (int32_t)c;
   }
   HostCSR& V = ops.vel;
   HostCSR& MA = ops.mall;
@@ -98,8 +160,8 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
     verts.clear();
     for (int32_t p = nc_ptr[n]; p < nc_ptr[n + 1]; ++p) {
       int64_t c = nc_idx[p];
-      for (int a = 0; a < 6; ++a) nodes.push_back(cell_node(c, a));
-      for (int a = 0; a < 3; ++a) verts.push_back(m.cells[3 * c + a]);
+      for (int a = 0; a < nn; ++a) nodes.push_back(cell_node(c, a));
+      for (int a = 0; a < kv; ++a) verts.push_back(m.cells[kv * c + a]);
     }
     std::sort(nodes.begin(), nodes.end());
     nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
@@ -118,66 +180,51 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
   V.v[1].assign(V.col.size(), 0.0);
   MA.v[0].assign(MA.col.size(), 0.0);
   MA.v[1].assign(MA.col.size(), 0.0);
+  for (int c = 0; c < d; ++c) B.v[c].assign(B.col.size(), 0.0);
   // B with every P2 row (Dirichlet rows too), for the lifted right-hand side
-  std::vector<std::vector<std::pair<int32_t, double>>> bfull_x(m.np2), bfull_y(m.np2);
-  B.v[0].assign(B.col.size(), 0.0);
-  B.v[1].assign(B.col.size(), 0.0);
+  std::vector<std::vector<std::pair<int32_t, std::array<double, 3>>>> bfull(m.np2);
 
-  double Me[6][6], Ke[6][6], Be[2][6][3];
+  double Me[10][10], Ke[10][10], Be[3][10][4];
   for (int64_t c = 0; c < m.nc; ++c) {
-    const int32_t* t = &m.cells[3 * c];
-    const double x0 = m.xy[2 * t[0]], y0 = m.xy[2 * t[0] + 1];
-    const double d1x = m.xy[2 * t[1]] - x0, d1y = m.xy[2 * t[1] + 1] - y0;
-    const double d2x = m.xy[2 * t[2]] - x0, d2y = m.xy[2 * t[2] + 1] - y0;
-    const double det = d1x * d2y - d1y * d2x;
-    const double area = 0.5 * std::fabs(det);
-    double gl[3][2];
-    gl[1][0] = d2y / det;
-    gl[1][1] = -d2x / det;
-    gl[2][0] = -d1y / det;
-    gl[2][1] = d1x / det;
-    gl[0][0] = -gl[1][0] - gl[2][0];
-    gl[0][1] = -gl[1][1] - gl[2][1];
-    int32_t node[6];
-    for (int a = 0; a < 6; ++a) node[a] = cell_node(c, a);
-    for (int a = 0; a < 6; ++a)
-      for (int b = 0; b < 6; ++b) Me[a][b] = Ke[a][b] = 0.0;
-    for (int d = 0; d < 2; ++d)
-      for (int a = 0; a < 6; ++a)
-        for (int p = 0; p < 3; ++p) Be[d][a][p] = 0.0;
-    for (int k = 0; k < 7; ++k) {
-      double phi[6], g[6][2];
-      p2_eval(q.lam[k], gl, phi, g);
-      const double wk = q.w[k] * area;
-      double wx = 0.0, wy = 0.0;
-      if (wind) {
-        for (int a = 0; a < 6; ++a) {
-          wx += wind[2 * node[a]] * phi[a];
-          wy += wind[2 * node[a] + 1] * phi[a];
-        }
-      }
-      for (int a = 0; a < 6; ++a) {
-        for (int b = 0; b < 6; ++b) {
+    double gl[4][3];
+    const double vol = cell_geometry(m, c, gl);
+    const int32_t* t = &m.cells[kv * c];
+    int32_t node[10];
+    for (int a = 0; a < nn; ++a) node[a] = cell_node(c, a);
+    for (int a = 0; a < nn; ++a)
+      for (int b = 0; b < nn; ++b) Me[a][b] = Ke[a][b] = 0.0;
+    for (int k = 0; k < d; ++k)
+      for (int a = 0; a < nn; ++a)
+        for (int p = 0; p < kv; ++p) Be[k][a][p] = 0.0;
+    for (int iq = 0; iq < nq; ++iq) {
+      double phi[10], g[10][3];
+      p2_eval(d, q.lam[iq].data(), gl, phi, g);
+      const double wk = q.w[iq] * vol;
+      double wv[3] = {0.0, 0.0, 0.0};
+      if (wind && d == 2)
+        for (int a = 0; a < nn; ++a)
+          for (int k = 0; k < d; ++k) wv[k] += wind[d * node[a] + k] * phi[a];
+      for (int a = 0; a < nn; ++a) {
+        for (int b = 0; b < nn; ++b) {
           Me[a][b] += wk * phi[a] * phi[b];
-          double kab = nu * (g[a][0] * g[b][0] + g[a][1] * g[b][1]);
-          if (wind) kab += (wx * g[b][0] + wy * g[b][1]) * phi[a];
-          Ke[a][b] += wk * kab;
+          double gg = 0.0, conv = 0.0;
+          for (int k = 0; k < d; ++k) {
+            gg += g[a][k] * g[b][k];
+            conv += wv[k] * g[b][k];
+          }
+          Ke[a][b] += wk * (nu * gg + (wind && d == 2 ? conv * phi[a] : 0.0));
         }
-        for (int p = 0; p < 3; ++p) {
-          Be[0][a][p] -= wk * q.lam[k][p] * g[a][0];
-          Be[1][a][p] -= wk * q.lam[k][p] * g[a][1];
-        }
+        for (int p = 0; p < kv; ++p)
+          for (int k = 0; k < d; ++k) Be[k][a][p] -= wk * q.lam[iq][p] * g[a][k];
       }
     }
-    for (int a = 0; a < 6; ++a)
-      for (int p = 0; p < 3; ++p) {
-        bfull_x[node[a]].push_back({t[p], Be[0][a][p]});
-        bfull_y[node[a]].push_back({t[p], Be[1][a][p]});
-      }
-    for (int a = 0; a < 6; ++a) {
+    for (int a = 0; a < nn; ++a)
+      for (int p = 0; p < kv; ++p)
+        bfull[node[a]].push_back({t[p], {Be[0][a][p], Be[1][a][p], d == 3 ? Be[2][a][p] : 0.0}});
+    for (int a = 0; a < nn; ++a) {
       const int32_t row = m.p2_to_free[node[a]];
       if (row < 0) continue;
-      for (int b = 0; b < 6; ++b) {
+      for (int b = 0; b < nn; ++b) {
         int64_t sa = slot(MA, row, node[b]);
         MA.v[0][sa] += Me[a][b];
         MA.v[1][sa] += Ke[a][b];
@@ -188,10 +235,9 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
           V.v[1][sv] += Ke[a][b];
         }
       }
-      for (int p = 0; p < 3; ++p) {
+      for (int p = 0; p < kv; ++p) {
         int64_t sb = slot(B, row, t[p]);
-        B.v[0][sb] += Be[0][a][p];
-        B.v[1][sb] += Be[1][a][p];
+        for (int k = 0; k < d; ++k) B.v[k][sb] += Be[k][a][p];
       }
     }
   }
@@ -202,58 +248,51 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
       int64_t st = slot(V, V.col[p], (int32_t)i);
       V.v[2][p] = V.v[1][st];
     }
-  ops.bt = transpose_csr(B, 2);
+  ops.bt = transpose_csr(B, d);
   // Bᵀ over every velocity column: vertex rows, P2-node columns, summed per pair
   HostCSR Bf;
   Bf.nrows = m.np2;
   Bf.ncols = m.nv;
   Bf.ptr.assign(1, 0);
   for (int64_t n = 0; n < m.np2; ++n) {
-    std::vector<std::pair<int32_t, std::pair<double, double>>> e;
-    for (size_t k = 0; k < bfull_x[n].size(); ++k)
-      e.push_back({bfull_x[n][k].first, {bfull_x[n][k].second, bfull_y[n][k].second}});
+    auto& e = bfull[n];
     std::stable_sort(e.begin(), e.end(),
                      [](const auto& a, const auto& b) { return a.first < b.first; });
     for (size_t k = 0; k < e.size();) {
       size_t j = k;
-      double sx = 0.0, sy = 0.0;
-      for (; j < e.size() && e[j].first == e[k].first; ++j) {
-        sx += e[j].second.first;
-        sy += e[j].second.second;
-      }
+      double sum[3] = {0.0, 0.0, 0.0};
+      for (; j < e.size() && e[j].first == e[k].first; ++j)
+        for (int c = 0; c < 3; ++c) sum[c] += e[j].second[c];
       Bf.col.push_back(e[k].first);
-      Bf.v[0].push_back(sx);
-      Bf.v[1].push_back(sy);
+      for (int c = 0; c < d; ++c) Bf.v[c].push_back(sum[c]);
       k = j;
     }
     Bf.ptr.push_back((int32_t)Bf.col.size());
   }
-  ops.btall = transpose_csr(Bf, 2);
+  ops.btall = transpose_csr(Bf, d);
 }
 
 // Load of a per-cell constant (P0) forcing: C[a, c] = int_c phi_a for the free
-// P2 nodes a of cell c (the same for both velocity components).  P2 vertex
-// functions integrate to zero on a triangle, edge functions to |c|/3; the
-// degree-5 rule is exact for these quadratics.
+// P2 nodes a of cell c (the same for every velocity component).  P2 vertex
+// functions integrate to zero on a triangle, edge functions to |c|/3.
 void assemble_cell_load(const HostMesh& m, HostCSR& C) {
-  const QuadRule q = radon7();
   C = HostCSR();
   C.nrows = m.nf;
   C.ncols = m.nc;
+  C.ptr.assign(m.nf + 1, 0);
+  if (m.dim != 2) return;
+  const QuadRule q = radon7();
   std::vector<std::vector<std::pair<int32_t, double>>> rows(m.nf);
   for (int64_t c = 0; c < m.nc; ++c) {
-    const int32_t* t = &m.cells[3 * c];
-    const double x0 = m.xy[2 * t[0]], y0 = m.xy[2 * t[0] + 1];
-    const double d1x = m.xy[2 * t[1]] - x0, d1y = m.xy[2 * t[1] + 1] - y0;
-    const double d2x = m.xy[2 * t[2]] - x0, d2y = m.xy[2 * t[2] + 1] - y0;
-    const double area = 0.5 * std::fabs(d1x * d2y - d1y * d2x);
-    double gl[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    double gl[4][3];
+    const double area = cell_geometry(m, c, gl);
     double w[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = 0; k < 7; ++k) {
-      double phi[6], g[6][2];
-      p2_eval(q.lam[k], gl, phi, g);
+    for (size_t k = 0; k < q.w.size(); ++k) {
+      double phi[10], g[10][3];
+      p2_eval(2, q.lam[k].data(), gl, phi, g);
       for (int a = 0; a < 6; ++a) w[a] += q.w[k] * area * phi[a];
     }
+    const int32_t* t = &m.cells[3 * c];
     for (int a = 0; a < 6; ++a) {
       const int32_t node = a < 3 ? t[a] : (int32_t)(m.nv + m.cell_edges[3 * c + a - 3]);
       const int32_t f = m.p2_to_free[node];

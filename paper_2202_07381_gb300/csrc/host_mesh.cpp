@@ -1,15 +1,20 @@
 // Host-side mesh hierarchy, numbering, transfer weights and Butcher tableau.
 //
-// Section 4.1: levels are uniform (red) refinements of a coarsest triangle
-// mesh, and prolongation is canonical P2 (velocity) / P1 (pressure)
-// interpolation; restriction is its transpose.  Section 5: RadauIIA(s).
+// Section 4.1: levels are uniform refinements of a coarsest simplicial mesh
+// (red refinement of triangles, Bey's refinement of tetrahedra), and
+// prolongation is canonical P2 (velocity) / P1 (pressure) interpolation;
+// restriction is its transpose.  Section 5: RadauIIA(s).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <numeric>
 
 #include "irkmg_internal.h"
 
 namespace irkmg {
+
+// local edges of a cell; triangles use the first three
+const int kLocalEdges[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
 
 static inline uint64_t key2(int32_t a, int32_t b) {
   return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
@@ -34,40 +39,61 @@ int64_t find_edge(const HostMesh& m, int32_t a, int32_t b) {
 
 static void finish_mesh(HostMesh& m) {
   const int64_t nc = m.nc, nv = m.nv;
+  const int kv = m.nvc(), ke = m.nle();
   // edges: sorted vertex pairs, unique, lexicographic
-  std::vector<uint64_t> keys(3 * nc);
-  static const int le[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+  std::vector<uint64_t> keys(ke * nc);
   for (int64_t c = 0; c < nc; ++c)
-    for (int k = 0; k < 3; ++k) {
-      int32_t a = m.cells[3 * c + le[k][0]], b = m.cells[3 * c + le[k][1]];
+    for (int k = 0; k < ke; ++k) {
+      int32_t a = m.cells[kv * c + kLocalEdges[k][0]], b = m.cells[kv * c + kLocalEdges[k][1]];
       if (a > b) std::swap(a, b);
-      keys[3 * c + k] = key2(a, b);
+      keys[ke * c + k] = key2(a, b);
     }
-  std::vector<uint64_t> sorted = keys;
-  std::sort(sorted.begin(), sorted.end());
-  std::vector<int32_t> mult;
-  std::vector<uint64_t> uniq;
-  uniq.reserve(sorted.size());
-  for (size_t i = 0; i < sorted.size(); ++i) {
-    if (uniq.empty() || uniq.back() != sorted[i]) {
-      uniq.push_back(sorted[i]);
-      mult.push_back(1);
-    } else {
-      mult.back()++;
-    }
-  }
+  std::vector<uint64_t> uniq = keys;
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
   m.ne = (int64_t)uniq.size();
   m.edges.resize(2 * m.ne);
-  m.edge_dir.assign(m.ne, 0);
   for (int64_t e = 0; e < m.ne; ++e) {
     m.edges[2 * e] = (int32_t)(uniq[e] >> 32);
     m.edges[2 * e + 1] = (int32_t)(uniq[e] & 0xffffffffu);
-    m.edge_dir[e] = (mult[e] == 1 && m.bnd[m.edges[2 * e]] && m.bnd[m.edges[2 * e + 1]]) ? 1 : 0;
   }
-  m.cell_edges.resize(3 * nc);
-  for (int64_t i = 0; i < 3 * nc; ++i)
+  m.cell_edges.resize(ke * nc);
+  for (int64_t i = 0; i < ke * nc; ++i)
     m.cell_edges[i] =
         (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), keys[i]) - uniq.begin());
+  // boundary facets (edges in 2D, faces in 3D) belong to exactly one cell;
+  // an edge is on the boundary iff it lies in a boundary facet
+  std::vector<uint8_t> on_bnd(m.ne, 0);
+  if (m.dim == 2) {
+    std::vector<int32_t> cnt(m.ne, 0);
+    for (int32_t e : m.cell_edges) cnt[e]++;
+    for (int64_t e = 0; e < m.ne; ++e) on_bnd[e] = cnt[e] == 1;
+  } else {
+    std::vector<std::array<int32_t, 3>> faces;
+    faces.reserve(4 * nc);
+    static const int fv[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+    for (int64_t c = 0; c < nc; ++c)
+      for (int f = 0; f < 4; ++f) {
+        std::array<int32_t, 3> t = {m.cells[4 * c + fv[f][0]], m.cells[4 * c + fv[f][1]],
+                                    m.cells[4 * c + fv[f][2]]};
+        std::sort(t.begin(), t.end());
+        faces.push_back(t);
+      }
+    std::sort(faces.begin(), faces.end());
+    for (size_t i = 0; i < faces.size();) {
+      size_t j = i;
+      while (j < faces.size() && faces[j] == faces[i]) ++j;
+      if (j - i == 1) {
+        const auto& t = faces[i];
+        for (int a = 0; a < 3; ++a)
+          for (int b = a + 1; b < 3; ++b) on_bnd[find_edge(m, t[a], t[b])] = 1;
+      }
+      i = j;
+    }
+  }
+  m.edge_dir.assign(m.ne, 0);
+  for (int64_t e = 0; e < m.ne; ++e)
+    m.edge_dir[e] = (on_bnd[e] && m.bnd[m.edges[2 * e]] && m.bnd[m.edges[2 * e + 1]]) ? 1 : 0;
   // P2 nodes: vertices, then edges; free numbering in that order
   m.np2 = nv + m.ne;
   m.p2_to_free.assign(m.np2, -1);
@@ -82,12 +108,12 @@ static void finish_mesh(HostMesh& m) {
   m.nf = (int64_t)m.free_to_p2.size();
   // vertex -> cells
   m.vc_ptr.assign(nv + 1, 0);
-  for (int64_t i = 0; i < 3 * nc; ++i) m.vc_ptr[m.cells[i] + 1]++;
+  for (int64_t i = 0; i < kv * nc; ++i) m.vc_ptr[m.cells[i] + 1]++;
   for (int64_t v = 0; v < nv; ++v) m.vc_ptr[v + 1] += m.vc_ptr[v];
-  m.vc_idx.resize(3 * nc);
+  m.vc_idx.resize(kv * nc);
   std::vector<int32_t> fill(m.vc_ptr.begin(), m.vc_ptr.end() - 1);
   for (int64_t c = 0; c < nc; ++c)
-    for (int k = 0; k < 3; ++k) m.vc_idx[fill[m.cells[3 * c + k]]++] = (int32_t)c;
+    for (int k = 0; k < kv; ++k) m.vc_idx[fill[m.cells[kv * c + k]]++] = (int32_t)c;
   // vertex -> vertices (edge graph); edges are lexicographic so rows come out sorted
   m.vv_ptr.assign(nv + 1, 0);
   for (int64_t e = 0; e < m.ne; ++e) {
@@ -107,98 +133,137 @@ static void finish_mesh(HostMesh& m) {
 }
 
 std::string build_mesh(const double* xy, const int64_t* cells, const uint8_t* bnd, int64_t nv,
-                       int64_t nc, HostMesh& m) {
-  if (nv < 3 || nc < 1) return "mesh needs at least one triangle";
-  if (nv > (1LL << 30) || nc > (1LL << 29)) return "mesh too large for 32-bit indices";
+                       int64_t nc, int dim, HostMesh& m) {
+  if (dim != 2 && dim != 3) return "dim must be 2 or 3";
+  const int kv = dim + 1;
+  if (nv < kv || nc < 1) return "mesh needs at least one cell";
+  if (nv > (1LL << 30) || nc > (1LL << 28)) return "mesh too large for 32-bit indices";
+  m.dim = dim;
   m.nv = nv;
   m.nc = nc;
-  m.xy.assign(xy, xy + 2 * nv);
+  m.xy.assign(xy, xy + dim * nv);
   m.bnd.assign(bnd, bnd + nv);
-  m.cells.resize(3 * nc);
-  for (int64_t i = 0; i < 3 * nc; ++i) {
+  m.cells.resize(kv * nc);
+  for (int64_t i = 0; i < kv * nc; ++i) {
     if (cells[i] < 0 || cells[i] >= nv) return "cell vertex id out of range";
     m.cells[i] = (int32_t)cells[i];
   }
   for (int64_t c = 0; c < nc; ++c) {
-    const int32_t* t = &m.cells[3 * c];
-    if (t[0] == t[1] || t[1] == t[2] || t[0] == t[2]) return "degenerate cell";
-    double d1x = xy[2 * t[1]] - xy[2 * t[0]], d1y = xy[2 * t[1] + 1] - xy[2 * t[0] + 1];
-    double d2x = xy[2 * t[2]] - xy[2 * t[0]], d2y = xy[2 * t[2] + 1] - xy[2 * t[0] + 1];
-    if (std::fabs(d1x * d2y - d1y * d2x) <= 0.0) return "zero-area cell";
+    const int32_t* t = &m.cells[kv * c];
+    for (int a = 0; a < kv; ++a)
+      for (int b = a + 1; b < kv; ++b)
+        if (t[a] == t[b]) return "degenerate cell";
+    double J[3][3] = {{0}};
+    for (int i = 0; i < dim; ++i)
+      for (int k = 0; k < dim; ++k) J[k][i] = xy[dim * t[i + 1] + k] - xy[dim * t[0] + k];
+    const double det = dim == 2 ? J[0][0] * J[1][1] - J[0][1] * J[1][0]
+                                : J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                      J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                      J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (std::fabs(det) <= 0.0) return "zero-volume cell";
   }
   finish_mesh(m);
   return "";
 }
 
-// Red refinement: coarse vertices keep their ids, edge e gets vertex nv + e;
-// the children of (a, b, c) are (a, m01, m02), (m01, b, m12), (m02, m12, c),
-// (m01, m12, m02) with ids 4c + k.
+// Uniform refinement.  Coarse vertices keep their ids and edge e gets vertex
+// nv + e.  Triangles (red): the children of (a, b, c) are (a, m01, m02),
+// (m01, b, m12), (m02, m12, c), (m01, m12, m02) with ids 4c + k.
+// Tetrahedra (Bey): the children of (x0, x1, x2, x3) are (x0, x01, x02, x03),
+// (x01, x1, x12, x13), (x02, x12, x2, x23), (x03, x13, x23, x3) and the inner
+// octahedron cut along x02-x13: (x01, x02, x03, x13), (x01, x02, x12, x13),
+// (x02, x03, x13, x23), (x02, x12, x13, x23), with ids 8c + k.
 void refine_mesh(const HostMesh& c, HostMesh& f) {
+  const int d = c.dim;
   f = HostMesh();
+  f.dim = d;
   f.nv = c.np2;
-  f.nc = 4 * c.nc;
-  f.xy.resize(2 * f.nv);
+  f.nc = (d == 2 ? 4 : 8) * c.nc;
+  f.xy.resize(d * f.nv);
   std::copy(c.xy.begin(), c.xy.end(), f.xy.begin());
   f.bnd.resize(f.nv);
   std::copy(c.bnd.begin(), c.bnd.end(), f.bnd.begin());
   for (int64_t e = 0; e < c.ne; ++e) {
     int32_t a = c.edges[2 * e], b = c.edges[2 * e + 1];
-    f.xy[2 * (c.nv + e)] = 0.5 * (c.xy[2 * a] + c.xy[2 * b]);
-    f.xy[2 * (c.nv + e) + 1] = 0.5 * (c.xy[2 * a + 1] + c.xy[2 * b + 1]);
+    for (int k = 0; k < d; ++k) f.xy[d * (c.nv + e) + k] = 0.5 * (c.xy[d * a + k] + c.xy[d * b + k]);
     f.bnd[c.nv + e] = c.edge_dir[e];
   }
-  f.cells.resize(3 * f.nc);
+  const int kv = d + 1, ke = c.nle();
+  f.cells.resize(kv * f.nc);
   for (int64_t k = 0; k < c.nc; ++k) {
-    int32_t a = c.cells[3 * k], b = c.cells[3 * k + 1], cc = c.cells[3 * k + 2];
-    int32_t m01 = (int32_t)(c.nv + c.cell_edges[3 * k]);
-    int32_t m12 = (int32_t)(c.nv + c.cell_edges[3 * k + 1]);
-    int32_t m02 = (int32_t)(c.nv + c.cell_edges[3 * k + 2]);
-    int32_t kids[4][3] = {{a, m01, m02}, {m01, b, m12}, {m02, m12, cc}, {m01, m12, m02}};
-    for (int q = 0; q < 4; ++q)
-      for (int j = 0; j < 3; ++j) f.cells[3 * (4 * k + q) + j] = kids[q][j];
+    const int32_t* x = &c.cells[kv * k];
+    int32_t m[6];
+    for (int e = 0; e < ke; ++e) m[e] = (int32_t)(c.nv + c.cell_edges[ke * k + e]);
+    if (d == 2) {
+      // m[0] = m01, m[1] = m12, m[2] = m02
+      const int32_t kids[4][3] = {{x[0], m[0], m[2]}, {m[0], x[1], m[1]}, {m[2], m[1], x[2]},
+                                  {m[0], m[1], m[2]}};
+      for (int q = 0; q < 4; ++q)
+        for (int j = 0; j < 3; ++j) f.cells[3 * (4 * k + q) + j] = kids[q][j];
+    } else {
+      // m01 = m[0], m12 = m[1], m02 = m[2], m03 = m[3], m13 = m[4], m23 = m[5]
+      const int32_t m01 = m[0], m12 = m[1], m02 = m[2], m03 = m[3], m13 = m[4], m23 = m[5];
+      const int32_t kids[8][4] = {{x[0], m01, m02, m03}, {m01, x[1], m12, m13},
+                                  {m02, m12, x[2], m23}, {m03, m13, m23, x[3]},
+                                  {m01, m02, m03, m13},  {m01, m02, m12, m13},
+                                  {m02, m03, m13, m23},  {m02, m12, m13, m23}};
+      for (int q = 0; q < 8; ++q)
+        for (int j = 0; j < 4; ++j) f.cells[4 * (8 * k + q) + j] = kids[q][j];
+    }
   }
   finish_mesh(f);
 }
 
-// Canonical interpolation weights of a red refinement, in closed form:
+// Canonical interpolation weights of a uniform refinement, in closed form:
 //  * a fine vertex is a coarse P2 node (same id): weight 1;
 //  * the midpoint of a fine edge (u, m) with u a coarse vertex and m the
 //    midpoint of coarse edge (u, w) sits at barycentrics (3/4, 1/4) on that
 //    edge: weights 3/8 (u), -1/8 (w), 3/4 (edge node m);
-//  * the midpoint of a fine edge (m1, m2) joining the midpoints of coarse
-//    edges (a, b) and (b, c) sits at (1/4, 1/2, 1/4) in (a, b, c): weights
-//    -1/8 (a), 0 (b), -1/8 (c), 1/2 (m1), 1/2 (m2), 1/4 (edge node of (a, c)).
+//  * the midpoint of a fine edge (m1, m2) joining the midpoints of two coarse
+//    edges (p, b) and (b, q) that share the vertex b sits at (1/4, 1/2, 1/4) in
+//    the face (p, b, q): weights -1/8 (p), 0 (b), -1/8 (q), 1/2 (m1), 1/2 (m2),
+//    1/4 (edge node of (p, q));
+//  * (tetrahedra) the midpoint of the fine edge joining the midpoints of two
+//    opposite coarse edges is the centroid, barycentrics 1/4 each: weight
+//    -1/8 at the four vertices and 1/4 at the six edge nodes.
 //  P1: a fine vertex at a coarse vertex takes it with weight 1, a midpoint
 //  takes 1/2 from each end.
 void build_prolongation(const HostMesh& c, const HostMesh& f, HostCSR& Pu, HostCSR& Pp) {
   const int64_t nvc = c.nv;
-  // P2, all nodes, then restrict to free rows / cols
   std::vector<std::vector<std::pair<int32_t, double>>> rows(f.np2);
   for (int64_t v = 0; v < f.nv; ++v) rows[v].push_back({(int32_t)v, 1.0});
+  auto enode = [&](int32_t a, int32_t b) { return (int32_t)(nvc + find_edge(c, a, b)); };
   for (int64_t e = 0; e < f.ne; ++e) {
     int32_t u = f.edges[2 * e], w = f.edges[2 * e + 1];  // u < w
     auto& row = rows[f.nv + e];
     if (u < nvc) {
-      // w is the midpoint of coarse edge (u, other)
-      int64_t ce = w - nvc;
-      int32_t a = c.edges[2 * ce], b = c.edges[2 * ce + 1];
-      int32_t other = (a == u) ? b : a;
+      const int64_t ce = w - nvc;
+      const int32_t a = c.edges[2 * ce], b = c.edges[2 * ce + 1];
+      const int32_t other = (a == u) ? b : a;
       row.push_back({u, 3.0 / 8.0});
       row.push_back({other, -1.0 / 8.0});
       row.push_back({w, 3.0 / 4.0});
-    } else {
-      int64_t e1 = u - nvc, e2 = w - nvc;
-      int32_t a1 = c.edges[2 * e1], b1 = c.edges[2 * e1 + 1];
-      int32_t a2 = c.edges[2 * e2], b2 = c.edges[2 * e2 + 1];
-      int32_t shared = (a1 == a2 || a1 == b2) ? a1 : b1;
-      int32_t p = (a1 == shared) ? b1 : a1;
-      int32_t q = (a2 == shared) ? b2 : a2;
-      int64_t e3 = find_edge(c, p, q);
+      continue;
+    }
+    const int64_t e1 = u - nvc, e2 = w - nvc;
+    const int32_t a1 = c.edges[2 * e1], b1 = c.edges[2 * e1 + 1];
+    const int32_t a2 = c.edges[2 * e2], b2 = c.edges[2 * e2 + 1];
+    int32_t shared = -1;
+    if (a1 == a2 || a1 == b2) shared = a1;
+    if (b1 == a2 || b1 == b2) shared = b1;
+    if (shared >= 0) {
+      const int32_t p = (a1 == shared) ? b1 : a1;
+      const int32_t q = (a2 == shared) ? b2 : a2;
       row.push_back({p, -1.0 / 8.0});
       row.push_back({q, -1.0 / 8.0});
       row.push_back({u, 0.5});
       row.push_back({w, 0.5});
-      row.push_back({(int32_t)(nvc + e3), 0.25});
+      row.push_back({enode(p, q), 0.25});
+    } else {
+      const int32_t vt[4] = {a1, b1, a2, b2};
+      for (int i = 0; i < 4; ++i) row.push_back({vt[i], -1.0 / 8.0});
+      for (int i = 0; i < 4; ++i)
+        for (int j = i + 1; j < 4; ++j) row.push_back({enode(vt[i], vt[j]), 0.25});
     }
   }
   Pu = HostCSR();
@@ -225,7 +290,7 @@ void build_prolongation(const HostMesh& c, const HostMesh& f, HostCSR& Pu, HostC
       Pp.col.push_back((int32_t)v);
       Pp.v[0].push_back(1.0);
     } else {
-      int64_t ce = v - nvc;
+      const int64_t ce = v - nvc;
       Pp.col.push_back(c.edges[2 * ce]);
       Pp.v[0].push_back(0.5);
       Pp.col.push_back(c.edges[2 * ce + 1]);

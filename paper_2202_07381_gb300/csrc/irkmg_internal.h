@@ -17,12 +17,16 @@ namespace irkmg {
 // Section 3.1: Taylor–Hood P2–P1 numbering).
 // ---------------------------------------------------------------------------
 struct HostMesh {
+  int dim = 2;                      // 2: triangles, 3: tetrahedra
   int64_t nv = 0, nc = 0, ne = 0, np2 = 0, nf = 0;
-  std::vector<double> xy;           // nv*2
-  std::vector<int32_t> cells;       // nc*3
+  std::vector<double> xy;           // nv*dim
+  std::vector<int32_t> cells;       // nc*(dim+1)
   std::vector<uint8_t> bnd;         // nv, Dirichlet vertex flags
   std::vector<int32_t> edges;       // ne*2, sorted pairs, lexicographic
-  std::vector<int32_t> cell_edges;  // nc*3, local edges (0,1), (1,2), (0,2)
+  std::vector<int32_t> cell_edges;  // nc*nle: local edges (0,1),(1,2),(0,2)[,(0,3),(1,3),(2,3)]
+  int nvc() const { return dim + 1; }             // vertices per cell
+  int nle() const { return dim == 2 ? 3 : 6; }    // edges per cell
+  int nn() const { return nvc() + nle(); }        // P2 nodes per cell
   std::vector<uint8_t> edge_dir;    // ne, Dirichlet edge flags
   std::vector<int32_t> p2_to_free;  // np2, -1 on Dirichlet nodes
   std::vector<int32_t> free_to_p2;  // nf
@@ -32,7 +36,8 @@ struct HostMesh {
 
 // Returns an empty string on success, else the reason.
 std::string build_mesh(const double* xy, const int64_t* cells, const uint8_t* bnd, int64_t nv,
-                       int64_t nc, HostMesh& out);
+                       int64_t nc, int dim, HostMesh& out);
+extern const int kLocalEdges[6][2];
 void refine_mesh(const HostMesh& c, HostMesh& f);
 // Edge id of the sorted pair (a, b), or -1.
 int64_t find_edge(const HostMesh& m, int32_t a, int32_t b);
@@ -49,13 +54,14 @@ struct HostCSR {
 void build_prolongation(const HostMesh& c, const HostMesh& f, HostCSR& Pu, HostCSR& Pp);
 HostCSR transpose_csr(const HostCSR& A, int nvals);
 
-// Assembled free-DoF operators of one level (Section 3.1).
+// Assembled free-DoF operators of one level (Section 3.1).  Values per
+// velocity component d are in v[d] of the B structures (d < dim).
 struct HostOps {
   HostCSR vel;   // nf x nf: v[0] = M, v[1] = nu K (+ C), v[2] = transpose of v[1]
   HostCSR mall;  // nf x np2: v[0] = M, v[1] = nu K (+ C), with every column (for M f, K u)
-  HostCSR btall; // nv x np2: v[0] = B_x^T, v[1] = B_y^T with every velocity column
-  HostCSR b;     // nf x nv : v[0] = B_x, v[1] = B_y   (B = -int psi_q d phi_a / dx_d)
-  HostCSR bt;    // nv x nf : v[0] = B_x^T, v[1] = B_y^T
+  HostCSR btall; // nv x np2: v[d] = B_d^T with every velocity column
+  HostCSR b;     // nf x nv : v[d] = B_d   (B = -int psi_q d phi_a / dx_d)
+  HostCSR bt;    // nv x nf : v[d] = B_d^T
 };
 // wind: np2*2 nodal values or nullptr
 void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& ops);
@@ -89,6 +95,7 @@ struct DevSELL {
 
 struct Level {
   HostMesh mesh;
+  int dim = 2;
   int64_t nf = 0, nv = 0, np2 = 0, m = 0, N = 0;
   HostOps hops;
   DevCSR vel, b, bt, mall, btall;
@@ -110,7 +117,8 @@ struct Level {
   void* d_fac = nullptr;
   int64_t fac_elems = 0;
   int max_np = 0;
-  int apply_kernel = 1;                // 1 staged, 2 warp-per-patch (chosen at set-up)
+  bool big = false;                    // patches above kMaxSmallNp: blocked LU + LU apply
+  int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 LU (big patches)
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
@@ -121,6 +129,7 @@ struct Level {
 
 struct Ctx {
   int s = 0;
+  int dim = 2;
   double A[9] = {0}, AT[9] = {0}, b[3] = {0}, c[3] = {0};
   double dt = 0, nu = 1;
   irkmg_options opt{};
@@ -197,6 +206,12 @@ cudaError_t launch_dnu(Ctx& C, const double* lam, const double* k, const double*
 cudaError_t launch_tracking(Ctx& C, const double* u, const double* ut, double* grad, double* part,
                             double* out);
 
-constexpr int kMultidotBlocks = 304;  // 2 x 152 SMs; fixed for a deterministic sum order
+cudaError_t launch_patch_lu_big(Ctx& C, Level& L);
+cudaError_t launch_vanka_lu(Ctx& C, Level& L, int colour, const double* r, double* out,
+                            double scale);
+
+constexpr int kMultidotBlocks = 304;
+constexpr int kMaxSmallNp = 160;  // patches up to this size: explicit inverse in shared memory
+constexpr int kMaxBigNp = 512;    // patches up to this size: blocked LU in the patch block  // 2 x 152 SMs; fixed for a deterministic sum order
 
 }  // namespace irkmg

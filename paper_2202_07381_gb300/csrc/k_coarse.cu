@@ -14,7 +14,7 @@
 namespace irkmg {
 
 struct CoarseBuild {
-  int s;
+  int s, dim;
   int64_t nf, nv, m, n;  // n = bordered size
   double mix[9];
   const int32_t *vptr, *vcol;
@@ -23,6 +23,7 @@ struct CoarseBuild {
   const double *Bx, *By;
   const int32_t *btptr, *btcol;
   const double *BTx, *BTy;
+  const double *Bz, *BTz;
 };
 
 // One thread per (stage t, row of the single-stage operator).
@@ -32,8 +33,11 @@ __global__ void k_coarse_build(CoarseBuild P, double* __restrict__ D) {
   if (id >= P.s * rows1) return;
   const int t = (int)(id / rows1);
   const int64_t row = id - t * rows1;
+  const double* Bc[3] = {P.Bx, P.By, P.Bz};
+  const double* BTc[3] = {P.BTx, P.BTy, P.BTz};
+  const int64_t poff = P.dim * P.nf;
   if (row < P.nf) {
-    for (int d = 0; d < 2; ++d) {
+    for (int d = 0; d < P.dim; ++d) {
       double* Drow = D + (t * P.m + d * P.nf + row) * P.n;
       for (int32_t p = P.vptr[row]; p < P.vptr[row + 1]; ++p) {
         const int32_t j = P.vcol[p];
@@ -42,23 +46,21 @@ __global__ void k_coarse_build(CoarseBuild P, double* __restrict__ D) {
       }
       for (int32_t p = P.bptr[row]; p < P.bptr[row + 1]; ++p) {
         const int32_t vtx = P.bcol[p];
-        const double bv = d == 0 ? P.Bx[p] : P.By[p];
-        for (int u = 0; u < P.s; ++u) Drow[u * P.m + 2 * P.nf + vtx] = P.mix[t * 3 + u] * bv;
+        const double bv = Bc[d][p];
+        for (int u = 0; u < P.s; ++u) Drow[u * P.m + poff + vtx] = P.mix[t * 3 + u] * bv;
       }
     }
   } else {
     const int64_t v = row - P.nf;
-    double* Drow = D + (t * P.m + 2 * P.nf + v) * P.n;
+    double* Drow = D + (t * P.m + poff + v) * P.n;
     for (int32_t p = P.btptr[v]; p < P.btptr[v + 1]; ++p) {
       const int32_t j = P.btcol[p];
-      for (int u = 0; u < P.s; ++u) {
-        Drow[u * P.m + j] = P.mix[t * 3 + u] * P.BTx[p];
-        Drow[u * P.m + P.nf + j] = P.mix[t * 3 + u] * P.BTy[p];
-      }
+      for (int u = 0; u < P.s; ++u)
+        for (int d = 0; d < P.dim; ++d) Drow[u * P.m + d * P.nf + j] = P.mix[t * 3 + u] * BTc[d][p];
     }
     const int64_t N = P.s * P.m;
     Drow[N + t] = 1.0;                          // border column
-    D[(N + t) * P.n + t * P.m + 2 * P.nf + v] = 1.0;  // border row
+    D[(N + t) * P.n + t * P.m + poff + v] = 1.0;  // border row
   }
 }
 
@@ -66,6 +68,9 @@ cudaError_t launch_coarse_build(Ctx& C, double* dense) {
   Level& L = C.L[0];
   CoarseBuild P;
   P.s = C.s;
+  P.dim = L.dim;
+  P.Bz = L.b.v[2];
+  P.BTz = L.bt.v[2];
   P.nf = L.nf;
   P.nv = L.nv;
   P.m = L.m;

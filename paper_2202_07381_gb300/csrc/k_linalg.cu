@@ -17,6 +17,7 @@ namespace irkmg {
 
 struct OpParams {
   int64_t nf, nv, m;
+  const double* Bz;                          // third component (3D)
   int64_t nf_pad;  // velocity rows rounded up to a whole slice (SELL kernel)
   double mix[9];  // dt * A (or dt * Aᵀ), row-major 3x3
   const int32_t *vptr, *vcol;
@@ -28,66 +29,66 @@ struct OpParams {
   // SELL-32 copies
   const int64_t *svp, *sbp, *sbtp;
   const int32_t *svc, *sbc, *sbtc;
-  const double *sM, *sK, *sBx, *sBy, *sBTx, *sBTy;
+  const double *sM, *sK, *sBx, *sBy, *sBTx, *sBTy, *sBz, *sBTz;
 };
 
 // The stage operator on SELL-32 storage: threads [0, nf_pad) take velocity
 // rows, threads [nf_pad, nf_pad + nv) pressure rows, so every warp maps onto
-// one slice and all matrix reads are coalesced.
-template <int S>
+// one slice and all matrix reads are coalesced.  S stages, D velocity
+// components (a stage block is [u_1 .. u_D on the free nodes; p]).
+template <int S, int D>
 __global__ void __launch_bounds__(256) k_residual_sell(OpParams P, const double* __restrict__ F,
                                                        const double* __restrict__ x,
                                                        double* __restrict__ r) {
   const int64_t tidg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nf = P.nf, m = P.m;
+  const double* sB[3] = {P.sBx, P.sBy, P.sBz};
+  const double* sBT[3] = {P.sBTx, P.sBTy, P.sBTz};
   if (tidg < P.nf_pad) {
     const int64_t row = tidg;
     if (row >= nf) return;
-    double am[S][2], ak[S][2];
+    double am[S][D], ak[S][D];
 #pragma unroll
-    for (int t = 0; t < S; ++t) am[t][0] = am[t][1] = ak[t][0] = ak[t][1] = 0.0;
+    for (int t = 0; t < S; ++t)
+#pragma unroll
+      for (int c = 0; c < D; ++c) am[t][c] = ak[t][c] = 0.0;
     const int64_t sl = row >> 5, lane = row & 31;
     const int64_t b0 = P.svp[sl], b1 = P.svp[sl + 1];
     for (int64_t e = b0 + lane; e < b1; e += 32) {
       const int32_t j = P.svc[e];
       const double mv = P.sM[e], kv = P.sK[e];
 #pragma unroll
-      for (int t = 0; t < S; ++t) {
-        const double xx = x[t * m + j], xy = x[t * m + nf + j];
-        am[t][0] = fma(mv, xx, am[t][0]);
-        am[t][1] = fma(mv, xy, am[t][1]);
-        ak[t][0] = fma(kv, xx, ak[t][0]);
-        ak[t][1] = fma(kv, xy, ak[t][1]);
-      }
+      for (int t = 0; t < S; ++t)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const double xv = x[t * m + c * nf + j];
+          am[t][c] = fma(mv, xv, am[t][c]);
+          ak[t][c] = fma(kv, xv, ak[t][c]);
+        }
     }
     const int64_t c0 = P.sbp[sl], c1 = P.sbp[sl + 1];
     for (int64_t e = c0 + lane; e < c1; e += 32) {
       const int32_t vtx = P.sbc[e];
-      const double bx = P.sBx[e], by = P.sBy[e];
+      double bv[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) bv[c] = sB[c][e];
 #pragma unroll
       for (int t = 0; t < S; ++t) {
-        const double pv = x[t * m + 2 * nf + vtx];
-        ak[t][0] = fma(bx, pv, ak[t][0]);
-        ak[t][1] = fma(by, pv, ak[t][1]);
+        const double pv = x[t * m + D * nf + vtx];
+#pragma unroll
+        for (int c = 0; c < D; ++c) ak[t][c] = fma(bv[c], pv, ak[t][c]);
       }
     }
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      double yx = am[i][0], yy = am[i][1];
+    for (int i = 0; i < S; ++i)
 #pragma unroll
-      for (int t = 0; t < S; ++t) {
-        yx = fma(P.mix[i * 3 + t], ak[t][0], yx);
-        yy = fma(P.mix[i * 3 + t], ak[t][1], yy);
+      for (int c = 0; c < D; ++c) {
+        double y = am[i][c];
+#pragma unroll
+        for (int t = 0; t < S; ++t) y = fma(P.mix[i * 3 + t], ak[t][c], y);
+        const int64_t g = i * m + c * nf + row;
+        r[g] = F ? F[g] - y : y;
       }
-      const int64_t gx = i * m + row, gy = i * m + nf + row;
-      if (F) {
-        r[gx] = F[gx] - yx;
-        r[gy] = F[gy] - yy;
-      } else {
-        r[gx] = yx;
-        r[gy] = yy;
-      }
-    }
   } else {
     const int64_t v = tidg - P.nf_pad;
     if (v >= P.nv) return;
@@ -98,16 +99,19 @@ __global__ void __launch_bounds__(256) k_residual_sell(OpParams P, const double*
     const int64_t b0 = P.sbtp[sl], b1 = P.sbtp[sl + 1];
     for (int64_t e = b0 + lane; e < b1; e += 32) {
       const int32_t j = P.sbtc[e];
-      const double bx = P.sBTx[e], by = P.sBTy[e];
 #pragma unroll
-      for (int t = 0; t < S; ++t) ap[t] = fma(bx, x[t * m + j], fma(by, x[t * m + nf + j], ap[t]));
+      for (int c = 0; c < D; ++c) {
+        const double bv = sBT[c][e];
+#pragma unroll
+        for (int t = 0; t < S; ++t) ap[t] = fma(bv, x[t * m + c * nf + j], ap[t]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < S; ++i) {
       double y = 0.0;
 #pragma unroll
       for (int t = 0; t < S; ++t) y = fma(P.mix[i * 3 + t], ap[t], y);
-      const int64_t g = i * m + 2 * nf + v;
+      const int64_t g = i * m + D * nf + v;
       r[g] = F ? F[g] - y : y;
     }
   }
@@ -147,6 +151,9 @@ static OpParams op_params(Ctx& C, Level& L, int transpose) {
   P.sbtc = L.sbt.col;
   P.sBTx = L.sbt.v[0];
   P.sBTy = L.sbt.v[1];
+  P.sBz = L.sb.v[2];
+  P.sBTz = L.sbt.v[2];
+  P.Bz = L.b.v[2];
   return P;
 }
 
@@ -155,10 +162,18 @@ cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, 
   OpParams P = op_params(C, L, transpose);
   const int64_t rows = P.nf_pad + L.nv;
   const unsigned grid = (unsigned)((rows + 255) / 256);
-  switch (C.s) {
-    case 1: k_residual_sell<1><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
-    case 2: k_residual_sell<2><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
-    default: k_residual_sell<3><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+  if (L.dim == 2) {
+    switch (C.s) {
+      case 1: k_residual_sell<1, 2><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+      case 2: k_residual_sell<2, 2><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+      default: k_residual_sell<3, 2><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+    }
+  } else {
+    switch (C.s) {
+      case 1: k_residual_sell<1, 3><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+      case 2: k_residual_sell<2, 3><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+      default: k_residual_sell<3, 3><<<grid, 256, 0, C.stream>>>(P, F, x, r); break;
+    }
   }
   return cudaGetLastError();
 }
@@ -168,7 +183,7 @@ cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, 
 // vertices (pressure, every stage).
 // ---------------------------------------------------------------------------
 struct XferParams {
-  int s;
+  int s, dim;
   int64_t nf_out, nv_out, m_out, nf_in, m_in;
   const int32_t *uptr, *ucol;
   const double* uw;
@@ -180,30 +195,30 @@ __global__ void k_transfer(XferParams P, const double* __restrict__ in, double* 
                            int add) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row < P.nf_out) {
-    double acc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int32_t p = P.uptr[row]; p < P.uptr[row + 1]; ++p) {
       const int32_t j = P.ucol[p];
       const double w = P.uw[p];
-      for (int t = 0; t < P.s; ++t) {
-        acc[t][0] = fma(w, in[t * P.m_in + j], acc[t][0]);
-        acc[t][1] = fma(w, in[t * P.m_in + P.nf_in + j], acc[t][1]);
+      for (int t = 0; t < P.s; ++t)
+        for (int c = 0; c < P.dim; ++c)
+          acc[t][c] = fma(w, in[t * P.m_in + c * P.nf_in + j], acc[t][c]);
+    }
+    for (int t = 0; t < P.s; ++t)
+      for (int c = 0; c < P.dim; ++c) {
+        const int64_t g = t * P.m_out + c * P.nf_out + row;
+        out[g] = add ? out[g] + acc[t][c] : acc[t][c];
       }
-    }
-    for (int t = 0; t < P.s; ++t) {
-      const int64_t gx = t * P.m_out + row, gy = t * P.m_out + P.nf_out + row;
-      out[gx] = add ? out[gx] + acc[t][0] : acc[t][0];
-      out[gy] = add ? out[gy] + acc[t][1] : acc[t][1];
-    }
   } else if (row < P.nf_out + P.nv_out) {
     const int64_t v = row - P.nf_out;
     double acc[3] = {0, 0, 0};
     for (int32_t p = P.pptr[v]; p < P.pptr[v + 1]; ++p) {
       const int32_t j = P.pcol[p];
       const double w = P.pw[p];
-      for (int t = 0; t < P.s; ++t) acc[t] = fma(w, in[t * P.m_in + 2 * P.nf_in + j], acc[t]);
+      for (int t = 0; t < P.s; ++t)
+        acc[t] = fma(w, in[t * P.m_in + P.dim * P.nf_in + j], acc[t]);
     }
     for (int t = 0; t < P.s; ++t) {
-      const int64_t g = t * P.m_out + 2 * P.nf_out + v;
+      const int64_t g = t * P.m_out + P.dim * P.nf_out + v;
       out[g] = add ? out[g] + acc[t] : acc[t];
     }
   }
@@ -213,6 +228,7 @@ cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coars
   Level& Lc = *(&Lf - 1);
   XferParams P;
   P.s = C.s;
+  P.dim = Lf.dim;
   P.nf_out = Lc.nf;
   P.nv_out = Lc.nv;
   P.m_out = Lc.m;
@@ -233,6 +249,7 @@ cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine
   Level& Lc = *(&Lf - 1);
   XferParams P;
   P.s = C.s;
+  P.dim = Lf.dim;
   P.nf_out = Lf.nf;
   P.nv_out = Lf.nv;
   P.m_out = Lf.m;
@@ -364,7 +381,7 @@ __global__ void __launch_bounds__(1024) k_pressure_mean(double* x, int64_t m, in
 }
 
 cudaError_t launch_pressure_mean_remove(Ctx& C, Level& L, double* x) {
-  k_pressure_mean<<<C.s, 1024, 0, C.stream>>>(x, L.m, 2 * L.nf, L.nv);
+  k_pressure_mean<<<C.s, 1024, 0, C.stream>>>(x, L.m, L.dim * L.nf, L.nv);
   return cudaGetLastError();
 }
 
@@ -372,7 +389,7 @@ cudaError_t launch_pressure_mean_remove(Ctx& C, Level& L, double* x) {
 // Stage right-hand side and update (Section 3.1)
 // ---------------------------------------------------------------------------
 struct RhsParams {
-  int s;
+  int s, dim;
   int64_t nf, nv, np2, m;
   const int32_t *aptr, *acol;
   const double* Mall;
@@ -382,44 +399,41 @@ struct RhsParams {
   const double *Bx, *By;
   const int32_t *btptr, *btcol;
   const double *BTx, *BTy;
+  const double *Bz, *BTz;
 };
 
 __global__ void k_stage_rhs(RhsParams P, const double* __restrict__ un, const double* __restrict__ pn,
                             const double* __restrict__ f, double* __restrict__ F) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nf = P.nf;
+  const int D = P.dim;
+  const double* Bc[3] = {P.Bx, P.By, P.Bz};
+  const double* BTc[3] = {P.BTx, P.BTy, P.BTz};
   if (row < nf) {
-    double kx = 0.0, ky = 0.0;
+    double kc[3] = {0.0, 0.0, 0.0};
     for (int32_t p = P.vptr[row]; p < P.vptr[row + 1]; ++p) {
       const int32_t j = P.vcol[p];
-      kx = fma(P.K[p], un[j], kx);
-      ky = fma(P.K[p], un[nf + j], ky);
+      for (int c = 0; c < D; ++c) kc[c] = fma(P.K[p], un[c * nf + j], kc[c]);
     }
     for (int32_t p = P.bptr[row]; p < P.bptr[row + 1]; ++p) {
       const double pv = pn[P.bcol[p]];
-      kx = fma(P.Bx[p], pv, kx);
-      ky = fma(P.By[p], pv, ky);
+      for (int c = 0; c < D; ++c) kc[c] = fma(Bc[c][p], pv, kc[c]);
     }
-    for (int t = 0; t < P.s; ++t) {
-      double mx = 0.0, my = 0.0;
-      const double* fx = f + (int64_t)t * 2 * P.np2;
-      const double* fy = fx + P.np2;
-      for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) {
-        const int32_t j = P.acol[p];
-        mx = fma(P.Mall[p], fx[j], mx);
-        my = fma(P.Mall[p], fy[j], my);
+    for (int t = 0; t < P.s; ++t)
+      for (int c = 0; c < D; ++c) {
+        double mc = 0.0;
+        const double* fc = f + ((int64_t)t * D + c) * P.np2;
+        for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) mc = fma(P.Mall[p], fc[P.acol[p]], mc);
+        F[t * P.m + c * nf + row] = mc - kc[c];
       }
-      F[t * P.m + row] = mx - kx;
-      F[t * P.m + nf + row] = my - ky;
-    }
   } else if (row < nf + P.nv) {
     const int64_t v = row - nf;
     double a = 0.0;
     for (int32_t p = P.btptr[v]; p < P.btptr[v + 1]; ++p) {
       const int32_t j = P.btcol[p];
-      a = fma(P.BTx[p], un[j], fma(P.BTy[p], un[nf + j], a));
+      for (int c = 0; c < D; ++c) a = fma(BTc[c][p], un[c * nf + j], a);
     }
-    for (int t = 0; t < P.s; ++t) F[t * P.m + 2 * nf + v] = -a;
+    for (int t = 0; t < P.s; ++t) F[t * P.m + D * nf + v] = -a;
   }
 }
 
@@ -428,6 +442,9 @@ cudaError_t launch_stage_rhs(Ctx& C, const double* un, const double* pn, const d
   Level& L = C.L.back();
   RhsParams P;
   P.s = C.s;
+  P.dim = L.dim;
+  P.Bz = L.b.v[2];
+  P.BTz = L.bt.v[2];
   P.nf = L.nf;
   P.nv = L.nv;
   P.np2 = L.np2;
@@ -455,45 +472,41 @@ cudaError_t launch_stage_rhs(Ctx& C, const double* un, const double* pn, const d
 // included, e.g. a moving lid): F_i = [M f_i - K u^n - B p^n; -Bᵀ u^n] with K
 // and Bᵀ taken over every velocity column.
 __global__ void k_stage_rhs_full(RhsParams P, const int32_t* __restrict__ btaptr,
-                                 const int32_t* __restrict__ btacol,
-                                 const double* __restrict__ btax, const double* __restrict__ btay,
+                                 const int32_t* __restrict__ btacol, const double* btax,
+                                 const double* btay, const double* btaz,
                                  const double* __restrict__ Kall, const double* __restrict__ un,
                                  const double* __restrict__ pn, const double* __restrict__ f,
                                  double* __restrict__ F) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nf = P.nf, np2 = P.np2;
+  const int D = P.dim;
+  const double* Bc[3] = {P.Bx, P.By, P.Bz};
+  const double* BTA[3] = {btax, btay, btaz};
   if (row < nf) {
-    double kx = 0.0, ky = 0.0;
+    double kc[3] = {0.0, 0.0, 0.0};
     for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) {
       const int32_t j = P.acol[p];
-      kx = fma(Kall[p], un[j], kx);
-      ky = fma(Kall[p], un[np2 + j], ky);
+      for (int c = 0; c < D; ++c) kc[c] = fma(Kall[p], un[c * np2 + j], kc[c]);
     }
     for (int32_t p = P.bptr[row]; p < P.bptr[row + 1]; ++p) {
       const double pv = pn[P.bcol[p]];
-      kx = fma(P.Bx[p], pv, kx);
-      ky = fma(P.By[p], pv, ky);
+      for (int c = 0; c < D; ++c) kc[c] = fma(Bc[c][p], pv, kc[c]);
     }
-    for (int t = 0; t < P.s; ++t) {
-      double mx = 0.0, my = 0.0;
-      const double* fx = f + (int64_t)t * 2 * np2;
-      const double* fy = fx + np2;
-      for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) {
-        const int32_t j = P.acol[p];
-        mx = fma(P.Mall[p], fx[j], mx);
-        my = fma(P.Mall[p], fy[j], my);
+    for (int t = 0; t < P.s; ++t)
+      for (int c = 0; c < D; ++c) {
+        double mc = 0.0;
+        const double* fc = f + ((int64_t)t * D + c) * np2;
+        for (int32_t p = P.aptr[row]; p < P.aptr[row + 1]; ++p) mc = fma(P.Mall[p], fc[P.acol[p]], mc);
+        F[t * P.m + c * nf + row] = mc - kc[c];
       }
-      F[t * P.m + row] = mx - kx;
-      F[t * P.m + nf + row] = my - ky;
-    }
   } else if (row < nf + P.nv) {
     const int64_t v = row - nf;
     double a = 0.0;
     for (int32_t p = btaptr[v]; p < btaptr[v + 1]; ++p) {
       const int32_t j = btacol[p];
-      a = fma(btax[p], un[j], fma(btay[p], un[np2 + j], a));
+      for (int c = 0; c < D; ++c) a = fma(BTA[c][p], un[c * np2 + j], a);
     }
-    for (int t = 0; t < P.s; ++t) F[t * P.m + 2 * nf + v] = -a;
+    for (int t = 0; t < P.s; ++t) F[t * P.m + D * nf + v] = -a;
   }
 }
 
@@ -502,6 +515,9 @@ cudaError_t launch_stage_rhs_full(Ctx& C, const double* un_all, const double* pn
   Level& L = C.L.back();
   RhsParams P;
   P.s = C.s;
+  P.dim = L.dim;
+  P.Bz = L.b.v[2];
+  P.BTz = L.bt.v[2];
   P.nf = L.nf;
   P.nv = L.nv;
   P.np2 = L.np2;
@@ -521,8 +537,11 @@ cudaError_t launch_stage_rhs_full(Ctx& C, const double* un_all, const double* pn
   P.BTx = L.bt.v[0];
   P.BTy = L.bt.v[1];
   const int64_t rows = L.nf + L.nv;
+  P.dim = L.dim;
+  P.Bz = L.b.v[2];
   k_stage_rhs_full<<<(unsigned)((rows + 255) / 256), 256, 0, C.stream>>>(
-      P, L.btall.ptr, L.btall.col, L.btall.v[0], L.btall.v[1], L.mall.v[1], un_all, pn, f, F);
+      P, L.btall.ptr, L.btall.col, L.btall.v[0], L.btall.v[1], L.btall.v[2], L.mall.v[1], un_all,
+      pn, f, F);
   return cudaGetLastError();
 }
 
@@ -545,8 +564,8 @@ cudaError_t launch_advance(Ctx& C, const double* k, double* un, double* pn) {
   Level& L = C.L.back();
   double bw[3] = {0, 0, 0};
   for (int t = 0; t < C.s; ++t) bw[t] = C.dt * C.b[t];
-  k_advance<<<grid_for(L.m), 256, 0, C.stream>>>(C.s, 2 * L.nf, L.nv, L.m, bw[0], bw[1], bw[2], k,
-                                                 un, pn);
+  k_advance<<<grid_for(L.m), 256, 0, C.stream>>>(C.s, L.dim * L.nf, L.nv, L.m, bw[0], bw[1], bw[2],
+                                                 k, un, pn);
   return cudaGetLastError();
 }
 

@@ -18,19 +18,19 @@
 namespace irkmg {
 
 constexpr int kMaxStar = 24;        // cells around a vertex handled by the map kernel
-constexpr int kMaxPatchNodes = 64;  // free P2 nodes per patch (2D interior: 19)
+constexpr int kMaxPatchNodes = 96;  // free P2 nodes per patch (interior: 19 in 2D, 65 in 3D)
 
 // ---------------------------------------------------------------------------
 // Patch maps
 // ---------------------------------------------------------------------------
-__global__ void k_patch_maps(int32_t nv, const int32_t* __restrict__ cells,
+__global__ void k_patch_maps(int32_t nv, int kv, int ke, const int32_t* __restrict__ cells,
                              const int32_t* __restrict__ cell_edges,
                              const int32_t* __restrict__ vc_ptr, const int32_t* __restrict__ vc_idx,
                              const int32_t* __restrict__ p2_to_free, int32_t maxnodes,
                              int32_t* __restrict__ tmp, int32_t* __restrict__ cnt) {
   int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
-  int32_t buf[6 * kMaxStar];
+  int32_t buf[10 * kMaxStar];
   int n = 0;
   const int32_t b0 = vc_ptr[v], b1 = vc_ptr[v + 1];
   if (b1 - b0 > kMaxStar) {
@@ -39,12 +39,12 @@ __global__ void k_patch_maps(int32_t nv, const int32_t* __restrict__ cells,
   }
   for (int32_t p = b0; p < b1; ++p) {
     const int32_t c = vc_idx[p];
-    for (int a = 0; a < 3; ++a) {
-      int32_t f = p2_to_free[cells[3 * c + a]];
+    for (int a = 0; a < kv; ++a) {
+      int32_t f = p2_to_free[cells[kv * c + a]];
       if (f >= 0) buf[n++] = f;
     }
-    for (int a = 0; a < 3; ++a) {
-      int32_t f = p2_to_free[nv + cell_edges[3 * c + a]];
+    for (int a = 0; a < ke; ++a) {
+      int32_t f = p2_to_free[nv + cell_edges[ke * c + a]];
       if (f >= 0) buf[n++] = f;
     }
   }
@@ -105,9 +105,9 @@ __global__ void k_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out
 cudaError_t launch_patch_maps(Level& L, cudaStream_t st, int maxnodes, int32_t* d_tmp,
                               int32_t* d_cnt) {
   int32_t nv = (int32_t)L.nv;
-  k_patch_maps<<<(nv + 127) / 128, 128, 0, st>>>(nv, L.d_cells, L.d_cell_edges, L.d_vc_ptr,
-                                                  L.d_vc_idx, L.d_p2_to_free, maxnodes, d_tmp,
-                                                  d_cnt);
+  k_patch_maps<<<(nv + 127) / 128, 128, 0, st>>>(nv, L.mesh.nvc(), L.mesh.nle(), L.d_cells,
+                                                  L.d_cell_edges, L.d_vc_ptr, L.d_vc_idx,
+                                                  L.d_p2_to_free, maxnodes, d_tmp, d_cnt);
   return cudaGetLastError();
 }
 
@@ -205,7 +205,7 @@ __device__ __forceinline__ int csr_find(const int32_t* __restrict__ col, int32_t
 }
 
 struct InvParams {
-  int s;
+  int s, dim;
   double A[9];
   double dt;
   int64_t nf;
@@ -214,7 +214,7 @@ struct InvParams {
   const int32_t *vptr, *vcol;
   const double *M, *K;
   const int32_t *bptr, *bcol;
-  const double *Bx, *By;
+  const double *Bx, *By, *Bz;
   int* err;  // [0] status, [1] patch id
 };
 
@@ -231,7 +231,8 @@ __global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatc
   if (pi >= npatch) return;
   const int32_t v = P.order[pi];
   const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
-  const int q = 2 * L + 1, np = P.s * q;
+  const int D = P.dim;
+  const int q = D * L + 1, np = P.s * q;
   double* A = smem;  // row-major np x np
   for (int i = threadIdx.x; i < L; i += blockDim.x) nodes[i] = P.patch_nodes[nb + i];
   for (int i = threadIdx.x; i < np * np; i += blockDim.x) A[i] = 0.0;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatc
     for (int t = 0; t < P.s; ++t)
       for (int u = 0; u < P.s; ++u) {
         const double val = (t == u ? mab : 0.0) + P.dt * P.A[t * 3 + u] * kab;
-        for (int d = 0; d < 2; ++d) A[(t * q + d * L + a) * np + (u * q + d * L + b)] = val;
+        for (int d = 0; d < D; ++d) A[(t * q + d * L + a) * np + (u * q + d * L + b)] = val;
       }
   }
   // velocity-pressure and pressure-velocity blocks
@@ -258,18 +259,17 @@ __global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatc
     const int32_t ra = nodes[a];
     const int32_t p0 = P.bptr[ra], p1 = P.bptr[ra + 1];
     const int32_t pos = csr_find(P.bcol, p0, p1, v);
-    double bx = 0.0, by = 0.0;
-    if (pos < p1 && P.bcol[pos] == v) {
-      bx = P.Bx[pos];
-      by = P.By[pos];
-    }
+    double bv[3] = {0.0, 0.0, 0.0};
+    const double* Bc[3] = {P.Bx, P.By, P.Bz};
+    if (pos < p1 && P.bcol[pos] == v)
+      for (int d = 0; d < D; ++d) bv[d] = Bc[d][pos];
     for (int t = 0; t < P.s; ++t)
       for (int u = 0; u < P.s; ++u) {
         const double f = P.dt * P.A[t * 3 + u];
-        A[(t * q + a) * np + (u * q + 2 * L)] = f * bx;
-        A[(t * q + L + a) * np + (u * q + 2 * L)] = f * by;
-        A[(t * q + 2 * L) * np + (u * q + a)] = f * bx;
-        A[(t * q + 2 * L) * np + (u * q + L + a)] = f * by;
+        for (int d = 0; d < D; ++d) {
+          A[(t * q + d * L + a) * np + (u * q + D * L)] = f * bv[d];
+          A[(t * q + D * L) * np + (u * q + d * L + a)] = f * bv[d];
+        }
       }
   }
   __syncthreads();
@@ -358,6 +358,8 @@ __global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatc
 cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
   InvParams P;
   P.s = C.s;
+  P.dim = L.dim;
+  P.Bz = L.b.v[2];
   for (int i = 0; i < 9; ++i) P.A[i] = 0.0;
   for (int i = 0; i < C.s; ++i)
     for (int j = 0; j < C.s; ++j) P.A[i * 3 + j] = C.A[i * C.s + j];
@@ -391,7 +393,7 @@ cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
 
 // Global DoF index list of every ordered patch, stored after its inverse.
 template <typename T>
-__global__ void k_patch_gidx(int s, int64_t nf, int64_t m, int64_t npatch,
+__global__ void k_patch_gidx(int s, int D, int64_t nf, int64_t m, int64_t npatch,
                              const int32_t* __restrict__ patch_ptr,
                              const int32_t* __restrict__ patch_nodes,
                              const int32_t* __restrict__ order, const int64_t* __restrict__ fac_off,
@@ -401,18 +403,18 @@ __global__ void k_patch_gidx(int s, int64_t nf, int64_t m, int64_t npatch,
   if (pi >= npatch) return;
   const int32_t v = order[pi];
   const int32_t nb = patch_ptr[v], L = patch_ptr[v + 1] - nb;
-  const int q = 2 * L + 1, np = s * q;
+  const int q = D * L + 1, np = s * q;
   const int64_t xbytes = ((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15;
   int32_t* g = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(fac + fac_off[pi]) + xbytes);
   for (int i = lane; i < np; i += 32) {
     const int t = i / q, k = i - t * q;
     int64_t gi;
-    if (k < L)
-      gi = t * m + patch_nodes[nb + k];
-    else if (k < 2 * L)
-      gi = t * m + nf + patch_nodes[nb + k - L];
-    else
-      gi = t * m + 2 * nf + v;
+    if (k < D * L) {
+      const int c = k / L;
+      gi = t * m + c * nf + patch_nodes[nb + k - c * L];
+    } else {
+      gi = t * m + D * nf + v;
+    }
     g[i] = (int32_t)gi;
   }
 }
@@ -420,11 +422,11 @@ __global__ void k_patch_gidx(int s, int64_t nf, int64_t m, int64_t npatch,
 cudaError_t launch_patch_gidx(Ctx& C, Level& L) {
   const unsigned grid = (unsigned)((L.nv * 32 + 255) / 256);
   if (C.opt.patch_precision == 64)
-    k_patch_gidx<double><<<grid, 256, 0, C.stream>>>(C.s, L.nf, L.m, L.nv, L.d_patch_ptr,
+    k_patch_gidx<double><<<grid, 256, 0, C.stream>>>(C.s, L.dim, L.nf, L.m, L.nv, L.d_patch_ptr,
                                                      L.d_patch_nodes, L.d_order, L.d_fac_off,
                                                      (double*)L.d_fac);
   else
-    k_patch_gidx<float><<<grid, 256, 0, C.stream>>>(C.s, L.nf, L.m, L.nv, L.d_patch_ptr,
+    k_patch_gidx<float><<<grid, 256, 0, C.stream>>>(C.s, L.dim, L.nf, L.m, L.nv, L.d_patch_ptr,
                                                     L.d_patch_nodes, L.d_order, L.d_fac_off,
                                                     (float*)L.d_fac);
   return cudaGetLastError();
@@ -441,7 +443,7 @@ constexpr int kApplyWarps = 8;
 constexpr int kMaxNp = 160;
 
 struct ApplyParams {
-  int s;
+  int s, dim;
   int64_t nf, m;
   const int32_t *patch_ptr, *patch_nodes, *order, *np;
   const int64_t* fac_off;
@@ -461,16 +463,16 @@ __global__ void __launch_bounds__(kApplyWarps * 32) k_vanka_apply(ApplyParams P,
   const int64_t pi = P.first + w;
   const int32_t v = P.order[pi];
   const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
-  const int q = 2 * L + 1, np = P.s * q;
+  const int q = P.dim * L + 1, np = P.s * q;
   for (int i = lane; i < np; i += 32) {
     const int t = i / q, k = i - t * q;
     int64_t g;
-    if (k < L)
-      g = t * P.m + P.patch_nodes[nb + k];
-    else if (k < 2 * L)
-      g = t * P.m + P.nf + P.patch_nodes[nb + k - L];
-    else
-      g = t * P.m + 2 * P.nf + v;
+    if (k < P.dim * L) {
+      const int c = k / L;
+      g = t * P.m + c * P.nf + P.patch_nodes[nb + k - c * L];
+    } else {
+      g = t * P.m + P.dim * P.nf + v;
+    }
     s_g[warp][i] = (int32_t)g;
     s_r[warp][i] = (T)P.r[g];
   }
@@ -509,16 +511,16 @@ __global__ void __launch_bounds__(kApplyWarps * 32) k_vanka_apply_t(ApplyParams 
   const int64_t pi = P.first + w;
   const int32_t v = P.order[pi];
   const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
-  const int q = 2 * L + 1, np = P.s * q;
+  const int q = P.dim * L + 1, np = P.s * q;
   for (int i = lane; i < np; i += 32) {
     const int t = i / q, k = i - t * q;
     int64_t g;
-    if (k < L)
-      g = t * P.m + P.patch_nodes[nb + k];
-    else if (k < 2 * L)
-      g = t * P.m + P.nf + P.patch_nodes[nb + k - L];
-    else
-      g = t * P.m + 2 * P.nf + v;
+    if (k < P.dim * L) {
+      const int c = k / L;
+      g = t * P.m + c * P.nf + P.patch_nodes[nb + k - c * L];
+    } else {
+      g = t * P.m + P.dim * P.nf + v;
+    }
     s_g[warp][i] = (int32_t)g;
     s_r[warp][i] = (T)P.r[g];
   }
@@ -760,6 +762,7 @@ cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* 
                          int transpose) {
   ApplyParams P;
   P.s = C.s;
+  P.dim = L.dim;
   P.nf = L.nf;
   P.m = L.m;
   P.patch_ptr = L.d_patch_ptr;

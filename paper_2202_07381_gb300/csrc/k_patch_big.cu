@@ -1,0 +1,398 @@
+// Vanka patches too large for one shared-memory inverse (3D: up to 392 DoFs
+// for s = 2, Section 4.2 with all stages in every patch).
+//
+//   k_patch_lu_big: gather A_v = R_v J R_vᵀ from the assembled operators into
+//     the patch's block (column-major, in place) and factor it,
+//     P A_v = L U, by a blocked right-looking LU with partial pivoting:
+//     32-column panels factored in shared memory, row interchanges applied to
+//     the rest of the matrix, a triangular solve for the U block row, and the
+//     trailing update A22 -= L21 U12 from shared-memory tiles.
+//   k_vanka_apply_lu: out[S_v] += scale · U⁻¹ L⁻¹ P r|_{S_v}: the pivots, then
+//     blocked forward and backward substitution (each 32 x 32 diagonal block is
+//     staged in shared memory and solved by one warp; the off-diagonal blocks
+//     are streamed once with coalesced column reads).  One launch per colour.
+// Block layout of a patch: [n_p^2 values][n_p int32 DoF indices][n_p int32
+// pivots], each part padded to 16 bytes.
+#include <cfloat>
+
+#include "irkmg_internal.h"
+
+namespace irkmg {
+
+constexpr int kBigThreads = 256;
+constexpr int kPanel = 32;
+constexpr int kUChunk = 128;
+
+struct BigParams {
+  int s, dim;
+  double A[9];
+  double dt;
+  int64_t nf, m;
+  const int32_t *patch_ptr, *patch_nodes, *order, *np;
+  const int64_t* fac_off;
+  const int32_t *vptr, *vcol;
+  const double *M, *K;
+  const int32_t *bptr, *bcol;
+  const double *Bx, *By, *Bz;
+  int* err;
+  // apply
+  const double* r;
+  double* out;
+  double scale;
+  int64_t first, count;
+};
+
+__device__ __forceinline__ int big_csr_find(const int32_t* __restrict__ col, int32_t b, int32_t e,
+                                            int32_t key) {
+  while (b < e) {
+    int32_t mid = (b + e) >> 1;
+    if (col[mid] < key)
+      b = mid + 1;
+    else
+      e = mid;
+  }
+  return b;
+}
+
+template <typename T>
+__device__ __forceinline__ int64_t big_x_bytes(int np) {
+  return ((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15;
+}
+__device__ __forceinline__ int64_t big_i_bytes(int np) { return ((int64_t)np * 4 + 15) & ~(int64_t)15; }
+
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64_t npatch, T* fac) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ double red_v[kBigThreads];
+  __shared__ int red_i[kBigThreads];
+  __shared__ int s_piv[kPanel];
+  __shared__ int32_t nodes[96];
+  __shared__ double s_thr;
+  const int64_t pi = blockIdx.x;
+  if (pi >= npatch) return;
+  const int tid = threadIdx.x;
+  const int32_t v = P.order[pi];
+  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+  const int D = P.dim;
+  const int q = D * L + 1, np = P.s * q;
+  T* A = fac + P.fac_off[pi];  // column-major: A[c * np + r]
+  int32_t* piv = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(A) + big_x_bytes<T>(np) +
+                                            big_i_bytes(np));
+  T* Pn = reinterpret_cast<T*>(dyn);               // panel, [kPanel][np - k0]
+  T* Ub = Pn + (size_t)kPanel * np;                // U12 chunk, [kPanel][kUChunk]
+  for (int i = tid; i < L; i += kBigThreads) nodes[i] = P.patch_nodes[nb + i];
+  for (int64_t i = tid; i < (int64_t)np * np; i += kBigThreads) A[i] = (T)0;
+  __syncthreads();
+  // ---- gather A_v (Section 3.1 Kronecker blocks) ----
+  double mx = 0.0;
+  const double* Bc[3] = {P.Bx, P.By, P.Bz};
+  for (int idx = tid; idx < L * L; idx += kBigThreads) {
+    const int a = idx / L, b = idx % L;
+    const int32_t ra = nodes[a], cb = nodes[b];
+    const int32_t p0 = P.vptr[ra], p1 = P.vptr[ra + 1];
+    const int32_t pos = big_csr_find(P.vcol, p0, p1, cb);
+    double mab = 0.0, kab = 0.0;
+    if (pos < p1 && P.vcol[pos] == cb) {
+      mab = P.M[pos];
+      kab = P.K[pos];
+    }
+    for (int t = 0; t < P.s; ++t)
+      for (int u = 0; u < P.s; ++u) {
+        const double val = (t == u ? mab : 0.0) + P.dt * P.A[t * 3 + u] * kab;
+        mx = fmax(mx, fabs(val));
+        for (int d = 0; d < D; ++d)
+          A[(int64_t)(u * q + d * L + b) * np + (t * q + d * L + a)] = (T)val;
+      }
+  }
+  for (int a = tid; a < L; a += kBigThreads) {
+    const int32_t ra = nodes[a];
+    const int32_t p0 = P.bptr[ra], p1 = P.bptr[ra + 1];
+    const int32_t pos = big_csr_find(P.bcol, p0, p1, v);
+    double bv[3] = {0.0, 0.0, 0.0};
+    if (pos < p1 && P.bcol[pos] == v)
+      for (int d = 0; d < D; ++d) bv[d] = Bc[d][pos];
+    for (int t = 0; t < P.s; ++t)
+      for (int u = 0; u < P.s; ++u) {
+        const double f = P.dt * P.A[t * 3 + u];
+        for (int d = 0; d < D; ++d) {
+          mx = fmax(mx, fabs(f * bv[d]));
+          A[(int64_t)(u * q + D * L) * np + (t * q + d * L + a)] = (T)(f * bv[d]);
+          A[(int64_t)(u * q + d * L + a) * np + (t * q + D * L)] = (T)(f * bv[d]);
+        }
+      }
+  }
+  red_v[tid] = mx;
+  __syncthreads();
+  for (int o = kBigThreads / 2; o > 0; o >>= 1) {
+    if (tid < o) red_v[tid] = fmax(red_v[tid], red_v[tid + o]);
+    __syncthreads();
+  }
+  if (tid == 0) s_thr = 1e3 * DBL_EPSILON * red_v[0];
+  __syncthreads();
+
+  // ---- blocked LU with partial pivoting ----
+  for (int k0 = 0; k0 < np; k0 += kPanel) {
+    const int kb = min(kPanel, np - k0), prow = np - k0;
+    for (int idx = tid; idx < prow * kb; idx += kBigThreads) {
+      const int l = idx / prow, r = idx - l * prow;
+      Pn[l * prow + r] = A[(int64_t)(k0 + l) * np + k0 + r];
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+      double best = -1.0;
+      int bi = j;
+      for (int r = j + tid; r < prow; r += kBigThreads) {
+        const double a = fabs((double)Pn[j * prow + r]);
+        if (a > best) {
+          best = a;
+          bi = r;
+        }
+      }
+      red_v[tid] = best;
+      red_i[tid] = bi;
+      __syncthreads();
+      for (int o = kBigThreads / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+          const double a = red_v[tid + o];
+          const int ia = red_i[tid + o];
+          if (a > red_v[tid] || (a == red_v[tid] && ia < red_i[tid])) {
+            red_v[tid] = a;
+            red_i[tid] = ia;
+          }
+        }
+        __syncthreads();
+      }
+      const int p = red_i[0];
+      const double pabs = red_v[0];
+      if (tid == 0) {
+        s_piv[j] = p;
+        piv[k0 + j] = k0 + p;
+        if (!(pabs > s_thr) && atomicCAS(&P.err[0], 0, IRKMG_ESINGULAR) == 0) P.err[1] = v;
+      }
+      if (p != j)
+        for (int l = tid; l < kb; l += kBigThreads) {
+          const T x = Pn[l * prow + j];
+          Pn[l * prow + j] = Pn[l * prow + p];
+          Pn[l * prow + p] = x;
+        }
+      __syncthreads();
+      const T pv = Pn[j * prow + j];
+      const T inv = pabs > 0.0 ? (T)1 / pv : (T)0;
+      for (int r = j + 1 + tid; r < prow; r += kBigThreads) Pn[j * prow + r] *= inv;
+      __syncthreads();
+      const int rows = prow - j - 1, cols = kb - j - 1;
+      for (int idx = tid; idx < rows * cols; idx += kBigThreads) {
+        const int l = j + 1 + idx / rows, r = j + 1 + idx % rows;
+        Pn[l * prow + r] -= Pn[j * prow + r] * Pn[l * prow + j];
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < prow * kb; idx += kBigThreads) {
+      const int l = idx / prow, r = idx - l * prow;
+      A[(int64_t)(k0 + l) * np + k0 + r] = Pn[l * prow + r];
+    }
+    // row interchanges of this panel, applied (in order) to every other column
+    for (int c = tid; c < np; c += kBigThreads) {
+      if (c >= k0 && c < k0 + kb) continue;
+      T* col = A + (int64_t)c * np + k0;
+      for (int j = 0; j < kb; ++j) {
+        const int p = s_piv[j];
+        if (p != j) {
+          const T x = col[j];
+          col[j] = col[p];
+          col[p] = x;
+        }
+      }
+    }
+    __syncthreads();
+    // U12 = L11^{-1} A12 (unit lower L11 from the panel)
+    const int ncol = np - k0 - kb;
+    for (int c = tid; c < ncol; c += kBigThreads) {
+      T* col = A + (int64_t)(k0 + kb + c) * np + k0;
+      T x[kPanel];
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l) x[l] = l < kb ? col[l] : (T)0;
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l)
+#pragma unroll
+        for (int i = 0; i < kPanel; ++i)
+          if (i > l && i < kb) x[i] -= Pn[l * prow + i] * x[l];
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l)
+        if (l < kb) col[l] = x[l];
+    }
+    __syncthreads();
+    // A22 -= L21 U12, U12 staged in chunks of kUChunk columns
+    const int mrow = prow - kb;
+    for (int cc0 = 0; cc0 < ncol; cc0 += kUChunk) {
+      const int cw = min(kUChunk, ncol - cc0);
+      for (int idx = tid; idx < kb * cw; idx += kBigThreads) {
+        const int l = idx % kb, c = idx / kb;
+        Ub[l * kUChunk + c] = A[(int64_t)(k0 + kb + cc0 + c) * np + k0 + l];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < mrow * cw; idx += kBigThreads) {
+        const int i = idx % mrow, c = idx / mrow;
+        T* a = A + (int64_t)(k0 + kb + cc0 + c) * np + k0 + kb + i;
+        T acc = *a;
+        for (int l = 0; l < kb; ++l) acc -= Pn[l * prow + kb + i] * Ub[l * kUChunk + c];
+        *a = acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) k_vanka_apply_lu(BigParams P, const T* __restrict__ fac) {
+  __shared__ T y[kMaxBigNp];
+  __shared__ T Db[kPanel * kPanel];
+  __shared__ int32_t g[kMaxBigNp];
+  const int64_t w = blockIdx.x;
+  if (w >= P.count) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t pi = P.first + w;
+  const int np = P.np[pi];
+  const T* A = fac + P.fac_off[pi];
+  const int32_t* G = reinterpret_cast<const int32_t*>(reinterpret_cast<const unsigned char*>(A) +
+                                                      big_x_bytes<T>(np));
+  const int32_t* piv = reinterpret_cast<const int32_t*>(reinterpret_cast<const unsigned char*>(A) +
+                                                        big_x_bytes<T>(np) + big_i_bytes(np));
+  for (int i = tid; i < np; i += kBigThreads) {
+    const int32_t gi = G[i];
+    g[i] = gi;
+    y[i] = (T)P.r[gi];
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < np; ++j) {
+      const int p = piv[j];
+      if (p != j) {
+        const T x = y[j];
+        y[j] = y[p];
+        y[p] = x;
+      }
+    }
+  __syncthreads();
+  // L y = P r (unit lower)
+  for (int k0 = 0; k0 < np; k0 += kPanel) {
+    const int kb = min(kPanel, np - k0);
+    for (int idx = tid; idx < kb * kb; idx += kBigThreads) {
+      const int l = idx / kb, i = idx % kb;
+      Db[l * kPanel + i] = A[(int64_t)(k0 + l) * np + k0 + i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T yi = lane < kb ? y[k0 + lane] : (T)0;
+      for (int l = 0; l < kb; ++l) {
+        const T yl = __shfl_sync(0xffffffffu, yi, l);
+        if (lane > l && lane < kb) yi -= Db[l * kPanel + lane] * yl;
+      }
+      if (lane < kb) y[k0 + lane] = yi;
+    }
+    __syncthreads();
+    for (int i = k0 + kb + tid; i < np; i += kBigThreads) {
+      T acc = y[i];
+      for (int l = 0; l < kb; ++l) acc -= A[(int64_t)(k0 + l) * np + i] * y[k0 + l];
+      y[i] = acc;
+    }
+    __syncthreads();
+  }
+  // U x = y
+  const int last = ((np - 1) / kPanel) * kPanel;
+  for (int k0 = last; k0 >= 0; k0 -= kPanel) {
+    const int kb = min(kPanel, np - k0);
+    for (int idx = tid; idx < kb * kb; idx += kBigThreads) {
+      const int l = idx / kb, i = idx % kb;
+      Db[l * kPanel + i] = A[(int64_t)(k0 + l) * np + k0 + i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T yi = lane < kb ? y[k0 + lane] : (T)0;
+      for (int l = kb - 1; l >= 0; --l) {
+        if (lane == l) yi = yi / Db[l * kPanel + l];
+        const T yl = __shfl_sync(0xffffffffu, yi, l);
+        if (lane < l) yi -= Db[l * kPanel + lane] * yl;
+      }
+      if (lane < kb) y[k0 + lane] = yi;
+    }
+    __syncthreads();
+    for (int i = tid; i < k0; i += kBigThreads) {
+      T acc = y[i];
+      for (int l = 0; l < kb; ++l) acc -= A[(int64_t)(k0 + l) * np + i] * y[k0 + l];
+      y[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < np; i += kBigThreads) P.out[g[i]] += P.scale * (double)y[i];
+}
+
+static BigParams big_params(Ctx& C, Level& L) {
+  BigParams P;
+  P.s = C.s;
+  P.dim = L.dim;
+  for (int i = 0; i < 9; ++i) P.A[i] = 0.0;
+  for (int i = 0; i < C.s; ++i)
+    for (int j = 0; j < C.s; ++j) P.A[i * 3 + j] = C.A[i * C.s + j];
+  P.dt = C.dt;
+  P.nf = L.nf;
+  P.m = L.m;
+  P.patch_ptr = L.d_patch_ptr;
+  P.patch_nodes = L.d_patch_nodes;
+  P.order = L.d_order;
+  P.np = L.d_np;
+  P.fac_off = L.d_fac_off;
+  P.vptr = L.vel.ptr;
+  P.vcol = L.vel.col;
+  P.M = L.vel.v[0];
+  P.K = L.vel.v[1];
+  P.bptr = L.b.ptr;
+  P.bcol = L.b.col;
+  P.Bx = L.b.v[0];
+  P.By = L.b.v[1];
+  P.Bz = L.b.v[2];
+  P.err = C.d_err;
+  P.r = nullptr;
+  P.out = nullptr;
+  P.scale = 0.0;
+  P.first = P.count = 0;
+  return P;
+}
+
+cudaError_t launch_patch_lu_big(Ctx& C, Level& L) {
+  BigParams P = big_params(C, L);
+  if (C.opt.patch_precision == 64) {
+    const size_t smem = (size_t)kPanel * (kMaxBigNp + kUChunk) * sizeof(double);
+    cudaFuncSetAttribute(k_patch_lu_big<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_lu_big<double><<<(unsigned)L.nv, kBigThreads, smem, C.stream>>>(P, L.nv,
+                                                                            (double*)L.d_fac);
+  } else {
+    const size_t smem = (size_t)kPanel * (kMaxBigNp + kUChunk) * sizeof(float);
+    cudaFuncSetAttribute(k_patch_lu_big<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_lu_big<float><<<(unsigned)L.nv, kBigThreads, smem, C.stream>>>(P, L.nv,
+                                                                           (float*)L.d_fac);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vanka_lu(Ctx& C, Level& L, int colour, const double* r, double* out,
+                            double scale) {
+  BigParams P = big_params(C, L);
+  P.r = r;
+  P.out = out;
+  P.scale = scale;
+  P.first = L.colour_start[colour];
+  P.count = L.colour_start[colour + 1] - P.first;
+  if (P.count <= 0) return cudaSuccess;
+  if (C.opt.patch_precision == 64)
+    k_vanka_apply_lu<double><<<(unsigned)P.count, kBigThreads, 0, C.stream>>>(
+        P, (const double*)L.d_fac);
+  else
+    k_vanka_apply_lu<float><<<(unsigned)P.count, kBigThreads, 0, C.stream>>>(
+        P, (const float*)L.d_fac);
+  return cudaGetLastError();
+}
+
+}  // namespace irkmg

@@ -54,7 +54,8 @@ class Stats(ct.Structure):
 class LevelInfo(ct.Structure):
     _fields_ = [(k, ct.c_int64) for k in ("nv", "ne", "nc", "np2", "nf", "m", "N", "npatch",
                                           "ncolours", "max_patch_dofs", "factor_bytes",
-                                          "apply_kernel")] + [("apply_ms", ct.c_double * 2)]
+                                          "apply_kernel")] + [("apply_ms", ct.c_double * 2),
+                                                              ("dim", ct.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "apply_ms"}
@@ -210,7 +211,7 @@ def irkmg_setup(coords, cells, bnd, A, b, c, dt, nu, options=None, wind=None, st
     xy, pxy = _hptr(coords, np.float64)
     cl, pcl = _hptr(cells, np.int64)
     bd, pbd = _hptr(bnd, np.uint8)
-    mesh = Mesh(2, xy.shape[0], cl.shape[0], pxy, pcl, pbd)
+    mesh = Mesh(xy.shape[1], xy.shape[0], cl.shape[0], pxy, pcl, pbd)
     s = int(np.asarray(b).size)
     Aa, pA = _hptr(A, np.float64)
     ba, pb = _hptr(b, np.float64)
@@ -247,7 +248,7 @@ def irkmg_set_wind(ctx, wind):
 
 def irkmg_p2_coords(ctx, level=-1):
     level %= ctx.nlevels
-    out = np.zeros((ctx.levels[level]["np2"], 2))
+    out = np.zeros((ctx.levels[level]["np2"], ctx.levels[level]["dim"]))
     _check(lib().irkmg_p2_coords(ctx.handle, level, out.ctypes.data))
     return out
 
@@ -263,7 +264,7 @@ def irkmg_patch_map(ctx, level=-1):
     level %= ctx.nlevels
     nv = ctx.levels[level]["nv"]
     ptr = np.zeros(nv + 1, dtype=np.int64)
-    nodes = np.zeros(64 * nv, dtype=np.int32)
+    nodes = np.zeros(96 * nv, dtype=np.int32)
     _check(lib().irkmg_patch_map(ctx.handle, level, ptr.ctypes.data, nodes.ctypes.data))
     return ptr, nodes[: ptr[-1]].copy()
 
@@ -347,13 +348,14 @@ def irkmg_adjoint_solve(ctx, G, lam, raise_on_noconv=False):
 
 def irkmg_stage_rhs(ctx, un, pn, f, F):
     L = ctx.finest
-    _check(lib().irkmg_stage_rhs(ctx.handle, _dptr(un, 2 * L["nf"], "un"), _dptr(pn, L["nv"], "pn"),
-                                 _dptr(f, ctx.s * 2 * L["np2"], "f"), _dptr(F, L["N"], "F")))
+    d = L["dim"]
+    _check(lib().irkmg_stage_rhs(ctx.handle, _dptr(un, d * L["nf"], "un"), _dptr(pn, L["nv"], "pn"),
+                                 _dptr(f, ctx.s * d * L["np2"], "f"), _dptr(F, L["N"], "F")))
 
 
 def irkmg_advance(ctx, k, un, pn):
     L = ctx.finest
-    _check(lib().irkmg_advance(ctx.handle, _dptr(k, L["N"], "k"), _dptr(un, 2 * L["nf"], "un"),
+    _check(lib().irkmg_advance(ctx.handle, _dptr(k, L["N"], "k"), _dptr(un, L["dim"] * L["nf"], "un"),
                                _dptr(pn, L["nv"], "pn")))
 
 

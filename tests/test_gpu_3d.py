@@ -1,0 +1,138 @@
+"""GPU parity in 3D (Taylor-Hood P2-P1 on Kuhn tetrahedra, Bey refinement,
+s = 2, patches of up to 392 DoFs factored by blocked LU on the GPU): every step
+against the oracle through the C ABI.  Smoother: Chebyshev on [2, 17] (the
+3D spectrum of the Vanka-preconditioned operator reaches ~16.7)."""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import dev, host, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(2, 2, 2, 1 / 16), (2, 3, 2, 1 / 16)]
+
+
+def _ctx(irkmg, n0, nl, s, dt, precision=64, **kw):
+    A, b, c = irkmg.irkmg_radau_iia(s)
+    o = irkmg.irkmg_default_options()
+    o.nlevels = nl
+    o.cheb_lo, o.cheb_hi = 2.0, 17.0
+    o.patch_precision = precision
+    o.maxit = 400
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return irkmg.irkmg_setup(*synth.cube_mesh(n0), A, b, c, dt, 1.0, o)
+
+
+_H = {}
+
+
+def _oracle(n0, nl, s, dt):
+    key = (n0, nl, s, dt)
+    if key not in _H:
+        from oracle import mg, tableau
+        A, _, _ = tableau.radau_iia(s)
+        _H[key] = mg.Hierarchy(*synth.cube_mesh(n0), nl, A, dt, cheb=(2.0, 17.0))
+    return _H[key]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "n0=%d,L=%d" % c[:2])
+def pair3(request):
+    irkmg = need_gpu()
+    n0, nl, s, dt = request.param
+    ctx = _ctx(irkmg, n0, nl, s, dt)
+    yield irkmg, ctx, _oracle(n0, nl, s, dt)
+    ctx.close()
+
+
+def test_3d_sizes_patches_colours(pair3):
+    irkmg, ctx, H = pair3
+    from oracle import vanka
+    for l, L in enumerate(H.levels):
+        info = ctx.levels[l]
+        assert info["dim"] == 3
+        assert (info["nv"], info["nf"], info["np2"], info["N"]) == (L.mesh.nv, L.mesh.nf, L.mesh.np2, L.N)
+        np.testing.assert_array_equal(irkmg.irkmg_free_nodes(ctx, l), L.mesh.free_p2)
+        np.testing.assert_array_equal(irkmg.irkmg_p2_coords(ctx, l), L.mesh.p2_coords)
+        if l == 0:
+            continue
+        ptr, nodes = irkmg.irkmg_patch_map(ctx, l)
+        ref = vanka.patch_nodes(L.mesh)
+        assert np.array_equal(nodes, np.concatenate(ref))
+        np.testing.assert_array_equal(irkmg.irkmg_colouring(ctx, l), vanka.distance2_colouring(L.mesh))
+        assert info["max_patch_dofs"] == max(len(d) for d in L.dofs)
+        assert info["apply_kernel"] == (3 if info["max_patch_dofs"] > 160 else info["apply_kernel"])
+
+
+def test_3d_operator_transfers(pair3):
+    irkmg, ctx, H = pair3
+    for l, L in enumerate(H.levels):
+        x = synth.random_vector(700 + l, L.N)
+        y = dev(np.zeros(L.N))
+        irkmg.irkmg_apply(ctx, dev(x), y, level=l)
+        assert rel(host(y), L.J @ x) < 1e-13
+        if l > 0:
+            xc = synth.random_vector(710 + l, H.levels[l - 1].N)
+            yc, yf = dev(np.zeros(H.levels[l - 1].N)), dev(np.zeros(L.N))
+            irkmg.irkmg_restrict(ctx, dev(x), yc, level=l)
+            irkmg.irkmg_prolong(ctx, dev(xc), yf, level=l)
+            assert rel(host(yc), L.P.T @ x) < 1e-14
+            assert rel(host(yf), L.P @ xc) < 1e-14
+
+
+def test_3d_blocked_lu_vanka_smoother_vcycle(pair3):
+    irkmg, ctx, H = pair3
+    for l in range(1, len(H.levels)):
+        L = H.levels[l]
+        r = synth.random_vector(720 + l, L.N)
+        c = dev(np.zeros(L.N))
+        irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l)
+        assert rel(host(c), L.vanka.correction(r)) < 1e-11
+        F = synth.random_vector(730 + l, L.N)
+        x0 = 0.1 * synth.random_vector(740 + l, L.N)
+        x = dev(x0)
+        irkmg.irkmg_smooth(ctx, dev(F), x, 2, level=l)
+        assert rel(host(x), L.vanka.chebyshev(L.J, F, x0, 2, 2.0, 17.0)) < 1e-11
+    r = synth.random_vector(750, H.finest.N)
+    z = dev(np.zeros(H.finest.N))
+    irkmg.irkmg_vcycle(ctx, dev(r), z)
+    assert rel(host(z), H.vcycle(r)) < 1e-11
+
+
+def test_3d_solve_and_fp32_form(pair3):
+    irkmg, ctx, H = pair3
+    from oracle import fgmres, stage
+    L = H.finest
+    m = L.mesh
+    X = m.p2_coords
+    f = np.stack([np.stack(synth.mms3_forcing(*X.T))] * H.s)
+    un = np.concatenate(synth.mms3_velocity(*m.p2_coords[m.free_p2].T))
+    pn = synth.mms3_pressure(*m.coords.T)
+    pn = pn - pn.mean()
+    F_ref = stage.stage_rhs(L.ops, un, pn, f)
+    F = dev(np.zeros(L.N))
+    irkmg.irkmg_stage_rhs(ctx, dev(un), dev(pn), dev(f.ravel()), F)
+    assert rel(host(F), F_ref) < 1e-12
+    k = dev(np.zeros(L.N))
+    st = irkmg.irkmg_solve(ctx, dev(F_ref), k)
+    assert st["status"] == 0
+    x_ref, its_ref, _ = fgmres.fgmres(L.J, F_ref, H.vcycle, rtol=1e-10, project=H.project_pressure,
+                                      maxit=400)
+    assert rel(H.project_pressure(host(k)), H.project_pressure(x_ref)) < 1e-6
+    assert abs(st["iters"] - its_ref) <= 2
+    # FP32 patch factors and applies inside the FP64 FGMRES
+    n0, nl = int(round(m.nv ** (1 / 3))) - 1, len(H.levels)
+    c32 = _ctx(irkmg, 2, nl, H.s, H.dt, precision=32)
+    k32 = dev(np.zeros(L.N))
+    st32 = irkmg.irkmg_solve(c32, dev(F_ref), k32)
+    assert st32["status"] == 0 and st32["rfinal"] <= 1e-10 * np.linalg.norm(F_ref)
+    assert rel(H.project_pressure(host(k32)), H.project_pressure(host(k))) < 1e-6
+    c32.close()
+
+
+def test_3d_unsupported_forms_say_so(pair3):
+    irkmg, ctx, H = pair3
+    with pytest.raises(irkmg.IrkmgError) as e:
+        irkmg.irkmg_adjoint_solve(ctx, dev(np.zeros(ctx.N())), dev(np.zeros(ctx.N())))
+    assert e.value.status == irkmg.IRKMG_ENOTIMPL
