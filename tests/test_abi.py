@@ -93,7 +93,7 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(irkmg, bad):
         Aa, pA = irkmg._hptr(A, np.float64)
         ba, pb = irkmg._hptr(b, np.float64)
         ca, pc = irkmg._hptr(c, np.float64)
-        mesh = irkmg.Mesh(3, xy.shape[0], cl.shape[0], pxy, pcl, pbd)
+        mesh = irkmg.Mesh(4, xy.shape[0], cl.shape[0], pxy, pcl, pbd)
         tab = irkmg.Tableau(2, pA, pb, pc)
         h = ct.c_void_p()
         rc = irkmg.lib().irkmg_setup(ct.byref(mesh), ct.byref(tab), 0.1, 1.0, ct.byref(o), ct.byref(h))
@@ -103,3 +103,14 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(irkmg, bad):
         irkmg.irkmg_setup(coords, cells, bnd, A, b, c, dt, 1.0, o)
     assert e.value.status == irkmg.IRKMG_EINVAL
     assert irkmg.lib().irkmg_last_error().decode()
+
+
+def test_3d_wind_is_rejected_before_touching_the_gpu(irkmg):
+    """The Oseen wind is built for 2D meshes only: a 3D set-up with a wind
+    returns ENOTIMPL from validation, before any CUDA call."""
+    A, b, c = irkmg.irkmg_radau_iia(2)
+    coords, cells, bnd = synth.cube_mesh(1)
+    with pytest.raises(irkmg.IrkmgError) as e:
+        irkmg.irkmg_setup(coords, cells, bnd, A, b, c, 0.1, 1.0, irkmg.irkmg_default_options(),
+                          wind=np.zeros((27, 2)))
+    assert e.value.status == irkmg.IRKMG_ENOTIMPL

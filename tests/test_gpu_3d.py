@@ -133,6 +133,7 @@ def test_3d_solve_and_fp32_form(pair3):
 
 def test_3d_unsupported_forms_say_so(pair3):
     irkmg, ctx, H = pair3
+    G = dev(H.project_pressure(synth.random_vector(760, ctx.N())))
     with pytest.raises(irkmg.IrkmgError) as e:
-        irkmg.irkmg_adjoint_solve(ctx, dev(np.zeros(ctx.N())), dev(np.zeros(ctx.N())))
+        irkmg.irkmg_adjoint_solve(ctx, G, dev(np.zeros(ctx.N())))
     assert e.value.status == irkmg.IRKMG_ENOTIMPL
