@@ -74,6 +74,14 @@ def peaks():
 
 
 def workload(args):
+    if getattr(args, "dim", 2) == 3:
+        n = args.n3
+        levels = int(round(np.log2(n / 4))) + 1
+        if n < 8 or 4 * 2 ** (levels - 1) != n:
+            raise SystemExit("--n3 must be 4 * 2^k with k >= 1")
+        return dict(name=f"3D Stokes RadauIIA(2) {n}^3 cubes x 6 tets ({levels} levels from 4^3), "
+                         "dt=1/16, FP32 blocked patch LU", n0=4, levels=levels, s=2, dt=1 / 16,
+                    nu=1.0, n=n, dim=3, cheb=(2.0, 17.0))
     if args.small:
         return dict(name="2D Stokes RadauIIA(2) 8x8 (3 levels), dt=1/8", n0=2, levels=3, s=2,
                     dt=1 / 8, nu=1.0, n=8)
@@ -186,13 +194,15 @@ def make_context(irkmg, wl, precision, stream, apply_variant=0):
     A, b, c = irkmg.irkmg_radau_iia(wl["s"])
     o = irkmg.irkmg_default_options()
     o.apply_variant = apply_variant
+    if "cheb" in wl:
+        o.cheb_lo, o.cheb_hi = wl["cheb"]
     o.nlevels = wl["levels"]
     o.patch_precision = precision
     o.rtol = 1e-10
     o.maxit = 300
+    mesh = synth.cube_mesh(wl["n0"]) if wl.get("dim", 2) == 3 else synth.square_mesh(wl["n0"])
     t0 = time.perf_counter()
-    ctx = irkmg.irkmg_setup(*synth.square_mesh(wl["n0"]), A, b, c, wl["dt"], wl["nu"], o,
-                            stream=stream)
+    ctx = irkmg.irkmg_setup(*mesh, A, b, c, wl["dt"], wl["nu"], o, stream=stream)
     return ctx, time.perf_counter() - t0, c
 
 
@@ -200,6 +210,11 @@ def initial_data(irkmg, ctx, wl, c):
     xy = irkmg.irkmg_p2_coords(ctx)
     free = irkmg.irkmg_free_nodes(ctx)
     nv = ctx.finest["nv"]
+    if wl.get("dim", 2) == 3:
+        u0 = np.concatenate(synth.mms3_velocity(*xy[free].T))
+        p0 = synth.mms3_pressure(*xy[:nv].T)
+        f1 = np.concatenate(synth.mms3_forcing(*xy.T, nu=wl["nu"]))
+        return u0, p0 - p0.mean(), np.concatenate([f1 for _ in c])
     ux, uy = synth.mms_velocity(xy[free, 0], xy[free, 1])
     u0 = np.concatenate([ux, uy])
     p0 = synth.mms_pressure(xy[:nv, 0], xy[:nv, 1])
@@ -302,6 +317,49 @@ def run_batched(args, dev, stream):
             "setup_s": setup_s}
 
 
+def run_3d(args, dev, stream):
+    """The 3D configuration (Kuhn tetrahedra, FP32 blocked patch LU, FP64
+    FGMRES): time per stage solve, iterations, residual, roofline of the
+    finest-level patch solves."""
+    import torch
+    from paper_2202_07381_gb300 import irkmg
+    a3 = argparse.Namespace(**vars(args))
+    a3.dim = 3
+    wl = workload(a3)
+    ctx, setup_s, c = make_context(irkmg, wl, 32, stream.cuda_stream, 0)
+    u0, p0, f = initial_data(irkmg, ctx, wl, c)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    u, p, fd = T(u0), T(p0), T(f)
+    F = torch.zeros(ctx.N(), dtype=torch.float64, device=dev)
+    k = torch.zeros_like(F)
+    irkmg.irkmg_stage_rhs(ctx, u, p, fd, F)
+    stats = []
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            irkmg.irkmg_trace_enable(ctx, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        irkmg.irkmg_stage_rhs(ctx, u, p, fd, F)
+        k.zero_()
+        stats.append(irkmg.irkmg_solve(ctx, F, k))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tr = irkmg.irkmg_trace_read(ctx)
+    hbm, _ = peaks()
+    gbs = tr["vanka_bytes"] / (tr["vanka_ms"] * 1e-3) / 1e9 if tr["vanka_ms"] else None
+    out = {"workload": wl["name"], "N": ctx.N(), "patches_finest": ctx.finest["nv"],
+           "max_patch_dofs": ctx.finest["max_patch_dofs"], "ms_per_step": ms,
+           "iters": stats[-1]["iters"], "rel_residual": stats[-1]["rfinal"] / stats[-1]["r0"],
+           "setup_s": setup_s, "all_converged": all(s_["status"] == 0 for s_ in stats),
+           "vanka_lu_finest": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": gbs / hbm if gbs else None,
+                               "avg_launch_ms": tr["vanka_ms"] / max(tr["vanka_launches"], 1)}}
+    ctx.close()
+    return out
+
+
 def run_ours(args, wl, rank, world, local_rank):
     import torch
     from paper_2202_07381_gb300 import irkmg
@@ -309,7 +367,7 @@ def run_ours(args, wl, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    prec = 32 if args.form == "fp32" else 64
+    prec = 32 if (args.form == "fp32" or wl.get("dim", 2) == 3) else 64
     ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream, args.apply)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
@@ -392,6 +450,7 @@ def run_ours(args, wl, rank, world, local_rank):
         forms["fp32_patch"] = run_fp32_form(irkmg, torch, wl, args, dev, stream, k)
         forms["fp32_patch"]["speedup_vs_fp64"] = (ms / args.steps) / forms["fp32_patch"]["ms_per_step"]
         forms["batched"] = run_batched(args, dev, stream)
+        forms["3d"] = run_3d(args, dev, stream)
     result = None
     if rank == 0:
         hbm, hbm_kind = peaks()
@@ -400,7 +459,8 @@ def run_ours(args, wl, rank, world, local_rank):
         op_tf = trace["op_flops"] / (trace["op_ms"] * 1e-3) / 1e12 if trace["op_ms"] else None
         nvl = max(trace["vanka_launches"], 1)
         h = kernel_source_hash()
-        kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply"}[ctx.finest["apply_kernel"]]
+        kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
+                 3: "k_vanka_apply_lu"}[ctx.finest["apply_kernel"]]
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
         value = ms * 1e-3 / (args.steps * world)
@@ -426,8 +486,10 @@ def run_ours(args, wl, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == 64 else "f64+f32patch", "data": "synthetic",
+            "dim": wl.get("dim", 2),
             "config": {"workload": wl["name"], "N": N, "patches_finest": ctx.finest["nv"],
-                       "patch_precision": prec, "smoother": "Chebyshev[2,8] V(2,2)",
+                       "patch_precision": prec,
+                       "smoother": "Chebyshev[%g,%g] V(2,2)" % wl.get("cheb", (2.0, 8.0)),
                        "fgmres_restart": 30, "rtol": 1e-10,
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
@@ -460,6 +522,9 @@ def main():
     ap.add_argument("--form", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--small", action="store_true", help="8x8 mesh (quick check)")
     ap.add_argument("--n", type=int, default=512, help="finest mesh n x n (8 * 2^k)")
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
+                    help="3: the 3D Kuhn-tetrahedra configuration as the headline")
+    ap.add_argument("--n3", type=int, default=32, help="3D finest mesh n^3 cubes (4 * 2^k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32-patch and batched forms reported beside the headline")
@@ -480,7 +545,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     res = run_ours(args, wl, rank, world, local_rank)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and wl.get("dim", 2) == 2:
             n_sample = 8 if args.small else min(64, wl["n"])
             _, scaled, desc = oracle_sample(wl, n_sample)
             res["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
