@@ -65,9 +65,9 @@ typedef struct irkmg_ctx irkmg_ctx;
  * coords: nverts·dim doubles; cells: ncells·(dim+1) vertex ids; bnd_vertex: 1
  * on Dirichlet (no-slip) vertices.  An edge is Dirichlet iff it lies on a
  * boundary facet and both ends are flagged.  In 3D, vectors hold u_x, u_y and
- * u_z blocks before the pressure block; patches above 160 DoFs are factored
- * by blocked LU (their transposed solves, the Oseen wind and the adjoint
- * entry points return IRKMG_ENOTIMPL in 3D). */
+ * u_z blocks before the pressure block; patches above 160 DoFs are inverted
+ * through a blocked LU on the GPU (their transposed solves, the Oseen wind and
+ * the adjoint entry points return IRKMG_ENOTIMPL in 3D). */
 typedef struct {
   int dim;
   int64_t nverts, ncells;
@@ -123,7 +123,8 @@ typedef struct {
   int64_t max_patch_dofs;  /* largest patch size s·(2·nodes + 1)                    */
   int64_t factor_bytes;    /* bytes of stored patch blocks (inverse + index list)   */
   int64_t apply_kernel;    /* Vanka apply kernel in use: 1 TMA-staged, 2 warp-per-patch,
-                              3 blocked-LU solves (patches above 160 DoFs, 3D)       */
+                              3 CTA-per-patch mat-vec (patches above 160 DoFs, whose
+                              inverses come from a blocked LU; 3D)                  */
   double apply_ms[2];      /* autotuner: one sweep with kernel 1 / kernel 2 (0 if untimed) */
   int64_t dim;             /* 2 or 3                                                */
 } irkmg_level_info;

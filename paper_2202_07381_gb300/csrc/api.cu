@@ -314,10 +314,25 @@ int build_patches(Ctx& C, Level& L) {
 }
 
 int factor_level(Ctx& C, Level& L) {
-  if (L.big)
-    CK(launch_patch_lu_big(C, L));
-  else
+  if (!L.big) {
     CK(launch_patch_invert(C, L, C.opt.patch_precision));
+    return IRKMG_OK;
+  }
+  // large patches: blocked LU in place, then the explicit inverse from it
+  CK(launch_patch_lu_big(C, L));
+  const int ctas = (int)std::min<int64_t>(L.nv, 2 * 152);
+  const int64_t ws = (int64_t)L.max_np * L.max_np;
+  const size_t esz = C.opt.patch_precision == 64 ? 8 : 4;
+  void* work = nullptr;
+  cudaError_t e = cudaMallocAsync(&work, esz * ws * ctas, C.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IRKMG_ENOMEM, "workspace for the large-patch inverses");
+  }
+  e = launch_patch_inv_from_lu(C, L, work, ws, ctas);
+  cudaError_t e2 = cudaFreeAsync(work, C.stream);
+  CK(e);
+  CK(e2);
   return IRKMG_OK;
 }
 
@@ -417,7 +432,7 @@ int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int 
       CK(cudaEventRecord(a, C.stream));
     }
     if (L.big)
-      CK(launch_vanka_lu(C, L, c, r, out, scale));
+      CK(launch_vanka_big(C, L, c, r, out, scale));
     else
       CK(launch_vanka(C, L, c, r, out, scale, tr));
     C.launches++;

@@ -118,7 +118,7 @@ struct Level {
   int64_t fac_elems = 0;
   int max_np = 0;
   bool big = false;                    // patches above kMaxSmallNp: blocked LU + LU apply
-  int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 LU (big patches)
+  int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 big-patch mat-vec
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
@@ -207,8 +207,9 @@ cudaError_t launch_tracking(Ctx& C, const double* u, const double* ut, double* g
                             double* out);
 
 cudaError_t launch_patch_lu_big(Ctx& C, Level& L);
-cudaError_t launch_vanka_lu(Ctx& C, Level& L, int colour, const double* r, double* out,
-                            double scale);
+cudaError_t launch_patch_inv_from_lu(Ctx& C, Level& L, void* work, int64_t ws, int ctas);
+cudaError_t launch_vanka_big(Ctx& C, Level& L, int colour, const double* r, double* out,
+                             double scale);
 
 constexpr int kMultidotBlocks = 304;
 constexpr int kMaxSmallNp = 160;  // patches up to this size: explicit inverse in shared memory

@@ -7,12 +7,16 @@
 //     32-column panels factored in shared memory, row interchanges applied to
 //     the rest of the matrix, a triangular solve for the U block row, and the
 //     trailing update A22 -= L21 U12 from shared-memory tiles.
-//   k_vanka_apply_lu: out[S_v] += scale · U⁻¹ L⁻¹ P r|_{S_v}: the pivots, then
-//     blocked forward and backward substitution (each 32 x 32 diagonal block is
-//     staged in shared memory and solved by one warp; the off-diagonal blocks
-//     are streamed once with coalesced column reads).  One launch per colour.
-// Block layout of a patch: [n_p^2 values][n_p int32 DoF indices][n_p int32
-// pivots], each part padded to 16 bytes.
+//   k_patch_inv_from_lu: X = A_v⁻¹ = U⁻¹ L⁻¹ P, by blocked forward and
+//     backward substitution on all n_p columns of P at once (32-row blocks:
+//     a per-column triangular solve of the diagonal block, then a shared-
+//     memory tiled update of the remaining rows), in a per-CTA workspace;
+//     X then overwrites the factors, so every apply is one dense mat-vec.
+//   k_vanka_apply_big: out[S_v] += scale · X r|_{S_v}, one CTA per patch,
+//     threads over rows, columns streamed with coalesced loads.
+//     One launch per colour.
+// Block layout of a patch: [n_p^2 values (LU factors, then the inverse)]
+// [n_p int32 DoF indices][n_p int32 pivots], each part padded to 16 bytes.
 #include <cfloat>
 
 #include "irkmg_internal.h"
@@ -243,88 +247,165 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
   }
 }
 
+constexpr int kRowChunk = 128;
+
+// Work on W (column-major np x np): W := L⁻¹ W (lower = true, unit diagonal)
+// or W := U⁻¹ W (lower = false), with L / U the factors stored in A.
 template <typename T>
-__global__ void __launch_bounds__(kBigThreads) k_vanka_apply_lu(BigParams P, const T* __restrict__ fac) {
+__device__ void block_trsm_all_columns(const T* __restrict__ A, T* W, int np, bool lower, T* Ls,
+                                       T* Wb, T* Ms) {
+  const int tid = threadIdx.x;
+  const int nblk = (np + kPanel - 1) / kPanel;
+  for (int bb = 0; bb < nblk; ++bb) {
+    const int blk = lower ? bb : nblk - 1 - bb;
+    const int k0 = blk * kPanel, kb = min(kPanel, np - k0);
+    for (int idx = tid; idx < kb * kb; idx += kBigThreads) {
+      const int l = idx / kb, i = idx % kb;
+      Ls[l * kPanel + i] = A[(int64_t)(k0 + l) * np + k0 + i];
+    }
+    __syncthreads();
+    // diagonal block: every column solved by one thread
+    for (int c = tid; c < np; c += kBigThreads) {
+      T* col = W + (int64_t)c * np + k0;
+      T x[kPanel];
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l) x[l] = l < kb ? col[l] : (T)0;
+      if (lower) {
+#pragma unroll
+        for (int l = 0; l < kPanel; ++l)
+#pragma unroll
+          for (int i = 0; i < kPanel; ++i)
+            if (i > l && i < kb) x[i] -= Ls[l * kPanel + i] * x[l];
+      } else {
+#pragma unroll
+        for (int l = kPanel - 1; l >= 0; --l) {
+          if (l < kb) x[l] = x[l] / Ls[l * kPanel + l];
+#pragma unroll
+          for (int i = 0; i < kPanel; ++i)
+            if (i < l && l < kb) x[i] -= Ls[l * kPanel + i] * x[l];
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l)
+        if (l < kb) {
+          col[l] = x[l];
+          Wb[l * np + c] = x[l];
+        }
+    }
+    __syncthreads();
+    // remaining rows: W[r, :] -= A[r, k0:k0+kb] W[k0:k0+kb, :], rows below the
+    // block for L, above it for U, in chunks of kRowChunk rows
+    const int r0 = lower ? k0 + kb : 0, r1 = lower ? np : k0;
+    for (int ch = r0; ch < r1; ch += kRowChunk) {
+      const int mr = min(kRowChunk, r1 - ch);
+      for (int idx = tid; idx < kb * mr; idx += kBigThreads) {
+        const int l = idx / mr, i = idx % mr;
+        Ms[l * kRowChunk + i] = A[(int64_t)(k0 + l) * np + ch + i];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < mr * np; idx += kBigThreads) {
+        const int i = idx % mr, c = idx / mr;
+        T* w = W + (int64_t)c * np + ch + i;
+        T acc = *w;
+        for (int l = 0; l < kb; ++l) acc -= Ms[l * kRowChunk + i] * Wb[l * np + c];
+        *w = acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Persistent: CTA b inverts patches b, b + gridDim.x, ...; its workspace is
+// work + b * ws (ws >= np^2 for every patch of the level).
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) k_patch_inv_from_lu(BigParams P, int64_t npatch,
+                                                                  T* fac, T* work, int64_t ws) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ int32_t perm[kMaxBigNp];
+  T* W = work + (int64_t)blockIdx.x * ws;
+  const int tid = threadIdx.x;
+  for (int64_t pi = blockIdx.x; pi < npatch; pi += gridDim.x) {
+    const int np = P.np[pi];
+    T* A = fac + P.fac_off[pi];
+    const int32_t* piv = reinterpret_cast<const int32_t*>(
+        reinterpret_cast<const unsigned char*>(A) + big_x_bytes<T>(np) + big_i_bytes(np));
+    T* Ls = reinterpret_cast<T*>(dyn);                 // [kPanel][kPanel]
+    T* Wb = Ls + kPanel * kPanel;                      // [kPanel][np]
+    T* Ms = Wb + (size_t)kPanel * np;                  // [kPanel][kRowChunk]
+    if (tid == 0) {
+      for (int i = 0; i < np; ++i) perm[i] = i;
+      for (int j = 0; j < np; ++j) {
+        const int p = piv[j];
+        if (p != j) {
+          const int32_t x = perm[j];
+          perm[j] = perm[p];
+          perm[p] = x;
+        }
+      }
+    }
+    __syncthreads();
+    // W = P (row i of P is e_{perm[i]})
+    for (int64_t idx = tid; idx < (int64_t)np * np; idx += kBigThreads) {
+      const int c = (int)(idx / np), r = (int)(idx % np);
+      W[idx] = perm[r] == c ? (T)1 : (T)0;
+    }
+    __syncthreads();
+    block_trsm_all_columns<T>(A, W, np, true, Ls, Wb, Ms);
+    block_trsm_all_columns<T>(A, W, np, false, Ls, Wb, Ms);
+    for (int64_t idx = tid; idx < (int64_t)np * np; idx += kBigThreads) A[idx] = W[idx];
+    __syncthreads();
+  }
+}
+
+// out[S_v] += scale · X r|_{S_v} for large patches: one CTA per patch, thread t
+// owns rows t and t + 256, columns streamed with coalesced loads.
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) k_vanka_apply_big(BigParams P, const T* __restrict__ fac) {
   __shared__ T y[kMaxBigNp];
-  __shared__ T Db[kPanel * kPanel];
   __shared__ int32_t g[kMaxBigNp];
   const int64_t w = blockIdx.x;
   if (w >= P.count) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t pi = P.first + w;
   const int np = P.np[pi];
-  const T* A = fac + P.fac_off[pi];
-  const int32_t* G = reinterpret_cast<const int32_t*>(reinterpret_cast<const unsigned char*>(A) +
+  const T* X = fac + P.fac_off[pi];
+  const int32_t* G = reinterpret_cast<const int32_t*>(reinterpret_cast<const unsigned char*>(X) +
                                                       big_x_bytes<T>(np));
-  const int32_t* piv = reinterpret_cast<const int32_t*>(reinterpret_cast<const unsigned char*>(A) +
-                                                        big_x_bytes<T>(np) + big_i_bytes(np));
   for (int i = tid; i < np; i += kBigThreads) {
     const int32_t gi = G[i];
     g[i] = gi;
     y[i] = (T)P.r[gi];
   }
   __syncthreads();
-  if (tid == 0)
-    for (int j = 0; j < np; ++j) {
-      const int p = piv[j];
-      if (p != j) {
-        const T x = y[j];
-        y[j] = y[p];
-        y[p] = x;
-      }
+  const int i0 = tid, i1 = tid + kBigThreads;
+  T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;
+  if (i1 < np) {
+    int j = 0;
+#pragma unroll 2
+    for (; j + 1 < np; j += 2) {
+      const T r0 = y[j], r1 = y[j + 1];
+      const T* c0 = X + (int64_t)j * np;
+      const T* c1 = c0 + np;
+      a0 = fma(__ldcs(c0 + i0), r0, a0);
+      b0 = fma(__ldcs(c1 + i0), r1, b0);
+      a1 = fma(__ldcs(c0 + i1), r0, a1);
+      b1 = fma(__ldcs(c1 + i1), r1, b1);
     }
-  __syncthreads();
-  // L y = P r (unit lower)
-  for (int k0 = 0; k0 < np; k0 += kPanel) {
-    const int kb = min(kPanel, np - k0);
-    for (int idx = tid; idx < kb * kb; idx += kBigThreads) {
-      const int l = idx / kb, i = idx % kb;
-      Db[l * kPanel + i] = A[(int64_t)(k0 + l) * np + k0 + i];
+    for (; j < np; ++j) {
+      a0 = fma(__ldcs(X + (int64_t)j * np + i0), y[j], a0);
+      a1 = fma(__ldcs(X + (int64_t)j * np + i1), y[j], a1);
     }
-    __syncthreads();
-    if (warp == 0) {
-      T yi = lane < kb ? y[k0 + lane] : (T)0;
-      for (int l = 0; l < kb; ++l) {
-        const T yl = __shfl_sync(0xffffffffu, yi, l);
-        if (lane > l && lane < kb) yi -= Db[l * kPanel + lane] * yl;
-      }
-      if (lane < kb) y[k0 + lane] = yi;
+  } else if (i0 < np) {
+    int j = 0;
+#pragma unroll 4
+    for (; j + 1 < np; j += 2) {
+      a0 = fma(__ldcs(X + (int64_t)j * np + i0), y[j], a0);
+      b0 = fma(__ldcs(X + (int64_t)(j + 1) * np + i0), y[j + 1], b0);
     }
-    __syncthreads();
-    for (int i = k0 + kb + tid; i < np; i += kBigThreads) {
-      T acc = y[i];
-      for (int l = 0; l < kb; ++l) acc -= A[(int64_t)(k0 + l) * np + i] * y[k0 + l];
-      y[i] = acc;
-    }
-    __syncthreads();
+    for (; j < np; ++j) a0 = fma(__ldcs(X + (int64_t)j * np + i0), y[j], a0);
   }
-  // U x = y
-  const int last = ((np - 1) / kPanel) * kPanel;
-  for (int k0 = last; k0 >= 0; k0 -= kPanel) {
-    const int kb = min(kPanel, np - k0);
-    for (int idx = tid; idx < kb * kb; idx += kBigThreads) {
-      const int l = idx / kb, i = idx % kb;
-      Db[l * kPanel + i] = A[(int64_t)(k0 + l) * np + k0 + i];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      T yi = lane < kb ? y[k0 + lane] : (T)0;
-      for (int l = kb - 1; l >= 0; --l) {
-        if (lane == l) yi = yi / Db[l * kPanel + l];
-        const T yl = __shfl_sync(0xffffffffu, yi, l);
-        if (lane < l) yi -= Db[l * kPanel + lane] * yl;
-      }
-      if (lane < kb) y[k0 + lane] = yi;
-    }
-    __syncthreads();
-    for (int i = tid; i < k0; i += kBigThreads) {
-      T acc = y[i];
-      for (int l = 0; l < kb; ++l) acc -= A[(int64_t)(k0 + l) * np + i] * y[k0 + l];
-      y[i] = acc;
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < np; i += kBigThreads) P.out[g[i]] += P.scale * (double)y[i];
+  if (i0 < np) P.out[g[i0]] += P.scale * (double)(a0 + b0);
+  if (i1 < np) P.out[g[i1]] += P.scale * (double)(a1 + b1);
 }
 
 static BigParams big_params(Ctx& C, Level& L) {
@@ -377,8 +458,27 @@ cudaError_t launch_patch_lu_big(Ctx& C, Level& L) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_vanka_lu(Ctx& C, Level& L, int colour, const double* r, double* out,
-                            double scale) {
+cudaError_t launch_patch_inv_from_lu(Ctx& C, Level& L, void* work, int64_t ws, int ctas) {
+  BigParams P = big_params(C, L);
+  const int np = L.max_np;
+  if (C.opt.patch_precision == 64) {
+    const size_t smem = (size_t)(kPanel * kPanel + kPanel * np + kPanel * kRowChunk) * sizeof(double);
+    cudaFuncSetAttribute(k_patch_inv_from_lu<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_inv_from_lu<double><<<(unsigned)ctas, kBigThreads, smem, C.stream>>>(
+        P, L.nv, (double*)L.d_fac, (double*)work, ws);
+  } else {
+    const size_t smem = (size_t)(kPanel * kPanel + kPanel * np + kPanel * kRowChunk) * sizeof(float);
+    cudaFuncSetAttribute(k_patch_inv_from_lu<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_inv_from_lu<float><<<(unsigned)ctas, kBigThreads, smem, C.stream>>>(
+        P, L.nv, (float*)L.d_fac, (float*)work, ws);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vanka_big(Ctx& C, Level& L, int colour, const double* r, double* out,
+                             double scale) {
   BigParams P = big_params(C, L);
   P.r = r;
   P.out = out;
@@ -387,10 +487,10 @@ cudaError_t launch_vanka_lu(Ctx& C, Level& L, int colour, const double* r, doubl
   P.count = L.colour_start[colour + 1] - P.first;
   if (P.count <= 0) return cudaSuccess;
   if (C.opt.patch_precision == 64)
-    k_vanka_apply_lu<double><<<(unsigned)P.count, kBigThreads, 0, C.stream>>>(
+    k_vanka_apply_big<double><<<(unsigned)P.count, kBigThreads, 0, C.stream>>>(
         P, (const double*)L.d_fac);
   else
-    k_vanka_apply_lu<float><<<(unsigned)P.count, kBigThreads, 0, C.stream>>>(
+    k_vanka_apply_big<float><<<(unsigned)P.count, kBigThreads, 0, C.stream>>>(
         P, (const float*)L.d_fac);
   return cudaGetLastError();
 }
