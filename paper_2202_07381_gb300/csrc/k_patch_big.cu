@@ -377,32 +377,37 @@ __global__ void __launch_bounds__(kBigThreads) k_vanka_apply_big(BigParams P, co
     y[i] = (T)P.r[gi];
   }
   __syncthreads();
+  // loads of kBatch columns are issued before their FMAs, so every thread
+  // keeps kBatch (or 2 kBatch) independent loads in flight
+  constexpr int kBatch = 8;
   const int i0 = tid, i1 = tid + kBigThreads;
+  const bool has0 = i0 < np, has1 = i1 < np;
   T a0 = (T)0, b0 = (T)0, a1 = (T)0, b1 = (T)0;
-  if (i1 < np) {
+  if (has0) {
+    const T* x0 = X + i0;
+    const T* x1 = X + (has1 ? i1 : i0);
     int j = 0;
-#pragma unroll 2
-    for (; j + 1 < np; j += 2) {
-      const T r0 = y[j], r1 = y[j + 1];
-      const T* c0 = X + (int64_t)j * np;
-      const T* c1 = c0 + np;
-      a0 = fma(__ldcs(c0 + i0), r0, a0);
-      b0 = fma(__ldcs(c1 + i0), r1, b0);
-      a1 = fma(__ldcs(c0 + i1), r0, a1);
-      b1 = fma(__ldcs(c1 + i1), r1, b1);
+    for (; j + kBatch <= np; j += kBatch) {
+      T v0[kBatch], v1[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        v0[u] = __ldcs(x0 + (int64_t)(j + u) * np);
+        if (has1) v1[u] = __ldcs(x1 + (int64_t)(j + u) * np);
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; u += 2) {
+        a0 = fma(v0[u], y[j + u], a0);
+        b0 = fma(v0[u + 1], y[j + u + 1], b0);
+        if (has1) {
+          a1 = fma(v1[u], y[j + u], a1);
+          b1 = fma(v1[u + 1], y[j + u + 1], b1);
+        }
+      }
     }
     for (; j < np; ++j) {
-      a0 = fma(__ldcs(X + (int64_t)j * np + i0), y[j], a0);
-      a1 = fma(__ldcs(X + (int64_t)j * np + i1), y[j], a1);
+      a0 = fma(__ldcs(x0 + (int64_t)j * np), y[j], a0);
+      if (has1) a1 = fma(__ldcs(x1 + (int64_t)j * np), y[j], a1);
     }
-  } else if (i0 < np) {
-    int j = 0;
-#pragma unroll 4
-    for (; j + 1 < np; j += 2) {
-      a0 = fma(__ldcs(X + (int64_t)j * np + i0), y[j], a0);
-      b0 = fma(__ldcs(X + (int64_t)(j + 1) * np + i0), y[j + 1], b0);
-    }
-    for (; j < np; ++j) a0 = fma(__ldcs(X + (int64_t)j * np + i0), y[j], a0);
   }
   if (i0 < np) P.out[g[i0]] += P.scale * (double)(a0 + b0);
   if (i1 < np) P.out[g[i1]] += P.scale * (double)(a1 + b1);
