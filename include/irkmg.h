@@ -138,6 +138,12 @@ void irkmg_default_options(irkmg_options *opt);
  * standard RadauIIA family).  s in 1..3 from closed forms.  EINVAL otherwise. */
 int irkmg_radau_iia(int s, double *A, double *b, double *c);
 
+/* Gauss(s) (order 2s, A-stable) and LobattoIIIC(s) (order 2s - 2, L-stable)
+ * tableaux, s = 2, 3, from closed forms; the paper runs both families beside
+ * RadauIIA (Section 5, Tables 1 and 2).  Same output layout as above. */
+int irkmg_gauss(int s, double *A, double *b, double *c);
+int irkmg_lobatto_iiic(int s, double *A, double *b, double *c);
+
 /* Build the hierarchy, assemble every level, build patch maps and colourings,
  * factor (invert) every patch and the bordered coarsest system.  Host inputs
  * are copied.  On failure *out is NULL. */

@@ -1035,6 +1035,20 @@ int irkmg_radau_iia(int s, double* A, double* b, double* c) {
   return IRKMG_OK;
 }
 
+int irkmg_gauss(int s, double* A, double* b, double* c) {
+  if (!A || !b || !c) return fail(IRKMG_EINVAL, "null output");
+  int rc = gauss_tableau(s, A, b, c);
+  if (rc) return fail(rc, "Gauss closed forms exist here for s = 2, 3");
+  return IRKMG_OK;
+}
+
+int irkmg_lobatto_iiic(int s, double* A, double* b, double* c) {
+  if (!A || !b || !c) return fail(IRKMG_EINVAL, "null output");
+  int rc = lobatto_iiic_tableau(s, A, b, c);
+  if (rc) return fail(rc, "LobattoIIIC closed forms exist here for s = 2, 3");
+  return IRKMG_OK;
+}
+
 int irkmg_setup(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double nu,
                 const irkmg_options* opt, irkmg_ctx** out) {
   if (!out) return fail(IRKMG_EINVAL, "null out");

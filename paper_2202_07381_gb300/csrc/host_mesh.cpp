@@ -355,4 +355,58 @@ int radau_iia(int s, double* A, double* b, double* c) {
   return IRKMG_EINVAL;
 }
 
+// Gauss(s) (collocation at the Gauss points, order 2s) and LobattoIIIC(s)
+// (Lobatto points, order 2s - 2, L-stable), s = 2, 3, in closed form (Hairer &
+// Wanner, Section IV.5); the paper runs both beside RadauIIA (Section 5).
+int gauss_tableau(int s, double* A, double* b, double* c) {
+  if (s == 2) {
+    const double r3 = std::sqrt(3.0);
+    const double a[4] = {0.25, 0.25 - r3 / 6.0, 0.25 + r3 / 6.0, 0.25};
+    std::copy(a, a + 4, A);
+    b[0] = b[1] = 0.5;
+    c[0] = 0.5 - r3 / 6.0;
+    c[1] = 0.5 + r3 / 6.0;
+    return IRKMG_OK;
+  }
+  if (s == 3) {
+    const double r = std::sqrt(15.0);
+    const double a[9] = {5.0 / 36.0,          2.0 / 9.0 - r / 15.0, 5.0 / 36.0 - r / 30.0,
+                         5.0 / 36.0 + r / 24.0, 2.0 / 9.0,            5.0 / 36.0 - r / 24.0,
+                         5.0 / 36.0 + r / 30.0, 2.0 / 9.0 + r / 15.0, 5.0 / 36.0};
+    std::copy(a, a + 9, A);
+    b[0] = 5.0 / 18.0;
+    b[1] = 4.0 / 9.0;
+    b[2] = 5.0 / 18.0;
+    c[0] = 0.5 - r / 10.0;
+    c[1] = 0.5;
+    c[2] = 0.5 + r / 10.0;
+    return IRKMG_OK;
+  }
+  return IRKMG_EINVAL;
+}
+
+int lobatto_iiic_tableau(int s, double* A, double* b, double* c) {
+  if (s == 2) {
+    const double a[4] = {0.5, -0.5, 0.5, 0.5};
+    std::copy(a, a + 4, A);
+    b[0] = b[1] = 0.5;
+    c[0] = 0.0;
+    c[1] = 1.0;
+    return IRKMG_OK;
+  }
+  if (s == 3) {
+    const double a[9] = {1.0 / 6.0, -1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 5.0 / 12.0,
+                         -1.0 / 12.0, 1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    std::copy(a, a + 9, A);
+    b[0] = 1.0 / 6.0;
+    b[1] = 2.0 / 3.0;
+    b[2] = 1.0 / 6.0;
+    c[0] = 0.0;
+    c[1] = 0.5;
+    c[2] = 1.0;
+    return IRKMG_OK;
+  }
+  return IRKMG_EINVAL;
+}
+
 }  // namespace irkmg

@@ -70,6 +70,8 @@ void assemble_cell_load(const HostMesh& m, HostCSR& C);
 
 // Radau IIA closed forms.
 int radau_iia(int s, double* A, double* b, double* c);
+int gauss_tableau(int s, double* A, double* b, double* c);
+int lobatto_iiic_tableau(int s, double* A, double* b, double* c);
 
 // ---------------------------------------------------------------------------
 // Device data.

@@ -77,6 +77,8 @@ _P = ct.c_void_p
 _SIGS = {
     "irkmg_default_options": (None, [ct.POINTER(Options)]),
     "irkmg_radau_iia": (ct.c_int, [ct.c_int, _P, _P, _P]),
+    "irkmg_gauss": (ct.c_int, [ct.c_int, _P, _P, _P]),
+    "irkmg_lobatto_iiic": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_setup": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(Tableau), ct.c_double, ct.c_double,
                                ct.POINTER(Options), ct.POINTER(_P)]),
     "irkmg_update": (ct.c_int, [_P, ct.c_double, ct.c_double]),
@@ -163,10 +165,22 @@ def irkmg_default_options():
     return o
 
 
-def irkmg_radau_iia(s):
+def _tableau(fn, s):
     A, b, c = np.zeros(s * s), np.zeros(s), np.zeros(s)
-    _check(lib().irkmg_radau_iia(s, A.ctypes.data, b.ctypes.data, c.ctypes.data))
+    _check(fn(s, A.ctypes.data, b.ctypes.data, c.ctypes.data))
     return A.reshape(s, s), b, c
+
+
+def irkmg_radau_iia(s):
+    return _tableau(lib().irkmg_radau_iia, s)
+
+
+def irkmg_gauss(s):
+    return _tableau(lib().irkmg_gauss, s)
+
+
+def irkmg_lobatto_iiic(s):
+    return _tableau(lib().irkmg_lobatto_iiic, s)
 
 
 class Context:

@@ -52,6 +52,16 @@ def test_radau_closed_forms_match_oracle(irkmg, s):
     np.testing.assert_allclose(c, co, atol=2e-15)
 
 
+@pytest.mark.parametrize("fam,s", [("gauss", 2), ("gauss", 3), ("lobatto_iiic", 2), ("lobatto_iiic", 3)])
+def test_gauss_lobatto_closed_forms_match_oracle(irkmg, fam, s):
+    from oracle import tableau
+    A, b, c = getattr(irkmg, "irkmg_" + fam)(s)
+    Ao, bo, co = getattr(tableau, fam)(s)
+    np.testing.assert_allclose(A, Ao, atol=3e-15)
+    np.testing.assert_allclose(b, bo, atol=3e-15)
+    np.testing.assert_allclose(c, co, atol=3e-15)
+
+
 def test_radau_rejects_unsupported_stage_count(irkmg):
     with pytest.raises(irkmg.IrkmgError) as e:
         irkmg.irkmg_radau_iia(4)

@@ -62,3 +62,28 @@ def test_autotuner_records_both_timings():
             assert lv["apply_kernel"] == (1 if lv["apply_ms"][0] <= lv["apply_ms"][1] else 2)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("fam,s,dt", [("gauss", 2, 1 / 8), ("lobatto_iiic", 3, 1 / 64)])
+def test_other_irk_families_match_oracle(fam, s, dt):
+    """The path takes any consistent tableau: Gauss and LobattoIIIC (Section 5)
+    on the 8x8 problem, V-cycle and FGMRES solution against the oracle."""
+    irkmg = need_gpu()
+    import synth
+    from oracle import fgmres, mg, problem, tableau
+    A, b, c = getattr(irkmg, "irkmg_" + fam)(s)
+    o = irkmg.irkmg_default_options()
+    ctx = irkmg.irkmg_setup(*synth.square_mesh(2), A, b, c, dt, 1.0, o)
+    Ao, bo, co = getattr(tableau, fam)(s)
+    H = mg.Hierarchy(*synth.square_mesh(2), 3, Ao, dt)
+    r = synth.random_vector(901, H.finest.N)
+    z = dev(np.zeros(H.finest.N))
+    irkmg.irkmg_vcycle(ctx, dev(r), z)
+    assert rel(host(z), H.vcycle(r)) < 1e-12
+    F, _, _ = problem.mms_rhs(H, co)
+    k = dev(np.zeros(H.finest.N))
+    st = irkmg.irkmg_solve(ctx, dev(F), k)
+    x_ref, its, _ = fgmres.fgmres(H.finest.J, F, H.vcycle, rtol=1e-10, project=H.project_pressure)
+    assert st["status"] == 0 and abs(st["iters"] - its) <= 1
+    assert rel(H.project_pressure(host(k)), H.project_pressure(x_ref)) < 1e-8
+    ctx.close()
