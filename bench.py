@@ -190,10 +190,11 @@ def run_reference(args, wl, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def make_context(irkmg, wl, precision, stream, apply_variant=0):
+def make_context(irkmg, wl, precision, stream, apply_variant=0, patch_form=0):
     A, b, c = irkmg.irkmg_radau_iia(wl["s"])
     o = irkmg.irkmg_default_options()
     o.apply_variant = apply_variant
+    o.patch_form = patch_form
     if "cheb" in wl:
         o.cheb_lo, o.cheb_hi = wl["cheb"]
     o.nlevels = wl["levels"]
@@ -224,10 +225,12 @@ def initial_data(irkmg, ctx, wl, c):
     return u0, p0, f
 
 
-def run_fp32_form(irkmg, torch, wl, args, dev, stream, k_ref):
-    """The FP32-patch form on the same workload: time per solve, iterations and
-    the difference of its solution from the FP64 form's."""
-    ctx, setup_s, c = make_context(irkmg, wl, 32, stream.cuda_stream, 0)
+def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form):
+    """Another form on the same workload (FP32 patches and/or decoupled patch
+    solves): time per solve, iterations, the difference of its solution from
+    the plain FP64 form's, and the finest-level Vanka roofline from the live
+    trace (FP64 patches: FP64-pipe bound; FP32 patches: HBM bound)."""
+    ctx, setup_s, c = make_context(irkmg, wl, precision, stream.cuda_stream, 0, patch_form)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -247,10 +250,32 @@ def run_fp32_form(irkmg, torch, wl, args, dev, stream, k_ref):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     diff = float(irkmg_rel_diff(torch, k, k_ref))
+    # one traced solve for the finest-level Vanka figures
+    irkmg.irkmg_trace_enable(ctx, True)
+    k.zero_()
+    irkmg.irkmg_solve(ctx, F, k)
+    torch.cuda.synchronize()
+    tr = irkmg.irkmg_trace_read(ctx)
+    irkmg.irkmg_trace_enable(ctx, False)
+    out = {"ms_per_step": ms, "iters": stats[-1]["iters"],
+           "rel_residual": stats[-1]["rfinal"] / stats[-1]["r0"], "setup_s": setup_s,
+           "rel_diff_vs_fp64_solution": diff, "patch_precision": precision,
+           "patch_form": patch_form,
+           "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
+           "factor_bytes_finest": ctx.finest["factor_bytes"]}
+    if tr["vanka_ms"]:
+        nvl = max(tr["vanka_launches"], 1)
+        gbs = tr["vanka_bytes"] / (tr["vanka_ms"] * 1e-3) / 1e9
+        tf = tr["vanka_flops"] / (tr["vanka_ms"] * 1e-3) / 1e12
+        hbm, hbm_kind = peaks()
+        out["vanka_finest"] = {"avg_launch_ms": tr["vanka_ms"] / nvl, "launches": tr["vanka_launches"],
+                               "bytes_per_launch": tr["vanka_bytes"] / nvl,
+                               "flops_per_launch": tr["vanka_flops"] / nvl,
+                               "hbm_gbs": gbs, "hbm_frac": gbs / hbm, "tflops": tf,
+                               "fp64_frac": tf / FP64_PEAK_TFLOPS if precision == 64 else None,
+                               "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
     ctx.close()
-    return {"ms_per_step": ms, "iters": stats[-1]["iters"],
-            "rel_residual": stats[-1]["rfinal"] / stats[-1]["r0"], "setup_s": setup_s,
-            "rel_diff_vs_fp64_solution": diff}
+    return out
 
 
 def irkmg_rel_diff(torch, a, b):
@@ -368,7 +393,8 @@ def run_ours(args, wl, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     prec = 32 if (args.form == "fp32" or wl.get("dim", 2) == 3) else 64
-    ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream, args.apply)
+    ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream, args.apply,
+                                   args.patch_form)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -447,8 +473,11 @@ def run_ours(args, wl, rank, world, local_rank):
 
     forms = {}
     if rank == 0 and not args.small and prec == 64 and not args.no_forms:
-        forms["fp32_patch"] = run_fp32_form(irkmg, torch, wl, args, dev, stream, k)
-        forms["fp32_patch"]["speedup_vs_fp64"] = (ms / args.steps) / forms["fp32_patch"]["ms_per_step"]
+        for name, fp, pf in (("fp32_patch", 32, 0), ("kron_fp64", 64, 1), ("kron_fp32", 32, 1)):
+            if pf == args.patch_form and fp == prec:
+                continue
+            forms[name] = run_form(irkmg, torch, wl, args, dev, stream, k, fp, pf)
+            forms[name]["speedup_vs_headline"] = (ms / args.steps) / forms[name]["ms_per_step"]
         forms["batched"] = run_batched(args, dev, stream)
         forms["3d"] = run_3d(args, dev, stream)
     result = None
@@ -460,7 +489,7 @@ def run_ours(args, wl, rank, world, local_rank):
         nvl = max(trace["vanka_launches"], 1)
         h = kernel_source_hash()
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
-                 3: "k_vanka_apply_lu"}[ctx.finest["apply_kernel"]]
+                 3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron"}[ctx.finest["apply_kernel"]]
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
         value = ms * 1e-3 / (args.steps * world)
@@ -488,7 +517,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "dtype": "f64" if prec == 64 else "f64+f32patch", "data": "synthetic",
             "dim": wl.get("dim", 2),
             "config": {"workload": wl["name"], "N": N, "patches_finest": ctx.finest["nv"],
-                       "patch_precision": prec,
+                       "patch_precision": prec, "patch_form": args.patch_form,
                        "smoother": "Chebyshev[%g,%g] V(2,2)" % wl.get("cheb", (2.0, 8.0)),
                        "fgmres_restart": 30, "rtol": 1e-10,
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
@@ -529,6 +558,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32-patch and batched forms reported beside the headline")
     ap.add_argument("--batch", type=int, default=64, help="systems in the batched form")
+    ap.add_argument("--patch-form", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0 dense patch systems; 1..3 Kronecker-decoupled (irkmg_options.patch_form)")
     ap.add_argument("--apply", type=int, default=0, choices=[0, 1, 2],
                     help="Vanka apply kernel: 0 autotuned per level, 1 TMA-staged, 2 warp-per-patch")
     args = ap.parse_args()

@@ -105,6 +105,20 @@ typedef struct {
                               1 = TMA-staged (patch blocks streamed to shared memory
                               by cp.async.bulk) wherever it fits; 2 = warp-per-patch
                               mat-vec everywhere                                    */
+  int patch_form;          /* 0 = one dense s·n patch system per vertex (Section 4.2);
+                              1..3 = Kronecker-decoupled patch solves: with the
+                              Butcher matrix A = T D T⁻¹ (D real block diagonal,
+                              2×2 blocks for complex eigenvalue pairs) every patch
+                              system I⊗M̃ + Δt A⊗K̃ splits into one n×n system per
+                              real eigenvalue and one complex n×n system per pair
+                              (the Kronecker form of Section 3), stored as s n×n
+                              matrices (2: complex form X, Y) or s + pairs of them
+                              (3: X + Y, X, Y, three real mat-vecs per pair);
+                              1 picks 3 for FP64 patches and 2 for FP32.  Exact in
+                              exact arithmetic; used on every level whose pair
+                              system (2n) has at most 160 DoFs, the dense form
+                              elsewhere.  IRKMG_ENOTIMPL if A has a repeated
+                              eigenvalue.                                          */
 } irkmg_options;
 
 typedef struct {
@@ -121,10 +135,11 @@ typedef struct {
   int64_t m, N;            /* per-stage length 2 nf + nv, full length s·m           */
   int64_t npatch, ncolours;/* Vanka patches (one per vertex), colours               */
   int64_t max_patch_dofs;  /* largest patch size s·(2·nodes + 1)                    */
-  int64_t factor_bytes;    /* bytes of stored patch blocks (inverse + index list)   */
+  int64_t factor_bytes;    /* bytes of stored patch blocks (inverses + index list)  */
   int64_t apply_kernel;    /* Vanka apply kernel in use: 1 TMA-staged, 2 warp-per-patch,
                               3 CTA-per-patch mat-vec (patches above 160 DoFs, whose
-                              inverses come from a blocked LU; 3D)                  */
+                              inverses come from a blocked LU; 3D), 4 Kronecker-
+                              decoupled warp-per-patch (patch_form != 0)            */
   double apply_ms[2];      /* autotuner: one sweep with kernel 1 / kernel 2 (0 if untimed) */
   int64_t dim;             /* 2 or 3                                                */
 } irkmg_level_info;
@@ -143,6 +158,16 @@ int irkmg_radau_iia(int s, double *A, double *b, double *c);
  * RadauIIA (Section 5, Tables 1 and 2).  Same output layout as above. */
 int irkmg_gauss(int s, double *A, double *b, double *c);
 int irkmg_lobatto_iiic(int s, double *A, double *b, double *c);
+
+/* The real block diagonalisation A = T D T⁻¹ (s ≤ 3, row-major s×s outputs)
+ * behind the decoupled patch solves (patch_form != 0): D holds the real
+ * eigenvalues of A as 1×1 blocks and each complex pair α ± iβ (β > 0) as the
+ * 2×2 block [[α, β], [−β, α]], real blocks first; T holds unit eigenvectors
+ * for real eigenvalues and, for a pair, Re v and Im v of a unit eigenvector v
+ * whose phase makes them orthogonal.  It rests on the Kronecker form
+ * of the stage system (Section 3).  IRKMG_ENOTIMPL when two eigenvalues
+ * coincide.  Host only; no device work. */
+int irkmg_kron_split(int s, const double *A, double *T, double *Tinv, double *D);
 
 /* Build the hierarchy, assemble every level, build patch maps and colourings,
  * factor (invert) every patch and the bordered coarsest system.  Host inputs

@@ -191,11 +191,24 @@ void level_trace_bytes(Ctx& C, Level& L) {
   L.colour_flops.assign(L.ncolours, 0.0);
   double total = 0.0;
   std::vector<double> inv(L.ncolours, 0.0);
+  const double s = (double)C.s;
   for (int64_t v = 0; v < L.nv; ++v) {
-    const double np = (double)C.s * (2 * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
-    inv[L.h_colour[v]] += np * np * w;
-    L.colour_flops[L.h_colour[v]] += 2.0 * np * np;
-    total += np * np * w + 4.0 * np;
+    const double n = (double)(L.dim * (L.h_patch_ptr[v + 1] - L.h_patch_ptr[v]) + 1);
+    double fb, fl;
+    if (L.kron) {
+      // nm stored n x n matrices, n indices; nt mat-vecs plus the source and
+      // output transforms (ns·s and s·nt multiply-adds per spatial DoF)
+      const KronPlan& K = C.kplan;
+      fb = K.nm * n * n * w + 4.0 * n;
+      fl = 2.0 * (K.nt * n * n + (double)K.ns * s * n + s * K.nt * n);
+    } else {
+      const double np = s * n;
+      fb = np * np * w + 4.0 * np;
+      fl = 2.0 * np * np;
+    }
+    inv[L.h_colour[v]] += fb;
+    L.colour_flops[L.h_colour[v]] += fl;
+    total += fb;
   }
   double invsum = 0.0;
   for (double x : inv) invsum += x;
@@ -289,8 +302,27 @@ int build_patches(Ctx& C, Level& L) {
   if (L.max_np > kMaxBigNp)
     return fail(IRKMG_ENOTIMPL, "patches above " + std::to_string(kMaxBigNp) + " DoFs");
   L.big = L.max_np > kMaxSmallNp;
+  // Decoupled patch factors where the largest block (2n for a complex pair)
+  // fits the shared-memory inversion and the apply's lane slots.
+  L.kron = false;
+  if (C.kron) {
+    int q = 1;
+    for (int b = 0; b < C.kplan.nblk; ++b) q = std::max(q, C.kplan.blk_size[b]);
+    const int nmax = L.max_np / C.s;
+    if (q * nmax <= kMaxSmallNp && C.kplan.nt * nmax <= 32 * kron_max_slots()) {
+      L.kron = true;
+      L.big = false;
+      L.kron_nmax = nmax;
+      for (int64_t i = 0; i < L.nv; ++i) npv[i] /= C.s;
+    }
+  }
   for (int64_t i = 0; i < L.nv; ++i) {
     const int64_t np = npv[i];
+    if (L.kron) {
+      const int64_t xbytes = (C.kplan.nm * np * np * w + 15) / 16 * 16;
+      off[i + 1] = off[i] + (xbytes + (np * 4 + 15) / 16 * 16) / w;
+      continue;
+    }
     const int64_t xbytes = (np * np * w + 15) / 16 * 16, gbytes = (np * 4 + 15) / 16 * 16;
     off[i + 1] = off[i] + (xbytes + gbytes * (L.big ? 2 : 1)) / w;
   }
@@ -309,11 +341,18 @@ int build_patches(Ctx& C, Level& L) {
   C.allocs.push_back(fac);
   C.dev_bytes += esz * L.fac_elems;
   L.d_fac = fac;
-  CK(launch_patch_gidx(C, L));
+  if (L.kron)
+    CK(launch_patch_gidx_kron(C, L));
+  else
+    CK(launch_patch_gidx(C, L));
   return IRKMG_OK;
 }
 
 int factor_level(Ctx& C, Level& L) {
+  if (L.kron) {
+    CK(launch_patch_invert_kron(C, L));
+    return IRKMG_OK;
+  }
   if (!L.big) {
     CK(launch_patch_invert(C, L, C.opt.patch_precision));
     return IRKMG_OK;
@@ -378,6 +417,10 @@ int tune_apply(Ctx& C) {
   int rc = IRKMG_OK;
   for (size_t l = 1; l < C.L.size() && rc == IRKMG_OK; ++l) {
     Level& L = C.L[l];
+    if (L.kron) {
+      L.apply_kernel = 4;
+      continue;
+    }
     if (L.big) {
       L.apply_kernel = 3;
       continue;
@@ -421,7 +464,7 @@ int tune_apply(Ctx& C) {
 
 // --- smoothers and V-cycle -------------------------------------------------
 int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr) {
-  if (L.big && tr)
+  if (L.big && !L.kron && tr)
     return fail(IRKMG_ENOTIMPL, "transposed patch solves of LU-factored (3D) patches");
   const bool timed = C.trace_on && &L == &C.L.back();
   for (int c = 0; c < L.ncolours; ++c) {
@@ -431,7 +474,9 @@ int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int 
       if (rc) return rc;
       CK(cudaEventRecord(a, C.stream));
     }
-    if (L.big)
+    if (L.kron)
+      CK(launch_vanka_kron(C, L, c, r, out, scale, tr));
+    else if (L.big)
       CK(launch_vanka_big(C, L, c, r, out, scale));
     else
       CK(launch_vanka(C, L, c, r, out, scale, tr));
@@ -651,6 +696,14 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
     return fail(IRKMG_EINVAL, "patch_precision is 64 or 32");
   if (o->apply_variant < 0 || o->apply_variant > 2)
     return fail(IRKMG_EINVAL, "apply_variant is 0, 1 or 2");
+  if (o->patch_form < 0 || o->patch_form > 3)
+    return fail(IRKMG_EINVAL, "patch_form is 0, 1, 2 or 3");
+  if (o->patch_form != 0) {
+    KronSplit K;
+    if (kron_split(tab->s, tab->A, &K) != IRKMG_OK)
+      return fail(IRKMG_ENOTIMPL,
+                  "decoupled patch solves need a Butcher matrix with distinct eigenvalues");
+  }
   if (o->timeout_spins < 0) return fail(IRKMG_EINVAL, "timeout_spins >= 0");
   return IRKMG_OK;
 }
@@ -667,6 +720,15 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   C->nu = nu;
   C->stream = (cudaStream_t)opt->cuda_stream;
   int rc;
+  if (opt->patch_form != 0) {
+    KronSplit K;
+    if (kron_split(C->s, C->A, &K) != IRKMG_OK) return fail(IRKMG_ENOTIMPL, "Butcher matrix split");
+    const int layout = opt->patch_form == 2 ? 1
+                       : opt->patch_form == 3 ? 2
+                                              : (opt->patch_precision == 64 ? 2 : 1);
+    if ((rc = kron_plan(K, layout, &C->kplan))) return fail(rc, "decoupled patch plan");
+    C->kron = true;
+  }
   const int nl = opt->nlevels;
   C->L.resize(nl);
   C->dim = mesh->dim;
@@ -1026,6 +1088,7 @@ void irkmg_default_options(irkmg_options* o) {
   o->cuda_stream = nullptr;
   o->timeout_spins = 0;
   o->apply_variant = 0;
+  o->patch_form = 0;
 }
 
 int irkmg_radau_iia(int s, double* A, double* b, double* c) {
@@ -1046,6 +1109,25 @@ int irkmg_lobatto_iiic(int s, double* A, double* b, double* c) {
   if (!A || !b || !c) return fail(IRKMG_EINVAL, "null output");
   int rc = lobatto_iiic_tableau(s, A, b, c);
   if (rc) return fail(rc, "LobattoIIIC closed forms exist here for s = 2, 3");
+  return IRKMG_OK;
+}
+
+int irkmg_kron_split(int s, const double* A, double* T, double* Tinv, double* D) {
+  if (!A || !T || !Tinv || !D) return fail(IRKMG_EINVAL, "null argument");
+  if (s < 1 || s > 3) return fail(IRKMG_EINVAL, "s in [1, 3]");
+  KronSplit K;
+  if (kron_split(s, A, &K) != IRKMG_OK)
+    return fail(IRKMG_ENOTIMPL, "no real block diagonalisation with distinct eigenvalues");
+  for (int i = 0; i < s * s; ++i) {
+    T[i] = K.T[i];
+    Tinv[i] = K.Tinv[i];
+    D[i] = 0.0;
+  }
+  for (int b = 0; b < K.nblk; ++b) {
+    const int c0 = K.col0[b], q = K.blk_size[b];
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) D[(c0 + i) * s + c0 + j] = K.blk[b][i * q + j];
+  }
   return IRKMG_OK;
 }
 

@@ -73,6 +73,31 @@ int radau_iia(int s, double* A, double* b, double* c);
 int gauss_tableau(int s, double* A, double* b, double* c);
 int lobatto_iiic_tableau(int s, double* A, double* b, double* c);
 
+// Real block diagonalisation A = T D T⁻¹ of the Butcher matrix (s ≤ 3): D has
+// 1×1 blocks (real eigenvalues) and 2×2 blocks [[α, β], [−β, α]] (pairs α ± iβ);
+// block b covers columns col0[b] .. col0[b] + blk_size[b] − 1 of T.
+constexpr int kKronMaxTasks = 6;
+constexpr int kKronMaxSrc = 6;
+struct KronSplit {
+  int s, nblk;
+  int blk_size[3], col0[3];
+  double blk[3][4];  // row-major blk_size x blk_size
+  double T[9], Tinv[9];
+};
+// Apply plan of the decoupled patch solve (host_kron.cpp): ns source vectors
+// src_c = Σ_t G[c][t] r_t, nt tasks acc_τ = M_{task_mat[τ]} src_{task_src[τ]},
+// and x_t = Σ_τ H[t][τ] acc_τ; nm stored n×n matrices per patch.
+struct KronPlan {
+  int s, layout, nblk, ns, nt, nm;
+  int blk_size[3], blk_kind[3], blk_mat[3];  // kind 0 real, 1 (X, Y), 2 (X + Y, X, Y)
+  double blk[3][4];
+  double G[kKronMaxSrc * 3];
+  double H[3 * kKronMaxTasks];
+  int task_mat[kKronMaxTasks], task_src[kKronMaxTasks];
+};
+int kron_split(int s, const double* A, KronSplit* out);
+int kron_plan(const KronSplit& K, int layout, KronPlan* out);
+
 // ---------------------------------------------------------------------------
 // Device data.
 // ---------------------------------------------------------------------------
@@ -120,7 +145,10 @@ struct Level {
   int64_t fac_elems = 0;
   int max_np = 0;
   bool big = false;                    // patches above kMaxSmallNp: blocked LU + LU apply
-  int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 big-patch mat-vec
+  bool kron = false;                   // Kronecker-decoupled patch factors (KronPlan)
+  int kron_nmax = 0;                   // largest spatial patch size n on a decoupled level
+  int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 big-patch mat-vec,
+                                       // 4 decoupled warp-per-patch
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
@@ -135,6 +163,8 @@ struct Ctx {
   double A[9] = {0}, AT[9] = {0}, b[3] = {0}, c[3] = {0};
   double dt = 0, nu = 1;
   irkmg_options opt{};
+  KronPlan kplan{};
+  bool kron = false;          // decoupled patch solves requested and the tableau splits
   cudaStream_t stream = nullptr;
   std::vector<double> wind;  // finest-level nodal wind (empty for Stokes)
   std::vector<Level> L;
@@ -174,6 +204,11 @@ cudaError_t launch_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t
 cudaError_t launch_colour_round(Level& L, cudaStream_t st, int* d_remaining, int* d_overflow);
 cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision);
 cudaError_t launch_patch_gidx(Ctx& C, Level& L);
+cudaError_t launch_patch_invert_kron(Ctx& C, Level& L);
+cudaError_t launch_patch_gidx_kron(Ctx& C, Level& L);
+cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, double* out,
+                              double scale, int transpose);
+int kron_max_slots();
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose);
 bool vanka_staged_fits(Ctx& C, Level& L);

@@ -218,23 +218,28 @@ struct InvParams {
   int* err;  // [0] status, [1] patch id
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatch, T* fac) {
-  extern __shared__ double smem[];
-  __shared__ int32_t nodes[kMaxPatchNodes];
-  __shared__ int32_t s_perm[3 * (2 * kMaxPatchNodes + 1)];
-  __shared__ double colk[3 * (2 * kMaxPatchNodes + 1)];
-  __shared__ double red_v[256];
-  __shared__ int red_i[256];
-  __shared__ double s_maxabs;
-  const int64_t pi = blockIdx.x;
-  if (pi >= npatch) return;
-  const int32_t v = P.order[pi];
-  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+// Shared-memory scratch of one patch inversion.
+struct InvScratch {
+  int32_t nodes[kMaxPatchNodes];
+  int32_t perm[3 * (2 * kMaxPatchNodes + 1)];
+  double colk[3 * (2 * kMaxPatchNodes + 1)];
+  double red_v[256];
+  int red_i[256];
+  double maxabs;
+};
+
+// Builds I_s ⊗ M̃ + dt A ⊗ K̃ of patch v (s = P.s, A = P.A, nodes already in
+// W.nodes, L of them) row-major in A_ (np = s (D L + 1)), and overwrites it
+// with its inverse (Gauss–Jordan, partial pivoting).  All threads of the block
+// take part; a pivot below 1e3 eps max|A| records IRKMG_ESINGULAR for v.
+__device__ void patch_build_invert(const InvParams& P, int32_t v, int L, double* A, InvScratch& W) {
   const int D = P.dim;
   const int q = D * L + 1, np = P.s * q;
-  double* A = smem;  // row-major np x np
-  for (int i = threadIdx.x; i < L; i += blockDim.x) nodes[i] = P.patch_nodes[nb + i];
+  int32_t* nodes = W.nodes;
+  int32_t* s_perm = W.perm;
+  double* colk = W.colk;
+  double* red_v = W.red_v;
+  int* red_i = W.red_i;
   for (int i = threadIdx.x; i < np * np; i += blockDim.x) A[i] = 0.0;
   __syncthreads();
   // velocity-velocity blocks
@@ -282,9 +287,9 @@ __global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatc
     if (threadIdx.x < (unsigned)o) red_v[threadIdx.x] = fmax(red_v[threadIdx.x], red_v[threadIdx.x + o]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) s_maxabs = red_v[0];
+  if (threadIdx.x == 0) W.maxabs = red_v[0];
   __syncthreads();
-  const double thresh = 1e3 * DBL_EPSILON * s_maxabs;
+  const double thresh = 1e3 * DBL_EPSILON * W.maxabs;
   // Gauss–Jordan with partial pivoting (first largest |.|), in place
   for (int k = 0; k < np; ++k) {
     double best = -1.0;
@@ -347,11 +352,77 @@ __global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatc
       }
     __syncthreads();
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_patch_invert(InvParams P, int64_t npatch, T* fac) {
+  extern __shared__ double smem[];
+  __shared__ InvScratch W;
+  const int64_t pi = blockIdx.x;
+  if (pi >= npatch) return;
+  const int32_t v = P.order[pi];
+  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+  const int np = P.s * (P.dim * L + 1);
+  double* A = smem;  // row-major np x np
+  for (int i = threadIdx.x; i < L; i += blockDim.x) W.nodes[i] = P.patch_nodes[nb + i];
+  patch_build_invert(P, v, L, A, W);
   // store column-major: X[j*np + i] = Ainv[i][j]
   T* X = fac + P.fac_off[pi];
   for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
     const int j = idx / np, i = idx - j * np;
     X[idx] = (T)A[i * np + j];
+  }
+}
+
+// Kronecker-decoupled patch factors: for every block of the real block
+// diagonalisation A = T D T⁻¹ (one real eigenvalue λ, or one pair α ± iβ as
+// [[α, β], [−β, α]]) the patch matrix I ⊗ M̃ + dt D_b ⊗ K̃ of that block is
+// built and inverted, and its n×n pieces are stored column-major one after
+// the other: kind 0 (real): the inverse; kind 1 (pair): X, Y from the first
+// block column [X; Y] of the inverse; kind 2 (pair): X + Y, X, Y.  The n
+// spatial DoF indices follow the matrices (see k_patch_gidx_kron).
+template <typename T>
+__global__ void __launch_bounds__(256) k_patch_invert_kron(InvParams P, KronPlan K, int64_t npatch,
+                                                           T* fac) {
+  extern __shared__ double smem[];
+  __shared__ InvScratch W;
+  const int64_t pi = blockIdx.x;
+  if (pi >= npatch) return;
+  const int32_t v = P.order[pi];
+  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+  const int n = P.dim * L + 1;
+  const int64_t nn = (int64_t)n * n;
+  double* A = smem;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) W.nodes[i] = P.patch_nodes[nb + i];
+  T* base = fac + P.fac_off[pi];
+  for (int b = 0; b < K.nblk; ++b) {
+    InvParams Q = P;
+    const int q = K.blk_size[b];
+    Q.s = q;
+    for (int i = 0; i < 9; ++i) Q.A[i] = 0.0;
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) Q.A[i * 3 + j] = K.blk[b][i * q + j];
+    patch_build_invert(Q, v, L, A, W);
+    const int np = q * n;  // row-major np x np inverse in A
+    T* X = base + (int64_t)K.blk_mat[b] * nn;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int j = idx / n, i = idx - j * n;  // column-major (i, j)
+      const double x = A[i * np + j];
+      if (K.blk_kind[b] == 0) {
+        X[idx] = (T)x;
+      } else {
+        const double y = A[(n + i) * np + j];
+        if (K.blk_kind[b] == 1) {
+          X[idx] = (T)x;
+          X[nn + idx] = (T)y;
+        } else {
+          X[idx] = (T)(x + y);
+          X[nn + idx] = (T)x;
+          X[2 * nn + idx] = (T)y;
+        }
+      }
+    }
+    __syncthreads();  // A is rebuilt by the next block
   }
 }
 
@@ -388,6 +459,86 @@ cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
                          (int)smem);
     k_patch_invert<float><<<(unsigned)L.nv, 256, smem, C.stream>>>(P, L.nv, (float*)L.d_fac);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_patch_invert_kron(Ctx& C, Level& L) {
+  InvParams P;
+  P.s = C.s;
+  P.dim = L.dim;
+  P.Bz = L.b.v[2];
+  for (int i = 0; i < 9; ++i) P.A[i] = 0.0;
+  P.dt = C.dt;
+  P.nf = L.nf;
+  P.patch_ptr = L.d_patch_ptr;
+  P.patch_nodes = L.d_patch_nodes;
+  P.order = L.d_order;
+  P.fac_off = L.d_fac_off;
+  P.vptr = L.vel.ptr;
+  P.vcol = L.vel.col;
+  P.M = L.vel.v[0];
+  P.K = L.vel.v[1];
+  P.bptr = L.b.ptr;
+  P.bcol = L.b.col;
+  P.Bx = L.b.v[0];
+  P.By = L.b.v[1];
+  P.err = C.d_err;
+  int q = 1;
+  for (int b = 0; b < C.kplan.nblk; ++b) q = std::max(q, C.kplan.blk_size[b]);
+  const size_t smem = (size_t)(q * L.kron_nmax) * (q * L.kron_nmax) * sizeof(double);
+  if (C.opt.patch_precision == 64) {
+    cudaFuncSetAttribute(k_patch_invert_kron<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_invert_kron<double><<<(unsigned)L.nv, 256, smem, C.stream>>>(P, C.kplan, L.nv,
+                                                                        (double*)L.d_fac);
+  } else {
+    cudaFuncSetAttribute(k_patch_invert_kron<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_patch_invert_kron<float><<<(unsigned)L.nv, 256, smem, C.stream>>>(P, C.kplan, L.nv,
+                                                                       (float*)L.d_fac);
+  }
+  return cudaGetLastError();
+}
+
+// Spatial DoF indices of every ordered patch of a decoupled level (n of them,
+// velocity components then the pressure vertex), stored after its nm
+// matrices; stage t adds t·m.
+template <typename T>
+__global__ void k_patch_gidx_kron(int D, int nm, int64_t nf, int64_t npatch,
+                                  const int32_t* __restrict__ patch_ptr,
+                                  const int32_t* __restrict__ patch_nodes,
+                                  const int32_t* __restrict__ order,
+                                  const int64_t* __restrict__ fac_off, T* fac) {
+  const int64_t pi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (pi >= npatch) return;
+  const int32_t v = order[pi];
+  const int32_t nb = patch_ptr[v], L = patch_ptr[v + 1] - nb;
+  const int n = D * L + 1;
+  const int64_t xbytes = ((int64_t)nm * n * n * (int64_t)sizeof(T) + 15) & ~(int64_t)15;
+  int32_t* g = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(fac + fac_off[pi]) + xbytes);
+  for (int k = lane; k < n; k += 32) {
+    int64_t gi;
+    if (k < D * L) {
+      const int c = k / L;
+      gi = c * nf + patch_nodes[nb + k - c * L];
+    } else {
+      gi = D * nf + v;
+    }
+    g[k] = (int32_t)gi;
+  }
+}
+
+cudaError_t launch_patch_gidx_kron(Ctx& C, Level& L) {
+  const unsigned grid = (unsigned)((L.nv * 32 + 255) / 256);
+  if (C.opt.patch_precision == 64)
+    k_patch_gidx_kron<double><<<grid, 256, 0, C.stream>>>(L.dim, C.kplan.nm, L.nf, L.nv,
+                                                          L.d_patch_ptr, L.d_patch_nodes,
+                                                          L.d_order, L.d_fac_off, (double*)L.d_fac);
+  else
+    k_patch_gidx_kron<float><<<grid, 256, 0, C.stream>>>(L.dim, C.kplan.nm, L.nf, L.nv,
+                                                         L.d_patch_ptr, L.d_patch_nodes, L.d_order,
+                                                         L.d_fac_off, (float*)L.d_fac);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,8 @@ class Options(ct.Structure):
                 ("cheb_hi", ct.c_double), ("rtol", ct.c_double), ("atol", ct.c_double),
                 ("restart", ct.c_int), ("maxit", ct.c_int), ("patch_precision", ct.c_int),
                 ("wind", ct.POINTER(ct.c_double)), ("cuda_stream", ct.c_void_p),
-                ("timeout_spins", ct.c_int64), ("apply_variant", ct.c_int)]
+                ("timeout_spins", ct.c_int64), ("apply_variant", ct.c_int),
+                ("patch_form", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -78,6 +79,7 @@ _SIGS = {
     "irkmg_default_options": (None, [ct.POINTER(Options)]),
     "irkmg_radau_iia": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_gauss": (ct.c_int, [ct.c_int, _P, _P, _P]),
+    "irkmg_kron_split": (ct.c_int, [ct.c_int, _P, _P, _P, _P]),
     "irkmg_lobatto_iiic": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_setup": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(Tableau), ct.c_double, ct.c_double,
                                ct.POINTER(Options), ct.POINTER(_P)]),
@@ -173,6 +175,15 @@ def _tableau(fn, s):
 
 def irkmg_radau_iia(s):
     return _tableau(lib().irkmg_radau_iia, s)
+
+
+def irkmg_kron_split(A):
+    """(T, Tinv, D) with A = T D Tinv, D real block diagonal."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    s = A.shape[0]
+    T, Ti, D = np.zeros(s * s), np.zeros(s * s), np.zeros(s * s)
+    _check(lib().irkmg_kron_split(s, A.ctypes.data, T.ctypes.data, Ti.ctypes.data, D.ctypes.data))
+    return T.reshape(s, s), Ti.reshape(s, s), D.reshape(s, s)
 
 
 def irkmg_gauss(s):

@@ -124,3 +124,64 @@ def test_3d_wind_is_rejected_before_touching_the_gpu(irkmg):
         irkmg.irkmg_setup(coords, cells, bnd, A, b, c, 0.1, 1.0, irkmg.irkmg_default_options(),
                           wind=np.zeros((27, 2)))
     assert e.value.status == irkmg.IRKMG_ENOTIMPL
+
+
+def _tableaux():
+    from oracle import tableau
+    out = [("radau_iia", s, tableau.radau_iia(s)[0]) for s in (1, 2, 3)]
+    out += [(f, s, getattr(tableau, f)(s)[0]) for f in ("gauss", "lobatto_iiic") for s in (2, 3)]
+    return out
+
+
+@pytest.mark.parametrize("name,s,A", _tableaux(), ids=lambda x: str(x) if not hasattr(x, "shape") else "")
+def test_kron_split_block_diagonalises_the_butcher_matrix(irkmg, name, s, A):
+    """The decoupled patch solves rest on A = T D T⁻¹ (the Kronecker form of
+    the stage system, Section 3): T D T⁻¹ gives back A, T⁻¹ inverts T, D is
+    block diagonal with [[α, β], [−β, α]] (β > 0) for each complex pair and its
+    eigenvalues are those of A (LAPACK on the oracle's tableau)."""
+    T, Ti, D = irkmg.irkmg_kron_split(A)
+    np.testing.assert_allclose(T @ D @ Ti, A, atol=1e-14)
+    np.testing.assert_allclose(T @ Ti, np.eye(s), atol=1e-14)
+    lam = np.linalg.eigvals(A)
+    i = 0
+    while i < s:
+        if i + 1 < s and D[i, i + 1] != 0.0:
+            al, be = D[i, i], D[i, i + 1]
+            assert be > 0 and D[i + 1, i] == -be and D[i + 1, i + 1] == al
+            assert np.min(np.abs(lam - complex(al, be))) < 1e-13
+            assert abs(T[:, i] @ T[:, i + 1]) < 1e-13   # Re v and Im v rotated orthogonal
+            assert abs(T[:, i] @ T[:, i] + T[:, i + 1] @ T[:, i + 1] - 1.0) < 1e-14
+            i += 2
+        else:
+            assert np.min(np.abs(lam - D[i, i])) < 1e-13
+            assert abs(np.linalg.norm(T[:, i]) - 1.0) < 1e-14
+            i += 1
+    off = D.copy()
+    for k in range(s):
+        off[k, k] = 0.0
+        if k + 1 < s:
+            off[k, k + 1] = off[k + 1, k] = 0.0 if D[k, k + 1] != 0.0 else off[k, k + 1]
+    assert np.all(off == 0.0)
+
+
+def test_decoupled_form_needs_distinct_eigenvalues(irkmg):
+    """Two copies of the implicit midpoint rule (a valid tableau whose Butcher
+    matrix is 0.5 I) cannot be split into distinct eigen-blocks: the split and
+    a set-up asking for decoupled patches report ENOTIMPL before any CUDA call;
+    patch_form outside 0..3 is EINVAL."""
+    A = 0.5 * np.eye(2)
+    with pytest.raises(irkmg.IrkmgError) as e:
+        irkmg.irkmg_kron_split(A)
+    assert e.value.status == irkmg.IRKMG_ENOTIMPL
+    coords, cells, bnd = synth.square_mesh(2)
+    o = irkmg.irkmg_default_options()
+    o.patch_form = 1
+    with pytest.raises(irkmg.IrkmgError) as e:
+        irkmg.irkmg_setup(coords, cells, bnd, A, np.array([0.5, 0.5]), np.array([0.5, 0.5]),
+                          0.1, 1.0, o)
+    assert e.value.status == irkmg.IRKMG_ENOTIMPL
+    A, b, c = irkmg.irkmg_radau_iia(2)
+    o.patch_form = 4
+    with pytest.raises(irkmg.IrkmgError) as e:
+        irkmg.irkmg_setup(coords, cells, bnd, A, b, c, 0.1, 1.0, o)
+    assert e.value.status == irkmg.IRKMG_EINVAL

@@ -2,6 +2,7 @@
 (Section 4.2, Fig. 1; Section 5.1 Chebyshev acceleration)."""
 import numpy as np
 import pytest
+import scipy.linalg as sla
 
 import synth
 from oracle import mesh as M, mg, tableau, vanka
@@ -111,3 +112,41 @@ def test_smoother_spectrum_matches_paper_interval():
     DJ = np.stack([L.vanka.correction(Jd[:, j]) for j in range(L.N)], axis=1)
     ev = np.linalg.eigvals(DJ)
     assert 7.0 < ev.real.max() < 8.5
+
+
+@pytest.mark.parametrize("fam,s,dt,wind", [("radau_iia", 3, 1 / 64, False), ("gauss", 2, 1 / 8, False),
+                                           ("lobatto_iiic", 3, 1 / 16, True)])
+def test_patch_system_decouples_by_eigenvectors_of_A(fam, s, dt, wind):
+    """A patch cut from the assembled stage operator has the Kronecker form
+    I_s ⊗ M̃ + dt A ⊗ K̃ (Section 3 and the patch definition of Section 4.2),
+    so with A = V Λ V⁻¹ (LAPACK eig) its inverse is
+    (V ⊗ I) diag((M̃ + dt λ_k K̃)⁻¹) (V⁻¹ ⊗ I).  Checked on every patch of an
+    8x8 level, Stokes and (LobattoIIIC) Oseen with a seeded wind."""
+    from oracle import stage
+    A = getattr(tableau, fam)(s)[0]
+    coords, cells, bnd = synth.square_mesh(2)
+    w = None
+    if wind:
+        fine = M.hierarchy(coords, cells, bnd, 2)[-1]
+        wx, wy = synth.wind_field(fine.p2_coords[:, 0], fine.p2_coords[:, 1],
+                                  synth.wind_coefficients(7))
+        w = np.stack([wx, wy], axis=1) / np.max(np.hypot(wx, wy))
+    H = mg.Hierarchy(coords, cells, bnd, 2, A, dt, nu=1.0 / 300 if wind else 1.0, wind_finest=w)
+    L = H.levels[-1]
+    Mt, St = stage.single_stage_blocks(L.ops)
+    lam, V = np.linalg.eig(A)
+    Vi = np.linalg.inv(V)
+    J = L.J.tocsr()
+    worst = 0.0
+    for idx in L.dofs:
+        n = len(idx) // s
+        one = idx[:n]
+        Mv = Mt[one][:, one].toarray()
+        Kv = St[one][:, one].toarray()
+        Av = J[idx][:, idx].toarray()
+        blocks = [np.linalg.inv(Mv + dt * l * Kv) for l in lam]
+        Xd = np.kron(V, np.eye(n)) @ sla.block_diag(*blocks) @ np.kron(Vi, np.eye(n))
+        X = np.linalg.inv(Av)
+        assert np.abs(Xd.imag).max() < 1e-10 * np.abs(X).max()
+        worst = max(worst, np.abs(Xd.real - X).max() / np.abs(X).max())
+    assert worst < 1e-11
