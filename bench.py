@@ -473,7 +473,8 @@ def run_ours(args, wl, rank, world, local_rank):
 
     forms = {}
     if rank == 0 and not args.small and prec == 64 and not args.no_forms:
-        for name, fp, pf in (("fp32_patch", 32, 0), ("kron_fp64", 64, 1), ("kron_fp32", 32, 1)):
+        for name, fp, pf in (("dense_fp64", 64, 0), ("dense_fp32", 32, 0), ("kron_fp64", 64, 1),
+                             ("kron_fp32", 32, 1)):
             if pf == args.patch_form and fp == prec:
                 continue
             forms[name] = run_form(irkmg, torch, wl, args, dev, stream, k, fp, pf)
@@ -489,7 +490,8 @@ def run_ours(args, wl, rank, world, local_rank):
         nvl = max(trace["vanka_launches"], 1)
         h = kernel_source_hash()
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
-                 3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron"}[ctx.finest["apply_kernel"]]
+                 3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
+                 5: "k_vanka_apply_kron_staged"}[ctx.finest["apply_kernel"]]
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
         value = ms * 1e-3 / (args.steps * world)
@@ -558,7 +560,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32-patch and batched forms reported beside the headline")
     ap.add_argument("--batch", type=int, default=64, help="systems in the batched form")
-    ap.add_argument("--patch-form", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--patch-form", type=int, default=1, choices=[0, 1, 2, 3],
                     help="0 dense patch systems; 1..3 Kronecker-decoupled (irkmg_options.patch_form)")
     ap.add_argument("--apply", type=int, default=0, choices=[0, 1, 2],
                     help="Vanka apply kernel: 0 autotuned per level, 1 TMA-staged, 2 warp-per-patch")

@@ -100,10 +100,11 @@ typedef struct {
   int64_t timeout_spins;   /* bound on polls of one device-side wait (0 = 2^26; each
                               wait also gives up after 2 s); an expired wait makes
                               FGMRES return IRKMG_ETIMEOUT                          */
-  int apply_variant;       /* Vanka apply kernel per level: 0 = autotuned at set-up
-                              (both kernels timed once per level, the faster kept);
-                              1 = TMA-staged (patch blocks streamed to shared memory
-                              by cp.async.bulk) wherever it fits; 2 = warp-per-patch
+  int apply_variant;       /* Vanka apply kernel per level (dense or decoupled form
+                              alike): 0 = autotuned at set-up (both kernels timed
+                              once per level, the faster kept); 1 = TMA-staged
+                              (patch blocks streamed to shared memory by
+                              cp.async.bulk) wherever it fits; 2 = warp-per-patch
                               mat-vec everywhere                                    */
   int patch_form;          /* 0 = one dense s·n patch system per vertex (Section 4.2);
                               1..3 = Kronecker-decoupled patch solves: with the
@@ -138,9 +139,10 @@ typedef struct {
   int64_t factor_bytes;    /* bytes of stored patch blocks (inverses + index list)  */
   int64_t apply_kernel;    /* Vanka apply kernel in use: 1 TMA-staged, 2 warp-per-patch,
                               3 CTA-per-patch mat-vec (patches above 160 DoFs, whose
-                              inverses come from a blocked LU; 3D), 4 Kronecker-
-                              decoupled warp-per-patch (patch_form != 0)            */
-  double apply_ms[2];      /* autotuner: one sweep with kernel 1 / kernel 2 (0 if untimed) */
+                              inverses come from a blocked LU; 3D); decoupled form
+                              (patch_form != 0): 4 warp-per-patch, 5 TMA-staged    */
+  double apply_ms[2];      /* autotuner: one sweep with the staged / warp-per-patch
+                              kernel of the level's form (0 if untimed)            */
   int64_t dim;             /* 2 or 3                                                */
 } irkmg_level_info;
 

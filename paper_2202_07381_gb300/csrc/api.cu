@@ -417,27 +417,31 @@ int tune_apply(Ctx& C) {
   int rc = IRKMG_OK;
   for (size_t l = 1; l < C.L.size() && rc == IRKMG_OK; ++l) {
     Level& L = C.L[l];
-    if (L.kron) {
-      L.apply_kernel = 4;
-      continue;
-    }
-    if (L.big) {
+    if (L.big && !L.kron) {
       L.apply_kernel = 3;
       continue;
     }
-    const bool fits = vanka_staged_fits(C, L);
+    // candidate kernels: staged (TMA) and warp-per-patch, dense or decoupled
+    // (the decoupled staged kernel with each of its launch shapes)
+    const int ks = L.kron ? 5 : 1, kw = L.kron ? 4 : 2;
+    L.kron_shape = 0;
+    const bool fits = L.kron ? kron_staged_fits(C, L, 0) : vanka_staged_fits(C, L);
     if (C.opt.apply_variant == 1 || C.opt.apply_variant == 2) {
-      L.apply_kernel = (C.opt.apply_variant == 1 && fits) ? 1 : 2;
+      L.apply_kernel = (C.opt.apply_variant == 1 && fits) ? ks : kw;
       continue;
     }
     if (!fits) {
-      L.apply_kernel = 2;
+      L.apply_kernel = kw;
       continue;
     }
     cudaError_t e = cudaMemsetAsync(L.t, 0, sizeof(double) * L.N, C.stream);
     if (e != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e)); break; }
-    for (int kern = 1; kern <= 2 && rc == IRKMG_OK; ++kern) {
-      L.apply_kernel = kern;
+    float shape_ms[2] = {1e30f, 1e30f};
+    const int nshape = L.kron ? 2 : 1;
+    for (int cand = 0; cand < nshape + 1 && rc == IRKMG_OK; ++cand) {
+      const int kern = cand < nshape ? 1 : 2;
+      L.apply_kernel = kern == 1 ? ks : kw;
+      if (kern == 1) L.kron_shape = cand;
       float best = 1e30f;
       for (int rep = 0; rep < 3 && rc == IRKMG_OK; ++rep) {
         cudaEventRecord(a, C.stream);
@@ -449,9 +453,11 @@ int tune_apply(Ctx& C) {
         cudaEventElapsedTime(&ms, a, b);
         if (rep > 0 && ms < best) best = ms;   // rep 0 is the warm-up
       }
-      L.apply_ms[kern] = best;
+      if (kern == 1) shape_ms[cand] = best;
+      L.apply_ms[kern] = kern == 1 ? std::min(shape_ms[0], shape_ms[1]) : best;
     }
-    L.apply_kernel = (L.apply_ms[1] <= L.apply_ms[2]) ? 1 : 2;
+    L.kron_shape = shape_ms[1] < shape_ms[0] ? 1 : 0;
+    L.apply_kernel = (L.apply_ms[1] <= L.apply_ms[2]) ? ks : kw;
   }
   C.trace_on = saved;
   C.launches = 0;
@@ -539,6 +545,8 @@ int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_i
   return IRKMG_OK;
 }
 
+int coarse_graph(Ctx& C, int tr);
+
 int vcycle_level(Ctx& C, int l, const double* b, double* z, int tr) {
   if (l == 0) {
     CK(launch_coarse_apply(C, b, z, tr));
@@ -551,7 +559,18 @@ int vcycle_level(Ctx& C, int l, const double* b, double* z, int tr) {
   if ((rc = smooth(C, L, b, z, C.opt.nu_pre, true, tr))) return rc;
   { int rc_ = op(C, L, b, z, L.t, tr); if (rc_) return rc_; }
   CK(launch_restrict(C, L, L.t, Lc.r));
-  if ((rc = vcycle_level(C, l - 1, Lc.r, Lc.z, tr))) return rc;
+  if (l == (int)C.L.size() - 1 && l >= 2 && !C.capturing) {
+    // everything below the finest level: one graph launch
+    if ((rc = coarse_graph(C, tr))) return rc;
+    CK(cudaEventRecord(C.gev[0], C.stream));
+    CK(cudaStreamWaitEvent(C.gstream, C.gev[0], 0));
+    CK(cudaGraphLaunch(C.cgraph[tr], C.gstream));
+    CK(cudaEventRecord(C.gev[1], C.gstream));
+    CK(cudaStreamWaitEvent(C.stream, C.gev[1], 0));
+    C.launches += C.cgraph_launches[tr];
+  } else if ((rc = vcycle_level(C, l - 1, Lc.r, Lc.z, tr))) {
+    return rc;
+  }
   CK(launch_prolong(C, L, Lc.z, z, 1));
   C.launches += 2;
   return smooth(C, L, b, z, C.opt.nu_post, false, tr);
@@ -878,6 +897,57 @@ int smooth_in(Ctx& C, Level& L, const double* b, double* x, int nsteps, int tr, 
   return IRKMG_OK;
 }
 
+// Levels 0 .. nl-2 of the V-cycle as one CUDA graph (from L[nl-2].r to
+// L[nl-2].z), captured on the library's own non-blocking stream the first time
+// it is needed: the hundreds of short colour launches of the coarse levels
+// then cost one graph launch.  Kernel parameters (dt·A among them) are baked
+// in, so irkmg_update drops the graphs.
+int coarse_graph(Ctx& C, int tr) {
+  if (C.cgraph[tr]) return IRKMG_OK;
+  if (!C.gstream) {
+    CK(cudaStreamCreateWithFlags(&C.gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&C.gev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&C.gev[1], cudaEventDisableTiming));
+  }
+  const int lc = (int)C.L.size() - 2;
+  cudaStream_t saved_stream = C.stream;
+  const bool saved_trace = C.trace_on;
+  const int64_t l0 = C.launches;
+  C.stream = C.gstream;
+  C.trace_on = false;
+  C.capturing = true;
+  cudaGraph_t g = nullptr;
+  int rc = IRKMG_OK;
+  cudaError_t e = cudaStreamBeginCapture(C.gstream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = vcycle_level(C, lc, C.L[lc].r, C.L[lc].z, tr);
+    e = cudaStreamEndCapture(C.gstream, &g);
+  }
+  C.stream = saved_stream;
+  C.trace_on = saved_trace;
+  C.capturing = false;
+  C.cgraph_launches[tr] = C.launches - l0;
+  C.launches = l0;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CK(e);
+  e = cudaGraphInstantiate(&C.cgraph[tr], g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  return IRKMG_OK;
+}
+
+void drop_graphs(Ctx& C) {
+  if (C.vgraph) cudaGraphExecDestroy(C.vgraph);
+  C.vgraph = nullptr;
+  for (int t = 0; t < 2; ++t) {
+    if (C.cgraph[t]) cudaGraphExecDestroy(C.cgraph[t]);
+    C.cgraph[t] = nullptr;
+  }
+}
+
 // --- batched solves ----------------------------------------------------------
 // One V-cycle of C captured as a CUDA graph that reads d_gin and writes
 // d_gout; captured once, on the context's (non-default) stream.
@@ -891,7 +961,9 @@ int capture_vcycle(Ctx& C) {
   C.trace_on = false;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(C.stream, cudaStreamCaptureModeThreadLocal));
+  C.capturing = true;
   rc = vcycle_level(C, (int)C.L.size() - 1, C.d_gin, C.d_gout, 0);
+  C.capturing = false;
   cudaError_t e = cudaStreamEndCapture(C.stream, &g);
   C.trace_on = saved;
   if (rc) {
@@ -1155,6 +1227,7 @@ int irkmg_update(irkmg_ctx* C, double dt, double nu) {
   CK(C->stream ? cudaStreamSynchronize(C->stream) : cudaDeviceSynchronize());
   C->dt = dt;
   C->nu = nu;
+  drop_graphs(*C);
   int rc;
   if ((rc = assemble_all(*C))) return rc;
   for (size_t l = 0; l < C->L.size(); ++l) {
@@ -1494,7 +1567,11 @@ void irkmg_destroy(irkmg_ctx* C) {
   if (C->stream) cudaStreamSynchronize(C->stream);
   else cudaDeviceSynchronize();
   for (cudaEvent_t e : C->ev) cudaEventDestroy(e);
-  if (C->vgraph) cudaGraphExecDestroy(C->vgraph);
+  drop_graphs(*C);
+  if (C->gstream) cudaStreamSynchronize(C->gstream);
+  for (cudaEvent_t e : C->gev)
+    if (e) cudaEventDestroy(e);
+  if (C->gstream) cudaStreamDestroy(C->gstream);
   for (void* p : C->allocs) cudaFree(p);
   if (C->h_h) cudaFreeHost(C->h_h);
   if (C->h_err) cudaFreeHost(C->h_err);

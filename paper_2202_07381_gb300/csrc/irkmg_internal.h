@@ -148,8 +148,10 @@ struct Level {
   bool kron = false;                   // Kronecker-decoupled patch factors (KronPlan)
   int kron_nmax = 0;                   // largest spatial patch size n on a decoupled level
   int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 big-patch mat-vec,
-                                       // 4 decoupled warp-per-patch
+                                       // 4 decoupled warp-per-patch, 5 decoupled staged
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
+  int kron_shape = 0;                  // launch shape of the staged decoupled apply (0, 1)
+  int kron_cap[2][2] = {{0, 0}, {0, 0}};  // its resident CTAs per [shape][transpose] (0 unset)
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
   // algorithmic bytes for tracing
@@ -188,6 +190,13 @@ struct Ctx {
   bool trace_on = false;
   // CUDA graph of one V-cycle from d_gin to d_gout (batched solves)
   cudaGraphExec_t vgraph = nullptr;
+  // CUDA graphs of the coarse part of the V-cycle (levels 0 .. nl-2, from
+  // L[nl-2].r to L[nl-2].z; [0] J, [1] Jᵀ), launched on gstream between events
+  cudaGraphExec_t cgraph[2] = {nullptr, nullptr};
+  int64_t cgraph_launches[2] = {0, 0};
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  bool capturing = false;
   double *d_gin = nullptr, *d_gout = nullptr;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_class;       // 0 vanka, 1 operator (one per event pair)
@@ -209,6 +218,7 @@ cudaError_t launch_patch_gidx_kron(Ctx& C, Level& L);
 cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, double* out,
                               double scale, int transpose);
 int kron_max_slots();
+bool kron_staged_fits(Ctx& C, Level& L, int shape);
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose);
 bool vanka_staged_fits(Ctx& C, Level& L);

@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "irkmg_internal.h"
+#include "tma.cuh"
 
 namespace irkmg {
 
@@ -50,7 +51,7 @@ __host__ __device__ inline size_t kron_warp_bytes(int s, int ns, int nt, int nma
 template <typename T, int R, bool TR>
 __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply P,
                                                                       const T* __restrict__ fac) {
-  extern __shared__ __align__(16) unsigned char dyn[];
+  extern __shared__ __align__(128) unsigned char dyn[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kKronWarps + warp;
   if (w >= P.count) return;
@@ -128,6 +129,255 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply 
 
 int kron_max_slots() { return kKronMaxSlots; }
 
+// ---------------------------------------------------------------------------
+// TMA-staged decoupled apply (persistent over the patches of one colour).
+// Each patch block (nm matrices + index list) is one contiguous 16-byte-aligned
+// run, streamed into a ring of shared-memory stages by cp.async.bulk; the CTA
+// works on one patch at a time from shared memory while the next blocks are
+// in flight, so the latency of a patch is one pass over its block instead of
+// one memory round trip per column.  The target values out[S_v] are read
+// together with the residual (patches of one colour are disjoint, so no other
+// CTA writes them during the launch).  Every mbarrier wait is bounded: on
+// expiry the CTA records IRKMG_ETIMEOUT, waits (bounded) for its own copies
+// still in flight and returns.
+// ---------------------------------------------------------------------------
+constexpr int kKronStagedThreads = 256;
+constexpr int kKronMaxStages = 4;
+
+struct KronStaged {
+  KronApply a;
+  int stages;
+  uint32_t stage_bytes;  // bytes per stage (largest patch block, rounded to 128)
+  uint32_t work_off;     // offset of the work arrays in dynamic shared memory
+  int64_t spins;
+  int* err;
+};
+
+template <typename T, bool TR>
+__global__ void __launch_bounds__(kKronStagedThreads, 5)
+    k_vanka_apply_kron_staged(KronStaged S, const T* __restrict__ fac) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ __align__(8) uint64_t bar[kKronMaxStages];
+  __shared__ int s_n[kKronMaxStages];  // patch size n of the block in each stage
+  __shared__ int s_abort;
+  const KronApply& P = S.a;
+  const int tid = threadIdx.x;
+  const int nmax = P.nmax;
+  double* s_r = reinterpret_cast<double*>(dyn + S.work_off);  // s · nmax
+  double* s_acc = s_r + P.s * nmax;                           // nt · nmax
+  T* s_src = reinterpret_cast<T*>(s_acc + P.nt * nmax);        // max(ns, nt) · nmax
+  const int nsrc = TR ? P.nt : P.ns;
+  const int64_t nmine = (P.count > blockIdx.x) ? (P.count - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (tid == 0) {
+    for (int st = 0; st < S.stages; ++st) mbar_init(&bar[st], 1);
+    s_abort = 0;
+  }
+  fence_proxy_async();
+  __syncthreads();
+
+  auto mats_bytes = [&](int n) -> int64_t {
+    return ((int64_t)P.nm * n * n * (int64_t)sizeof(T) + 15) & ~(int64_t)15;
+  };
+  const uint64_t pol = l2_evict_first_policy();
+  // Thread 0 issues the copies.  The size and offset of the next patch to be
+  // issued are loaded one issue ahead (nx, ox), so no issue waits on a global
+  // load; the size travels to the other threads through s_n.
+  int nx = 0;
+  int64_t ox = 0;
+  auto meta = [&](int64_t k) {
+    if (k < nmine) {
+      const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+      nx = P.np[pi];
+      ox = P.fac_off[pi];
+    }
+  };
+  auto issue = [&](int st) {  // the patch whose metadata is in (nx, ox)
+    const uint32_t bytes = (uint32_t)(mats_bytes(nx) + (((int64_t)nx * 4 + 15) & ~(int64_t)15));
+    s_n[st] = nx;
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_g2s(dyn + (size_t)st * S.stage_bytes, fac + ox, bytes, &bar[st], pol);
+  };
+  if (tid == 0) {
+    const int64_t pre = nmine < S.stages ? nmine : S.stages;
+    for (int64_t k = 0; k < pre; ++k) {
+      meta(k);
+      issue((int)k);
+    }
+    meta(pre);
+  }
+
+  // Thread tid < s·n owns entry tid of the gathered stage residual: its global
+  // index, the residual value and the current target value.  Patch k+1's
+  // entries are loaded while patch k is computed (patches of one colour are
+  // disjoint, so patch k's writes never touch them).
+  int64_t gix = -1;
+  double rv = 0.0, ov = 0.0;
+  auto wait_stage = [&](int64_t k) {
+    if (!mbar_wait_bounded(&bar[k % S.stages], (uint32_t)((k / S.stages) & 1), S.spins)) {
+      s_abort = 1;
+      atomicCAS(&S.err[0], 0, IRKMG_ETIMEOUT);
+      return false;
+    }
+    return true;
+  };
+  auto gather = [&](int64_t k) {
+    const int n = s_n[k % S.stages];
+    const int32_t* G = reinterpret_cast<const int32_t*>(dyn + (size_t)(k % S.stages) * S.stage_bytes +
+                                                        mats_bytes(n));
+    gix = -1;
+    if (tid < P.s * n) {
+      const int t = tid / n, i = tid - t * n;
+      gix = t * P.m + G[i];
+      rv = P.r[gix];
+      ov = P.out[gix];
+    }
+  };
+  // in flight after the prologue: copies 0 .. min(nmine, stages) - 1
+  auto drain = [&](int64_t from) {
+    for (int64_t j = from; j < nmine && j < from + S.stages; ++j)
+      mbar_wait_bounded(&bar[j % S.stages], (uint32_t)((j / S.stages) & 1), S.spins);
+  };
+  __syncthreads();  // s_n of the first stages
+  if (nmine > 0 && wait_stage(0)) gather(0);
+  __syncthreads();
+  if (s_abort) {
+    drain(0);
+    return;
+  }
+
+  for (int64_t k = 0; k < nmine; ++k) {
+    const int st = (int)(k % S.stages);
+    const int n = s_n[st];
+    const T* X = reinterpret_cast<const T*>(dyn + (size_t)st * S.stage_bytes);
+    const int64_t nn = (int64_t)n * n;
+    const int64_t gk = gix;
+    const double ok_ = ov;
+    if (gk >= 0) s_r[tid] = rv;
+    __syncthreads();
+    if (k + 1 < nmine && wait_stage(k + 1)) gather(k + 1);
+    for (int idx = tid; idx < nsrc * n; idx += kKronStagedThreads) {
+      const int c = idx / n, i = idx - c * n;
+      double a = 0.0;
+      for (int t = 0; t < P.s; ++t)
+        a += (TR ? P.H[t * kKronMaxTasks + c] : P.G[c * 3 + t]) * s_r[t * n + i];
+      s_src[idx] = (T)a;
+    }
+    __syncthreads();
+    for (int tau = tid; tau < P.nt * n; tau += kKronStagedThreads) {
+      const int task = tau / n, i = tau - task * n;
+      const T* M = X + (int64_t)P.task_mat[task] * nn + (TR ? (int64_t)i * n : (int64_t)i);
+      const T* src = s_src + (TR ? task : P.task_src[task]) * n;
+      const int64_t step = TR ? 1 : n;
+      T a0 = (T)0, a1 = (T)0;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < n; j += 2) {
+        a0 = fma(M[j * step], src[j], a0);
+        a1 = fma(M[(j + 1) * step], src[j + 1], a1);
+      }
+      if (j < n) a0 = fma(M[j * step], src[j], a0);
+      s_acc[tau] = (double)(a0 + a1);
+    }
+    __syncthreads();
+    if (gk >= 0) {
+      const int t = tid / n, i = tid - t * n;
+      double x = 0.0;
+      for (int tau = 0; tau < P.nt; ++tau) {
+        const double h = TR ? P.G[P.task_src[tau] * 3 + t] : P.H[t * kKronMaxTasks + tau];
+        x += h * s_acc[tau * n + i];
+      }
+      P.out[gk] = ok_ + P.scale * x;
+    }
+    fence_proxy_async();
+    __syncthreads();  // stage st and the work arrays fully consumed
+    if (s_abort) {
+      drain(k + 1);
+      return;
+    }
+    if (tid == 0 && k + S.stages < nmine) {
+      issue(st);
+      meta(k + S.stages + 1);
+    }
+  }
+}
+
+// Launch shapes of the staged decoupled apply for a level.  Shape 0: the most
+// CTAs per SM (up to 5, the register bound) that leave room for three stages
+// each (the block of patch k+1 is waited for while patch k is computed, so
+// three stages keep one block of look-ahead in flight), else for two.  Shape
+// 1: the most CTAs with two stages.  The autotuner times both.  False when
+// s·n_max exceeds the CTA or not even one CTA with two stages fits.
+struct KronShape {
+  int stages, ctas_per_sm;
+  uint32_t stage_bytes, work_off, dyn_bytes;
+};
+
+static bool kron_staged_config(const KronPlan& K, int nmax, int prec, int shape, KronShape* out) {
+  if (K.s * nmax > kKronStagedThreads) return false;
+  const size_t w = prec == 64 ? 8 : 4;
+  const size_t blk = (((size_t)K.nm * nmax * nmax * w + 15) & ~(size_t)15) +
+                     (((size_t)nmax * 4 + 15) & ~(size_t)15);
+  const size_t sb = (blk + 127) & ~(size_t)127;
+  const int nsrc = K.ns > K.nt ? K.ns : K.nt;
+  const size_t work = (size_t)(K.s + K.nt) * nmax * 8 + (size_t)nsrc * nmax * w + 16;
+  const size_t static_b = 128;
+  const size_t per_sm = 233472, reserved = 1024, per_block = 232448;
+  for (int want = shape == 0 ? 3 : 2; want >= 2; --want)
+    for (int ctas = 5; ctas >= 1; --ctas) {
+      const size_t lim = std::min(per_sm / ctas - reserved, per_block);
+      if (lim < static_b + work + want * sb) continue;
+      int st = (int)((lim - static_b - work) / sb);
+      if (st > kKronMaxStages) st = kKronMaxStages;
+      out->stages = st;
+      out->ctas_per_sm = ctas;
+      out->stage_bytes = (uint32_t)sb;
+      out->work_off = (uint32_t)(st * sb);
+      out->dyn_bytes = (uint32_t)(st * sb + work);
+      return true;
+    }
+  return false;
+}
+
+bool kron_staged_fits(Ctx& C, Level& L, int shape) {
+  KronShape shp;
+  return kron_staged_config(C.kplan, L.kron_nmax, C.opt.patch_precision, shape, &shp);
+}
+
+// The kernel's dynamic shared-memory limit is a property of the function: it
+// is only ever raised (per device), so launches of other levels with smaller
+// shapes stay valid.  The residency for the level's shape is looked up once
+// (cached in *cap); one CTA is launched per resident slot (at most one per
+// patch).
+template <typename T, bool TR>
+cudaError_t launch_kron_staged(const KronStaged& S, const T* fac, const KronShape& shp,
+                               cudaStream_t st, int* cap_cache) {
+  auto kern = k_vanka_apply_kron_staged<T, TR>;
+  static uint32_t limit[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (shp.dyn_bytes > limit[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shp.dyn_bytes);
+    if (e != cudaSuccess) return e;
+    limit[dev] = shp.dyn_bytes;
+  }
+  if (*cap_cache == 0) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKronStagedThreads,
+                                                      shp.dyn_bytes);
+    if (e != cudaSuccess) return e;
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *cap_cache = nsm * (per_sm < 1 ? 1 : per_sm);
+  }
+  const int64_t cap = *cap_cache;
+  const int64_t ctas = S.a.count < cap ? S.a.count : cap;
+  kern<<<(unsigned)ctas, kKronStagedThreads, shp.dyn_bytes, st>>>(S, fac);
+  return cudaGetLastError();
+}
+
 template <typename T, bool TR>
 cudaError_t launch_kron_t(const KronApply& P, const T* fac, int R, unsigned grid, size_t smem,
                           cudaStream_t st) {
@@ -187,6 +437,25 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   P.nmax = L.kron_nmax;
   if (P.count <= 0) return cudaSuccess;
   const int prec = C.opt.patch_precision;
+  KronShape shp;
+  if (L.apply_kernel == 5 && kron_staged_config(K, L.kron_nmax, prec, L.kron_shape, &shp)) {
+    KronStaged S;
+    S.a = P;
+    S.stages = shp.stages;
+    S.stage_bytes = shp.stage_bytes;
+    S.work_off = shp.work_off;
+    S.spins = C.opt.timeout_spins > 0 ? C.opt.timeout_spins : (int64_t)1 << 26;
+    S.err = C.d_err;
+    int* cap = &L.kron_cap[L.kron_shape][transpose ? 1 : 0];
+    if (prec == 64) {
+      const double* f = (const double*)L.d_fac;
+      return transpose ? launch_kron_staged<double, true>(S, f, shp, C.stream, cap)
+                       : launch_kron_staged<double, false>(S, f, shp, C.stream, cap);
+    }
+    const float* f = (const float*)L.d_fac;
+    return transpose ? launch_kron_staged<float, true>(S, f, shp, C.stream, cap)
+                     : launch_kron_staged<float, false>(S, f, shp, C.stream, cap);
+  }
   const size_t smem =
       (size_t)kKronWarps * kron_warp_bytes(P.s, P.ns, P.nt, P.nmax, prec == 64 ? 8 : 4);
   const unsigned grid = (unsigned)((P.count + kKronWarps - 1) / kKronWarps);

@@ -27,26 +27,30 @@ def _oracle(fam, s, dt, n0, nl, nu=1.0):
     return mg.Hierarchy(*synth.square_mesh(n0), nl, getattr(tableau, fam)(s)[0], dt, nu=nu)
 
 
-def _context(irkmg, fam, s, dt, n0, nl, form, precision=64, nu=1.0, wind=None):
+def _context(irkmg, fam, s, dt, n0, nl, form, precision=64, nu=1.0, wind=None, variant=0):
     A, b, c = getattr(irkmg, "irkmg_" + fam)(s)
     o = irkmg.irkmg_default_options()
     o.nlevels = nl
     o.patch_form = form
     o.patch_precision = precision
+    o.apply_variant = variant
     return irkmg.irkmg_setup(*synth.square_mesh(n0), A, b, c, dt, nu, o, wind=wind)
 
 
+@pytest.mark.parametrize("variant", [1, 2], ids=["tma_staged", "warp_per_patch"])
 @pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
 @pytest.mark.parametrize("fam,s,dt", CASES)
-def test_decoupled_vanka_and_vcycle_match_oracle(fam, s, dt, form):
+def test_decoupled_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
+    """Both decoupled apply kernels (forced on every level), both layouts:
+    one correction per level with J and Jᵀ patches, and one V-cycle."""
     irkmg = need_gpu()
     n0, nl = 2, 4
     H = _oracle(fam, s, dt, n0, nl)
-    ctx = _context(irkmg, fam, s, dt, n0, nl, form)
+    ctx = _context(irkmg, fam, s, dt, n0, nl, form, variant=variant)
     try:
         for l in range(1, nl):
             info = ctx.levels[l]
-            assert info["apply_kernel"] == 4
+            assert info["apply_kernel"] == (5 if variant == 1 else 4)
             n = 2 * 19 + 1   # largest patch of a structured triangle mesh: 19 nodes
             pairs = s // 2
             nm = s if form == 2 else s + pairs
@@ -91,6 +95,18 @@ def test_decoupled_solve_matches_oracle(fam, s, dt, precision):
             assert abs(st["iters"] - its) <= 1
         else:
             assert st["iters"] <= its + 3
+    finally:
+        ctx.close()
+
+
+def test_decoupled_autotuner_picks_the_faster_kernel():
+    irkmg = need_gpu()
+    ctx = _context(irkmg, "radau_iia", 3, 1 / 64, 2, 5, 1)
+    try:
+        for lv in ctx.levels[1:]:
+            assert lv["apply_kernel"] in (4, 5)
+            assert all(t > 0 for t in lv["apply_ms"])
+            assert lv["apply_kernel"] == (5 if lv["apply_ms"][0] <= lv["apply_ms"][1] else 4)
     finally:
         ctx.close()
 
@@ -145,7 +161,7 @@ def test_3d_keeps_dense_factors_where_pairs_do_not_fit():
     the shared-memory inversion, so those levels keep the dense blocked-LU
     form; coarse levels with small patches decouple.  The solve is unchanged."""
     irkmg = need_gpu()
-    from oracle import fgmres, mg, tableau
+    from oracle import mg, tableau
     A, b, c = irkmg.irkmg_radau_iia(2)
     o = irkmg.irkmg_default_options()
     o.nlevels = 2
@@ -154,11 +170,11 @@ def test_3d_keeps_dense_factors_where_pairs_do_not_fit():
     ctx = irkmg.irkmg_setup(*synth.cube_mesh(2), A, b, c, 1 / 16, 1.0, o)
     try:
         kinds = [lv["apply_kernel"] for lv in ctx.levels[1:]]
-        assert all(k in (3, 4) for k in kinds)
+        assert all(k in (3, 4, 5) for k in kinds)
         H = mg.Hierarchy(*synth.cube_mesh(2), 2, tableau.radau_iia(2)[0], 1 / 16, cheb=(2.0, 17.0))
         r = synth.random_vector(909, H.finest.N)
         z = dev(np.zeros(H.finest.N))
         irkmg.irkmg_vcycle(ctx, dev(r), z)
-        assert rel(host(z), H.vcycle(r)) < 1e-9
+        assert rel(host(z), H.vcycle(r)) < 1e-11
     finally:
         ctx.close()
