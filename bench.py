@@ -423,11 +423,15 @@ def run_ours(args, wl, rank, world, local_rank):
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # the timed region is the profiler range (a no-op unless a profiler
+        # started with profiling off is attached, e.g. ncu --profile-from-start off)
+        torch.cuda.profiler.start()
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         barrier()
         time.sleep(0.25)
     ms = e0.elapsed_time(e1)

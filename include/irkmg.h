@@ -101,11 +101,14 @@ typedef struct {
                               wait also gives up after 2 s); an expired wait makes
                               FGMRES return IRKMG_ETIMEOUT                          */
   int apply_variant;       /* Vanka apply kernel per level (dense or decoupled form
-                              alike): 0 = autotuned at set-up (both kernels timed
-                              once per level, the faster kept); 1 = TMA-staged
-                              (patch blocks streamed to shared memory by
+                              alike): 0 = autotuned at set-up (every candidate
+                              timed once per level, the fastest kept); 1 = TMA-
+                              staged (patch blocks streamed to shared memory by
                               cp.async.bulk) wherever it fits; 2 = warp-per-patch
-                              mat-vec everywhere                                    */
+                              mat-vec everywhere; 3, 4 = as 1, 2 and, on decoupled
+                              levels, one launch over all patches whose results
+                              are summed per DoF by a second, deterministic
+                              launch (instead of one launch per colour)            */
   int patch_form;          /* 0 = one dense s·n patch system per vertex (Section 4.2);
                               1..3 = Kronecker-decoupled patch solves: with the
                               Butcher matrix A = T D T⁻¹ (D real block diagonal,
@@ -144,6 +147,9 @@ typedef struct {
   double apply_ms[2];      /* autotuner: one sweep with the staged / warp-per-patch
                               kernel of the level's form (0 if untimed)            */
   int64_t dim;             /* 2 or 3                                                */
+  int64_t single_launch;   /* 1: the level relaxes by one launch over all patches
+                              plus a deterministic per-DoF sum (decoupled form);
+                              0: one launch per colour                             */
 } irkmg_level_info;
 
 /* ---- set-up -------------------------------------------------------------- */
@@ -345,9 +351,13 @@ typedef struct {
   double vanka_ms, vanka_bytes;
   int64_t op_launches;
   double op_ms, op_bytes;
-  double vanka_flops;      /* 2·n_p^2 per patch applied in the timed Vanka launches */
+  double vanka_flops;      /* 2·n_p^2 per patch applied in the timed Vanka launches
+                              (decoupled form: 2·(nt·n² + (ns + nt)·s·n), see
+                              patch_form)                                           */
   double op_flops;         /* 2·(4s·nnz(vel) + 2s·(nnz(B) + nnz(Bᵀ)) + 2s²·n_f + s²·n_v)
                               per timed operator launch                              */
+  int64_t reduce_launches; /* timed per-DoF sums of the one-launch relaxation      */
+  double reduce_ms, reduce_bytes;
 } irkmg_trace;
 
 /* Reset the counters; on = 1 also starts event timing.  Never fails on a valid ctx. */

@@ -345,6 +345,38 @@ int build_patches(Ctx& C, Level& L) {
     CK(launch_patch_gidx_kron(C, L));
   else
     CK(launch_patch_gidx(C, L));
+  if (L.kron) {
+    // one-launch relaxation: offsets of the ordered patches' results and, per
+    // spatial DoF d, its entries qoff[p] + i in ordered-patch order
+    std::vector<int64_t> qoff(L.nv);
+    int64_t Q = 0;
+    for (int64_t p = 0; p < L.nv; ++p) {
+      qoff[p] = Q;
+      Q += npv[p];
+    }
+    if (Q > INT32_MAX) return fail(IRKMG_ENOTIMPL, "patch results exceed 2^31 entries");
+    std::vector<int32_t> cptr(L.m + 1, 0), cidx(Q);
+    auto dof = [&](int32_t v, int64_t i) -> int64_t {
+      const int32_t nb = L.h_patch_ptr[v], nl = L.h_patch_ptr[v + 1] - nb;
+      if (i < (int64_t)L.dim * nl) {
+        const int64_t c = i / nl;
+        return c * L.nf + L.h_patch_nodes[nb + i - c * nl];
+      }
+      return L.dim * L.nf + v;
+    };
+    for (int64_t p = 0; p < L.nv; ++p)
+      for (int64_t i = 0; i < npv[p]; ++i) cptr[dof(order[p], i) + 1]++;
+    for (int64_t d = 0; d < L.m; ++d) cptr[d + 1] += cptr[d];
+    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int64_t p = 0; p < L.nv; ++p)
+      for (int64_t i = 0; i < npv[p]; ++i) cidx[fill[dof(order[p], i)]++] = (int32_t)(qoff[p] + i);
+    if ((rc = upload(C, &L.d_qoff, qoff))) return rc;
+    if ((rc = upload(C, &L.d_cptr, cptr))) return rc;
+    if ((rc = upload(C, &L.d_cidx, cidx))) return rc;
+    L.Q = Q;
+    // the reduction reads every result and its index once, and out per DoF
+    L.reduce_bytes = (double)C.s * (8.0 * Q + 16.0 * L.m) + 4.0 * Q + 4.0 * L.m;
+  }
   return IRKMG_OK;
 }
 
@@ -421,27 +453,38 @@ int tune_apply(Ctx& C) {
       L.apply_kernel = 3;
       continue;
     }
-    // candidate kernels: staged (TMA) and warp-per-patch, dense or decoupled
-    // (the decoupled staged kernel with each of its launch shapes)
+    // candidates: staged (TMA) and warp-per-patch kernels, dense or decoupled;
+    // on decoupled levels each staged launch shape, and both relaxation
+    // modes (one launch per colour, or one launch and the per-DoF reduction)
     const int ks = L.kron ? 5 : 1, kw = L.kron ? 4 : 2;
     L.kron_shape = 0;
+    L.single = false;
     const bool fits = L.kron ? kron_staged_fits(C, L, 0) : vanka_staged_fits(C, L);
-    if (C.opt.apply_variant == 1 || C.opt.apply_variant == 2) {
-      L.apply_kernel = (C.opt.apply_variant == 1 && fits) ? ks : kw;
+    const int av = C.opt.apply_variant;
+    if (av != 0) {
+      const bool staged = (av == 1 || av == 3) && fits;
+      L.apply_kernel = staged ? ks : kw;
+      L.single = L.kron && av >= 3;
       continue;
     }
-    if (!fits) {
-      L.apply_kernel = kw;
-      continue;
+    struct Cand { int kern, shape; bool single; };
+    std::vector<Cand> cands;
+    for (int single = 0; single <= (L.kron ? 1 : 0); ++single) {
+      if (fits)
+        for (int shape = 0; shape < (L.kron ? 2 : 1); ++shape) cands.push_back({ks, shape, single != 0});
+      cands.push_back({kw, 0, single != 0});
     }
     cudaError_t e = cudaMemsetAsync(L.t, 0, sizeof(double) * L.N, C.stream);
     if (e != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e)); break; }
-    float shape_ms[2] = {1e30f, 1e30f};
-    const int nshape = L.kron ? 2 : 1;
-    for (int cand = 0; cand < nshape + 1 && rc == IRKMG_OK; ++cand) {
-      const int kern = cand < nshape ? 1 : 2;
-      L.apply_kernel = kern == 1 ? ks : kw;
-      if (kern == 1) L.kron_shape = cand;
+    float best_all = 1e30f;
+    Cand pick = cands.back();
+    L.apply_ms[1] = L.apply_ms[2] = 0.f;
+    float best_kind[2] = {1e30f, 1e30f};
+    for (const Cand& cd : cands) {
+      if (rc != IRKMG_OK) break;
+      L.apply_kernel = cd.kern;
+      L.kron_shape = cd.shape;
+      L.single = cd.single;
       float best = 1e30f;
       for (int rep = 0; rep < 3 && rc == IRKMG_OK; ++rep) {
         cudaEventRecord(a, C.stream);
@@ -453,11 +496,18 @@ int tune_apply(Ctx& C) {
         cudaEventElapsedTime(&ms, a, b);
         if (rep > 0 && ms < best) best = ms;   // rep 0 is the warm-up
       }
-      if (kern == 1) shape_ms[cand] = best;
-      L.apply_ms[kern] = kern == 1 ? std::min(shape_ms[0], shape_ms[1]) : best;
+      const int kind = cd.kern == ks ? 0 : 1;
+      best_kind[kind] = std::min(best_kind[kind], best);
+      if (best < best_all) {
+        best_all = best;
+        pick = cd;
+      }
     }
-    L.kron_shape = shape_ms[1] < shape_ms[0] ? 1 : 0;
-    L.apply_kernel = (L.apply_ms[1] <= L.apply_ms[2]) ? ks : kw;
+    L.apply_ms[1] = best_kind[0] < 1e29f ? best_kind[0] : 0.f;
+    L.apply_ms[2] = best_kind[1] < 1e29f ? best_kind[1] : 0.f;
+    L.apply_kernel = pick.kern;
+    L.kron_shape = pick.shape;
+    L.single = pick.single;
   }
   C.trace_on = saved;
   C.launches = 0;
@@ -473,6 +523,34 @@ int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int 
   if (L.big && !L.kron && tr)
     return fail(IRKMG_ENOTIMPL, "transposed patch solves of LU-factored (3D) patches");
   const bool timed = C.trace_on && &L == &C.L.back();
+  if (L.kron && L.single) {
+    // one launch over all patches into d_Y, then the deterministic per-DoF sum
+    cudaEvent_t a = nullptr, b = nullptr, c2 = nullptr, d2 = nullptr;
+    if (timed) {
+      double bytes = 0.0, flops = 0.0;
+      for (int c = 0; c < L.ncolours; ++c) {
+        bytes += L.colour_bytes[c];
+        flops += L.colour_flops[c];
+      }
+      // the colour bytes count r and out per DoF; here the launch reads r and
+      // writes its results once (24 B per stage DoF either way)
+      int rc = trace_pair(C, 0, bytes, &a, &b, flops);
+      if (rc) return rc;
+      CK(cudaEventRecord(a, C.stream));
+    }
+    CK(launch_vanka_kron(C, L, -1, r, out, scale, tr));
+    C.launches++;
+    if (timed) {
+      CK(cudaEventRecord(b, C.stream));
+      int rc = trace_pair(C, 2, L.reduce_bytes, &c2, &d2, 0.0);
+      if (rc) return rc;
+      CK(cudaEventRecord(c2, C.stream));
+    }
+    CK(launch_vanka_reduce(C, L, out, scale));
+    C.launches++;
+    if (timed) CK(cudaEventRecord(d2, C.stream));
+    return IRKMG_OK;
+  }
   for (int c = 0; c < L.ncolours; ++c) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (timed) {
@@ -713,8 +791,8 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
   if (o->maxit < 1) return fail(IRKMG_EINVAL, "maxit >= 1");
   if (o->patch_precision != 64 && o->patch_precision != 32)
     return fail(IRKMG_EINVAL, "patch_precision is 64 or 32");
-  if (o->apply_variant < 0 || o->apply_variant > 2)
-    return fail(IRKMG_EINVAL, "apply_variant is 0, 1 or 2");
+  if (o->apply_variant < 0 || o->apply_variant > 4)
+    return fail(IRKMG_EINVAL, "apply_variant is 0 .. 4");
   if (o->patch_form < 0 || o->patch_form > 3)
     return fail(IRKMG_EINVAL, "patch_form is 0, 1, 2 or 3");
   if (o->patch_form != 0) {
@@ -813,6 +891,11 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
     if ((rc = dalloc(*C, &C->d_kb, Lf.N))) return rc;
     if ((rc = dalloc(*C, &C->d_lam, Lf.N))) return rc;
     if ((rc = dalloc(*C, &C->d_scalar, 8))) return rc;
+  }
+  if (C->kron) {
+    int64_t qmax = 0;
+    for (const Level& L : C->L) qmax = std::max(qmax, L.Q);
+    if (qmax > 0 && (rc = dalloc(*C, &C->d_Y, (size_t)C->s * qmax))) return rc;
   }
   C->nb = C->L[0].N + C->s;
   if (C->nb > 20000) return fail(IRKMG_EINVAL, "coarsest level too large for the dense solve");
@@ -1274,6 +1357,7 @@ int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) 
   info->dim = L.dim;
   info->apply_ms[0] = L.apply_ms[1];
   info->apply_ms[1] = L.apply_ms[2];
+  info->single_launch = level > 0 && L.kron && L.single ? 1 : 0;
   return IRKMG_OK;
 }
 
@@ -1548,6 +1632,10 @@ int irkmg_trace_read(irkmg_ctx* C, irkmg_trace* out) {
       out->vanka_ms += ms;
       out->vanka_bytes += C->ev_bytes[k];
       out->vanka_flops += C->ev_flops[k];
+    } else if (C->ev_class[k] == 2) {
+      out->reduce_launches++;
+      out->reduce_ms += ms;
+      out->reduce_bytes += C->ev_bytes[k];
     } else {
       out->op_launches++;
       out->op_ms += ms;

@@ -151,6 +151,13 @@ struct Level {
                                        // 4 decoupled warp-per-patch, 5 decoupled staged
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   int kron_shape = 0;                  // launch shape of the staged decoupled apply (0, 1)
+  // one-launch relaxation of a decoupled level: patch results to Ctx::d_Y at
+  // t·Q + qoff[p] + i, then the per-DoF sum over the contribution lists
+  bool single = false;
+  int64_t Q = 0;                       // Σ n over the patches
+  int64_t* d_qoff = nullptr;           // per ordered patch
+  int32_t *d_cptr = nullptr, *d_cidx = nullptr;  // spatial DoF -> entries qoff[p] + i
+  double reduce_bytes = 0.0;           // algorithmic bytes of one reduction launch
   int kron_cap[2][2] = {{0, 0}, {0, 0}};  // its resident CTAs per [shape][transpose] (0 unset)
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
@@ -167,6 +174,7 @@ struct Ctx {
   irkmg_options opt{};
   KronPlan kplan{};
   bool kron = false;          // decoupled patch solves requested and the tableau splits
+  double* d_Y = nullptr;      // s · max Q patch results of the one-launch relaxation
   cudaStream_t stream = nullptr;
   std::vector<double> wind;  // finest-level nodal wind (empty for Stokes)
   std::vector<Level> L;
@@ -216,7 +224,8 @@ cudaError_t launch_patch_gidx(Ctx& C, Level& L);
 cudaError_t launch_patch_invert_kron(Ctx& C, Level& L);
 cudaError_t launch_patch_gidx_kron(Ctx& C, Level& L);
 cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, double* out,
-                              double scale, int transpose);
+                              double scale, int transpose);  // colour -1: all patches to d_Y
+cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale);
 int kron_max_slots();
 bool kron_staged_fits(Ctx& C, Level& L, int shape);
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,

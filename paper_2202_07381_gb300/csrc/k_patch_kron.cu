@@ -36,8 +36,13 @@ struct KronApply {
   const double* r;
   double* out;
   double scale;
-  int64_t first, count;  // ordered-patch range of this colour
+  int64_t first, count;  // ordered-patch range of this colour (or of all patches)
   int nmax;              // per-warp shared-memory stride
+  // one-launch mode: the patch results go to ybuf[t·Q + qoff[p] + i] instead
+  // of out, and k_vanka_reduce adds them up per DoF afterwards
+  double* ybuf;
+  const int64_t* qoff;
+  int64_t Q;
 };
 
 // Shared memory of one warp: residuals (s·nmax doubles), task results
@@ -123,7 +128,10 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply 
       const double h = TR ? P.G[P.task_src[tau] * 3 + t] : P.H[t * kKronMaxTasks + tau];
       x += h * s_acc[tau * n + i];
     }
-    P.out[t * P.m + s_g[i]] += P.scale * x;
+    if (P.ybuf)
+      P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
+    else
+      P.out[t * P.m + s_g[i]] += P.scale * x;
   }
 }
 
@@ -210,7 +218,7 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
   // index, the residual value and the current target value.  Patch k+1's
   // entries are loaded while patch k is computed (patches of one colour are
   // disjoint, so patch k's writes never touch them).
-  int64_t gix = -1;
+  int64_t gix = -1, qo = 0;
   double rv = 0.0, ov = 0.0;
   auto wait_stage = [&](int64_t k) {
     if (!mbar_wait_bounded(&bar[k % S.stages], (uint32_t)((k / S.stages) & 1), S.spins)) {
@@ -229,7 +237,10 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
       const int t = tid / n, i = tid - t * n;
       gix = t * P.m + G[i];
       rv = P.r[gix];
-      ov = P.out[gix];
+      if (P.ybuf)
+        qo = P.qoff[P.first + blockIdx.x + k * gridDim.x];
+      else
+        ov = P.out[gix];
     }
   };
   // in flight after the prologue: copies 0 .. min(nmine, stages) - 1
@@ -250,7 +261,7 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
     const int n = s_n[st];
     const T* X = reinterpret_cast<const T*>(dyn + (size_t)st * S.stage_bytes);
     const int64_t nn = (int64_t)n * n;
-    const int64_t gk = gix;
+    const int64_t gk = gix, qk = qo;
     const double ok_ = ov;
     if (gk >= 0) s_r[tid] = rv;
     __syncthreads();
@@ -286,7 +297,10 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
         const double h = TR ? P.G[P.task_src[tau] * 3 + t] : P.H[t * kKronMaxTasks + tau];
         x += h * s_acc[tau * n + i];
       }
-      P.out[gk] = ok_ + P.scale * x;
+      if (P.ybuf)
+        P.ybuf[t * P.Q + qk + i] = x;
+      else
+        P.out[gk] = ok_ + P.scale * x;
     }
     fence_proxy_async();
     __syncthreads();  // stage st and the work arrays fully consumed
@@ -432,8 +446,19 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   P.r = r;
   P.out = out;
   P.scale = scale;
-  P.first = L.colour_start[colour];
-  P.count = L.colour_start[colour + 1] - P.first;
+  if (colour < 0) {  // one launch over all patches, results to the reduction buffer
+    P.first = 0;
+    P.count = L.nv;
+    P.ybuf = C.d_Y;
+    P.qoff = L.d_qoff;
+    P.Q = L.Q;
+  } else {
+    P.first = L.colour_start[colour];
+    P.count = L.colour_start[colour + 1] - P.first;
+    P.ybuf = nullptr;
+    P.qoff = nullptr;
+    P.Q = 0;
+  }
   P.nmax = L.kron_nmax;
   if (P.count <= 0) return cudaSuccess;
   const int prec = C.opt.patch_precision;
@@ -468,6 +493,32 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   const float* f = (const float*)L.d_fac;
   return transpose ? launch_kron_t<float, true>(P, f, R, grid, smem, C.stream)
                    : launch_kron_t<float, false>(P, f, R, grid, smem, C.stream);
+}
+
+}  // namespace irkmg
+
+namespace irkmg {
+
+// Deterministic gather of the one-launch patch results: for every stage t and
+// spatial DoF d, out[t·m + d] += scale · Σ_e ybuf[t·Q + e] over the entries e
+// of d (one per patch containing d, in the colour-ordered patch order).
+__global__ void k_vanka_reduce(int s, int64_t m, int64_t Q, const int32_t* __restrict__ cptr,
+                               const int32_t* __restrict__ cidx, const double* __restrict__ y,
+                               double scale, double* __restrict__ out) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= s * m) return;
+  const int64_t t = id / m, d = id - t * m;
+  const double* yt = y + t * Q;
+  double a = 0.0;
+  for (int32_t e = cptr[d]; e < cptr[d + 1]; ++e) a += yt[cidx[e]];
+  out[id] += scale * a;
+}
+
+cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale) {
+  const int64_t thr = (int64_t)C.s * L.m;
+  k_vanka_reduce<<<(unsigned)((thr + 255) / 256), 256, 0, C.stream>>>(C.s, L.m, L.Q, L.d_cptr,
+                                                                     L.d_cidx, C.d_Y, scale, out);
+  return cudaGetLastError();
 }
 
 }  // namespace irkmg

@@ -56,7 +56,8 @@ class LevelInfo(ct.Structure):
     _fields_ = [(k, ct.c_int64) for k in ("nv", "ne", "nc", "np2", "nf", "m", "N", "npatch",
                                           "ncolours", "max_patch_dofs", "factor_bytes",
                                           "apply_kernel")] + [("apply_ms", ct.c_double * 2),
-                                                              ("dim", ct.c_int64)]
+                                                              ("dim", ct.c_int64),
+                                                              ("single_launch", ct.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "apply_ms"}
@@ -67,7 +68,9 @@ class LevelInfo(ct.Structure):
 class Trace(ct.Structure):
     _fields_ = [("launches", ct.c_int64), ("vanka_launches", ct.c_int64), ("vanka_ms", ct.c_double),
                 ("vanka_bytes", ct.c_double), ("op_launches", ct.c_int64), ("op_ms", ct.c_double),
-                ("op_bytes", ct.c_double), ("vanka_flops", ct.c_double), ("op_flops", ct.c_double)]
+                ("op_bytes", ct.c_double), ("vanka_flops", ct.c_double), ("op_flops", ct.c_double),
+                ("reduce_launches", ct.c_int64), ("reduce_ms", ct.c_double),
+                ("reduce_bytes", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -37,12 +37,15 @@ def _context(irkmg, fam, s, dt, n0, nl, form, precision=64, nu=1.0, wind=None, v
     return irkmg.irkmg_setup(*synth.square_mesh(n0), A, b, c, dt, nu, o, wind=wind)
 
 
-@pytest.mark.parametrize("variant", [1, 2], ids=["tma_staged", "warp_per_patch"])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4],
+                         ids=["tma_staged", "warp_per_patch", "tma_staged_one_launch",
+                              "warp_one_launch"])
 @pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
 @pytest.mark.parametrize("fam,s,dt", CASES)
 def test_decoupled_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
-    """Both decoupled apply kernels (forced on every level), both layouts:
-    one correction per level with J and Jᵀ patches, and one V-cycle."""
+    """Both decoupled apply kernels (forced on every level), both layouts, one
+    launch per colour or one launch plus the per-DoF reduction: one correction
+    per level with J and Jᵀ patches, and one V-cycle."""
     irkmg = need_gpu()
     n0, nl = 2, 4
     H = _oracle(fam, s, dt, n0, nl)
@@ -50,7 +53,8 @@ def test_decoupled_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
     try:
         for l in range(1, nl):
             info = ctx.levels[l]
-            assert info["apply_kernel"] == (5 if variant == 1 else 4)
+            assert info["apply_kernel"] == (5 if variant in (1, 3) else 4)
+            assert info["single_launch"] == (1 if variant >= 3 else 0)
             n = 2 * 19 + 1   # largest patch of a structured triangle mesh: 19 nodes
             pairs = s // 2
             nm = s if form == 2 else s + pairs
