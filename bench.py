@@ -51,16 +51,22 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM traffic of the finest-level Vanka kernel from an ncu capture, as the
 # ratio (dram__bytes_read + dram__bytes_write) / algorithmic bytes of the
-# captured launch, keyed by kernel and by the hash of the kernel source it was
-# taken with; reported as ratio x algorithmic bytes per launch, null once the
-# source has changed.  Captures: profiles/vanka_apply_128x128.md.
+# captured launch, keyed by kernel and by the hash of the kernel's source file
+# at capture time; reported as ratio x algorithmic bytes per launch, null once
+# the source has changed.  Captures: profiles/vanka_apply_128x128.md,
+# profiles/vanka_apply_kron_fp64_256x256.md.
 NCU_TRAFFIC = {
     ("k_vanka_apply", "c01e3c9fe148"): 0.97,
+    ("k_vanka_apply_kron", "8aaaaec3a97e"): 1.02,
 }
+KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
+               "k_vanka_apply_lu": "k_patch_big.cu", "k_vanka_apply_kron": "k_patch_kron.cu",
+               "k_vanka_apply_kron_staged": "k_patch_kron.cu"}
 
 
-def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2202_07381_gb300", "csrc", "k_patch.cu"), "rb") as fh:
+def kernel_source_hash(kernel="k_vanka_apply_kron"):
+    path = os.path.join(ROOT, "paper_2202_07381_gb300", "csrc", KERNEL_FILE[kernel])
+    with open(path, "rb") as fh:
         return hashlib.sha1(fh.read()).hexdigest()[:12]
 
 
@@ -492,10 +498,10 @@ def run_ours(args, wl, rank, world, local_rank):
         op_gbs = trace["op_bytes"] / (trace["op_ms"] * 1e-3) / 1e9 if trace["op_ms"] else None
         op_tf = trace["op_flops"] / (trace["op_ms"] * 1e-3) / 1e12 if trace["op_ms"] else None
         nvl = max(trace["vanka_launches"], 1)
-        h = kernel_source_hash()
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
                  3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
                  5: "k_vanka_apply_kron_staged"}[ctx.finest["apply_kernel"]]
+        h = kernel_source_hash(kname)
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
         value = ms * 1e-3 / (args.steps * world)
