@@ -123,6 +123,10 @@ typedef struct {
                               system (2n) has at most 160 DoFs, the dense form
                               elsewhere.  IRKMG_ENOTIMPL if A has a repeated
                               eigenvalue.                                          */
+  int patch_lu_tc;         /* FP32 patches above 160 DoFs (3D): 1 = trailing updates
+                              of the blocked patch LU on the tensor cores
+                              (tcgen05.mma kind::tf32, operands split hi + lo for
+                              FP32-level products), 0 = on the CUDA cores          */
 } irkmg_options;
 
 typedef struct {

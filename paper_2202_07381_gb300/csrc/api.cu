@@ -795,6 +795,7 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
     return fail(IRKMG_EINVAL, "apply_variant is 0 .. 4");
   if (o->patch_form < 0 || o->patch_form > 3)
     return fail(IRKMG_EINVAL, "patch_form is 0, 1, 2 or 3");
+  if (o->patch_lu_tc != 0 && o->patch_lu_tc != 1) return fail(IRKMG_EINVAL, "patch_lu_tc is 0 or 1");
   if (o->patch_form != 0) {
     KronSplit K;
     if (kron_split(tab->s, tab->A, &K) != IRKMG_OK)
@@ -1244,6 +1245,7 @@ void irkmg_default_options(irkmg_options* o) {
   o->timeout_spins = 0;
   o->apply_variant = 0;
   o->patch_form = 0;
+  o->patch_lu_tc = 1;
 }
 
 int irkmg_radau_iia(int s, double* A, double* b, double* c) {

@@ -17,9 +17,19 @@
 //     One launch per colour.
 // Block layout of a patch: [n_p^2 values (LU factors, then the inverse)]
 // [n_p int32 DoF indices][n_p int32 pivots], each part padded to 16 bytes.
+//
+// FP32 patches take the trailing update A22 -= L21 U12 on the 5th-generation
+// tensor cores (tcgen05.mma kind::tf32, one elected thread, operands staged in
+// shared memory, a 128x64 FP32 accumulator in tensor memory, read back with
+// tcgen05.ld).  TF32 keeps 10 mantissa bits, so each operand is split as
+// x = hi + lo (hi = x with its 13 low mantissa bits cleared, lo = x - hi
+// exactly) and D = Lhi Uhi + Lhi Ulo + Llo Uhi: three MMAs per K step give
+// FP32-level products ("3xTF32").
 #include <cfloat>
+#include <type_traits>
 
 #include "irkmg_internal.h"
+#include "tma.cuh"
 
 namespace irkmg {
 
@@ -29,6 +39,8 @@ constexpr int kUChunk = 128;
 
 struct BigParams {
   int s, dim;
+  int tc;      // FP32 LU: 1 = tcgen05 trailing updates, 0 = CUDA cores
+  int max_np;  // largest patch of the level (sizes the shared-memory panel)
   double A[9];
   double dt;
   int64_t nf, m;
@@ -58,6 +70,78 @@ __device__ __forceinline__ int big_csr_find(const int32_t* __restrict__ col, int
   return b;
 }
 
+// ---- tcgen05 helpers (trailing update of the FP32 patch LU) ----------------
+// Tiles of 128 x 64 (two CTAs of the LU fit an SM with their operands).
+constexpr int kTcM = 128, kTcN = 64, kTcK = 32;
+constexpr int kTcOperandBytes = (kTcM + kTcN) * kTcK * 4 * 2;  // A and B tiles, hi and lo
+constexpr uint32_t kTcCols = kTcN;                               // TMEM columns of the accumulator
+
+// Element offset of (row m, k) in the K-major, unswizzled canonical layout:
+// 8-row x 16-byte core matrices, rows 16 B apart; core matrices adjacent in K
+// 128 B apart (leading-dimension offset), 8-row groups 1024 B apart (stride
+// offset), for a rows x 32 FP32 tile.
+__device__ __forceinline__ int tc_off(int m, int k) {
+  return (m >> 3) * 256 + (k >> 2) * 32 + (m & 7) * 4 + (k & 3);
+}
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset 128, stride-dimension byte offset 1024 (all >> 4), descriptor
+// version 1 (bits 46-47), no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+// 10-12 = 2), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void tc_alloc(uint32_t* dst) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(kTcCols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 16 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
 template <typename T>
 __device__ __forceinline__ int64_t big_x_bytes(int np) {
   return ((int64_t)np * np * (int64_t)sizeof(T) + 15) & ~(int64_t)15;
@@ -72,6 +156,9 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
   __shared__ int s_piv[kPanel];
   __shared__ int32_t nodes[96];
   __shared__ double s_thr;
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ uint32_t s_taddr;
+  __shared__ int s_abort;
   const int64_t pi = blockIdx.x;
   if (pi >= npatch) return;
   const int tid = threadIdx.x;
@@ -84,6 +171,14 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
                                             big_i_bytes(np));
   T* Pn = reinterpret_cast<T*>(dyn);               // panel, [kPanel][np - k0]
   T* Ub = Pn + (size_t)kPanel * np;                // U12 chunk, [kPanel][kUChunk]
+  // tcgen05 operands (FP32 only): L21 hi/lo and U12ᵀ hi/lo tiles, 1024-aligned
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  const bool tc = kF32 && P.tc != 0;
+  const size_t tc_base = (((size_t)kPanel * P.max_np * sizeof(T)) + 1023) & ~(size_t)1023;
+  float* tA_hi = reinterpret_cast<float*>(dyn + tc_base);
+  float* tA_lo = tA_hi + kTcM * kTcK;
+  float* tB_hi = tA_lo + kTcM * kTcK;
+  float* tB_lo = tB_hi + kTcN * kTcK;
   for (int i = tid; i < L; i += kBigThreads) nodes[i] = P.patch_nodes[nb + i];
   for (int64_t i = tid; i < (int64_t)np * np; i += kBigThreads) A[i] = (T)0;
   __syncthreads();
@@ -132,10 +227,23 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
     __syncthreads();
   }
   if (tid == 0) s_thr = 1e3 * DBL_EPSILON * red_v[0];
+  if (tid == 0) s_abort = 0;
+  if (tc) {
+    if (tid < 32) tc_alloc(&s_taddr);  // warp 0: 128 TMEM columns
+    if (tid == 0) {
+      mbar_init(&s_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+  }
   __syncthreads();
+  if (tc) tc_fence_after();
+  const uint32_t taddr = tc ? s_taddr : 0u;
+  uint32_t tc_phase = 0;
+  const int warp = tid >> 5, lane = tid & 31;
 
   // ---- blocked LU with partial pivoting ----
-  for (int k0 = 0; k0 < np; k0 += kPanel) {
+  for (int k0 = 0; k0 < np && !s_abort; k0 += kPanel) {
     const int kb = min(kPanel, np - k0), prow = np - k0;
     for (int idx = tid; idx < prow * kb; idx += kBigThreads) {
       const int l = idx / prow, r = idx - l * prow;
@@ -226,8 +334,78 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
         if (l < kb) col[l] = x[l];
     }
     __syncthreads();
-    // A22 -= L21 U12, U12 staged in chunks of kUChunk columns
+    // A22 -= L21 U12
     const int mrow = prow - kb;
+    if (tc) {
+      // 128 x 64 tiles on the tensor cores: D = L21 U12 in TMEM (3xTF32),
+      // then every thread subtracts its row of D from A22 in global memory
+      for (int r0 = 0; r0 < mrow && !s_abort; r0 += kTcM)
+        for (int c0 = 0; c0 < ncol && !s_abort; c0 += kTcN) {
+          for (int idx = tid; idx < kTcM * kTcK; idx += kBigThreads) {
+            const int k = idx / kTcM, m = idx - k * kTcM;
+            const float x = (k < kb && r0 + m < mrow) ? (float)Pn[k * prow + kb + r0 + m] : 0.f;
+            const float h = tf32_hi(x);
+            tA_hi[tc_off(m, k)] = h;
+            tA_lo[tc_off(m, k)] = x - h;
+          }
+          for (int idx = tid; idx < kTcN * kTcK; idx += kBigThreads) {
+            const int n = idx / kTcK, k = idx - n * kTcK;
+            const float x = (k < kb && c0 + n < ncol)
+                                ? (float)A[(int64_t)(k0 + kb + c0 + n) * np + k0 + k]
+                                : 0.f;
+            const float h = tf32_hi(x);
+            tB_hi[tc_off(n, k)] = h;
+            tB_lo[tc_off(n, k)] = x - h;
+          }
+          fence_proxy_async();  // generic-proxy writes visible to the tensor core
+          __syncthreads();
+          if (tid == 0) {
+            tc_fence_after();
+            const uint32_t ah = smem_u32(tA_hi), al = smem_u32(tA_lo);
+            const uint32_t bh = smem_u32(tB_hi), bl = smem_u32(tB_lo);
+#pragma unroll
+            for (int ks = 0; ks < kTcK / 8; ++ks) {  // K = 8 per MMA: two core matrices
+              const uint32_t o = ks * 256;
+              tc_mma(taddr, tc_desc(ah + o), tc_desc(bh + o), ks > 0 ? 1u : 0u);
+              tc_mma(taddr, tc_desc(ah + o), tc_desc(bl + o), 1u);
+              tc_mma(taddr, tc_desc(al + o), tc_desc(bh + o), 1u);
+            }
+            tc_commit(&s_mbar);
+          }
+          if (!mbar_wait_bounded(&s_mbar, tc_phase, (int64_t)1 << 26)) {
+            s_abort = 1;
+            atomicCAS(&P.err[0], 0, IRKMG_ETIMEOUT);
+          }
+          tc_phase ^= 1u;
+          __syncthreads();
+          if (s_abort) {
+            // the MMAs may still be in flight: one more bounded wait before
+            // the tensor memory is released below
+            mbar_wait_bounded(&s_mbar, tc_phase ^ 1u, (int64_t)1 << 26);
+            break;
+          }
+          tc_fence_after();
+          // warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and half
+          // w / 4 of the tile's columns
+          const int q = warp & 3, row = q * 32 + lane;
+          const bool row_ok = r0 + row < mrow;
+#pragma unroll 1
+          for (int cc = 0; cc < kTcN / 32; ++cc) {
+            const int col0 = (warp >> 2) * (kTcN / 2) + cc * 16;
+            float v[16];
+            tc_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int c = c0 + col0 + j;
+              if (row_ok && c < ncol) A[(int64_t)(k0 + kb + c) * np + k0 + kb + r0 + row] -= (T)v[j];
+            }
+          }
+          tc_fence_before();
+          __syncthreads();  // TMEM and the operand tiles are reused by the next tile
+        }
+      __syncthreads();
+      continue;
+    }
     for (int cc0 = 0; cc0 < ncol; cc0 += kUChunk) {
       const int cw = min(kUChunk, ncol - cc0);
       for (int idx = tid; idx < kb * cw; idx += kBigThreads) {
@@ -243,6 +421,14 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
         *a = acc;
       }
       __syncthreads();
+    }
+  }
+  if (tc) {
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 32) {
+      tc_fence_after();
+      tc_dealloc(taddr);
     }
   }
 }
@@ -417,6 +603,8 @@ static BigParams big_params(Ctx& C, Level& L) {
   BigParams P;
   P.s = C.s;
   P.dim = L.dim;
+  P.tc = C.opt.patch_lu_tc;
+  P.max_np = L.max_np;
   for (int i = 0; i < 9; ++i) P.A[i] = 0.0;
   for (int i = 0; i < C.s; ++i)
     for (int j = 0; j < C.s; ++j) P.A[i * 3 + j] = C.A[i * C.s + j];
@@ -445,16 +633,21 @@ static BigParams big_params(Ctx& C, Level& L) {
   return P;
 }
 
+// Shared memory of the LU: the panel (kPanel x max_np) and either the U12
+// chunk (CUDA-core update) or the four tcgen05 operand tiles, 1024-aligned.
 cudaError_t launch_patch_lu_big(Ctx& C, Level& L) {
   BigParams P = big_params(C, L);
   if (C.opt.patch_precision == 64) {
-    const size_t smem = (size_t)kPanel * (kMaxBigNp + kUChunk) * sizeof(double);
+    const size_t smem = (size_t)kPanel * (L.max_np + kUChunk) * sizeof(double);
     cudaFuncSetAttribute(k_patch_lu_big<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_patch_lu_big<double><<<(unsigned)L.nv, kBigThreads, smem, C.stream>>>(P, L.nv,
                                                                             (double*)L.d_fac);
   } else {
-    const size_t smem = (size_t)kPanel * (kMaxBigNp + kUChunk) * sizeof(float);
+    size_t smem = (size_t)kPanel * (L.max_np + kUChunk) * sizeof(float);
+    if (P.tc)
+      smem = (((size_t)kPanel * L.max_np * sizeof(float) + 1023) & ~(size_t)1023) +
+             (size_t)kTcOperandBytes;
     cudaFuncSetAttribute(k_patch_lu_big<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_patch_lu_big<float><<<(unsigned)L.nv, kBigThreads, smem, C.stream>>>(P, L.nv,

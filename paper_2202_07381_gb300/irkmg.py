@@ -40,7 +40,7 @@ class Options(ct.Structure):
                 ("restart", ct.c_int), ("maxit", ct.c_int), ("patch_precision", ct.c_int),
                 ("wind", ct.POINTER(ct.c_double)), ("cuda_stream", ct.c_void_p),
                 ("timeout_spins", ct.c_int64), ("apply_variant", ct.c_int),
-                ("patch_form", ct.c_int)]
+                ("patch_form", ct.c_int), ("patch_lu_tc", ct.c_int)]
 
 
 class Stats(ct.Structure):
