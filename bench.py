@@ -171,6 +171,31 @@ def oracle_sample(wl, n_sample):
     return dt, scaled, desc
 
 
+def max_over_ranks(x, device):
+    """Largest x over the ranks of the default process group (the slowest
+    replica's time decides the job's time)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms_max, steps, world):
+    """Whole-job seconds per solve: world replicas each ran `steps` solves in
+    at most ms_max milliseconds."""
+    return ms_max * 1e-3 / (steps * world)
+
+
+def base_config(wl):
+    """Workload description shared by both arms (sizes from the mesh
+    formulas: (n+1)^2 vertices, (2n-1)^2 free P2 nodes in 2D)."""
+    n, d = wl["n"], wl.get("dim", 2)
+    nv, nf = (n + 1) ** d, (2 * n - 1) ** d
+    return {"workload": wl["name"], "N": wl["s"] * (d * nf + nv), "patches_finest": nv,
+            "smoother": "Chebyshev[%g,%g] V(2,2)" % wl.get("cheb", (2.0, 8.0)),
+            "fgmres_restart": 30, "rtol": 1e-10}
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return
@@ -187,7 +212,7 @@ def run_reference(args, wl, rank):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl["name"]},
+            "data": "synthetic", "config": base_config(wl),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -444,9 +469,7 @@ def run_ours(args, wl, rank, world, local_rank):
     trace = irkmg.irkmg_trace_read(ctx)
     irkmg.irkmg_trace_enable(ctx, False)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
     iters = [s_["iters"] for s_ in stats]
     resid = [s_["rfinal"] / max(s_["r0"], 1e-300) for s_ in stats]
     assert all(s_["status"] == 0 for s_ in stats), stats
@@ -477,10 +500,9 @@ def run_ours(args, wl, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     barrier()
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dev)
 
+    assert base_config(wl)["N"] == N and base_config(wl)["patches_finest"] == ctx.finest["nv"]
     forms = {}
     if rank == 0 and not args.small and prec == 64 and not args.no_forms:
         for name, fp, pf in (("dense_fp64", 64, 0), ("dense_fp32", 32, 0), ("kron_fp64", 64, 1),
@@ -504,7 +526,7 @@ def run_ours(args, wl, rank, world, local_rank):
         h = kernel_source_hash(kname)
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
-        value = ms * 1e-3 / (args.steps * world)
+        value = replica_value(ms, args.steps, world)
         van_tf = trace["vanka_flops"] / (trace["vanka_ms"] * 1e-3) / 1e12 if trace["vanka_ms"] else None
         common = {"kernel": kname + " (finest level)", "traffic": traffic,
                   "launches": trace["vanka_launches"], "bytes_per_launch": trace["vanka_bytes"] / nvl,
@@ -528,10 +550,8 @@ def run_ours(args, wl, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == 64 else "f64+f32patch", "data": "synthetic",
             "dim": wl.get("dim", 2),
-            "config": {"workload": wl["name"], "N": N, "patches_finest": ctx.finest["nv"],
+            "config": {**base_config(wl),
                        "patch_precision": prec, "patch_form": args.patch_form,
-                       "smoother": "Chebyshev[%g,%g] V(2,2)" % wl.get("cheb", (2.0, 8.0)),
-                       "fgmres_restart": 30, "rtol": 1e-10,
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
                              % (ctx.finest["factor_bytes"] / 1e9),
@@ -547,7 +567,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "gpu_launches": trace["launches"],
             "forms": forms,
             "clocks": clk.summary(),
-            "e2e": {"value": e2e_s / (args.steps * world), "unit": UNIT,
+            "e2e": {"value": replica_value(e2e_s * 1e3, args.steps, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         }
     ctx.close()
