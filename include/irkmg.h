@@ -119,10 +119,11 @@ typedef struct {
                               matrices (2: complex form X, Y) or s + pairs of them
                               (3: X + Y, X, Y, three real mat-vecs per pair);
                               1 picks 3 for FP64 patches and 2 for FP32.  Exact in
-                              exact arithmetic; used on every level whose pair
-                              system (2n) has at most 160 DoFs, the dense form
-                              elsewhere.  IRKMG_ENOTIMPL if A has a repeated
-                              eigenvalue.                                          */
+                              exact arithmetic.  Blocks up to 160 DoFs are
+                              inverted in shared memory, larger ones (3D, up to
+                              512) by the blocked LU; with decoupling, 3D works
+                              for s = 3 too (dense: 588 DoFs, above the limit).
+                              IRKMG_ENOTIMPL if A has a repeated eigenvalue.       */
   int patch_lu_tc;         /* FP32 patches above 160 DoFs (3D): 1 = trailing updates
                               of the blocked patch LU on the tensor cores
                               (tcgen05.mma kind::tf32, operands split hi + lo for
@@ -147,7 +148,9 @@ typedef struct {
   int64_t apply_kernel;    /* Vanka apply kernel in use: 1 TMA-staged, 2 warp-per-patch,
                               3 CTA-per-patch mat-vec (patches above 160 DoFs, whose
                               inverses come from a blocked LU; 3D); decoupled form
-                              (patch_form != 0): 4 warp-per-patch, 5 TMA-staged    */
+                              (patch_form != 0): 4 warp-per-patch, 5 TMA-staged,
+                              6 CTA-per-patch (blocks above 160 DoFs, factored by
+                              the blocked LU; 3D)                                   */
   double apply_ms[2];      /* autotuner: one sweep with the staged / warp-per-patch
                               kernel of the level's form (0 if untimed)            */
   int64_t dim;             /* 2 or 3                                                */

@@ -299,23 +299,28 @@ int build_patches(Ctx& C, Level& L) {
     L.max_np = std::max<int>(L.max_np, (int)np);
     npv[i] = (int32_t)np;
   }
-  if (L.max_np > kMaxBigNp)
-    return fail(IRKMG_ENOTIMPL, "patches above " + std::to_string(kMaxBigNp) + " DoFs");
   L.big = L.max_np > kMaxSmallNp;
-  // Decoupled patch factors where the largest block (2n for a complex pair)
-  // fits the shared-memory inversion and the apply's lane slots.
+  // Decoupled patch factors: inverted in shared memory where the largest
+  // block (2n for a complex pair) fits, else by the blocked LU up to
+  // kMaxBigNp; the dense form otherwise.
   L.kron = false;
+  L.kron_big = false;
   if (C.kron) {
     int q = 1;
     for (int b = 0; b < C.kplan.nblk; ++b) q = std::max(q, C.kplan.blk_size[b]);
     const int nmax = L.max_np / C.s;
-    if (q * nmax <= kMaxSmallNp && C.kplan.nt * nmax <= 32 * kron_max_slots()) {
+    const bool small = q * nmax <= kMaxSmallNp && C.kplan.nt * nmax <= 32 * kron_max_slots();
+    const bool big = !small && q * nmax <= kMaxBigNp && nmax <= kron_big_max_n();
+    if (small || big) {
       L.kron = true;
-      L.big = false;
+      L.kron_big = big;
+      L.big = big;
       L.kron_nmax = nmax;
       for (int64_t i = 0; i < L.nv; ++i) npv[i] /= C.s;
     }
   }
+  if (!L.kron && L.max_np > kMaxBigNp)
+    return fail(IRKMG_ENOTIMPL, "patches above " + std::to_string(kMaxBigNp) + " DoFs");
   for (int64_t i = 0; i < L.nv; ++i) {
     const int64_t np = npv[i];
     if (L.kron) {
@@ -381,6 +386,24 @@ int build_patches(Ctx& C, Level& L) {
 }
 
 int factor_level(Ctx& C, Level& L) {
+  if (L.kron && L.kron_big) {
+    int q = 1;
+    for (int b = 0; b < C.kplan.nblk; ++b) q = std::max(q, C.kplan.blk_size[b]);
+    const int ctas = (int)std::min<int64_t>(L.nv, 2 * 152);
+    const int64_t ws = kron_big_workspace(q * L.kron_nmax, L.kron_nmax, C.opt.patch_precision);
+    const size_t esz = C.opt.patch_precision == 64 ? 8 : 4;
+    void* work = nullptr;
+    cudaError_t e = cudaMallocAsync(&work, esz * ws * ctas, C.stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(IRKMG_ENOMEM, "workspace for the decoupled large-patch factors");
+    }
+    e = launch_patch_factor_kron_big(C, L, work, ws, ctas);
+    cudaError_t e2 = cudaFreeAsync(work, C.stream);
+    CK(e);
+    CK(e2);
+    return IRKMG_OK;
+  }
   if (L.kron) {
     CK(launch_patch_invert_kron(C, L));
     return IRKMG_OK;
@@ -453,6 +476,38 @@ int tune_apply(Ctx& C) {
       L.apply_kernel = 3;
       continue;
     }
+    if (L.kron_big) {
+      // one kernel (CTA per patch); per-colour launches or one launch + sum
+      L.apply_kernel = 6;
+      L.single = false;
+      const int av = C.opt.apply_variant;
+      if (av != 0) {
+        L.single = av >= 3;
+        continue;
+      }
+      cudaError_t ez = cudaMemsetAsync(L.t, 0, sizeof(double) * L.N, C.stream);
+      if (ez != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(ez)); break; }
+      float t2[2] = {0.f, 0.f};
+      for (int single = 0; single < 2 && rc == IRKMG_OK; ++single) {
+        L.single = single != 0;
+        float best = 1e30f;
+        for (int rep = 0; rep < 3 && rc == IRKMG_OK; ++rep) {
+          cudaEventRecord(a, C.stream);
+          rc = vanka_all(C, L, L.t, L.d, 1.0, 0);
+          cudaEventRecord(b, C.stream);
+          cudaError_t e2 = cudaEventSynchronize(b);
+          if (e2 != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e2)); break; }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, b);
+          if (rep > 0 && ms < best) best = ms;
+        }
+        t2[single] = best;
+      }
+      L.single = t2[1] < t2[0];
+      L.apply_ms[1] = 0.f;
+      L.apply_ms[2] = std::min(t2[0], t2[1]);
+      continue;
+    }
     // candidates: staged (TMA) and warp-per-patch kernels, dense or decoupled;
     // on decoupled levels each staged launch shape, and both relaxation
     // modes (one launch per colour, or one launch and the per-DoF reduction)
@@ -520,7 +575,7 @@ int tune_apply(Ctx& C) {
 
 // --- smoothers and V-cycle -------------------------------------------------
 int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr) {
-  if (L.big && !L.kron && tr)
+  if (L.big && tr)
     return fail(IRKMG_ENOTIMPL, "transposed patch solves of LU-factored (3D) patches");
   const bool timed = C.trace_on && &L == &C.L.back();
   if (L.kron && L.single) {

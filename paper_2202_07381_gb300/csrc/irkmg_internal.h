@@ -146,9 +146,11 @@ struct Level {
   int max_np = 0;
   bool big = false;                    // patches above kMaxSmallNp: blocked LU + LU apply
   bool kron = false;                   // Kronecker-decoupled patch factors (KronPlan)
+  bool kron_big = false;               // ... factored by the blocked LU (blocks above 160 DoFs)
   int kron_nmax = 0;                   // largest spatial patch size n on a decoupled level
   int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 big-patch mat-vec,
-                                       // 4 decoupled warp-per-patch, 5 decoupled staged
+                                       // 4 decoupled warp-per-patch, 5 decoupled staged,
+                                       // 6 decoupled CTA-per-patch (large patches)
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   int kron_shape = 0;                  // launch shape of the staged decoupled apply (0, 1)
   // one-launch relaxation of a decoupled level: patch results to Ctx::d_Y at
@@ -266,6 +268,9 @@ cudaError_t launch_patch_lu_big(Ctx& C, Level& L);
 cudaError_t launch_patch_inv_from_lu(Ctx& C, Level& L, void* work, int64_t ws, int ctas);
 cudaError_t launch_vanka_big(Ctx& C, Level& L, int colour, const double* r, double* out,
                              double scale);
+cudaError_t launch_patch_factor_kron_big(Ctx& C, Level& L, void* work, int64_t ws, int ctas);
+int64_t kron_big_workspace(int pmax, int nmax, int prec);
+int kron_big_max_n();
 
 constexpr int kMultidotBlocks = 304;
 constexpr int kMaxSmallNp = 160;  // patches up to this size: explicit inverse in shared memory

@@ -148,38 +148,28 @@ __device__ __forceinline__ int64_t big_x_bytes(int np) {
 }
 __device__ __forceinline__ int64_t big_i_bytes(int np) { return ((int64_t)np * 4 + 15) & ~(int64_t)15; }
 
+// Static shared scratch of one big-patch factorisation.
+struct BigLuShared {
+  double red_v[kBigThreads];
+  int red_i[kBigThreads];
+  int piv[kPanel];
+  int32_t nodes[96];
+  double thr;
+  uint64_t mbar;
+  uint32_t taddr;
+  int abort;
+};
+
+// Zeroes the column-major np x np matrix A and gathers I_s ⊗ M̃ + dt Am ⊗ K̃ of
+// patch v into it (s stages, Am with row stride 3, np = s (D L + 1)); S.nodes
+// holds the patch's L free nodes.  Sets S.thr = 1e3 eps max|A| (singular-pivot
+// threshold).  All threads of the block.
 template <typename T>
-__global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64_t npatch, T* fac) {
-  extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ double red_v[kBigThreads];
-  __shared__ int red_i[kBigThreads];
-  __shared__ int s_piv[kPanel];
-  __shared__ int32_t nodes[96];
-  __shared__ double s_thr;
-  __shared__ __align__(8) uint64_t s_mbar;
-  __shared__ uint32_t s_taddr;
-  __shared__ int s_abort;
-  const int64_t pi = blockIdx.x;
-  if (pi >= npatch) return;
+__device__ void big_gather(const BigParams& P, int s, const double* Am, int32_t v, int L, T* A,
+                           int np, BigLuShared& S) {
   const int tid = threadIdx.x;
-  const int32_t v = P.order[pi];
-  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
   const int D = P.dim;
-  const int q = D * L + 1, np = P.s * q;
-  T* A = fac + P.fac_off[pi];  // column-major: A[c * np + r]
-  int32_t* piv = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(A) + big_x_bytes<T>(np) +
-                                            big_i_bytes(np));
-  T* Pn = reinterpret_cast<T*>(dyn);               // panel, [kPanel][np - k0]
-  T* Ub = Pn + (size_t)kPanel * np;                // U12 chunk, [kPanel][kUChunk]
-  // tcgen05 operands (FP32 only): L21 hi/lo and U12ᵀ hi/lo tiles, 1024-aligned
-  constexpr bool kF32 = std::is_same<T, float>::value;
-  const bool tc = kF32 && P.tc != 0;
-  const size_t tc_base = (((size_t)kPanel * P.max_np * sizeof(T)) + 1023) & ~(size_t)1023;
-  float* tA_hi = reinterpret_cast<float*>(dyn + tc_base);
-  float* tA_lo = tA_hi + kTcM * kTcK;
-  float* tB_hi = tA_lo + kTcM * kTcK;
-  float* tB_lo = tB_hi + kTcN * kTcK;
-  for (int i = tid; i < L; i += kBigThreads) nodes[i] = P.patch_nodes[nb + i];
+  const int q = D * L + 1;
   for (int64_t i = tid; i < (int64_t)np * np; i += kBigThreads) A[i] = (T)0;
   __syncthreads();
   // ---- gather A_v (Section 3.1 Kronecker blocks) ----
@@ -187,7 +177,7 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
   const double* Bc[3] = {P.Bx, P.By, P.Bz};
   for (int idx = tid; idx < L * L; idx += kBigThreads) {
     const int a = idx / L, b = idx % L;
-    const int32_t ra = nodes[a], cb = nodes[b];
+    const int32_t ra = S.nodes[a], cb = S.nodes[b];
     const int32_t p0 = P.vptr[ra], p1 = P.vptr[ra + 1];
     const int32_t pos = big_csr_find(P.vcol, p0, p1, cb);
     double mab = 0.0, kab = 0.0;
@@ -195,24 +185,24 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
       mab = P.M[pos];
       kab = P.K[pos];
     }
-    for (int t = 0; t < P.s; ++t)
-      for (int u = 0; u < P.s; ++u) {
-        const double val = (t == u ? mab : 0.0) + P.dt * P.A[t * 3 + u] * kab;
+    for (int t = 0; t < s; ++t)
+      for (int u = 0; u < s; ++u) {
+        const double val = (t == u ? mab : 0.0) + P.dt * Am[t * 3 + u] * kab;
         mx = fmax(mx, fabs(val));
         for (int d = 0; d < D; ++d)
           A[(int64_t)(u * q + d * L + b) * np + (t * q + d * L + a)] = (T)val;
       }
   }
   for (int a = tid; a < L; a += kBigThreads) {
-    const int32_t ra = nodes[a];
+    const int32_t ra = S.nodes[a];
     const int32_t p0 = P.bptr[ra], p1 = P.bptr[ra + 1];
     const int32_t pos = big_csr_find(P.bcol, p0, p1, v);
     double bv[3] = {0.0, 0.0, 0.0};
     if (pos < p1 && P.bcol[pos] == v)
       for (int d = 0; d < D; ++d) bv[d] = Bc[d][pos];
-    for (int t = 0; t < P.s; ++t)
-      for (int u = 0; u < P.s; ++u) {
-        const double f = P.dt * P.A[t * 3 + u];
+    for (int t = 0; t < s; ++t)
+      for (int u = 0; u < s; ++u) {
+        const double f = P.dt * Am[t * 3 + u];
         for (int d = 0; d < D; ++d) {
           mx = fmax(mx, fabs(f * bv[d]));
           A[(int64_t)(u * q + D * L) * np + (t * q + d * L + a)] = (T)(f * bv[d]);
@@ -220,30 +210,36 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
         }
       }
   }
-  red_v[tid] = mx;
+  S.red_v[tid] = mx;
   __syncthreads();
   for (int o = kBigThreads / 2; o > 0; o >>= 1) {
-    if (tid < o) red_v[tid] = fmax(red_v[tid], red_v[tid + o]);
+    if (tid < o) S.red_v[tid] = fmax(S.red_v[tid], S.red_v[tid + o]);
     __syncthreads();
   }
-  if (tid == 0) s_thr = 1e3 * DBL_EPSILON * red_v[0];
-  if (tid == 0) s_abort = 0;
-  if (tc) {
-    if (tid < 32) tc_alloc(&s_taddr);  // warp 0: 128 TMEM columns
-    if (tid == 0) {
-      mbar_init(&s_mbar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    tc_fence_before();
-  }
+  if (tid == 0) S.thr = 1e3 * DBL_EPSILON * S.red_v[0];
   __syncthreads();
-  if (tc) tc_fence_after();
-  const uint32_t taddr = tc ? s_taddr : 0u;
-  uint32_t tc_phase = 0;
-  const int warp = tid >> 5, lane = tid & 31;
+}
 
+// Blocked right-looking LU with partial pivoting of the column-major np x np
+// matrix A in place (pivots to piv), for patch v (error reports).  dyn holds
+// the panel (kPanel x pmax rows) and, after it (1024-aligned), either the
+// U12 chunk or the tcgen05 operand tiles.  With tc the trailing updates run on
+// the tensor cores with the TMEM accumulator at S.taddr (big_tc_begin).
+template <typename T>
+__device__ void big_lu(const BigParams& P, int32_t v, T* A, int np, int32_t* piv, int pmax,
+                       unsigned char* dyn, BigLuShared& S, bool tc, uint32_t& tc_phase) {
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const uint32_t taddr = S.taddr;
+  T* Pn = reinterpret_cast<T*>(dyn);               // panel, [kPanel][np - k0]
+  T* Ub = Pn + (size_t)kPanel * np;                // U12 chunk, [kPanel][kUChunk]
+  const size_t tc_base = (((size_t)kPanel * pmax * sizeof(T)) + 1023) & ~(size_t)1023;
+  float* tA_hi = reinterpret_cast<float*>(dyn + tc_base);
+  float* tA_lo = tA_hi + kTcM * kTcK;
+  float* tB_hi = tA_lo + kTcM * kTcK;
+  float* tB_lo = tB_hi + kTcN * kTcK;
   // ---- blocked LU with partial pivoting ----
-  for (int k0 = 0; k0 < np && !s_abort; k0 += kPanel) {
+  for (int k0 = 0; k0 < np && !S.abort; k0 += kPanel) {
     const int kb = min(kPanel, np - k0), prow = np - k0;
     for (int idx = tid; idx < prow * kb; idx += kBigThreads) {
       const int l = idx / prow, r = idx - l * prow;
@@ -260,26 +256,26 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
           bi = r;
         }
       }
-      red_v[tid] = best;
-      red_i[tid] = bi;
+      S.red_v[tid] = best;
+      S.red_i[tid] = bi;
       __syncthreads();
       for (int o = kBigThreads / 2; o > 0; o >>= 1) {
         if (tid < o) {
-          const double a = red_v[tid + o];
-          const int ia = red_i[tid + o];
-          if (a > red_v[tid] || (a == red_v[tid] && ia < red_i[tid])) {
-            red_v[tid] = a;
-            red_i[tid] = ia;
+          const double a = S.red_v[tid + o];
+          const int ia = S.red_i[tid + o];
+          if (a > S.red_v[tid] || (a == S.red_v[tid] && ia < S.red_i[tid])) {
+            S.red_v[tid] = a;
+            S.red_i[tid] = ia;
           }
         }
         __syncthreads();
       }
-      const int p = red_i[0];
-      const double pabs = red_v[0];
+      const int p = S.red_i[0];
+      const double pabs = S.red_v[0];
       if (tid == 0) {
-        s_piv[j] = p;
+        S.piv[j] = p;
         piv[k0 + j] = k0 + p;
-        if (!(pabs > s_thr) && atomicCAS(&P.err[0], 0, IRKMG_ESINGULAR) == 0) P.err[1] = v;
+        if (!(pabs > S.thr) && atomicCAS(&P.err[0], 0, IRKMG_ESINGULAR) == 0) P.err[1] = v;
       }
       if (p != j)
         for (int l = tid; l < kb; l += kBigThreads) {
@@ -308,7 +304,7 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
       if (c >= k0 && c < k0 + kb) continue;
       T* col = A + (int64_t)c * np + k0;
       for (int j = 0; j < kb; ++j) {
-        const int p = s_piv[j];
+        const int p = S.piv[j];
         if (p != j) {
           const T x = col[j];
           col[j] = col[p];
@@ -339,8 +335,8 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
     if (tc) {
       // 128 x 64 tiles on the tensor cores: D = L21 U12 in TMEM (3xTF32),
       // then every thread subtracts its row of D from A22 in global memory
-      for (int r0 = 0; r0 < mrow && !s_abort; r0 += kTcM)
-        for (int c0 = 0; c0 < ncol && !s_abort; c0 += kTcN) {
+      for (int r0 = 0; r0 < mrow && !S.abort; r0 += kTcM)
+        for (int c0 = 0; c0 < ncol && !S.abort; c0 += kTcN) {
           for (int idx = tid; idx < kTcM * kTcK; idx += kBigThreads) {
             const int k = idx / kTcM, m = idx - k * kTcM;
             const float x = (k < kb && r0 + m < mrow) ? (float)Pn[k * prow + kb + r0 + m] : 0.f;
@@ -370,18 +366,18 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
               tc_mma(taddr, tc_desc(ah + o), tc_desc(bl + o), 1u);
               tc_mma(taddr, tc_desc(al + o), tc_desc(bh + o), 1u);
             }
-            tc_commit(&s_mbar);
+            tc_commit(&S.mbar);
           }
-          if (!mbar_wait_bounded(&s_mbar, tc_phase, (int64_t)1 << 26)) {
-            s_abort = 1;
+          if (!mbar_wait_bounded(&S.mbar, tc_phase, (int64_t)1 << 26)) {
+            S.abort = 1;
             atomicCAS(&P.err[0], 0, IRKMG_ETIMEOUT);
           }
           tc_phase ^= 1u;
           __syncthreads();
-          if (s_abort) {
+          if (S.abort) {
             // the MMAs may still be in flight: one more bounded wait before
             // the tensor memory is released below
-            mbar_wait_bounded(&s_mbar, tc_phase ^ 1u, (int64_t)1 << 26);
+            mbar_wait_bounded(&S.mbar, tc_phase ^ 1u, (int64_t)1 << 26);
             break;
           }
           tc_fence_after();
@@ -423,23 +419,66 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64
       __syncthreads();
     }
   }
+}
+
+// TMEM for the tcgen05 trailing updates: warp 0 allocates kTcCols columns,
+// thread 0 initialises the completion mbarrier.  All threads of the block.
+__device__ void big_tc_begin(BigLuShared& S, bool tc) {
+  const int tid = threadIdx.x;
+  if (tid == 0) S.abort = 0;
   if (tc) {
-    tc_fence_before();
-    __syncthreads();
-    if (tid < 32) {
-      tc_fence_after();
-      tc_dealloc(taddr);
+    if (tid < 32) tc_alloc(&S.taddr);
+    if (tid == 0) {
+      mbar_init(&S.mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (tc) tc_fence_after();
+}
+
+__device__ void big_tc_end(BigLuShared& S, bool tc) {
+  if (!tc) return;
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tc_dealloc(S.taddr);
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) k_patch_lu_big(BigParams P, int64_t npatch, T* fac) {
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  __shared__ BigLuShared S;
+  const int64_t pi = blockIdx.x;
+  if (pi >= npatch) return;
+  const int tid = threadIdx.x;
+  const int32_t v = P.order[pi];
+  const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+  const int np = P.s * (P.dim * L + 1);
+  T* A = fac + P.fac_off[pi];  // column-major: A[c * np + r]
+  int32_t* piv = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(A) + big_x_bytes<T>(np) +
+                                            big_i_bytes(np));
+  const bool tc = std::is_same<T, float>::value && P.tc != 0;
+  for (int i = tid; i < L; i += kBigThreads) S.nodes[i] = P.patch_nodes[nb + i];
+  big_gather<T>(P, P.s, P.A, v, L, A, np, S);
+  big_tc_begin(S, tc);
+  uint32_t tc_phase = 0;
+  big_lu<T>(P, v, A, np, piv, P.max_np, dyn, S, tc, tc_phase);
+  big_tc_end(S, tc);
+}
+
+
 constexpr int kRowChunk = 128;
 
-// Work on W (column-major np x np): W := L⁻¹ W (lower = true, unit diagonal)
-// or W := U⁻¹ W (lower = false), with L / U the factors stored in A.
+// Work on W (column-major np x ncols): W := L⁻¹ W (lower = true, unit
+// diagonal) or W := U⁻¹ W (lower = false), with L / U the factors stored in A.
+// Wb holds kPanel x ncols, Ms kPanel x kRowChunk, Ls kPanel x kPanel.
 template <typename T>
-__device__ void block_trsm_all_columns(const T* __restrict__ A, T* W, int np, bool lower, T* Ls,
-                                       T* Wb, T* Ms) {
+__device__ void block_trsm(const T* __restrict__ A, T* W, int np, int ncols, bool lower, T* Ls,
+                           T* Wb, T* Ms) {
   const int tid = threadIdx.x;
   const int nblk = (np + kPanel - 1) / kPanel;
   for (int bb = 0; bb < nblk; ++bb) {
@@ -451,7 +490,7 @@ __device__ void block_trsm_all_columns(const T* __restrict__ A, T* W, int np, bo
     }
     __syncthreads();
     // diagonal block: every column solved by one thread
-    for (int c = tid; c < np; c += kBigThreads) {
+    for (int c = tid; c < ncols; c += kBigThreads) {
       T* col = W + (int64_t)c * np + k0;
       T x[kPanel];
 #pragma unroll
@@ -475,7 +514,7 @@ __device__ void block_trsm_all_columns(const T* __restrict__ A, T* W, int np, bo
       for (int l = 0; l < kPanel; ++l)
         if (l < kb) {
           col[l] = x[l];
-          Wb[l * np + c] = x[l];
+          Wb[l * ncols + c] = x[l];
         }
     }
     __syncthreads();
@@ -489,11 +528,11 @@ __device__ void block_trsm_all_columns(const T* __restrict__ A, T* W, int np, bo
         Ms[l * kRowChunk + i] = A[(int64_t)(k0 + l) * np + ch + i];
       }
       __syncthreads();
-      for (int idx = tid; idx < mr * np; idx += kBigThreads) {
+      for (int idx = tid; idx < mr * ncols; idx += kBigThreads) {
         const int i = idx % mr, c = idx / mr;
         T* w = W + (int64_t)c * np + ch + i;
         T acc = *w;
-        for (int l = 0; l < kb; ++l) acc -= Ms[l * kRowChunk + i] * Wb[l * np + c];
+        for (int l = 0; l < kb; ++l) acc -= Ms[l * kRowChunk + i] * Wb[l * ncols + c];
         *w = acc;
       }
       __syncthreads();
@@ -506,7 +545,7 @@ __device__ void block_trsm_all_columns(const T* __restrict__ A, T* W, int np, bo
 template <typename T>
 __global__ void __launch_bounds__(kBigThreads) k_patch_inv_from_lu(BigParams P, int64_t npatch,
                                                                   T* fac, T* work, int64_t ws) {
-  extern __shared__ __align__(16) unsigned char dyn[];
+  extern __shared__ __align__(1024) unsigned char dyn[];
   __shared__ int32_t perm[kMaxBigNp];
   T* W = work + (int64_t)blockIdx.x * ws;
   const int tid = threadIdx.x;
@@ -536,11 +575,98 @@ __global__ void __launch_bounds__(kBigThreads) k_patch_inv_from_lu(BigParams P, 
       W[idx] = perm[r] == c ? (T)1 : (T)0;
     }
     __syncthreads();
-    block_trsm_all_columns<T>(A, W, np, true, Ls, Wb, Ms);
-    block_trsm_all_columns<T>(A, W, np, false, Ls, Wb, Ms);
+    block_trsm<T>(A, W, np, np, true, Ls, Wb, Ms);
+    block_trsm<T>(A, W, np, np, false, Ls, Wb, Ms);
     for (int64_t idx = tid; idx < (int64_t)np * np; idx += kBigThreads) A[idx] = W[idx];
     __syncthreads();
   }
+}
+
+// Decoupled factors of large patches (persistent: CTA b takes patches b,
+// b + gridDim.x, ...).  For each block of the real block diagonalisation of A
+// (one real eigenvalue, or a pair as [[α, β], [−β, α]]) the block system
+// I ⊗ M̃ + dt D_b ⊗ K̃ (q·n DoFs) is gathered into the CTA's workspace, factored
+// by the blocked LU, and the first n columns of its inverse are formed by the
+// blocked triangular solves; they give the block's stored matrices (real: the
+// inverse; pair: X, Y of its first block column, or X + Y, X, Y), written into
+// the patch block like the shared-memory kernel does.  Workspace per CTA:
+// pmax² (factors) + pmax·nmax (inverse columns) + pmax int32 (pivots).
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) k_patch_factor_kron_big(BigParams P, KronPlan K,
+                                                                      int64_t npatch, T* fac, T* work,
+                                                                      int64_t ws, int pmax, int nmax) {
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  __shared__ BigLuShared S;
+  __shared__ int32_t perm[kMaxBigNp];
+  const int tid = threadIdx.x;
+  const bool tc = std::is_same<T, float>::value && P.tc != 0;
+  big_tc_begin(S, tc);
+  uint32_t tc_phase = 0;
+  T* Wa = work + (int64_t)blockIdx.x * ws;
+  T* W = Wa + (int64_t)pmax * pmax;
+  int32_t* piv = reinterpret_cast<int32_t*>(W + (int64_t)pmax * nmax);
+  T* Ls = reinterpret_cast<T*>(dyn);                 // [kPanel][kPanel]
+  T* Wb = Ls + kPanel * kPanel;                      // [kPanel][nmax]
+  T* Ms = Wb + (size_t)kPanel * nmax;                // [kPanel][kRowChunk]
+  for (int64_t pi = blockIdx.x; pi < npatch && !S.abort; pi += gridDim.x) {
+    const int32_t v = P.order[pi];
+    const int32_t nb = P.patch_ptr[v], L = P.patch_ptr[v + 1] - nb;
+    const int n = P.dim * L + 1;
+    const int64_t nn = (int64_t)n * n;
+    for (int i = tid; i < L; i += kBigThreads) S.nodes[i] = P.patch_nodes[nb + i];
+    __syncthreads();
+    T* base = fac + P.fac_off[pi];
+    for (int b = 0; b < K.nblk && !S.abort; ++b) {
+      const int q = K.blk_size[b], nq = q * n;
+      double Am[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) Am[i * 3 + j] = K.blk[b][i * q + j];
+      big_gather<T>(P, q, Am, v, L, Wa, nq, S);
+      big_lu<T>(P, v, Wa, nq, piv, pmax, dyn, S, tc, tc_phase);
+      __syncthreads();
+      if (S.abort) break;
+      // W = first n columns of the row-permuted identity: row r of P is e_perm[r]
+      if (tid == 0) {
+        for (int i = 0; i < nq; ++i) perm[i] = i;
+        for (int j = 0; j < nq; ++j) {
+          const int p = piv[j];
+          if (p != j) {
+            const int32_t x = perm[j];
+            perm[j] = perm[p];
+            perm[p] = x;
+          }
+        }
+      }
+      __syncthreads();
+      for (int64_t idx = tid; idx < (int64_t)nq * n; idx += kBigThreads) {
+        const int c = (int)(idx / nq), r = (int)(idx % nq);
+        W[idx] = perm[r] == c ? (T)1 : (T)0;
+      }
+      __syncthreads();
+      block_trsm<T>(Wa, W, nq, n, true, Ls, Wb, Ms);
+      block_trsm<T>(Wa, W, nq, n, false, Ls, Wb, Ms);
+      T* X = base + (int64_t)K.blk_mat[b] * nn;
+      for (int64_t idx = tid; idx < nn; idx += kBigThreads) {
+        const int c = (int)(idx / n), r = (int)(idx % n);  // column-major (r, c)
+        const T x = W[(int64_t)c * nq + r];
+        if (K.blk_kind[b] == 0) {
+          X[idx] = x;
+        } else {
+          const T y = W[(int64_t)c * nq + n + r];
+          if (K.blk_kind[b] == 1) {
+            X[idx] = x;
+            X[nn + idx] = y;
+          } else {
+            X[idx] = x + y;
+            X[nn + idx] = x;
+            X[2 * nn + idx] = y;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  big_tc_end(S, tc);
 }
 
 // out[S_v] += scale · X r|_{S_v} for large patches: one CTA per patch, thread t
@@ -671,6 +797,42 @@ cudaError_t launch_patch_inv_from_lu(Ctx& C, Level& L, void* work, int64_t ws, i
                          (int)smem);
     k_patch_inv_from_lu<float><<<(unsigned)ctas, kBigThreads, smem, C.stream>>>(
         P, L.nv, (float*)L.d_fac, (float*)work, ws);
+  }
+  return cudaGetLastError();
+}
+
+// Shared memory of the decoupled factorisation: the larger of the LU's needs
+// (panel of pmax rows, then the U12 chunk or the tcgen05 tiles) and the
+// triangular solves' (Ls, Wb, Ms).
+static size_t kron_big_smem(int pmax, int nmax, size_t w, bool tc) {
+  size_t lu = (size_t)kPanel * pmax * w;
+  lu = tc ? ((lu + 1023) & ~(size_t)1023) + (size_t)kTcOperandBytes : lu + (size_t)kPanel * kUChunk * w;
+  const size_t tr = (size_t)(kPanel * kPanel + kPanel * nmax + kPanel * kRowChunk) * w;
+  return lu > tr ? lu : tr;
+}
+
+int64_t kron_big_workspace(int pmax, int nmax, int prec) {
+  const int64_t w = prec == 64 ? 8 : 4;
+  return (int64_t)pmax * pmax + (int64_t)pmax * nmax + ((int64_t)pmax * 4 + w - 1) / w;
+}
+
+cudaError_t launch_patch_factor_kron_big(Ctx& C, Level& L, void* work, int64_t ws, int ctas) {
+  BigParams P = big_params(C, L);
+  int q = 1;
+  for (int b = 0; b < C.kplan.nblk; ++b) q = q > C.kplan.blk_size[b] ? q : C.kplan.blk_size[b];
+  const int nmax = L.kron_nmax, pmax = q * nmax;
+  if (C.opt.patch_precision == 64) {
+    const size_t smem = kron_big_smem(pmax, nmax, 8, false);
+    cudaFuncSetAttribute(k_patch_factor_kron_big<double>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_patch_factor_kron_big<double><<<(unsigned)ctas, kBigThreads, smem, C.stream>>>(
+        P, C.kplan, L.nv, (double*)L.d_fac, (double*)work, ws, pmax, nmax);
+  } else {
+    const size_t smem = kron_big_smem(pmax, nmax, 4, P.tc != 0);
+    cudaFuncSetAttribute(k_patch_factor_kron_big<float>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_patch_factor_kron_big<float><<<(unsigned)ctas, kBigThreads, smem, C.stream>>>(
+        P, C.kplan, L.nv, (float*)L.d_fac, (float*)work, ws, pmax, nmax);
   }
   return cudaGetLastError();
 }

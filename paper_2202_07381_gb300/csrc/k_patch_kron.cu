@@ -138,6 +138,82 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply 
 int kron_max_slots() { return kKronMaxSlots; }
 
 // ---------------------------------------------------------------------------
+// Decoupled apply for large patches (3D: n up to kKronBigMaxN per stage): one
+// CTA per patch.  The gathered residual, the sources and the task results
+// live in shared memory; thread t owns tasks (matrix, row) t, t + 256, ...,
+// streaming each row's entries with coalesced loads (consecutive threads take
+// consecutive rows of one column-major matrix), eight columns loaded before
+// their multiply-adds.
+// ---------------------------------------------------------------------------
+constexpr int kKronBigThreads = 256;
+constexpr int kKronBigMaxN = 256;
+
+int kron_big_max_n() { return kKronBigMaxN; }
+
+template <typename T>
+__global__ void __launch_bounds__(kKronBigThreads)
+    k_vanka_apply_kron_big(KronApply P, const T* __restrict__ fac) {
+  __shared__ double s_r[3 * kKronBigMaxN];
+  __shared__ T s_src[kKronMaxSrc * kKronBigMaxN];
+  __shared__ double s_acc[kKronMaxTasks * kKronBigMaxN];
+  __shared__ int32_t s_g[kKronBigMaxN];
+  const int64_t w = blockIdx.x;
+  if (w >= P.count) return;
+  const int tid = threadIdx.x;
+  const int64_t pi = P.first + w;
+  const int n = P.np[pi];
+  const int64_t nn = (int64_t)n * n;
+  const T* X = fac + P.fac_off[pi];
+  const int32_t* gidx = reinterpret_cast<const int32_t*>(
+      reinterpret_cast<const unsigned char*>(X) +
+      (((int64_t)P.nm * nn * (int64_t)sizeof(T) + 15) & ~(int64_t)15));
+  for (int i = tid; i < n; i += kKronBigThreads) s_g[i] = gidx[i];
+  __syncthreads();
+  for (int idx = tid; idx < P.s * n; idx += kKronBigThreads) {
+    const int t = idx / n, i = idx - t * n;
+    s_r[idx] = P.r[t * P.m + s_g[i]];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < P.ns * n; idx += kKronBigThreads) {
+    const int c = idx / n, i = idx - c * n;
+    double a = 0.0;
+    for (int t = 0; t < P.s; ++t) a += P.G[c * 3 + t] * s_r[t * n + i];
+    s_src[idx] = (T)a;
+  }
+  __syncthreads();
+  constexpr int kBatch = 8;
+  for (int tau = tid; tau < P.nt * n; tau += kKronBigThreads) {
+    const int task = tau / n, i = tau - task * n;
+    const T* M = X + (int64_t)P.task_mat[task] * nn + i;
+    const T* src = s_src + P.task_src[task] * n;
+    T a0 = (T)0, a1 = (T)0;
+    int j = 0;
+    for (; j + kBatch <= n; j += kBatch) {
+      T v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) v[u] = __ldcs(M + (int64_t)(j + u) * n);
+#pragma unroll
+      for (int u = 0; u < kBatch; u += 2) {
+        a0 = fma(v[u], src[j + u], a0);
+        a1 = fma(v[u + 1], src[j + u + 1], a1);
+      }
+    }
+    for (; j < n; ++j) a0 = fma(__ldcs(M + (int64_t)j * n), src[j], a0);
+    s_acc[tau] = (double)(a0 + a1);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < P.s * n; idx += kKronBigThreads) {
+    const int t = idx / n, i = idx - t * n;
+    double x = 0.0;
+    for (int tau = 0; tau < P.nt; ++tau) x += P.H[t * kKronMaxTasks + tau] * s_acc[tau * n + i];
+    if (P.ybuf)
+      P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
+    else
+      P.out[t * P.m + s_g[i]] += P.scale * x;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // TMA-staged decoupled apply (persistent over the patches of one colour).
 // Each patch block (nm matrices + index list) is one contiguous 16-byte-aligned
 // run, streamed into a ring of shared-memory stages by cp.async.bulk; the CTA
@@ -462,6 +538,16 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   P.nmax = L.kron_nmax;
   if (P.count <= 0) return cudaSuccess;
   const int prec = C.opt.patch_precision;
+  if (L.apply_kernel == 6) {
+    if (transpose) return cudaErrorNotSupported;
+    if (prec == 64)
+      k_vanka_apply_kron_big<double><<<(unsigned)P.count, kKronBigThreads, 0, C.stream>>>(
+          P, (const double*)L.d_fac);
+    else
+      k_vanka_apply_kron_big<float><<<(unsigned)P.count, kKronBigThreads, 0, C.stream>>>(
+          P, (const float*)L.d_fac);
+    return cudaGetLastError();
+  }
   KronShape shp;
   if (L.apply_kernel == 5 && kron_staged_config(K, L.kron_nmax, prec, L.kron_shape, &shp)) {
     KronStaged S;

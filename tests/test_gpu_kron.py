@@ -160,25 +160,70 @@ def test_decoupled_oseen_matches_oracle():
         ctx.close()
 
 
-def test_3d_keeps_dense_factors_where_pairs_do_not_fit():
-    """In 3D (n = 196 per stage on interior patches) the pair system exceeds
-    the shared-memory inversion, so those levels keep the dense blocked-LU
-    form; coarse levels with small patches decouple.  The solve is unchanged."""
+@pytest.mark.parametrize("variant", [2, 4], ids=["per_colour", "one_launch"])
+@pytest.mark.parametrize("s", [2, 3])
+def test_3d_decoupled_large_patches_match_oracle(s, variant):
+    """3D patches (n = 196 per stage inside): the pair block (2n = 392) is
+    factored by the blocked LU and its first block column gives X and Y
+    (`apply_kernel` 6, CTA per patch).  With s = 3 the dense patch (588 DoFs)
+    exceeds the dense limit, the decoupled blocks (196 and 392) do not.
+    FP64 patches: one Vanka correction per level and one V-cycle against the
+    oracle at 1e-11."""
     irkmg = need_gpu()
     from oracle import mg, tableau
-    A, b, c = irkmg.irkmg_radau_iia(2)
+    A, b, c = irkmg.irkmg_radau_iia(s)
     o = irkmg.irkmg_default_options()
     o.nlevels = 2
-    o.cheb_hi = 17.0
+    o.cheb_lo, o.cheb_hi = 2.0, 17.0
     o.patch_form = 1
-    ctx = irkmg.irkmg_setup(*synth.cube_mesh(2), A, b, c, 1 / 16, 1.0, o)
+    o.apply_variant = variant
+    dt = 1 / 16
+    ctx = irkmg.irkmg_setup(*synth.cube_mesh(2), A, b, c, dt, 1.0, o)
     try:
-        kinds = [lv["apply_kernel"] for lv in ctx.levels[1:]]
-        assert all(k in (3, 4, 5) for k in kinds)
-        H = mg.Hierarchy(*synth.cube_mesh(2), 2, tableau.radau_iia(2)[0], 1 / 16, cheb=(2.0, 17.0))
-        r = synth.random_vector(909, H.finest.N)
-        z = dev(np.zeros(H.finest.N))
+        lv = ctx.levels[1]
+        assert lv["apply_kernel"] == 6 and lv["single_launch"] == (1 if variant == 4 else 0)
+        assert lv["max_patch_dofs"] == s * 196
+        H = mg.Hierarchy(*synth.cube_mesh(2), 2, tableau.radau_iia(s)[0], dt, cheb=(2.0, 17.0))
+        L = H.finest
+        r = synth.random_vector(909 + s, L.N)
+        cc = dev(np.zeros(L.N))
+        irkmg.irkmg_vanka_correction(ctx, dev(r), cc)
+        assert rel(host(cc), L.vanka.correction(r)) < 1e-11
+        z = dev(np.zeros(L.N))
         irkmg.irkmg_vcycle(ctx, dev(r), z)
         assert rel(host(z), H.vcycle(r)) < 1e-11
     finally:
         ctx.close()
+
+
+def test_3d_decoupled_fp32_solve():
+    """3D FP32 decoupled patches (complex layout, tensor-core LU) inside the
+    FP64 FGMRES reach the dense FP64 solution to 1e-6 in at most 2 more
+    iterations."""
+    irkmg = need_gpu()
+    A, b, c = irkmg.irkmg_radau_iia(2)
+    sols = {}
+    for form, prec in ((0, 64), (1, 32)):
+        o = irkmg.irkmg_default_options()
+        o.nlevels = 3
+        o.cheb_lo, o.cheb_hi = 2.0, 17.0
+        o.patch_form = form
+        o.patch_precision = prec
+        o.maxit = 400
+        ctx = irkmg.irkmg_setup(*synth.cube_mesh(2), A, b, c, 1 / 16, 1.0, o)
+        try:
+            fin = ctx.finest
+            m, nv = fin["m"], fin["nv"]
+            F = synth.random_vector(31, ctx.N())
+            for t in range(2):   # consistent right-hand side: zero pressure mean per stage
+                F[t * m + m - nv:(t + 1) * m] -= F[t * m + m - nv:(t + 1) * m].mean()
+            k = dev(np.zeros(ctx.N()))
+            st = irkmg.irkmg_solve(ctx, dev(F), k)
+            assert st["status"] == 0
+            sols[form] = (host(k), st["iters"], fin["apply_kernel"])
+        finally:
+            ctx.close()
+    assert sols[1][2] == 6 and sols[0][2] == 3
+    vel = np.concatenate([np.arange(t * m, t * m + m - nv) for t in range(2)])
+    assert rel(sols[1][0][vel], sols[0][0][vel]) < 1e-6
+    assert sols[1][1] <= sols[0][1] + 2
