@@ -61,7 +61,8 @@ NCU_TRAFFIC = {
 }
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
                "k_vanka_apply_lu": "k_patch_big.cu", "k_vanka_apply_kron": "k_patch_kron.cu",
-               "k_vanka_apply_kron_staged": "k_patch_kron.cu"}
+               "k_vanka_apply_kron_staged": "k_patch_kron.cu",
+               "k_vanka_apply_kron_big": "k_patch_kron.cu"}
 
 
 def kernel_source_hash(kernel="k_vanka_apply_kron"):
@@ -373,7 +374,7 @@ def run_batched(args, dev, stream):
             "setup_s": setup_s}
 
 
-def run_3d(args, dev, stream):
+def run_3d(args, dev, stream, patch_form=1):
     """The 3D configuration (Kuhn tetrahedra, FP32 blocked patch LU, FP64
     FGMRES): time per stage solve, iterations, residual, roofline of the
     finest-level patch solves."""
@@ -382,7 +383,7 @@ def run_3d(args, dev, stream):
     a3 = argparse.Namespace(**vars(args))
     a3.dim = 3
     wl = workload(a3)
-    ctx, setup_s, c = make_context(irkmg, wl, 32, stream.cuda_stream, 0)
+    ctx, setup_s, c = make_context(irkmg, wl, 32, stream.cuda_stream, 0, patch_form)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -406,6 +407,8 @@ def run_3d(args, dev, stream):
     hbm, _ = peaks()
     gbs = tr["vanka_bytes"] / (tr["vanka_ms"] * 1e-3) / 1e9 if tr["vanka_ms"] else None
     out = {"workload": wl["name"], "N": ctx.N(), "patches_finest": ctx.finest["nv"],
+           "patch_form": patch_form, "apply_kernel_finest": ctx.finest["apply_kernel"],
+           "factor_bytes_finest": ctx.finest["factor_bytes"],
            "max_patch_dofs": ctx.finest["max_patch_dofs"], "ms_per_step": ms,
            "iters": stats[-1]["iters"], "rel_residual": stats[-1]["rfinal"] / stats[-1]["r0"],
            "setup_s": setup_s, "all_converged": all(s_["status"] == 0 for s_ in stats),
@@ -512,7 +515,9 @@ def run_ours(args, wl, rank, world, local_rank):
             forms[name] = run_form(irkmg, torch, wl, args, dev, stream, k, fp, pf)
             forms[name]["speedup_vs_headline"] = (ms / args.steps) / forms[name]["ms_per_step"]
         forms["batched"] = run_batched(args, dev, stream)
-        forms["3d"] = run_3d(args, dev, stream)
+        forms["3d"] = run_3d(args, dev, stream, 1)
+        forms["3d_dense"] = run_3d(args, dev, stream, 0)
+        forms["3d"]["speedup_vs_dense"] = forms["3d_dense"]["ms_per_step"] / forms["3d"]["ms_per_step"]
     result = None
     if rank == 0:
         hbm, hbm_kind = peaks()
@@ -522,7 +527,8 @@ def run_ours(args, wl, rank, world, local_rank):
         nvl = max(trace["vanka_launches"], 1)
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
                  3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
-                 5: "k_vanka_apply_kron_staged"}[ctx.finest["apply_kernel"]]
+                 5: "k_vanka_apply_kron_staged",
+                 6: "k_vanka_apply_kron_big"}[ctx.finest["apply_kernel"]]
         h = kernel_source_hash(kname)
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None

@@ -43,6 +43,9 @@ struct KronApply {
   double* ybuf;
   const int64_t* qoff;
   int64_t Q;
+  // tasks reading each stored matrix (at most two: the complex layout applies
+  // X and Y to both sources of a pair), -1 if unused
+  int mat_task[kKronMaxTasks][2];
 };
 
 // Shared memory of one warp: residuals (s·nmax doubles), task results
@@ -181,25 +184,59 @@ __global__ void __launch_bounds__(kKronBigThreads)
     s_src[idx] = (T)a;
   }
   __syncthreads();
+  // units (matrix b, row i): every stored entry is loaded once and feeds the
+  // one or two tasks that read its matrix; thread t takes units t and t + 256
+  // together, eight columns of each loaded before their multiply-adds
   constexpr int kBatch = 8;
-  for (int tau = tid; tau < P.nt * n; tau += kKronBigThreads) {
-    const int task = tau / n, i = tau - task * n;
-    const T* M = X + (int64_t)P.task_mat[task] * nn + i;
-    const T* src = s_src + P.task_src[task] * n;
-    T a0 = (T)0, a1 = (T)0;
+  const int nunit = P.nm * n;
+  for (int u0 = tid; u0 < nunit; u0 += 2 * kKronBigThreads) {
+    const int u1 = u0 + kKronBigThreads;
+    const bool has1 = u1 < nunit;
+    const int b0 = u0 / n, i0 = u0 - b0 * n;
+    const int b1 = has1 ? u1 / n : b0, i1 = has1 ? u1 - b1 * n : i0;
+    const T* M0 = X + (int64_t)b0 * nn + i0;
+    const T* M1 = X + (int64_t)b1 * nn + i1;
+    const int t00 = P.mat_task[b0][0], t01 = P.mat_task[b0][1];
+    const int t10 = P.mat_task[b1][0], t11 = P.mat_task[b1][1];
+    const T* s00 = s_src + P.task_src[t00] * n;
+    const T* s01 = s_src + P.task_src[t01 >= 0 ? t01 : t00] * n;
+    const T* s10 = s_src + P.task_src[t10] * n;
+    const T* s11 = s_src + P.task_src[t11 >= 0 ? t11 : t10] * n;
+    T a00 = (T)0, a01 = (T)0, a10 = (T)0, a11 = (T)0;
     int j = 0;
     for (; j + kBatch <= n; j += kBatch) {
-      T v[kBatch];
+      T v0[kBatch], v1[kBatch];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) v[u] = __ldcs(M + (int64_t)(j + u) * n);
+      for (int u = 0; u < kBatch; ++u) {
+        v0[u] = __ldcs(M0 + (int64_t)(j + u) * n);
+        if (has1) v1[u] = __ldcs(M1 + (int64_t)(j + u) * n);
+      }
 #pragma unroll
-      for (int u = 0; u < kBatch; u += 2) {
-        a0 = fma(v[u], src[j + u], a0);
-        a1 = fma(v[u + 1], src[j + u + 1], a1);
+      for (int u = 0; u < kBatch; ++u) {
+        a00 = fma(v0[u], s00[j + u], a00);
+        a01 = fma(v0[u], s01[j + u], a01);
+        if (has1) {
+          a10 = fma(v1[u], s10[j + u], a10);
+          a11 = fma(v1[u], s11[j + u], a11);
+        }
       }
     }
-    for (; j < n; ++j) a0 = fma(__ldcs(M + (int64_t)j * n), src[j], a0);
-    s_acc[tau] = (double)(a0 + a1);
+    for (; j < n; ++j) {
+      const T w0 = __ldcs(M0 + (int64_t)j * n);
+      a00 = fma(w0, s00[j], a00);
+      a01 = fma(w0, s01[j], a01);
+      if (has1) {
+        const T w1 = __ldcs(M1 + (int64_t)j * n);
+        a10 = fma(w1, s10[j], a10);
+        a11 = fma(w1, s11[j], a11);
+      }
+    }
+    s_acc[t00 * n + i0] = (double)a00;
+    if (t01 >= 0) s_acc[t01 * n + i0] = (double)a01;
+    if (has1) {
+      s_acc[t10 * n + i1] = (double)a10;
+      if (t11 >= 0) s_acc[t11 * n + i1] = (double)a11;
+    }
   }
   __syncthreads();
   for (int idx = tid; idx < P.s * n; idx += kKronBigThreads) {
@@ -516,6 +553,14 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   for (int i = 0; i < kKronMaxTasks; ++i) {
     P.task_mat[i] = K.task_mat[i];
     P.task_src[i] = K.task_src[i];
+    P.mat_task[i][0] = P.mat_task[i][1] = -1;
+  }
+  for (int t = 0; t < K.nt; ++t) {
+    int* mt = P.mat_task[K.task_mat[t]];
+    if (mt[0] < 0)
+      mt[0] = t;
+    else
+      mt[1] = t;
   }
   P.np = L.d_np;
   P.fac_off = L.d_fac_off;
