@@ -151,8 +151,9 @@ typedef struct {
                               (patch_form != 0): 4 warp-per-patch, 5 TMA-staged,
                               6 CTA-per-patch (blocks above 160 DoFs, factored by
                               the blocked LU; 3D)                                   */
-  double apply_ms[2];      /* autotuner: one sweep with the staged / warp-per-patch
-                              kernel of the level's form (0 if untimed)            */
+  double apply_ms[2];      /* autotuner: one sweep with the fastest staged (or, for
+                              decoupled levels, CTA-per-patch) candidate / the
+                              fastest warp-per-patch candidate (0 if untimed)      */
   int64_t dim;             /* 2 or 3                                                */
   int64_t single_launch;   /* 1: the level relaxes by one launch over all patches
                               plus a deterministic per-DoF sum (decoupled form);

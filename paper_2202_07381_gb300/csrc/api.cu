@@ -528,6 +528,7 @@ int tune_apply(Ctx& C) {
       if (fits)
         for (int shape = 0; shape < (L.kron ? 2 : 1); ++shape) cands.push_back({ks, shape, single != 0});
       cands.push_back({kw, 0, single != 0});
+      if (L.kron && L.kron_nmax <= kron_big_max_n()) cands.push_back({6, 0, single != 0});
     }
     cudaError_t e = cudaMemsetAsync(L.t, 0, sizeof(double) * L.N, C.stream);
     if (e != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e)); break; }
@@ -551,7 +552,7 @@ int tune_apply(Ctx& C) {
         cudaEventElapsedTime(&ms, a, b);
         if (rep > 0 && ms < best) best = ms;   // rep 0 is the warm-up
       }
-      const int kind = cd.kern == ks ? 0 : 1;
+      const int kind = cd.kern == kw ? 1 : 0;  // [0]: staged or CTA-per-patch, [1]: warp
       best_kind[kind] = std::min(best_kind[kind], best);
       if (best < best_all) {
         best_all = best;

@@ -108,9 +108,9 @@ def test_decoupled_autotuner_picks_the_faster_kernel():
     ctx = _context(irkmg, "radau_iia", 3, 1 / 64, 2, 5, 1)
     try:
         for lv in ctx.levels[1:]:
-            assert lv["apply_kernel"] in (4, 5)
+            assert lv["apply_kernel"] in (4, 5, 6)
             assert all(t > 0 for t in lv["apply_ms"])
-            assert lv["apply_kernel"] == (5 if lv["apply_ms"][0] <= lv["apply_ms"][1] else 4)
+            assert (lv["apply_kernel"] != 4) == (lv["apply_ms"][0] <= lv["apply_ms"][1])
     finally:
         ctx.close()
 
