@@ -108,7 +108,11 @@ typedef struct {
                               mat-vec everywhere; 3, 4 = as 1, 2 and, on decoupled
                               levels, one launch over all patches whose results
                               are summed per DoF by a second, deterministic
-                              launch (instead of one launch per colour)            */
+                              launch (instead of one launch per colour); 5, 6 =
+                              on decoupled levels the warp-specialised TMA
+                              pipeline (one producer warp, seven consumer warps
+                              each working on whole patches), per colour / one
+                              launch; elsewhere as 1                               */
   int patch_form;          /* 0 = one dense s·n patch system per vertex (Section 4.2);
                               1..3 = Kronecker-decoupled patch solves: with the
                               Butcher matrix A = T D T⁻¹ (D real block diagonal,
@@ -150,7 +154,8 @@ typedef struct {
                               inverses come from a blocked LU; 3D); decoupled form
                               (patch_form != 0): 4 warp-per-patch, 5 TMA-staged,
                               6 CTA-per-patch (blocks above 160 DoFs, factored by
-                              the blocked LU; 3D)                                   */
+                              the blocked LU; 3D), 7 warp-specialised TMA
+                              pipeline                                             */
   double apply_ms[2];      /* autotuner: one sweep with the fastest staged (or, for
                               decoupled levels, CTA-per-patch) candidate / the
                               fastest warp-per-patch candidate (0 if untimed)      */

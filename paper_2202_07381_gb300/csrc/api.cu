@@ -519,7 +519,8 @@ int tune_apply(Ctx& C) {
     if (av != 0) {
       const bool staged = (av == 1 || av == 3) && fits;
       L.apply_kernel = staged ? ks : kw;
-      L.single = L.kron && av >= 3;
+      if (av >= 5 && L.kron && kron_ws_fits(C, L)) L.apply_kernel = 7;
+      L.single = L.kron && (av == 3 || av == 4 || av == 6);
       continue;
     }
     struct Cand { int kern, shape; bool single; };
@@ -529,6 +530,7 @@ int tune_apply(Ctx& C) {
         for (int shape = 0; shape < (L.kron ? 2 : 1); ++shape) cands.push_back({ks, shape, single != 0});
       cands.push_back({kw, 0, single != 0});
       if (L.kron && L.kron_nmax <= kron_big_max_n()) cands.push_back({6, 0, single != 0});
+      if (L.kron && kron_ws_fits(C, L)) cands.push_back({7, 0, single != 0});
     }
     cudaError_t e = cudaMemsetAsync(L.t, 0, sizeof(double) * L.N, C.stream);
     if (e != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e)); break; }
@@ -847,8 +849,8 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
   if (o->maxit < 1) return fail(IRKMG_EINVAL, "maxit >= 1");
   if (o->patch_precision != 64 && o->patch_precision != 32)
     return fail(IRKMG_EINVAL, "patch_precision is 64 or 32");
-  if (o->apply_variant < 0 || o->apply_variant > 4)
-    return fail(IRKMG_EINVAL, "apply_variant is 0 .. 4");
+  if (o->apply_variant < 0 || o->apply_variant > 6)
+    return fail(IRKMG_EINVAL, "apply_variant is 0 .. 6");
   if (o->patch_form < 0 || o->patch_form > 3)
     return fail(IRKMG_EINVAL, "patch_form is 0, 1, 2 or 3");
   if (o->patch_lu_tc != 0 && o->patch_lu_tc != 1) return fail(IRKMG_EINVAL, "patch_lu_tc is 0 or 1");

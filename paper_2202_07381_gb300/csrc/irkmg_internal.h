@@ -150,7 +150,8 @@ struct Level {
   int kron_nmax = 0;                   // largest spatial patch size n on a decoupled level
   int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 big-patch mat-vec,
                                        // 4 decoupled warp-per-patch, 5 decoupled staged,
-                                       // 6 decoupled CTA-per-patch (large patches)
+                                       // 6 decoupled CTA-per-patch (large patches),
+                                       // 7 decoupled warp-specialised TMA pipeline
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   int kron_shape = 0;                  // launch shape of the staged decoupled apply (0, 1)
   // one-launch relaxation of a decoupled level: patch results to Ctx::d_Y at
@@ -161,6 +162,7 @@ struct Level {
   int32_t *d_cptr = nullptr, *d_cidx = nullptr;  // spatial DoF -> entries qoff[p] + i
   double reduce_bytes = 0.0;           // algorithmic bytes of one reduction launch
   int kron_cap[2][2] = {{0, 0}, {0, 0}};  // its resident CTAs per [shape][transpose] (0 unset)
+  int ws_cap[2] = {0, 0};              // resident CTAs of the warp-specialised apply
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
   // algorithmic bytes for tracing
@@ -230,6 +232,7 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
 cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale);
 int kron_max_slots();
 bool kron_staged_fits(Ctx& C, Level& L, int shape);
+bool kron_ws_fits(Ctx& C, Level& L);
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose);
 bool vanka_staged_fits(Ctx& C, Level& L);

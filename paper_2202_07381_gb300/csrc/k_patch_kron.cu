@@ -428,6 +428,253 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised decoupled apply (persistent over the patches of a launch).
+// Warp 0 is the producer: lane 0 streams patch blocks into a ring of stages
+// with cp.async.bulk (completion on full[st]) and reuses a stage once its
+// consumer has arrived on empty[st].  Warps 1..kWsConsumers each take every
+// kWsConsumers-th patch of the CTA and work on it alone (warp-synchronous:
+// gather, sources, matrix-centric units from the stage, results), so no
+// CTA-wide barrier sits between patches.  The stage is released as soon as
+// its matrices are consumed.  Every wait is bounded; on expiry the CTA
+// records IRKMG_ETIMEOUT, the consumers leave and the producer waits (bounded)
+// for the copies it issued before it returns.
+// ---------------------------------------------------------------------------
+constexpr int kWsConsumers = 7;
+constexpr int kWsThreads = 32 * (kWsConsumers + 1);
+constexpr int kWsMaxStages = 8;
+
+struct KronWs {
+  KronApply a;
+  int stages;
+  uint32_t stage_bytes;
+  uint32_t work_off;    // per-warp work arrays after the stages
+  uint32_t warp_bytes;  // bytes of one consumer's work arrays
+  int64_t spins;
+  int* err;
+};
+
+__host__ __device__ inline uint32_t ws_warp_bytes(int s, int ns, int nt, int nmax, int tsize) {
+  const int nsrc = ns > nt ? ns : nt;
+  const size_t b = (size_t)(s + nt) * nmax * 8 + (size_t)nsrc * nmax * tsize + (size_t)nmax * 4;
+  return (uint32_t)((b + 15) & ~(size_t)15);
+}
+
+template <typename T, bool TR>
+__global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, const T* __restrict__ fac) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ __align__(8) uint64_t full[kWsMaxStages];
+  __shared__ __align__(8) uint64_t empty[kWsMaxStages];
+  __shared__ int s_n[kWsMaxStages];
+  __shared__ volatile long long s_seq[kWsMaxStages];  // patch index of each stage's current fill
+  __shared__ volatile int s_abort;
+  const KronApply& P = W.a;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nmine = (P.count > blockIdx.x) ? (P.count - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int S = W.stages;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+      s_seq[st] = -1;
+    }
+    s_abort = 0;
+  }
+  fence_proxy_async();
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  auto mats_bytes = [&](int n) -> int64_t {
+    return ((int64_t)P.nm * n * n * (int64_t)sizeof(T) + 15) & ~(int64_t)15;
+  };
+  if (warp == 0) {
+    // ---- producer ----
+    if (lane == 0) {
+      const uint64_t pol = l2_evict_first_policy();
+      int64_t issued = 0;
+      for (int64_t k = 0; k < nmine; ++k) {
+        const int st = (int)(k % S);
+        if (k >= S && !mbar_wait_bounded(&empty[st], (uint32_t)(((k / S) - 1) & 1), W.spins)) {
+          s_abort = 1;
+          atomicCAS(&W.err[0], 0, IRKMG_ETIMEOUT);
+        }
+        if (s_abort) break;
+        const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+        const int n = P.np[pi];
+        const uint32_t bytes = (uint32_t)(mats_bytes(n) + (((int64_t)n * 4 + 15) & ~(int64_t)15));
+        s_n[st] = n;
+        __threadfence_block();
+        s_seq[st] = k;  // after this the stage's barrier is one phase behind patch k
+        mbar_expect_tx(&full[st], bytes);
+        bulk_g2s(dyn + (size_t)st * W.stage_bytes, fac + P.fac_off[pi], bytes, &full[st], pol);
+        issued = k + 1;
+      }
+      if (s_abort)  // copies still in flight complete before the CTA leaves
+        for (int64_t k = issued > S ? issued - S : 0; k < issued; ++k)
+          mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), W.spins);
+    }
+    return;
+  }
+  // ---- consumers ----
+  const int c = warp - 1;
+  const int nmax = P.nmax;
+  unsigned char* wb = dyn + W.work_off + (size_t)c * W.warp_bytes;
+  double* s_r = reinterpret_cast<double*>(wb);
+  double* s_acc = s_r + P.s * nmax;
+  T* s_src = reinterpret_cast<T*>(s_acc + P.nt * nmax);
+  const int nsrc = TR ? P.nt : P.ns;
+  int32_t* s_g = reinterpret_cast<int32_t*>(s_src + (P.ns > P.nt ? P.ns : P.nt) * nmax);
+  for (int64_t k = c; k < nmine; k += kWsConsumers) {
+    const int st = (int)(k % S);
+    if (s_abort) return;
+    // Patches of one stage go to different consumers, so a consumer may reach
+    // stage st before the fill for patch k - S has completed; a parity wait
+    // would then match the older phase.  Waiting until the producer has
+    // started patch k's fill (s_seq) leaves the barrier exactly one phase
+    // behind, and the parity wait below is for patch k's copy.
+    bool started = s_seq[st] == k;
+    if (!started) {
+      const uint64_t t0 = global_ns();
+      for (int64_t it = 0; it < W.spins && !s_abort; ++it) {
+        if (s_seq[st] == k) {
+          started = true;
+          break;
+        }
+        if ((it & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
+      }
+    }
+    if (!started || !mbar_wait_bounded(&full[st], (uint32_t)((k / S) & 1), W.spins)) {
+      if (lane == 0) {
+        s_abort = 1;
+        atomicCAS(&W.err[0], 0, IRKMG_ETIMEOUT);
+      }
+      return;
+    }
+    const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+    const int n = s_n[st];
+    const int64_t nn = (int64_t)n * n;
+    const T* X = reinterpret_cast<const T*>(dyn + (size_t)st * W.stage_bytes);
+    const int32_t* G =
+        reinterpret_cast<const int32_t*>(dyn + (size_t)st * W.stage_bytes + mats_bytes(n));
+    for (int i = lane; i < n; i += 32) s_g[i] = G[i];
+    __syncwarp();
+    for (int idx = lane; idx < P.s * n; idx += 32) {
+      const int t = idx / n, i = idx - t * n;
+      s_r[idx] = P.r[t * P.m + s_g[i]];
+    }
+    __syncwarp();
+    for (int idx = lane; idx < nsrc * n; idx += 32) {
+      const int cc = idx / n, i = idx - cc * n;
+      double a = 0.0;
+      for (int t = 0; t < P.s; ++t)
+        a += (TR ? P.H[t * kKronMaxTasks + cc] : P.G[cc * 3 + t]) * s_r[t * n + i];
+      s_src[idx] = (T)a;
+    }
+    __syncwarp();
+    // units (matrix b, row i); transposed: row i of Mᵀ is column i of M
+    for (int u = lane; u < P.nm * n; u += 32) {
+      const int b = u / n, i = u - b * n;
+      const T* M = X + (int64_t)b * nn + (TR ? (int64_t)i * n : (int64_t)i);
+      const int64_t step = TR ? 1 : n;
+      const int t0 = P.mat_task[b][0], t1 = P.mat_task[b][1];
+      const int t1s = t1 >= 0 ? t1 : t0;
+      const T* q0 = s_src + (TR ? t0 : P.task_src[t0]) * n;
+      const T* q1 = s_src + (TR ? t1s : P.task_src[t1s]) * n;
+      T a0 = (T)0, a1 = (T)0;
+#pragma unroll 4
+      for (int j = 0; j < n; ++j) {
+        const T m = M[j * step];
+        a0 = fma(m, q0[j], a0);
+        a1 = fma(m, q1[j], a1);
+      }
+      s_acc[t0 * n + i] = (double)a0;
+      if (t1 >= 0) s_acc[t1 * n + i] = (double)a1;
+    }
+    fence_proxy_async();  // the stage's reads before the producer's next copy into it
+    __syncwarp();
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+    for (int idx = lane; idx < P.s * n; idx += 32) {
+      const int t = idx / n, i = idx - t * n;
+      double x = 0.0;
+      for (int tau = 0; tau < P.nt; ++tau) {
+        const double h = TR ? P.G[P.task_src[tau] * 3 + t] : P.H[t * kKronMaxTasks + tau];
+        x += h * s_acc[tau * n + i];
+      }
+      if (P.ybuf)
+        P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
+      else
+        P.out[t * P.m + s_g[i]] += P.scale * x;
+    }
+    __syncwarp();
+  }
+}
+
+// Launch shape of the warp-specialised apply: two CTAs per SM when each holds
+// at least four stages besides the consumers' work arrays, else one CTA with
+// as many stages as fit (at least two).
+struct WsShape {
+  int stages;
+  uint32_t stage_bytes, work_off, warp_bytes, dyn_bytes;
+};
+
+static bool kron_ws_config(const KronPlan& K, int nmax, int prec, WsShape* out) {
+  const size_t w = prec == 64 ? 8 : 4;
+  const size_t blk = (((size_t)K.nm * nmax * nmax * w + 15) & ~(size_t)15) +
+                     (((size_t)nmax * 4 + 15) & ~(size_t)15);
+  const size_t sb = (blk + 127) & ~(size_t)127;
+  const uint32_t wbytes = ws_warp_bytes(K.s, K.ns, K.nt, nmax, (int)w);
+  const size_t work = (size_t)kWsConsumers * wbytes;
+  const size_t static_b = 256;
+  for (int ctas = 2; ctas >= 1; --ctas) {
+    const size_t lim = std::min((size_t)233472 / ctas - 1024, (size_t)232448);
+    if (lim < static_b + work + 2 * sb) continue;
+    int st = (int)((lim - static_b - work) / sb);
+    if (st > kWsMaxStages) st = kWsMaxStages;
+    if (ctas == 2 && st < 4) continue;
+    out->stages = st;
+    out->stage_bytes = (uint32_t)sb;
+    out->work_off = (uint32_t)(st * sb);
+    out->warp_bytes = wbytes;
+    out->dyn_bytes = (uint32_t)(st * sb + work);
+    return true;
+  }
+  return false;
+}
+
+bool kron_ws_fits(Ctx& C, Level& L) {
+  WsShape shp;
+  return kron_ws_config(C.kplan, L.kron_nmax, C.opt.patch_precision, &shp);
+}
+
+template <typename T, bool TR>
+cudaError_t launch_kron_ws(const KronWs& W, const T* fac, const WsShape& shp, cudaStream_t st,
+                           int* cap_cache) {
+  auto kern = k_vanka_apply_kron_ws<T, TR>;
+  static uint32_t limit[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (shp.dyn_bytes > limit[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shp.dyn_bytes);
+    if (e != cudaSuccess) return e;
+    limit[dev] = shp.dyn_bytes;
+  }
+  if (*cap_cache == 0) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWsThreads, shp.dyn_bytes);
+    if (e != cudaSuccess) return e;
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *cap_cache = nsm * (per_sm < 1 ? 1 : per_sm);
+  }
+  const int64_t cap = *cap_cache;
+  const int64_t ctas = W.a.count < cap ? W.a.count : cap;
+  kern<<<(unsigned)ctas, kWsThreads, shp.dyn_bytes, st>>>(W, fac);
+  return cudaGetLastError();
+}
+
 // Launch shapes of the staged decoupled apply for a level.  Shape 0: the most
 // CTAs per SM (up to 5, the register bound) that leave room for three stages
 // each (the block of patch k+1 is waited for while patch k is computed, so
@@ -583,6 +830,27 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   P.nmax = L.kron_nmax;
   if (P.count <= 0) return cudaSuccess;
   const int prec = C.opt.patch_precision;
+  if (L.apply_kernel == 7) {
+    WsShape wsh;
+    if (!kron_ws_config(K, L.kron_nmax, prec, &wsh)) return cudaErrorInvalidConfiguration;
+    KronWs W;
+    W.a = P;
+    W.stages = wsh.stages;
+    W.stage_bytes = wsh.stage_bytes;
+    W.work_off = wsh.work_off;
+    W.warp_bytes = wsh.warp_bytes;
+    W.spins = C.opt.timeout_spins > 0 ? C.opt.timeout_spins : (int64_t)1 << 26;
+    W.err = C.d_err;
+    int* cap = &L.ws_cap[transpose ? 1 : 0];
+    if (prec == 64) {
+      const double* f = (const double*)L.d_fac;
+      return transpose ? launch_kron_ws<double, true>(W, f, wsh, C.stream, cap)
+                       : launch_kron_ws<double, false>(W, f, wsh, C.stream, cap);
+    }
+    const float* f = (const float*)L.d_fac;
+    return transpose ? launch_kron_ws<float, true>(W, f, wsh, C.stream, cap)
+                     : launch_kron_ws<float, false>(W, f, wsh, C.stream, cap);
+  }
   if (L.apply_kernel == 6) {
     if (transpose) return cudaErrorNotSupported;
     if (prec == 64)

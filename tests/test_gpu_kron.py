@@ -37,9 +37,9 @@ def _context(irkmg, fam, s, dt, n0, nl, form, precision=64, nu=1.0, wind=None, v
     return irkmg.irkmg_setup(*synth.square_mesh(n0), A, b, c, dt, nu, o, wind=wind)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4],
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6],
                          ids=["tma_staged", "warp_per_patch", "tma_staged_one_launch",
-                              "warp_one_launch"])
+                              "warp_one_launch", "warp_specialised", "warp_specialised_one_launch"])
 @pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
 @pytest.mark.parametrize("fam,s,dt", CASES)
 def test_decoupled_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
@@ -53,8 +53,8 @@ def test_decoupled_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
     try:
         for l in range(1, nl):
             info = ctx.levels[l]
-            assert info["apply_kernel"] == (5 if variant in (1, 3) else 4)
-            assert info["single_launch"] == (1 if variant >= 3 else 0)
+            assert info["apply_kernel"] == {1: 5, 2: 4, 3: 5, 4: 4, 5: 7, 6: 7}[variant]
+            assert info["single_launch"] == (1 if variant in (3, 4, 6) else 0)
             n = 2 * 19 + 1   # largest patch of a structured triangle mesh: 19 nodes
             pairs = s // 2
             nm = s if form == 2 else s + pairs
@@ -108,7 +108,7 @@ def test_decoupled_autotuner_picks_the_faster_kernel():
     ctx = _context(irkmg, "radau_iia", 3, 1 / 64, 2, 5, 1)
     try:
         for lv in ctx.levels[1:]:
-            assert lv["apply_kernel"] in (4, 5, 6)
+            assert lv["apply_kernel"] in (4, 5, 6, 7)
             assert all(t > 0 for t in lv["apply_ms"])
             assert (lv["apply_kernel"] != 4) == (lv["apply_ms"][0] <= lv["apply_ms"][1])
     finally:
