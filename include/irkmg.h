@@ -128,6 +128,11 @@ typedef struct {
                               512) by the blocked LU; with decoupling, 3D works
                               for s = 3 too (dense: 588 DoFs, above the limit).
                               IRKMG_ENOTIMPL if A has a repeated eigenvalue.       */
+  int cheb_auto;           /* 1: per level, the Chebyshev interval [λ/4, λ] with λ the
+                              largest real Ritz value of 20 Arnoldi steps on the
+                              Vanka-preconditioned operator of that level, found at
+                              set-up and on every update (Section 5.1's estimate);
+                              0: [cheb_lo, cheb_hi] on every level                 */
   int patch_lu_tc;         /* FP32 patches above 160 DoFs (3D): 1 = trailing updates
                               of the blocked patch LU on the tensor cores
                               (tcgen05.mma kind::tf32, operands split hi + lo for
@@ -163,6 +168,7 @@ typedef struct {
   int64_t single_launch;   /* 1: the level relaxes by one launch over all patches
                               plus a deterministic per-DoF sum (decoupled form);
                               0: one launch per colour                             */
+  double cheb[2];          /* Chebyshev interval used on the level                  */
 } irkmg_level_info;
 
 /* ---- set-up -------------------------------------------------------------- */
@@ -189,6 +195,19 @@ int irkmg_lobatto_iiic(int s, double *A, double *b, double *c);
  * of the stage system (Section 3).  IRKMG_ENOTIMPL when two eigenvalues
  * coincide.  Host only; no device work. */
 int irkmg_kron_split(int s, const double *A, double *T, double *Tinv, double *D);
+
+/* Eigenvalues wr + i·wi of the n×n upper Hessenberg H (row-major, n <= 512):
+ * the Ritz values of an Arnoldi process (shifted QR in complex arithmetic).
+ * Host only. */
+int irkmg_hessenberg_eigvals(int n, const double *H, double *wr, double *wi);
+
+/* Section 5.1's estimate of the largest eigenvalue of the Vanka-preconditioned
+ * operator D⁻¹J of a level (D⁻¹ = Σ_v R_vᵀ A_v⁻¹ R_v): nsteps (2 .. restart)
+ * Arnoldi steps from d_x0 (device, N of the level) or, if NULL, from
+ * x_i = sin(i + 1); *lambda = the largest real part of the Ritz values, which
+ * ritz_re / ritz_im (host, nsteps each, may be NULL) receive. */
+int irkmg_estimate_lambda(irkmg_ctx *ctx, int level, int nsteps, const double *d_x0,
+                          double *ritz_re, double *ritz_im, double *lambda);
 
 /* Build the hierarchy, assemble every level, build patch maps and colourings,
  * factor (invert) every patch and the bordered coarsest system.  Host inputs

@@ -116,3 +116,34 @@ class Hierarchy:
             sl = slice(t * L.m + L.mesh.dim * L.mesh.nf, (t + 1) * L.m)
             y[sl] -= y[sl].mean()
         return y
+
+    def ritz_estimate(self, level, k, x0=None):
+        """Section 5.1's eigenvalue estimate for the Chebyshev interval: k
+        Arnoldi steps on the Vanka-preconditioned operator D^{-1} J of a level
+        (D^{-1} the additive patch correction), modified Gram-Schmidt applied
+        twice, from x0 (default x0_i = sin(i + 1)).  Returns (lambda, Ritz
+        values), lambda = the largest real part of the Ritz values (the
+        eigenvalues of the k x k Hessenberg matrix, by LAPACK)."""
+        L = self.levels[level]
+        x = np.sin(np.arange(1, L.N + 1, dtype=np.float64)) if x0 is None else np.array(x0, float)
+        V = np.zeros((k + 1, L.N))
+        H = np.zeros((k + 1, k))
+        V[0] = x / np.linalg.norm(x)
+        kk = k
+        for j in range(k):
+            w = L.vanka.correction(L.J @ V[j])
+            for _ in range(2):
+                for i in range(j + 1):
+                    h = V[i] @ w
+                    H[i, j] += h
+                    w = w - h * V[i]
+            hn = np.linalg.norm(w)
+            if j + 1 == k:
+                break
+            if hn <= 1e-14 * abs(H[j, j]):
+                kk = j + 1
+                break
+            H[j + 1, j] = hn
+            V[j + 1] = w / hn
+        ritz = np.linalg.eigvals(H[:kk, :kk])
+        return float(ritz.real.max()), ritz

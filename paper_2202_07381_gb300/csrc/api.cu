@@ -651,8 +651,8 @@ int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_i
     }
     return IRKMG_OK;
   }
-  const double theta = 0.5 * (C.opt.cheb_hi + C.opt.cheb_lo);
-  const double delta = 0.5 * (C.opt.cheb_hi - C.opt.cheb_lo);
+  const double theta = 0.5 * (L.cheb_hi + L.cheb_lo);
+  const double delta = 0.5 * (L.cheb_hi - L.cheb_lo);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
   const double* res = b;
@@ -843,8 +843,10 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
   if (o->nlevels < 2 || o->nlevels > 12) return fail(IRKMG_EINVAL, "nlevels in [2, 12]");
   if (o->nu_pre < 0 || o->nu_post < 0) return fail(IRKMG_EINVAL, "negative sweep count");
   if (o->smoother != 0 && o->smoother != 1) return fail(IRKMG_EINVAL, "smoother is 0 or 1");
-  if (o->smoother == 1 && !(o->cheb_hi > o->cheb_lo && o->cheb_lo > 0.0))
+  if (o->smoother == 1 && !o->cheb_auto && !(o->cheb_hi > o->cheb_lo && o->cheb_lo > 0.0))
     return fail(IRKMG_EINVAL, "Chebyshev interval needs 0 < lo < hi");
+  if (o->cheb_auto != 0 && o->cheb_auto != 1) return fail(IRKMG_EINVAL, "cheb_auto is 0 or 1");
+  if (o->cheb_auto && o->smoother != 1) return fail(IRKMG_EINVAL, "cheb_auto needs smoother 1");
   if (o->restart < 1 || o->restart > 60) return fail(IRKMG_EINVAL, "restart in [1, 60]");
   if (o->maxit < 1) return fail(IRKMG_EINVAL, "maxit >= 1");
   if (o->patch_precision != 64 && o->patch_precision != 32)
@@ -863,6 +865,10 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
   if (o->timeout_spins < 0) return fail(IRKMG_EINVAL, "timeout_spins >= 0");
   return IRKMG_OK;
 }
+
+int set_chebyshev_intervals(Ctx& C);
+int estimate_lambda(Ctx& C, Level& L, int k, const double* x0, double* ritz_re, double* ritz_im,
+                    double* lambda);
 
 int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt,
                double nu, const irkmg_options* opt) {
@@ -971,6 +977,7 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   CK(cudaMallocHost(&C->h_err, sizeof(int) * 2));
   if ((rc = factor_all(*C))) return rc;
   if ((rc = tune_apply(*C))) return rc;
+  if ((rc = set_chebyshev_intervals(*C))) return rc;
   (void)t0;
   return IRKMG_OK;
 }
@@ -1017,8 +1024,8 @@ int smooth_in(Ctx& C, Level& L, const double* b, double* x, int nsteps, int tr, 
     }
     return IRKMG_OK;
   }
-  const double theta = 0.5 * (C.opt.cheb_hi + C.opt.cheb_lo);
-  const double delta = 0.5 * (C.opt.cheb_hi - C.opt.cheb_lo);
+  const double theta = 0.5 * (L.cheb_hi + L.cheb_lo);
+  const double delta = 0.5 * (L.cheb_hi - L.cheb_lo);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
   if ((rc = op(C, L, b, x, t, tr))) return rc;
@@ -1036,6 +1043,96 @@ int smooth_in(Ctx& C, Level& L, const double* b, double* x, int nsteps, int tr, 
     C.launches += 2;
     rho = rho_new;
   }
+  return IRKMG_OK;
+}
+
+// Ritz values of k Arnoldi steps on the relaxation-preconditioned operator
+// D⁻¹J of level L (D⁻¹ = Σ_v R_vᵀ A_v⁻¹ R_v, the additive Vanka step), from
+// x0 (device, length L.N) or, if null, x0_i = sin(i + 1); modified
+// Gram–Schmidt applied twice.  The basis lives in the FGMRES storage
+// (k <= restart).  lambda = the largest real part among the Ritz values
+// (Section 5.1: the Chebyshev interval is chosen as [λ/4, λ] from such an
+// estimate).  ritz_re / ritz_im (host, k each) may be null.
+int estimate_lambda(Ctx& C, Level& L, int k, const double* x0, double* ritz_re, double* ritz_im,
+                    double* lambda) {
+  if (k < 2 || k > C.opt.restart) return fail(IRKMG_EINVAL, "Arnoldi steps in [2, restart]");
+  const int64_t n = L.N;
+  double* V = C.d_V;
+  double* hd = C.d_h;
+  double* hh = C.h_h;
+  if (x0)
+    CK(cudaMemcpyAsync(V, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.stream));
+  else
+    CK(launch_fill_sin(V, n, C.stream));
+  auto dot_self = [&](const double* v, double* out) -> int {
+    CK(launch_multidot(v, 0, 1, v, n, C.d_part, hd + 192, C.stream));
+    CK(cudaMemcpyAsync(hh + 192, hd + 192, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
+    CK(cudaStreamSynchronize(C.stream));
+    *out = std::sqrt(hh[192]);
+    return IRKMG_OK;
+  };
+  int rc;
+  double nrm;
+  if ((rc = dot_self(V, &nrm))) return rc;
+  if (!(nrm > 0.0)) return fail(IRKMG_EINVAL, "zero Arnoldi start vector");
+  CK(launch_axpby(V, V, 1.0 / nrm, 0.0, n, C.stream));
+  std::vector<double> H((size_t)k * k, 0.0);  // row-major k x k Hessenberg
+  int kk = k;
+  for (int j = 0; j < k; ++j) {
+    double* vj = V + (int64_t)j * n;
+    double* w = C.d_w;
+    // w = D⁻¹ J v_j
+    if ((rc = op(C, L, nullptr, vj, L.t, 0))) return rc;
+    CK(launch_fill(w, 0.0, n, C.stream));
+    if ((rc = vanka_all(C, L, L.t, w, 1.0, 0))) return rc;
+    for (int pass = 0; pass < 2; ++pass) {
+      CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd, C.stream));
+      CK(launch_multiaxpy(w, V, n, j + 1, hd, -1.0, n, C.stream));
+      CK(cudaMemcpyAsync(hh, hd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, C.stream));
+      CK(cudaStreamSynchronize(C.stream));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * k + j] += hh[i];
+    }
+    double hn;
+    if ((rc = dot_self(w, &hn))) return rc;
+    if (j + 1 == k) break;
+    if (!(hn > 1e-14 * std::fabs(H[(size_t)j * k + j]) + 1e-300)) {  // invariant subspace
+      kk = j + 1;
+      break;
+    }
+    H[(size_t)(j + 1) * k + j] = hn;
+    CK(launch_axpby(V + (int64_t)(j + 1) * n, w, 1.0 / hn, 0.0, n, C.stream));
+  }
+  std::vector<double> Hk((size_t)kk * kk), wr(kk), wi(kk);
+  for (int i = 0; i < kk; ++i)
+    for (int j = 0; j < kk; ++j) Hk[(size_t)i * kk + j] = H[(size_t)i * k + j];
+  if ((rc = hessenberg_eigvals(kk, Hk.data(), wr.data(), wi.data())))
+    return fail(rc, "Ritz values did not converge");
+  double lam = -1e300;
+  for (int i = 0; i < kk; ++i) lam = std::max(lam, wr[i]);
+  for (int i = 0; i < k; ++i) {
+    if (ritz_re) ritz_re[i] = i < kk ? wr[i] : 0.0;
+    if (ritz_im) ritz_im[i] = i < kk ? wi[i] : 0.0;
+  }
+  *lambda = lam;
+  return check_err(C, "Arnoldi on the Vanka-preconditioned operator");
+}
+
+// Per-level Chebyshev intervals: the fixed [cheb_lo, cheb_hi], or with
+// cheb_auto [λ_l/4, λ_l] from 20 Arnoldi steps on level l.
+int set_chebyshev_intervals(Ctx& C) {
+  for (size_t l = 1; l < C.L.size(); ++l) {
+    Level& L = C.L[l];
+    L.cheb_lo = C.opt.cheb_lo;
+    L.cheb_hi = C.opt.cheb_hi;
+    if (!C.opt.cheb_auto) continue;
+    double lam = 0.0;
+    int rc = estimate_lambda(C, L, std::min(20, C.opt.restart), nullptr, nullptr, nullptr, &lam);
+    if (rc) return rc;
+    if (!(lam > 0.0)) return fail(IRKMG_ENOCONV, "no positive Ritz value for the Chebyshev interval");
+    L.cheb_lo = 0.25 * lam;
+    L.cheb_hi = lam;
+  }
+  C.launches = 0;
   return IRKMG_OK;
 }
 
@@ -1346,6 +1443,19 @@ int irkmg_kron_split(int s, const double* A, double* T, double* Tinv, double* D)
   return IRKMG_OK;
 }
 
+int irkmg_hessenberg_eigvals(int n, const double* H, double* wr, double* wi) {
+  if (!H || !wr || !wi || n < 1 || n > 512) return fail(IRKMG_EINVAL, "bad arguments");
+  const int rc = hessenberg_eigvals(n, H, wr, wi);
+  if (rc) return fail(rc, "QR iteration did not converge");
+  return IRKMG_OK;
+}
+
+int irkmg_estimate_lambda(irkmg_ctx* C, int level, int nsteps, const double* d_x0, double* ritz_re,
+                          double* ritz_im, double* lambda) {
+  if (!level_ok(C, level) || level == 0 || !lambda) return fail(IRKMG_EINVAL, "bad level");
+  return estimate_lambda(*C, C->L[level], nsteps, d_x0, ritz_re, ritz_im, lambda);
+}
+
 int irkmg_setup(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double nu,
                 const irkmg_options* opt, irkmg_ctx** out) {
   if (!out) return fail(IRKMG_EINVAL, "null out");
@@ -1385,7 +1495,8 @@ int irkmg_update(irkmg_ctx* C, double dt, double nu) {
     if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.btall, L.hops.btall, L.dim)))
       return rc;
   }
-  return factor_all(*C);
+  if ((rc = factor_all(*C))) return rc;
+  return set_chebyshev_intervals(*C);
 }
 
 int irkmg_set_wind(irkmg_ctx* C, const double* wind) {
@@ -1418,6 +1529,8 @@ int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) 
   info->apply_ms[0] = L.apply_ms[1];
   info->apply_ms[1] = L.apply_ms[2];
   info->single_launch = level > 0 && L.kron && L.single ? 1 : 0;
+  info->cheb[0] = level > 0 ? L.cheb_lo : 0.0;
+  info->cheb[1] = level > 0 ? L.cheb_hi : 0.0;
   return IRKMG_OK;
 }
 

@@ -96,6 +96,8 @@ struct KronPlan {
   int task_mat[kKronMaxTasks], task_src[kKronMaxTasks];
 };
 int kron_split(int s, const double* A, KronSplit* out);
+// Eigenvalues of the n x n upper Hessenberg H (row-major), wr + i wi.
+int hessenberg_eigvals(int n, const double* H, double* wr, double* wi);
 int kron_plan(const KronSplit& K, int layout, KronPlan* out);
 
 // ---------------------------------------------------------------------------
@@ -154,6 +156,7 @@ struct Level {
                                        // 7 decoupled warp-specialised TMA pipeline
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   int kron_shape = 0;                  // launch shape of the staged decoupled apply (0, 1)
+  double cheb_lo = 2.0, cheb_hi = 8.0; // Chebyshev interval of this level's smoother
   // one-launch relaxation of a decoupled level: patch results to Ctx::d_Y at
   // t·Q + qoff[p] + i, then the per-DoF sum over the contribution lists
   bool single = false;
@@ -243,6 +246,7 @@ cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine
 cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n,
                          cudaStream_t st);  // y = a*x + b*y
 cudaError_t launch_fill(double* y, double v, int64_t n, cudaStream_t st);
+cudaError_t launch_fill_sin(double* y, int64_t n, cudaStream_t st);  // y_i = sin(i + 1)
 cudaError_t launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                             double* part, double* out, cudaStream_t st);
 cudaError_t launch_multiaxpy(double* w, const double* V, int64_t ldv, int k, const double* h,

@@ -299,6 +299,16 @@ cudaError_t launch_fill(double* y, double v, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void k_fill_sin(double* __restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = sin((double)(i + 1));
+}
+
+cudaError_t launch_fill_sin(double* y, int64_t n, cudaStream_t st) {
+  k_fill_sin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, n);
+  return cudaGetLastError();
+}
+
 // part[b*k + j] = partial sum over block b's contiguous chunk of V_j . w
 __global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict__ V, int64_t ldv,
                                                        int k, const double* __restrict__ w,

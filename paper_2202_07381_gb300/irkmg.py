@@ -40,7 +40,7 @@ class Options(ct.Structure):
                 ("restart", ct.c_int), ("maxit", ct.c_int), ("patch_precision", ct.c_int),
                 ("wind", ct.POINTER(ct.c_double)), ("cuda_stream", ct.c_void_p),
                 ("timeout_spins", ct.c_int64), ("apply_variant", ct.c_int),
-                ("patch_form", ct.c_int), ("patch_lu_tc", ct.c_int)]
+                ("patch_form", ct.c_int), ("cheb_auto", ct.c_int), ("patch_lu_tc", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -57,11 +57,13 @@ class LevelInfo(ct.Structure):
                                           "ncolours", "max_patch_dofs", "factor_bytes",
                                           "apply_kernel")] + [("apply_ms", ct.c_double * 2),
                                                               ("dim", ct.c_int64),
-                                                              ("single_launch", ct.c_int64)]
+                                                              ("single_launch", ct.c_int64),
+                                                              ("cheb", ct.c_double * 2)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "apply_ms"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("apply_ms", "cheb")}
         d["apply_ms"] = list(self.apply_ms)
+        d["cheb"] = list(self.cheb)
         return d
 
 
@@ -83,6 +85,8 @@ _SIGS = {
     "irkmg_radau_iia": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_gauss": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_kron_split": (ct.c_int, [ct.c_int, _P, _P, _P, _P]),
+    "irkmg_hessenberg_eigvals": (ct.c_int, [ct.c_int, _P, _P, _P]),
+    "irkmg_estimate_lambda": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, _P, _P, _P]),
     "irkmg_lobatto_iiic": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_setup": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(Tableau), ct.c_double, ct.c_double,
                                ct.POINTER(Options), ct.POINTER(_P)]),
@@ -187,6 +191,26 @@ def irkmg_kron_split(A):
     T, Ti, D = np.zeros(s * s), np.zeros(s * s), np.zeros(s * s)
     _check(lib().irkmg_kron_split(s, A.ctypes.data, T.ctypes.data, Ti.ctypes.data, D.ctypes.data))
     return T.reshape(s, s), Ti.reshape(s, s), D.reshape(s, s)
+
+
+def irkmg_hessenberg_eigvals(H):
+    """Eigenvalues (complex array) of the upper Hessenberg matrix H."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    n = H.shape[0]
+    wr, wi = np.zeros(n), np.zeros(n)
+    _check(lib().irkmg_hessenberg_eigvals(n, H.ctypes.data, wr.ctypes.data, wi.ctypes.data))
+    return wr + 1j * wi
+
+
+def irkmg_estimate_lambda(ctx, nsteps=20, x0=None, level=-1):
+    """(lambda, Ritz values) of nsteps Arnoldi steps on the level's D⁻¹J."""
+    level %= ctx.nlevels
+    wr, wi = np.zeros(nsteps), np.zeros(nsteps)
+    lam = ct.c_double()
+    px = _dptr(x0, ctx.N(level), "x0") if x0 is not None else None
+    _check(lib().irkmg_estimate_lambda(ctx.handle, level, nsteps, px, wr.ctypes.data,
+                                       wi.ctypes.data, ct.byref(lam)))
+    return lam.value, wr + 1j * wi
 
 
 def irkmg_gauss(s):

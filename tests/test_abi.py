@@ -185,3 +185,30 @@ def test_decoupled_form_needs_distinct_eigenvalues(irkmg):
     with pytest.raises(irkmg.IrkmgError) as e:
         irkmg.irkmg_setup(coords, cells, bnd, A, b, c, 0.1, 1.0, o)
     assert e.value.status == irkmg.IRKMG_EINVAL
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (5, 2), (12, 3), (30, 4)])
+def test_hessenberg_eigenvalues_match_lapack(irkmg, n, seed):
+    """The Ritz-value solver (shifted QR in complex arithmetic) on seeded
+    upper Hessenberg matrices, which have real and complex-pair eigenvalues,
+    against LAPACK's eigenvalues."""
+    rng = np.random.default_rng(seed)
+    H = np.triu(rng.standard_normal((n, n)), -1)
+    ev = irkmg.irkmg_hessenberg_eigvals(H)
+    ref = np.linalg.eigvals(H)
+    for z in ref:
+        assert np.min(np.abs(ev - z)) <= 1e-10 * max(1.0, np.abs(ref).max())
+    assert ev.imag.sum() == pytest.approx(0.0, abs=1e-9)
+
+
+def test_hessenberg_eigenvalues_special_cases(irkmg):
+    """A rotation (eigenvalues ±i), a split matrix (zero subdiagonal) and a
+    Jordan-like block with a tiny perturbation."""
+    ev = irkmg.irkmg_hessenberg_eigvals(np.array([[0.0, -1.0], [1.0, 0.0]]))
+    np.testing.assert_allclose(np.sort_complex(ev), [-1j, 1j], atol=1e-14)
+    H = np.array([[2.0, 1.0, 3.0], [0.0, 5.0, 1.0], [0.0, 4.0, 1.0]])
+    ev = irkmg.irkmg_hessenberg_eigvals(H)
+    np.testing.assert_allclose(np.sort(ev.real), np.sort(np.linalg.eigvals(H).real), atol=1e-12)
+    H = np.array([[1.0, 1.0], [1e-12, 1.0]])
+    ev = irkmg.irkmg_hessenberg_eigvals(H)
+    np.testing.assert_allclose(np.sort(ev.real), np.sort(np.linalg.eigvals(H).real), atol=1e-9)
