@@ -13,12 +13,12 @@ from tests.gpu_util import gpu_context, need_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _problem(irkmg, n0, nl, s, dt, nsteps, nu=1.0, rtol=1e-13, atol=1e-15):
+def _problem(irkmg, n0, nl, s, dt, nsteps, nu=1.0, rtol=1e-13, atol=1e-15, **kw):
     import torch
     from paper_2202_07381_gb300.adjoint import TrackingProblem
     # the residual of a solve cannot go below ~1e-16 in absolute terms, and F
     # shrinks as the steps proceed, so the test stops at max(1e-13 |F|, 1e-15)
-    ctx = gpu_context(irkmg, n0, nl, s, dt, nu=nu, rtol=rtol, atol=atol, maxit=400)
+    ctx = gpu_context(irkmg, n0, nl, s, dt, nu=nu, rtol=rtol, atol=atol, maxit=400, **kw)
     xy = irkmg.irkmg_p2_coords(ctx)
     free = irkmg.irkmg_free_nodes(ctx)
     nv = ctx.finest["nv"]
@@ -34,13 +34,16 @@ def _problem(irkmg, n0, nl, s, dt, nsteps, nu=1.0, rtol=1e-13, atol=1e-15):
     return ctx, prob, theta, (u0, p0, 0.9 * u0)
 
 
-def test_adjoint_matches_oracle_adjoint():
+@pytest.mark.parametrize("form", [0, 1], ids=["dense_patches", "decoupled_patches"])
+def test_adjoint_matches_oracle_adjoint(form):
+    """The adjoint chain (forward steps, transposed solves with transposed
+    patches, dJ/dθ and dJ/dν) with dense or decoupled patch solves."""
     irkmg = need_gpu()
     import torch
     from oracle import adjoint as oadj, mesh as M, problem, tableau
     from paper_2202_07381_gb300.adjoint import tracking_objective
     n0, nl, s, dt, nsteps = 2, 3, 2, 1 / 32, 4
-    ctx, prob, theta, (u0, p0, ut) = _problem(irkmg, n0, nl, s, dt, nsteps)
+    ctx, prob, theta, (u0, p0, ut) = _problem(irkmg, n0, nl, s, dt, nsteps, patch_form=form)
     th = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
     nu = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
     J = tracking_objective(th, nu, prob)
