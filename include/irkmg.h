@@ -335,6 +335,38 @@ int irkmg_batch_solve(irkmg_batch *batch, const double *const *d_F, double *cons
                       irkmg_stats *stats);
 void irkmg_batch_destroy(irkmg_batch *batch);
 
+/* ---- Navier–Stokes: Newton on the stage equations (Section 3.2) ---------
+ * With U_t = u^n + dt Σ_j a_tj k_j and P_t = p^n + dt Σ_j a_tj k_j^p the stage
+ * residual is F_t = [ M k_t + N(U_t) + K U_t + B P_t − M f_t ; Bᵀ U_t ], N(U) =
+ * C(U) U the discrete <u·∇u, v>.  Its Jacobian has the velocity blocks
+ * δ_tu M + dt a_tu (K + C(U_t) + R(U_t)), R(w)_dc = ∫ φ_a φ_b ∂w_d/∂x_c, which
+ * depend on the row stage and couple the components: dense patches only
+ * (patch_form 0), 2D, no frozen wind. */
+typedef struct {
+  int newton_iters;        /* Newton steps taken                                    */
+  int linear_iters;        /* FGMRES iterations over all Newton steps               */
+  int status;
+  double f0, ffinal;       /* ||F(k0)||, ||F(k)|| at the end                         */
+  double t_solve;          /* seconds                                               */
+} irkmg_ns_stats;
+
+/* Set the Newton blocks for the stage velocities U (host, s x 2 x np2: stage,
+ * component, finest P2 node, Dirichlet values included) on every level
+ * (injected to coarse levels), refactor the patches and the coarsest solve. */
+int irkmg_ns_set_state(irkmg_ctx *ctx, const double *U);
+/* F(k) on the finest level for the state last set (that of k): u^n at every
+ * P2 node (2·np2), p^n, f (s·2·np2 nodal forcing), k and F (N each). */
+int irkmg_ns_residual(irkmg_ctx *ctx, const double *d_un_all, const double *d_pn,
+                      const double *d_f, const double *d_k, double *d_F);
+/* Inexact Newton from the guess in d_k (e.g. the previous step's stages,
+ * Section 3.2) until ||F|| <= atol or maxit steps: each step sets the state,
+ * forms F and solves J δ = −F by the preconditioned FGMRES to the relative
+ * tolerance of Eisenstat and Walker's choice 2 (γ = 0.9, α = 2, safeguard,
+ * η ≤ 0.9, η_0 = 0.5).  IRKMG_ENOCONV if maxit is reached. */
+int irkmg_ns_newton(irkmg_ctx *ctx, const double *d_un_all, const double *d_pn,
+                    const double *d_f, double *d_k, double atol, int maxit,
+                    irkmg_ns_stats *stats);
+
 /* ---- forcing control and the discrete adjoint (differentiation of the
  * Section 3.1 time stepping; the paper does not differentiate) ------------- */
 

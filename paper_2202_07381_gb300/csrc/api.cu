@@ -172,6 +172,8 @@ int trace_pair(Ctx& C, int cls, double bytes, cudaEvent_t* a, cudaEvent_t* b,
 
 // Stage operator (r = F - J x, or y = J x when F is null), counted and traced.
 int op(Ctx& C, Level& L, const double* F, const double* x, double* r, int tr) {
+  if (tr && C.ns && C.ns_active)
+    return fail(IRKMG_ENOTIMPL, "transposed Navier-Stokes Newton operator");
   const bool timed = C.trace_on && &L == &C.L.back();
   cudaEvent_t a = nullptr, b = nullptr;
   if (timed) {
@@ -867,6 +869,7 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
 }
 
 int set_chebyshev_intervals(Ctx& C);
+void drop_graphs(Ctx& C);
 int estimate_lambda(Ctx& C, Level& L, int k, const double* x0, double* ritz_re, double* ritz_im,
                     double* lambda);
 
@@ -1133,6 +1136,146 @@ int set_chebyshev_intervals(Ctx& C) {
     L.cheb_hi = lam;
   }
   C.launches = 0;
+  return IRKMG_OK;
+}
+
+// --- Navier-Stokes: Newton on the stage equations (Section 3.2) ------------
+// U: host, s x 2 x np2 (stage, component, finest P2 node), the stage
+// velocities U_t = u^n + dt sum_j a_tj k_j at every node.  Every level gets
+// the Newton blocks W_t,dc = delta_dc C(U_t) + R_dc(U_t) of its injected
+// U_t (coarse P2 nodes are fine vertices with the same ids), the finest level
+// also g_t = C(U_t) U_t, and the patches and the coarsest solve are
+// refactored with them.
+int ns_set_state(Ctx& C, const double* U) {
+  const int nl = (int)C.L.size();
+  const int64_t np2f = C.L.back().np2;
+  std::vector<double> Ut;
+  std::vector<double> W[4], g;
+  for (int l = 0; l < nl; ++l) {
+    Level& L = C.L[l];
+    for (int t = 0; t < C.s; ++t) {
+      Ut.assign(2 * L.np2, 0.0);
+      for (int64_t n = 0; n < L.np2; ++n)
+        for (int d = 0; d < 2; ++d) Ut[2 * n + d] = U[(int64_t)t * 2 * np2f + d * np2f + n];
+      assemble_ns_blocks(L.mesh, L.hops.vel, Ut.data(), W, g);
+      for (int k = 0; k < 4; ++k) {
+        HostCSR one;
+        one.nrows = L.hops.vel.nrows;
+        one.ncols = L.hops.vel.ncols;
+        one.ptr = L.hops.vel.ptr;
+        one.col = L.hops.vel.col;
+        one.v[0] = W[k];
+        HostSELL S = to_sell(one, 1);
+        int rc;
+        if (!L.d_ns_csr[t][k]) {
+          if ((rc = dalloc(C, &L.d_ns_csr[t][k], W[k].size()))) return rc;
+          if ((rc = dalloc(C, &L.d_ns_sell[t][k], S.v[0].size()))) return rc;
+        }
+        CK(cudaMemcpy(L.d_ns_csr[t][k], W[k].data(), sizeof(double) * W[k].size(),
+                      cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(L.d_ns_sell[t][k], S.v[0].data(), sizeof(double) * S.v[0].size(),
+                      cudaMemcpyHostToDevice));
+      }
+      if (l == nl - 1) {
+        int rc;
+        if (!C.d_ns_g && (rc = dalloc(C, &C.d_ns_g, (size_t)C.s * 2 * L.nf))) return rc;
+        CK(cudaMemcpy(C.d_ns_g + (int64_t)t * 2 * L.nf, g.data(), sizeof(double) * g.size(),
+                      cudaMemcpyHostToDevice));
+      }
+    }
+  }
+  C.ns = true;
+  drop_graphs(C);
+  int rc;
+  if ((rc = factor_all(C))) return rc;
+  return set_chebyshev_intervals(C);
+}
+
+// Newton residual of the stage equations at k (finest level):
+// F = J_S k - R_S + g with J_S the Stokes stage operator, R_S the stage
+// right-hand side with u^n at every node and g = C(U_t) U_t from the state
+// last set (which must be that of k).
+int ns_residual(Ctx& C, const double* un_all, const double* pn, const double* f, const double* k,
+                double* F) {
+  Level& L = C.L.back();
+  double* tmp = C.d_w;
+  CK(launch_stage_rhs_full(C, un_all, pn, f, tmp));
+  C.ns_active = false;
+  cudaError_t e = launch_residual(C, L, tmp, k, F, 0);  // F = R_S - J_S k
+  C.ns_active = true;
+  CK(e);
+  CK(launch_axpby(F, F, -1.0, 0.0, L.N, C.stream));
+  for (int t = 0; t < C.s; ++t)
+    CK(launch_axpby(F + (int64_t)t * L.m, C.d_ns_g + (int64_t)t * 2 * L.nf, 1.0, 1.0, 2 * L.nf,
+                    C.stream));
+  C.launches += 3 + C.s;
+  return IRKMG_OK;
+}
+
+// Eisenstat–Walker forcing term, choice 2 (gamma 0.9, alpha 2) with its
+// safeguard and the cap 0.9.
+double ew_eta(double eta_prev, double fn, double fprev) {
+  double eta = 0.9 * (fn / fprev) * (fn / fprev);
+  const double safe = 0.9 * eta_prev * eta_prev;
+  if (safe > 0.1) eta = std::max(eta, safe);
+  return std::min(eta, 0.9);
+}
+
+int ns_newton(Ctx& C, const double* un_all, const double* pn, const double* f, double* k,
+              double atol, int maxit, irkmg_ns_stats* st) {
+  const double t0 = now();
+  Level& L = C.L.back();
+  const int64_t np2 = L.np2, nf = L.nf, N = L.N;
+  std::vector<double> hu(2 * np2), hk(N), U((size_t)C.s * 2 * np2);
+  CK(cudaMemcpyAsync(hu.data(), un_all, sizeof(double) * 2 * np2, cudaMemcpyDeviceToHost, C.stream));
+  double* Fb = C.d_F;
+  double* db = C.d_kb;
+  double eta = 0.5, fprev = 0.0, fn = 0.0;
+  int its = 0, lin = 0, rc;
+  for (;; ++its) {
+    CK(cudaMemcpyAsync(hk.data(), k, sizeof(double) * N, cudaMemcpyDeviceToHost, C.stream));
+    CK(cudaStreamSynchronize(C.stream));
+    for (int t = 0; t < C.s; ++t)
+      for (int d = 0; d < 2; ++d) {
+        double* Ut = U.data() + ((int64_t)t * 2 + d) * np2;
+        std::copy(hu.begin() + d * np2, hu.begin() + (d + 1) * np2, Ut);
+        for (int j = 0; j < C.s; ++j) {
+          const double a = C.dt * C.A[t * C.s + j];
+          const double* kj = hk.data() + (int64_t)j * L.m + d * nf;
+          for (int64_t i = 0; i < nf; ++i) Ut[L.mesh.free_to_p2[i]] += a * kj[i];
+        }
+      }
+    if ((rc = ns_set_state(C, U.data()))) return rc;
+    if ((rc = ns_residual(C, un_all, pn, f, k, Fb))) return rc;
+    CK(launch_multidot(Fb, 0, 1, Fb, N, C.d_part, C.d_h + 192, C.stream));
+    CK(cudaMemcpyAsync(C.h_h + 192, C.d_h + 192, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
+    CK(cudaStreamSynchronize(C.stream));
+    fn = std::sqrt(C.h_h[192]);
+    if (st && its == 0) st->f0 = fn;
+    if (fn <= atol || its >= maxit) break;
+    if (its > 0) eta = ew_eta(eta, fn, fprev);
+    fprev = fn;
+    // J δ = -F to the relative tolerance eta
+    CK(launch_axpby(Fb, Fb, -1.0, 0.0, N, C.stream));
+    CK(cudaMemsetAsync(db, 0, sizeof(double) * N, C.stream));
+    const double rtol = C.opt.rtol;
+    C.opt.rtol = eta;
+    irkmg_stats ls{};
+    rc = fgmres(C, Fb, db, &ls, 0);
+    C.opt.rtol = rtol;
+    lin += ls.iters;
+    if (rc && rc != IRKMG_ENOCONV) return rc;
+    CK(launch_axpby(k, db, 1.0, 1.0, N, C.stream));
+  }
+  const int status = fn <= atol ? IRKMG_OK : IRKMG_ENOCONV;
+  if (st) {
+    st->newton_iters = its;
+    st->linear_iters = lin;
+    st->ffinal = fn;
+    st->status = status;
+    st->t_solve = now() - t0;
+  }
+  if (status) return fail(status, "Newton reached maxit on the Navier-Stokes stage equations");
   return IRKMG_OK;
 }
 
@@ -1632,6 +1775,40 @@ int irkmg_vcycle(irkmg_ctx* C, const double* r, double* z, int transpose) {
 int irkmg_solve(irkmg_ctx* C, const double* F, double* k, irkmg_stats* st) {
   if (!C || !F || !k) return fail(IRKMG_EINVAL, "bad arguments");
   return fgmres(*C, F, k, st, 0);
+}
+
+int ns_check(irkmg_ctx* C) {
+  if (!C) return fail(IRKMG_EINVAL, "null ctx");
+  if (C->dim != 2) return fail(IRKMG_ENOTIMPL, "Navier-Stokes stages are built for 2D");
+  if (C->kron) return fail(IRKMG_ENOTIMPL, "Newton blocks depend on the stage: dense patches only");
+  if (!C->wind.empty()) return fail(IRKMG_EINVAL, "a frozen Oseen wind and Newton blocks exclude each other");
+  return IRKMG_OK;
+}
+
+int irkmg_ns_set_state(irkmg_ctx* C, const double* U) {
+  int rc = ns_check(C);
+  if (rc) return rc;
+  if (!U) return fail(IRKMG_EINVAL, "null state");
+  CK(C->stream ? cudaStreamSynchronize(C->stream) : cudaDeviceSynchronize());
+  return ns_set_state(*C, U);
+}
+
+int irkmg_ns_residual(irkmg_ctx* C, const double* un_all, const double* pn, const double* f,
+                      const double* k, double* F) {
+  int rc = ns_check(C);
+  if (rc) return rc;
+  if (!C->ns) return fail(IRKMG_EINVAL, "irkmg_ns_set_state first");
+  if (!un_all || !pn || !f || !k || !F) return fail(IRKMG_EINVAL, "bad arguments");
+  return ns_residual(*C, un_all, pn, f, k, F);
+}
+
+int irkmg_ns_newton(irkmg_ctx* C, const double* un_all, const double* pn, const double* f,
+                    double* k, double atol, int maxit, irkmg_ns_stats* st) {
+  int rc = ns_check(C);
+  if (rc) return rc;
+  if (!un_all || !pn || !f || !k || !(atol > 0.0) || maxit < 1)
+    return fail(IRKMG_EINVAL, "bad arguments");
+  return ns_newton(*C, un_all, pn, f, k, atol, maxit, st);
 }
 
 int irkmg_adjoint_solve(irkmg_ctx* C, const double* G, double* lam, irkmg_stats* st) {

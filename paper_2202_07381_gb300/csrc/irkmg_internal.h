@@ -67,6 +67,10 @@ struct HostOps {
 void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& ops);
 
 void assemble_cell_load(const HostMesh& m, HostCSR& C);
+// Newton blocks of the convection at the nodal velocity U (2D): W[2d + c] on
+// the pattern V (free x free) and g = C(U) U on the free rows.
+void assemble_ns_blocks(const HostMesh& m, const HostCSR& V, const double* U,
+                        std::vector<double> W[4], std::vector<double>& g);
 
 // Radau IIA closed forms.
 int radau_iia(int s, double* A, double* b, double* c);
@@ -168,6 +172,10 @@ struct Level {
   int ws_cap[2] = {0, 0};              // resident CTAs of the warp-specialised apply
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
+  // Navier-Stokes Newton blocks W_t,dc per stage (2D): CSR-ordered on the
+  // velocity pattern (gathers, coarse build) and SELL-ordered (stage operator)
+  double* d_ns_csr[3][4] = {{nullptr}};
+  double* d_ns_sell[3][4] = {{nullptr}};
   // algorithmic bytes for tracing
   std::vector<double> colour_bytes, colour_flops;
   double op_bytes = 0.0, op_flops = 0.0;
@@ -182,6 +190,9 @@ struct Ctx {
   KronPlan kplan{};
   bool kron = false;          // decoupled patch solves requested and the tableau splits
   double* d_Y = nullptr;      // s · max Q patch results of the one-launch relaxation
+  bool ns = false;            // Navier-Stokes Newton blocks set (irkmg_ns_set_state)
+  bool ns_active = true;      // ... and included in the stage operator (off: Stokes part)
+  double* d_ns_g = nullptr;   // s x 2 nf: C(U_i) U_i on the finest free rows
   cudaStream_t stream = nullptr;
   std::vector<double> wind;  // finest-level nodal wind (empty for Stokes)
   std::vector<Level> L;

@@ -24,6 +24,8 @@ struct CoarseBuild {
   const int32_t *btptr, *btcol;
   const double *BTx, *BTy;
   const double *Bz, *BTz;
+  const double* W[3][4];  // Navier-Stokes Newton blocks per stage (CSR), 2D
+  int ns_on;
 };
 
 // One thread per (stage t, row of the single-stage operator).
@@ -41,8 +43,12 @@ __global__ void k_coarse_build(CoarseBuild P, double* __restrict__ D) {
       double* Drow = D + (t * P.m + d * P.nf + row) * P.n;
       for (int32_t p = P.vptr[row]; p < P.vptr[row + 1]; ++p) {
         const int32_t j = P.vcol[p];
-        for (int u = 0; u < P.s; ++u)
-          Drow[u * P.m + d * P.nf + j] = (t == u ? P.M[p] : 0.0) + P.mix[t * 3 + u] * P.K[p];
+        for (int u = 0; u < P.s; ++u) {
+          Drow[u * P.m + d * P.nf + j] += (t == u ? P.M[p] : 0.0) + P.mix[t * 3 + u] * P.K[p];
+          if (P.ns_on)
+            for (int c = 0; c < 2; ++c)
+              Drow[u * P.m + c * P.nf + j] += P.mix[t * 3 + u] * P.W[t][2 * d + c][p];
+        }
       }
       for (int32_t p = P.bptr[row]; p < P.bptr[row + 1]; ++p) {
         const int32_t vtx = P.bcol[p];
@@ -90,6 +96,9 @@ cudaError_t launch_coarse_build(Ctx& C, double* dense) {
   P.btcol = L.bt.col;
   P.BTx = L.bt.v[0];
   P.BTy = L.bt.v[1];
+  P.ns_on = C.ns ? 1 : 0;
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 4; ++k) P.W[i][k] = L.d_ns_csr[i][k];
   cudaError_t e = cudaMemsetAsync(dense, 0, sizeof(double) * C.nb * C.nb, C.stream);
   if (e != cudaSuccess) return e;
   const int64_t thr = C.s * (L.nf + L.nv);

@@ -30,6 +30,10 @@ struct OpParams {
   const int64_t *svp, *sbp, *sbtp;
   const int32_t *svc, *sbc, *sbtc;
   const double *sM, *sK, *sBx, *sBy, *sBTx, *sBTy, *sBz, *sBTz;
+  // Navier-Stokes Newton blocks (2D): SELL copies of W_i,dc per stage i, added
+  // as y_i,d += sum_c W_i,dc z_i,c with z_i = sum_t mix[i][t] x_t (null: off)
+  const double* sW[3][4];
+  int ns_on;
 };
 
 // The stage operator on SELL-32 storage: threads [0, nf_pad) take velocity
@@ -54,17 +58,39 @@ __global__ void __launch_bounds__(256) k_residual_sell(OpParams P, const double*
       for (int c = 0; c < D; ++c) am[t][c] = ak[t][c] = 0.0;
     const int64_t sl = row >> 5, lane = row & 31;
     const int64_t b0 = P.svp[sl], b1 = P.svp[sl + 1];
+    double an[S][D];
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+#pragma unroll
+      for (int c = 0; c < D; ++c) an[t][c] = 0.0;
     for (int64_t e = b0 + lane; e < b1; e += 32) {
       const int32_t j = P.svc[e];
       const double mv = P.sM[e], kv = P.sK[e];
+      double xv[S][D];
 #pragma unroll
       for (int t = 0; t < S; ++t)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          const double xv = x[t * m + c * nf + j];
-          am[t][c] = fma(mv, xv, am[t][c]);
-          ak[t][c] = fma(kv, xv, ak[t][c]);
+          xv[t][c] = x[t * m + c * nf + j];
+          am[t][c] = fma(mv, xv[t][c], am[t][c]);
+          ak[t][c] = fma(kv, xv[t][c], ak[t][c]);
         }
+      if (D == 2 && P.ns_on) {
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          double z[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            z[c] = 0.0;
+#pragma unroll
+            for (int t = 0; t < S; ++t) z[c] = fma(P.mix[i * 3 + t], xv[t][c], z[c]);
+          }
+#pragma unroll
+          for (int d = 0; d < D; ++d)
+#pragma unroll
+            for (int c = 0; c < D; ++c) an[i][d] = fma(P.sW[i][2 * d + c][e], z[c], an[i][d]);
+        }
+      }
     }
     const int64_t c0 = P.sbp[sl], c1 = P.sbp[sl + 1];
     for (int64_t e = c0 + lane; e < c1; e += 32) {
@@ -83,7 +109,7 @@ __global__ void __launch_bounds__(256) k_residual_sell(OpParams P, const double*
     for (int i = 0; i < S; ++i)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        double y = am[i][c];
+        double y = am[i][c] + an[i][c];
 #pragma unroll
         for (int t = 0; t < S; ++t) y = fma(P.mix[i * 3 + t], ak[t][c], y);
         const int64_t g = i * m + c * nf + row;
@@ -154,6 +180,9 @@ static OpParams op_params(Ctx& C, Level& L, int transpose) {
   P.sBz = L.sb.v[2];
   P.sBTz = L.sbt.v[2];
   P.Bz = L.b.v[2];
+  P.ns_on = (C.ns && C.ns_active && !transpose) ? 1 : 0;
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 4; ++k) P.sW[i][k] = L.d_ns_sell[i][k];
   return P;
 }
 

@@ -217,6 +217,10 @@ struct InvParams {
   const int32_t *bptr, *bcol;
   const double *Bx, *By, *Bz;
   int* err;  // [0] status, [1] patch id
+  // Navier-Stokes Newton blocks (2D): CSR copies of W_t,dc per stage t; the
+  // velocity block (t, u) gains dt a_tu W_t,dd' (null / ns_on = 0: off)
+  const double* W[3][4];
+  int ns_on;
 };
 
 // Shared-memory scratch of one patch inversion.
@@ -258,6 +262,12 @@ __device__ void patch_build_invert(const InvParams& P, int32_t v, int L, double*
       for (int u = 0; u < P.s; ++u) {
         const double val = (t == u ? mab : 0.0) + P.dt * P.A[t * 3 + u] * kab;
         for (int d = 0; d < D; ++d) A[(t * q + d * L + a) * np + (u * q + d * L + b)] = val;
+        if (P.ns_on && D == 2 && pos < p1 && P.vcol[pos] == cb) {
+          const double f = P.dt * P.A[t * 3 + u];
+          for (int d = 0; d < 2; ++d)
+            for (int c = 0; c < 2; ++c)
+              A[(t * q + d * L + a) * np + (u * q + c * L + b)] += f * P.W[t][2 * d + c][pos];
+        }
       }
   }
   // velocity-pressure and pressure-velocity blocks
@@ -450,6 +460,9 @@ cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
   P.Bx = L.b.v[0];
   P.By = L.b.v[1];
   P.err = C.d_err;
+  P.ns_on = C.ns ? 1 : 0;
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 4; ++k) P.W[i][k] = L.d_ns_csr[i][k];
   const size_t smem = (size_t)L.max_np * L.max_np * sizeof(double);
   if (precision == 64) {
     cudaFuncSetAttribute(k_patch_invert<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,

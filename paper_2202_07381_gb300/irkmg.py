@@ -67,6 +67,14 @@ class LevelInfo(ct.Structure):
         return d
 
 
+class NSStats(ct.Structure):
+    _fields_ = [("newton_iters", ct.c_int), ("linear_iters", ct.c_int), ("status", ct.c_int),
+                ("f0", ct.c_double), ("ffinal", ct.c_double), ("t_solve", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Trace(ct.Structure):
     _fields_ = [("launches", ct.c_int64), ("vanka_launches", ct.c_int64), ("vanka_ms", ct.c_double),
                 ("vanka_bytes", ct.c_double), ("op_launches", ct.c_int64), ("op_ms", ct.c_double),
@@ -86,6 +94,9 @@ _SIGS = {
     "irkmg_gauss": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_kron_split": (ct.c_int, [ct.c_int, _P, _P, _P, _P]),
     "irkmg_hessenberg_eigvals": (ct.c_int, [ct.c_int, _P, _P, _P]),
+    "irkmg_ns_set_state": (ct.c_int, [_P, _P]),
+    "irkmg_ns_residual": (ct.c_int, [_P, _P, _P, _P, _P, _P]),
+    "irkmg_ns_newton": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_double, ct.c_int, _P]),
     "irkmg_estimate_lambda": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, _P, _P, _P]),
     "irkmg_lobatto_iiic": (ct.c_int, [ct.c_int, _P, _P, _P]),
     "irkmg_setup": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(Tableau), ct.c_double, ct.c_double,
@@ -211,6 +222,34 @@ def irkmg_estimate_lambda(ctx, nsteps=20, x0=None, level=-1):
     _check(lib().irkmg_estimate_lambda(ctx.handle, level, nsteps, px, wr.ctypes.data,
                                        wi.ctypes.data, ct.byref(lam)))
     return lam.value, wr + 1j * wi
+
+
+def irkmg_ns_set_state(ctx, U):
+    """Newton blocks for the stage velocities U (host array s x 2 x np2)."""
+    L = ctx.finest
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    if U.shape != (ctx.s, 2, L["np2"]):
+        raise ValueError(f"U: expected shape {(ctx.s, 2, L['np2'])}")
+    _check(lib().irkmg_ns_set_state(ctx.handle, U.ctypes.data))
+
+
+def irkmg_ns_residual(ctx, un_all, pn, f, k, F):
+    L = ctx.finest
+    _check(lib().irkmg_ns_residual(ctx.handle, _dptr(un_all, 2 * L["np2"], "un_all"),
+                                   _dptr(pn, L["nv"], "pn"), _dptr(f, ctx.s * 2 * L["np2"], "f"),
+                                   _dptr(k, L["N"], "k"), _dptr(F, L["N"], "F")))
+
+
+def irkmg_ns_newton(ctx, un_all, pn, f, k, atol=1e-10, maxit=20, raise_on_noconv=True):
+    """Inexact Newton on the Navier-Stokes stage equations from the guess in k."""
+    L = ctx.finest
+    st = NSStats()
+    rc = lib().irkmg_ns_newton(ctx.handle, _dptr(un_all, 2 * L["np2"], "un_all"),
+                               _dptr(pn, L["nv"], "pn"), _dptr(f, ctx.s * 2 * L["np2"], "f"),
+                               _dptr(k, L["N"], "k"), float(atol), int(maxit), ct.byref(st))
+    if not (rc == IRKMG_ENOCONV and not raise_on_noconv):
+        _check(rc)
+    return st.as_dict()
 
 
 def irkmg_gauss(s):
