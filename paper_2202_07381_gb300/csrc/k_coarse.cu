@@ -72,7 +72,7 @@ __global__ void k_coarse_build(CoarseBuild P, double* __restrict__ D) {
 
 cudaError_t launch_coarse_build(Ctx& C, double* dense) {
   Level& L = C.L[0];
-  CoarseBuild P;
+  CoarseBuild P{};
   P.s = C.s;
   P.dim = L.dim;
   P.Bz = L.b.v[2];

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_residual_sell(OpParams P, const double*
 }
 
 static OpParams op_params(Ctx& C, Level& L, int transpose) {
-  OpParams P;
+  OpParams P{};
   P.nf = L.nf;
   P.nv = L.nv;
   P.m = L.m;
@@ -255,7 +255,7 @@ __global__ void k_transfer(XferParams P, const double* __restrict__ in, double* 
 
 cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coarse) {
   Level& Lc = *(&Lf - 1);
-  XferParams P;
+  XferParams P{};
   P.s = C.s;
   P.dim = Lf.dim;
   P.nf_out = Lc.nf;
@@ -276,7 +276,7 @@ cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coars
 
 cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine, int add) {
   Level& Lc = *(&Lf - 1);
-  XferParams P;
+  XferParams P{};
   P.s = C.s;
   P.dim = Lf.dim;
   P.nf_out = Lf.nf;

@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) k_patch_invert_kron(InvParams P, KronPlan
 }
 
 cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
-  InvParams P;
+  InvParams P{};
   P.s = C.s;
   P.dim = L.dim;
   P.Bz = L.b.v[2];
@@ -477,7 +477,7 @@ cudaError_t launch_patch_invert(Ctx& C, Level& L, int precision) {
 }
 
 cudaError_t launch_patch_invert_kron(Ctx& C, Level& L) {
-  InvParams P;
+  InvParams P{};
   P.s = C.s;
   P.dim = L.dim;
   P.Bz = L.b.v[2];
@@ -867,7 +867,7 @@ bool vanka_staged_fits(Ctx& C, Level& L) {
 
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                          int transpose) {
-  ApplyParams P;
+  ApplyParams P{};
   P.s = C.s;
   P.dim = L.dim;
   P.nf = L.nf;
@@ -886,7 +886,7 @@ cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* 
   const int prec = C.opt.patch_precision;
   StagedShape shp;
   if (!transpose && L.apply_kernel == 1 && staged_config(L.max_np, prec, &shp)) {
-    StagedParams S;
+    StagedParams S{};
     S.a = P;
     S.stages = shp.stages;
     S.stage_bytes = shp.stage_bytes;

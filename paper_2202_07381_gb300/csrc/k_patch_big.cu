@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(kBigThreads) k_vanka_apply_big(BigParams P, co
 }
 
 static BigParams big_params(Ctx& C, Level& L) {
-  BigParams P;
+  BigParams P{};
   P.s = C.s;
   P.dim = L.dim;
   P.tc = C.opt.patch_lu_tc;

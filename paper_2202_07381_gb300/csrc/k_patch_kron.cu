@@ -789,7 +789,7 @@ cudaError_t launch_kron_t(const KronApply& P, const T* fac, int R, unsigned grid
 cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, double* out,
                               double scale, int transpose) {
   const KronPlan& K = C.kplan;
-  KronApply P;
+  KronApply P{};
   P.s = C.s;
   P.ns = K.ns;
   P.nt = K.nt;
@@ -833,7 +833,7 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   if (L.apply_kernel == 7) {
     WsShape wsh;
     if (!kron_ws_config(K, L.kron_nmax, prec, &wsh)) return cudaErrorInvalidConfiguration;
-    KronWs W;
+    KronWs W{};
     W.a = P;
     W.stages = wsh.stages;
     W.stage_bytes = wsh.stage_bytes;
@@ -863,7 +863,7 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   }
   KronShape shp;
   if (L.apply_kernel == 5 && kron_staged_config(K, L.kron_nmax, prec, L.kron_shape, &shp)) {
-    KronStaged S;
+    KronStaged S{};
     S.a = P;
     S.stages = shp.stages;
     S.stage_bytes = shp.stage_bytes;
