@@ -1140,49 +1140,66 @@ int set_chebyshev_intervals(Ctx& C) {
 }
 
 // --- Navier-Stokes: Newton on the stage equations (Section 3.2) ------------
-// U: host, s x 2 x np2 (stage, component, finest P2 node), the stage
-// velocities U_t = u^n + dt sum_j a_tj k_j at every node.  Every level gets
-// the Newton blocks W_t,dc = delta_dc C(U_t) + R_dc(U_t) of its injected
-// U_t (coarse P2 nodes are fine vertices with the same ids), the finest level
-// also g_t = C(U_t) U_t, and the patches and the coarsest solve are
-// refactored with them.
-int ns_set_state(Ctx& C, const double* U) {
+// Once per context: the topology the GPU assembly of the Newton blocks needs
+// on every level (vertex coordinates, P2 node -> cells, free -> P2 node), the
+// SELL slot of every velocity CSR entry, and the block storage.
+int ns_prepare(Ctx& C) {
+  if (C.d_ns_U) return IRKMG_OK;
+  int rc;
+  for (Level& L : C.L) {
+    const HostMesh& m = L.mesh;
+    if (!L.d_cells && (rc = upload(C, &L.d_cells, m.cells))) return rc;
+    if (!L.d_cell_edges && (rc = upload(C, &L.d_cell_edges, m.cell_edges))) return rc;
+    if (!L.d_p2_to_free && (rc = upload(C, &L.d_p2_to_free, m.p2_to_free))) return rc;
+    if ((rc = upload(C, &L.d_xy, m.xy))) return rc;
+    if ((rc = upload(C, &L.d_free_to_p2, m.free_to_p2))) return rc;
+    std::vector<int32_t> ptr(m.np2 + 1, 0), idx;
+    for (int64_t c = 0; c < m.nc; ++c) {
+      for (int i = 0; i < 3; ++i) ptr[m.cells[3 * c + i] + 1]++;
+      for (int i = 0; i < 3; ++i) ptr[m.nv + m.cell_edges[3 * c + i] + 1]++;
+    }
+    for (int64_t n = 0; n < m.np2; ++n) ptr[n + 1] += ptr[n];
+    idx.resize(ptr[m.np2]);
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t c = 0; c < m.nc; ++c) {
+      for (int i = 0; i < 3; ++i) idx[fill[m.cells[3 * c + i]]++] = (int32_t)c;
+      for (int i = 0; i < 3; ++i) idx[fill[m.nv + m.cell_edges[3 * c + i]]++] = (int32_t)c;
+    }
+    if ((rc = upload(C, &L.d_nc_ptr, ptr))) return rc;
+    if ((rc = upload(C, &L.d_nc_idx, idx))) return rc;
+    const HostCSR& V = L.hops.vel;
+    std::vector<int64_t> perm(V.col.size());
+    HostSELL S = to_sell(V, 0);
+    for (int64_t r = 0; r < V.nrows; ++r)
+      for (int32_t p = V.ptr[r]; p < V.ptr[r + 1]; ++p)
+        perm[p] = S.ptr[r / 32] + r % 32 + 32 * (int64_t)(p - V.ptr[r]);
+    if ((rc = upload(C, &L.d_sell_perm, perm))) return rc;
+    for (int t = 0; t < C.s; ++t)
+      for (int k = 0; k < 4; ++k) {
+        if ((rc = dalloc(C, &L.d_ns_csr[t][k], V.col.size()))) return rc;
+        if ((rc = dalloc(C, &L.d_ns_sell[t][k], S.col.size()))) return rc;
+        CK(cudaMemsetAsync(L.d_ns_sell[t][k], 0, sizeof(double) * S.col.size(), C.stream));
+      }
+  }
+  Level& F = C.L.back();
+  if ((rc = dalloc(C, &C.d_ns_g, (size_t)C.s * 2 * F.nf))) return rc;
+  if ((rc = dalloc(C, &C.d_ns_U, (size_t)C.s * 2 * F.np2))) return rc;
+  return IRKMG_OK;
+}
+
+// Newton blocks W_t,dc = δ_dc C(U_t) + R_dc(U_t) on every level from the stage
+// velocities in C.d_ns_U (finest P2 nodes; a coarse level's P2 nodes are the
+// first ones of the finer level, with the same ids, so its U is a prefix),
+// g_t = C(U_t) U_t on the finest level, then the patches and the coarsest
+// solve are refactored with them.  All on the GPU.
+int ns_set_state(Ctx& C) {
   const int nl = (int)C.L.size();
   const int64_t np2f = C.L.back().np2;
-  std::vector<double> Ut;
-  std::vector<double> W[4], g;
   for (int l = 0; l < nl; ++l) {
     Level& L = C.L[l];
-    for (int t = 0; t < C.s; ++t) {
-      Ut.assign(2 * L.np2, 0.0);
-      for (int64_t n = 0; n < L.np2; ++n)
-        for (int d = 0; d < 2; ++d) Ut[2 * n + d] = U[(int64_t)t * 2 * np2f + d * np2f + n];
-      assemble_ns_blocks(L.mesh, L.hops.vel, Ut.data(), W, g);
-      for (int k = 0; k < 4; ++k) {
-        HostCSR one;
-        one.nrows = L.hops.vel.nrows;
-        one.ncols = L.hops.vel.ncols;
-        one.ptr = L.hops.vel.ptr;
-        one.col = L.hops.vel.col;
-        one.v[0] = W[k];
-        HostSELL S = to_sell(one, 1);
-        int rc;
-        if (!L.d_ns_csr[t][k]) {
-          if ((rc = dalloc(C, &L.d_ns_csr[t][k], W[k].size()))) return rc;
-          if ((rc = dalloc(C, &L.d_ns_sell[t][k], S.v[0].size()))) return rc;
-        }
-        CK(cudaMemcpy(L.d_ns_csr[t][k], W[k].data(), sizeof(double) * W[k].size(),
-                      cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(L.d_ns_sell[t][k], S.v[0].data(), sizeof(double) * S.v[0].size(),
-                      cudaMemcpyHostToDevice));
-      }
-      if (l == nl - 1) {
-        int rc;
-        if (!C.d_ns_g && (rc = dalloc(C, &C.d_ns_g, (size_t)C.s * 2 * L.nf))) return rc;
-        CK(cudaMemcpy(C.d_ns_g + (int64_t)t * 2 * L.nf, g.data(), sizeof(double) * g.size(),
-                      cudaMemcpyHostToDevice));
-      }
-    }
+    for (int t = 0; t < C.s; ++t)
+      CK(launch_ns_assemble(C, L, t, C.d_ns_U + (int64_t)t * 2 * np2f, np2f,
+                            l == nl - 1 ? C.d_ns_g + (int64_t)t * 2 * L.nf : nullptr));
   }
   C.ns = true;
   drop_graphs(C);
@@ -1224,28 +1241,16 @@ double ew_eta(double eta_prev, double fn, double fprev) {
 int ns_newton(Ctx& C, const double* un_all, const double* pn, const double* f, double* k,
               double atol, int maxit, irkmg_ns_stats* st) {
   const double t0 = now();
-  Level& L = C.L.back();
-  const int64_t np2 = L.np2, nf = L.nf, N = L.N;
-  std::vector<double> hu(2 * np2), hk(N), U((size_t)C.s * 2 * np2);
-  CK(cudaMemcpyAsync(hu.data(), un_all, sizeof(double) * 2 * np2, cudaMemcpyDeviceToHost, C.stream));
+  const int64_t N = C.L.back().N;
+  int rc;
+  if ((rc = ns_prepare(C))) return rc;
   double* Fb = C.d_F;
   double* db = C.d_kb;
   double eta = 0.5, fprev = 0.0, fn = 0.0;
-  int its = 0, lin = 0, rc;
+  int its = 0, lin = 0;
   for (;; ++its) {
-    CK(cudaMemcpyAsync(hk.data(), k, sizeof(double) * N, cudaMemcpyDeviceToHost, C.stream));
-    CK(cudaStreamSynchronize(C.stream));
-    for (int t = 0; t < C.s; ++t)
-      for (int d = 0; d < 2; ++d) {
-        double* Ut = U.data() + ((int64_t)t * 2 + d) * np2;
-        std::copy(hu.begin() + d * np2, hu.begin() + (d + 1) * np2, Ut);
-        for (int j = 0; j < C.s; ++j) {
-          const double a = C.dt * C.A[t * C.s + j];
-          const double* kj = hk.data() + (int64_t)j * L.m + d * nf;
-          for (int64_t i = 0; i < nf; ++i) Ut[L.mesh.free_to_p2[i]] += a * kj[i];
-        }
-      }
-    if ((rc = ns_set_state(C, U.data()))) return rc;
+    CK(launch_ns_stage_velocity(C, un_all, k, C.d_ns_U));
+    if ((rc = ns_set_state(C))) return rc;
     if ((rc = ns_residual(C, un_all, pn, f, k, Fb))) return rc;
     CK(launch_multidot(Fb, 0, 1, Fb, N, C.d_part, C.d_h + 192, C.stream));
     CK(cudaMemcpyAsync(C.h_h + 192, C.d_h + 192, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
@@ -1789,8 +1794,11 @@ int irkmg_ns_set_state(irkmg_ctx* C, const double* U) {
   int rc = ns_check(C);
   if (rc) return rc;
   if (!U) return fail(IRKMG_EINVAL, "null state");
-  CK(C->stream ? cudaStreamSynchronize(C->stream) : cudaDeviceSynchronize());
-  return ns_set_state(*C, U);
+  if ((rc = ns_prepare(*C))) return rc;
+  const Level& F = C->L.back();
+  CK(cudaMemcpyAsync(C->d_ns_U, U, sizeof(double) * C->s * 2 * F.np2, cudaMemcpyHostToDevice,
+                     C->stream));
+  return ns_set_state(*C);
 }
 
 int irkmg_ns_residual(irkmg_ctx* C, const double* un_all, const double* pn, const double* f,

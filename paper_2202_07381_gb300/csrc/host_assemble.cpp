@@ -272,68 +272,6 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
   ops.btall = transpose_csr(Bf, d);
 }
 
-// Newton blocks of the Navier-Stokes convection at the velocity U (P2 nodal,
-// np2 x 2, every node; Section 3.2): on the velocity pattern V (free x free),
-// W[2 d + c] = delta_dc C(U) + R_dc(U) with C(U)[a, b] = int (U . grad phi_b)
-// phi_a and R_dc(U)[a, b] = int phi_a phi_b dU_d/dx_c; and g = C(U) U on the
-// free rows (every column), component-major.  The integrands have degree 5,
-// which the 7-point rule integrates exactly.  2D only.
-void assemble_ns_blocks(const HostMesh& m, const HostCSR& V, const double* U,
-                        std::vector<double> W[4], std::vector<double>& g) {
-  const int kv = m.nvc(), nn = m.nn();
-  const QuadRule q = radon7();
-  const int nq = (int)q.w.size();
-  for (int k = 0; k < 4; ++k) W[k].assign(V.col.size(), 0.0);
-  g.assign(2 * m.nf, 0.0);
-  auto cell_node = [&](int64_t c, int a) -> int32_t {
-    return a < kv ? m.cells[kv * c + a] : (int32_t)(m.nv + m.cell_edges[m.nle() * c + a - kv]);
-  };
-  double Ce[6][6], Re[2][2][6][6];
-  for (int64_t c = 0; c < m.nc; ++c) {
-    double gl[4][3];
-    const double vol = cell_geometry(m, c, gl);
-    int32_t node[6];
-    for (int a = 0; a < nn; ++a) node[a] = cell_node(c, a);
-    for (int a = 0; a < nn; ++a)
-      for (int b = 0; b < nn; ++b) {
-        Ce[a][b] = 0.0;
-        for (int d = 0; d < 2; ++d)
-          for (int e = 0; e < 2; ++e) Re[d][e][a][b] = 0.0;
-      }
-    for (int iq = 0; iq < nq; ++iq) {
-      double phi[10], gr[10][3];
-      p2_eval(2, q.lam[iq].data(), gl, phi, gr);
-      const double wk = q.w[iq] * vol;
-      double u[2] = {0.0, 0.0}, du[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // du[d][c] = dU_d/dx_c
-      for (int a = 0; a < nn; ++a)
-        for (int d = 0; d < 2; ++d) {
-          const double ua = U[2 * node[a] + d];
-          u[d] += ua * phi[a];
-          for (int e = 0; e < 2; ++e) du[d][e] += ua * gr[a][e];
-        }
-      for (int a = 0; a < nn; ++a)
-        for (int b = 0; b < nn; ++b) {
-          Ce[a][b] += wk * phi[a] * (u[0] * gr[b][0] + u[1] * gr[b][1]);
-          const double pp = wk * phi[a] * phi[b];
-          for (int d = 0; d < 2; ++d)
-            for (int e = 0; e < 2; ++e) Re[d][e][a][b] += pp * du[d][e];
-        }
-    }
-    for (int a = 0; a < nn; ++a) {
-      const int32_t row = m.p2_to_free[node[a]];
-      if (row < 0) continue;
-      for (int b = 0; b < nn; ++b) {
-        for (int d = 0; d < 2; ++d) g[d * m.nf + row] += Ce[a][b] * U[2 * node[b] + d];
-        const int32_t cf = m.p2_to_free[node[b]];
-        if (cf < 0) continue;
-        const int64_t sv = slot(V, row, cf);
-        for (int d = 0; d < 2; ++d)
-          for (int e = 0; e < 2; ++e) W[2 * d + e][sv] += (d == e ? Ce[a][b] : 0.0) + Re[d][e][a][b];
-      }
-    }
-  }
-}
-
 // Load of a per-cell constant (P0) forcing: C[a, c] = int_c phi_a for the free
 // P2 nodes a of cell c (the same for every velocity component).  P2 vertex
 // functions integrate to zero on a triangle, edge functions to |c|/3.

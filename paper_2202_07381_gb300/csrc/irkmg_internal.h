@@ -67,10 +67,6 @@ struct HostOps {
 void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& ops);
 
 void assemble_cell_load(const HostMesh& m, HostCSR& C);
-// Newton blocks of the convection at the nodal velocity U (2D): W[2d + c] on
-// the pattern V (free x free) and g = C(U) U on the free rows.
-void assemble_ns_blocks(const HostMesh& m, const HostCSR& V, const double* U,
-                        std::vector<double> W[4], std::vector<double>& g);
 
 // Radau IIA closed forms.
 int radau_iia(int s, double* A, double* b, double* c);
@@ -176,6 +172,11 @@ struct Level {
   // velocity pattern (gathers, coarse build) and SELL-ordered (stage operator)
   double* d_ns_csr[3][4] = {{nullptr}};
   double* d_ns_sell[3][4] = {{nullptr}};
+  // topology for the GPU assembly of the Newton blocks
+  double* d_xy = nullptr;                        // vertex coordinates
+  int32_t *d_nc_ptr = nullptr, *d_nc_idx = nullptr;  // P2 node -> cells
+  int32_t* d_free_to_p2 = nullptr;
+  int64_t* d_sell_perm = nullptr;                // SELL slot of every velocity CSR entry
   // algorithmic bytes for tracing
   std::vector<double> colour_bytes, colour_flops;
   double op_bytes = 0.0, op_flops = 0.0;
@@ -193,6 +194,7 @@ struct Ctx {
   bool ns = false;            // Navier-Stokes Newton blocks set (irkmg_ns_set_state)
   bool ns_active = true;      // ... and included in the stage operator (off: Stokes part)
   double* d_ns_g = nullptr;   // s x 2 nf: C(U_i) U_i on the finest free rows
+  double* d_ns_U = nullptr;   // s x 2 x np2: stage velocities at every finest P2 node
   cudaStream_t stream = nullptr;
   std::vector<double> wind;  // finest-level nodal wind (empty for Stokes)
   std::vector<Level> L;
@@ -273,6 +275,8 @@ cudaError_t coarse_invert(Ctx& C, double* dense, int64_t n);
 cudaError_t launch_coarse_apply(Ctx& C, const double* r, double* x, int transpose);
 
 cudaError_t launch_cell_load(Ctx& C, const double* theta, double* g);
+cudaError_t launch_ns_stage_velocity(Ctx& C, const double* un_all, const double* k, double* U);
+cudaError_t launch_ns_assemble(Ctx& C, Level& L, int t, const double* U, int64_t stride, double* g);
 cudaError_t launch_add_to_stages(Ctx& C, const double* g, double* F);
 cudaError_t launch_kbar(Ctx& C, const double* ub, const double* pb, double* kb);
 cudaError_t launch_adjoint_update(Ctx& C, const double* lam, double* ub, double* pb);
