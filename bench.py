@@ -62,7 +62,9 @@ NCU_TRAFFIC = {
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
                "k_vanka_apply_lu": "k_patch_big.cu", "k_vanka_apply_kron": "k_patch_kron.cu",
                "k_vanka_apply_kron_staged": "k_patch_kron.cu",
-               "k_vanka_apply_kron_big": "k_patch_kron.cu"}
+               "k_vanka_apply_kron_big": "k_patch_kron.cu",
+               "k_vanka_apply_kron_ws": "k_patch_kron.cu",
+               "k_vanka_apply_kron_fx": "k_patch_fixed.cu"}
 
 
 def kernel_source_hash(kernel="k_vanka_apply_kron"):
@@ -222,11 +224,12 @@ def run_reference(args, wl, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def make_context(irkmg, wl, precision, stream, apply_variant=0, patch_form=0):
+def make_context(irkmg, wl, precision, stream, apply_variant=0, patch_form=0, patch_fixed=0):
     A, b, c = irkmg.irkmg_radau_iia(wl["s"])
     o = irkmg.irkmg_default_options()
     o.apply_variant = apply_variant
     o.patch_form = patch_form
+    o.patch_fixed = patch_fixed
     if "cheb" in wl:
         o.cheb_lo, o.cheb_hi = wl["cheb"]
     o.nlevels = wl["levels"]
@@ -257,12 +260,13 @@ def initial_data(irkmg, ctx, wl, c):
     return u0, p0, f
 
 
-def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form):
+def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form, patch_fixed=0):
     """Another form on the same workload (FP32 patches and/or decoupled patch
     solves): time per solve, iterations, the difference of its solution from
     the plain FP64 form's, and the finest-level Vanka roofline from the live
     trace (FP64 patches: FP64-pipe bound; FP32 patches: HBM bound)."""
-    ctx, setup_s, c = make_context(irkmg, wl, precision, stream.cuda_stream, 0, patch_form)
+    ctx, setup_s, c = make_context(irkmg, wl, precision, stream.cuda_stream, 0, patch_form,
+                                   patch_fixed)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -292,7 +296,7 @@ def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form):
     out = {"ms_per_step": ms, "iters": stats[-1]["iters"],
            "rel_residual": stats[-1]["rfinal"] / stats[-1]["r0"], "setup_s": setup_s,
            "rel_diff_vs_fp64_solution": diff, "patch_precision": precision,
-           "patch_form": patch_form,
+           "patch_form": patch_form, "patch_fixed": patch_fixed,
            "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
            "factor_bytes_finest": ctx.finest["factor_bytes"]}
     if tr["vanka_ms"]:
@@ -304,10 +308,41 @@ def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form):
                                "bytes_per_launch": tr["vanka_bytes"] / nvl,
                                "flops_per_launch": tr["vanka_flops"] / nvl,
                                "hbm_gbs": gbs, "hbm_frac": gbs / hbm, "tflops": tf,
-                               "fp64_frac": tf / FP64_PEAK_TFLOPS if precision == 64 else None,
+                               "fp64_frac": (tf / FP64_PEAK_TFLOPS
+                                             if precision == 64 and not patch_fixed else None),
                                "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
+    if patch_fixed:
+        out["finest_correction_ms_per_shape"] = shape_sweep(irkmg, torch, ctx, dev, stream)
     ctx.close()
     return out
+
+
+def shape_sweep(irkmg, torch, ctx, dev, stream, reps=10):
+    """Time of one finest-level Vanka correction (one launch over all patches
+    plus the per-DoF sum) for every launch shape of the level's kernel, pinned
+    with irkmg_level_set_apply; the tuned shape is restored afterwards."""
+    fin = ctx.nlevels - 1
+    keep = (ctx.finest["apply_shape"], ctx.finest["single_launch"])
+    r = torch.rand(ctx.N(), dtype=torch.float64, device=dev)
+    c = torch.zeros_like(r)
+    res = {}
+    for shape in range(16):
+        try:
+            irkmg.irkmg_level_set_apply(ctx, fin, shape, 1)
+        except irkmg.IrkmgError:
+            break
+        for _ in range(2):
+            irkmg.irkmg_vanka_correction(ctx, r, c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            irkmg.irkmg_vanka_correction(ctx, r, c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[f"kernel{ctx.finest['apply_kernel']}_shape{shape}"] = e0.elapsed_time(e1) / reps
+    irkmg.irkmg_level_set_apply(ctx, fin, *keep)
+    return res
 
 
 def irkmg_rel_diff(torch, a, b):
@@ -476,8 +511,9 @@ def run_ours(args, wl, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     prec = 32 if (args.form == "fp32" or wl.get("dim", 2) == 3) else 64
+    fixed = args.patch_fixed if prec == 64 and args.patch_form != 0 else 0
     ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream, args.apply,
-                                   args.patch_form)
+                                   args.patch_form, fixed)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -557,11 +593,12 @@ def run_ours(args, wl, rank, world, local_rank):
     assert base_config(wl)["N"] == N and base_config(wl)["patches_finest"] == ctx.finest["nv"]
     forms = {}
     if rank == 0 and not args.small and prec == 64 and not args.no_forms:
-        for name, fp, pf in (("dense_fp64", 64, 0), ("dense_fp32", 32, 0), ("kron_fp64", 64, 1),
-                             ("kron_fp32", 32, 1)):
-            if pf == args.patch_form and fp == prec:
+        for name, fp, pf, fx in (("dense_fp64", 64, 0, 0), ("dense_fp32", 32, 0, 0),
+                                 ("kron_fp64", 64, 1, 0), ("kron_fp64_fixed", 64, 1, 1),
+                                 ("kron_fp32", 32, 1, 0)):
+            if pf == args.patch_form and fp == prec and fx == fixed:
                 continue
-            forms[name] = run_form(irkmg, torch, wl, args, dev, stream, k, fp, pf)
+            forms[name] = run_form(irkmg, torch, wl, args, dev, stream, k, fp, pf, fx)
             forms[name]["speedup_vs_headline"] = (ms / args.steps) / forms[name]["ms_per_step"]
         forms["batched"] = run_batched(args, dev, stream)
         forms["ns_newton"] = run_ns(args, dev, stream)
@@ -578,7 +615,8 @@ def run_ours(args, wl, rank, world, local_rank):
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
                  3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
                  5: "k_vanka_apply_kron_staged",
-                 6: "k_vanka_apply_kron_big"}[ctx.finest["apply_kernel"]]
+                 6: "k_vanka_apply_kron_big", 7: "k_vanka_apply_kron_ws",
+                 8: "k_vanka_apply_kron_fx"}[ctx.finest["apply_kernel"]]
         h = kernel_source_hash(kname)
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
@@ -590,7 +628,7 @@ def run_ours(args, wl, rank, world, local_rank):
                   "avg_launch_ms": trace["vanka_ms"] / nvl, "kernel_src": h,
                   "hbm_gbs": van_gbs, "hbm_frac": van_gbs / hbm if van_gbs else None,
                   "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
-        if prec == 64:
+        if prec == 64 and not fixed:
             # FP64 on GB300 runs at 1/62 of FP32: a dense FP64 mat-vec (2 flop per
             # 8-byte entry) is bound by the FP64 pipe, not by HBM
             roofline = {"bound": "alu", "achieved": van_tf, "peak": FP64_PEAK_TFLOPS,
@@ -608,6 +646,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "dim": wl.get("dim", 2),
             "config": {**base_config(wl),
                        "patch_precision": prec, "patch_form": args.patch_form,
+                       "patch_fixed": fixed,
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
                              % (ctx.finest["factor_bytes"] / 1e9),
@@ -646,6 +685,9 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32-patch and batched forms reported beside the headline")
     ap.add_argument("--batch", type=int, default=64, help="systems in the batched form")
+    ap.add_argument("--patch-fixed", type=int, default=0, choices=[0, 1],
+                    help="decoupled FP64 patches: 1 = exact fixed-point mat-vecs "
+                         "(irkmg_options.patch_fixed)")
     ap.add_argument("--patch-form", type=int, default=1, choices=[0, 1, 2, 3],
                     help="0 dense patch systems; 1..3 Kronecker-decoupled (irkmg_options.patch_form)")
     ap.add_argument("--apply", type=int, default=0, choices=[0, 1, 2],

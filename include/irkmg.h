@@ -137,6 +137,14 @@ typedef struct {
                               of the blocked patch LU on the tensor cores
                               (tcgen05.mma kind::tf32, operands split hi + lo for
                               FP32-level products), 0 = on the CUDA cores          */
+  int patch_fixed;         /* decoupled FP64 patches (patch_form != 0, blocks of at
+                              most 63 DoFs: the 2D levels): 1 = every stored
+                              inverse row kept as 57-bit fixed point with its own
+                              power of two, applied by exact integer dot products
+                              (32×32→64-bit multiply-adds) against the patch's
+                              sources scaled to 58-bit integers, rounded once to
+                              FP64; 0 = FP64 entries and FP64 FMAs.  Levels that do
+                              not qualify keep FP64 entries                        */
 } irkmg_options;
 
 typedef struct {
@@ -160,7 +168,8 @@ typedef struct {
                               (patch_form != 0): 4 warp-per-patch, 5 TMA-staged,
                               6 CTA-per-patch (blocks above 160 DoFs, factored by
                               the blocked LU; 3D), 7 warp-specialised TMA
-                              pipeline                                             */
+                              pipeline; patch_fixed: 8 warp-per-patch, 9 TMA-
+                              staged exact fixed-point mat-vecs                    */
   double apply_ms[2];      /* autotuner: one sweep with the fastest staged (or, for
                               decoupled levels, CTA-per-patch) candidate / the
                               fastest warp-per-patch candidate (0 if untimed)      */
@@ -169,6 +178,11 @@ typedef struct {
                               plus a deterministic per-DoF sum (decoupled form);
                               0: one launch per colour                             */
   double cheb[2];          /* Chebyshev interval used on the level                  */
+  int64_t apply_shape;     /* launch shape of the apply kernel: 0..1 for kernel 5
+                              (staged, three- or two-stage ring); 0..3 for kernel 8
+                              (columns per load batch × resident CTAs per SM:
+                              8×3, 4×4, 6×3, 8×4) and 4..6 for kernel 9 (stages ×
+                              CTAs per SM: 4×1, 3×1, 2×2); 0 otherwise             */
 } irkmg_level_info;
 
 /* ---- set-up -------------------------------------------------------------- */
@@ -227,6 +241,13 @@ int irkmg_set_wind(irkmg_ctx *ctx, const double *wind);
 
 /* Sizes of level l (0 = coarsest, nlevels-1 = finest). */
 int irkmg_level_info_get(const irkmg_ctx *ctx, int level, irkmg_level_info *info);
+/* Pin the launch shape (see irkmg_level_info.apply_shape) and, on decoupled
+ * levels, the relaxation mode (single_launch 1: one launch over all patches and
+ * the per-DoF sum; 0: one launch per colour) of level >= 1, overriding the
+ * set-up autotuner.  IRKMG_EINVAL for a shape the level's kernel does not have
+ * (or whose shared memory does not fit) and for single_launch = 1 on a level
+ * with dense patches. */
+int irkmg_level_set_apply(irkmg_ctx *ctx, int level, int shape, int single_launch);
 
 /* Host copies of set-up data of level l, for inspection and tests.
  * irkmg_p2_coords: np2·2 doubles.  irkmg_free_nodes: nf int64 P2-node ids.

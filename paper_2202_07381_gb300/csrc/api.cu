@@ -348,6 +348,11 @@ int build_patches(Ctx& C, Level& L) {
   C.allocs.push_back(fac);
   C.dev_bytes += esz * L.fac_elems;
   L.d_fac = fac;
+  L.fixed = L.kron && C.opt.patch_fixed && fixed_fits(C, L);
+  if (L.fixed) {
+    std::vector<int16_t> ex((size_t)L.nv * C.kplan.nm * L.kron_nmax, 0);
+    if ((rc = upload(C, &L.d_fexp, ex))) return rc;
+  }
   if (L.kron)
     CK(launch_patch_gidx_kron(C, L));
   else
@@ -408,6 +413,7 @@ int factor_level(Ctx& C, Level& L) {
   }
   if (L.kron) {
     CK(launch_patch_invert_kron(C, L));
+    if (L.fixed) CK(launch_patch_to_fixed(C, L));
     return IRKMG_OK;
   }
   if (!L.big) {
@@ -508,6 +514,52 @@ int tune_apply(Ctx& C) {
       L.single = t2[1] < t2[0];
       L.apply_ms[1] = 0.f;
       L.apply_ms[2] = std::min(t2[0], t2[1]);
+      continue;
+    }
+    if (L.fixed) {
+      // one kernel (warp per patch, fixed point): its launch shapes and both
+      // relaxation modes timed, unless the variant fixes the mode
+      L.apply_kernel = 8;
+      L.single = false;
+      L.kron_shape = 0;
+      const int av = C.opt.apply_variant;
+      if (av != 0) {
+        L.single = av == 3 || av == 4 || av == 6;
+        continue;
+      }
+      cudaError_t ez = cudaMemsetAsync(L.t, 0, sizeof(double) * L.N, C.stream);
+      if (ez != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(ez)); break; }
+      float best_all = 1e30f;
+      int pick_shape = 0;
+      bool pick_single = false;
+      for (int single = 0; single < 2 && rc == IRKMG_OK; ++single)
+        for (int shape = 0; shape < fixed_shapes() && rc == IRKMG_OK; ++shape) {
+          if (!fixed_shape_fits(C, L, shape)) continue;
+          L.single = single != 0;
+          L.kron_shape = shape;
+          L.apply_kernel = shape < 4 ? 8 : 9;
+          float best = 1e30f;
+          for (int rep = 0; rep < 3 && rc == IRKMG_OK; ++rep) {
+            cudaEventRecord(a, C.stream);
+            rc = vanka_all(C, L, L.t, L.d, 1.0, 0);
+            cudaEventRecord(b, C.stream);
+            cudaError_t e2 = cudaEventSynchronize(b);
+            if (e2 != cudaSuccess) { rc = fail(IRKMG_ECUDA, cudaGetErrorString(e2)); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0 && ms < best) best = ms;
+          }
+          if (best < best_all) {
+            best_all = best;
+            pick_shape = shape;
+            pick_single = single != 0;
+          }
+        }
+      L.single = pick_single;
+      L.kron_shape = pick_shape;
+      L.apply_kernel = pick_shape < 4 ? 8 : 9;
+      L.apply_ms[1] = 0.f;
+      L.apply_ms[2] = best_all;
       continue;
     }
     // candidates: staged (TMA) and warp-per-patch kernels, dense or decoupled;
@@ -858,6 +910,7 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
   if (o->patch_form < 0 || o->patch_form > 3)
     return fail(IRKMG_EINVAL, "patch_form is 0, 1, 2 or 3");
   if (o->patch_lu_tc != 0 && o->patch_lu_tc != 1) return fail(IRKMG_EINVAL, "patch_lu_tc is 0 or 1");
+  if (o->patch_fixed != 0 && o->patch_fixed != 1) return fail(IRKMG_EINVAL, "patch_fixed is 0 or 1");
   if (o->patch_form != 0) {
     KronSplit K;
     if (kron_split(tab->s, tab->A, &K) != IRKMG_OK)
@@ -1679,6 +1732,24 @@ int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) 
   info->single_launch = level > 0 && L.kron && L.single ? 1 : 0;
   info->cheb[0] = level > 0 ? L.cheb_lo : 0.0;
   info->cheb[1] = level > 0 ? L.cheb_hi : 0.0;
+  info->apply_shape =
+      level > 0 && (L.apply_kernel == 5 || L.apply_kernel == 8 || L.apply_kernel == 9) ? L.kron_shape : 0;
+  return IRKMG_OK;
+}
+
+int irkmg_level_set_apply(irkmg_ctx* C, int level, int shape, int single_launch) {
+  if (!level_ok(C, level) || level < 1) return fail(IRKMG_EINVAL, "bad level (relaxed levels are 1 ..)");
+  Level& L = C->L[level];
+  if (single_launch != 0 && single_launch != 1) return fail(IRKMG_EINVAL, "single_launch is 0 or 1");
+  if (single_launch && !L.kron) return fail(IRKMG_EINVAL, "one-launch relaxation needs decoupled patches");
+  const int nshape = L.fixed ? fixed_shapes() : L.apply_kernel == 5 ? 2 : 1;
+  if (shape < 0 || shape >= nshape) return fail(IRKMG_EINVAL, "no such launch shape for the level's kernel");
+  if ((L.apply_kernel == 5 && !kron_staged_fits(*C, L, shape)) || (L.fixed && !fixed_shape_fits(*C, L, shape)))
+    return fail(IRKMG_EINVAL, "launch shape does not fit in shared memory");
+  L.kron_shape = shape;
+  if (L.fixed) L.apply_kernel = shape < 4 ? 8 : 9;
+  L.single = single_launch != 0;
+  drop_graphs(*C);  // captured coarse levels hold the previous launches
   return IRKMG_OK;
 }
 

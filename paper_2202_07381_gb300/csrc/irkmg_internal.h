@@ -150,10 +150,14 @@ struct Level {
   bool kron = false;                   // Kronecker-decoupled patch factors (KronPlan)
   bool kron_big = false;               // ... factored by the blocked LU (blocks above 160 DoFs)
   int kron_nmax = 0;                   // largest spatial patch size n on a decoupled level
+  bool fixed = false;                  // decoupled FP64 blocks stored as per-row fixed point
+  int16_t* d_fexp = nullptr;           // ... their row exponents [ordered patch][matrix][nmax]
   int apply_kernel = 1;                // 1 staged, 2 warp-per-patch, 3 big-patch mat-vec,
                                        // 4 decoupled warp-per-patch, 5 decoupled staged,
                                        // 6 decoupled CTA-per-patch (large patches),
-                                       // 7 decoupled warp-specialised TMA pipeline
+                                       // 7 decoupled warp-specialised TMA pipeline,
+                                       // 8 decoupled fixed point, warp per patch,
+                                       // 9 decoupled fixed point, TMA-staged
   float apply_ms[3] = {0, 0, 0};       // autotuner timings of one sweep per kernel
   int kron_shape = 0;                  // launch shape of the staged decoupled apply (0, 1)
   double cheb_lo = 2.0, cheb_hi = 8.0; // Chebyshev interval of this level's smoother
@@ -166,6 +170,7 @@ struct Level {
   double reduce_bytes = 0.0;           // algorithmic bytes of one reduction launch
   int kron_cap[2][2] = {{0, 0}, {0, 0}};  // its resident CTAs per [shape][transpose] (0 unset)
   int ws_cap[2] = {0, 0};              // resident CTAs of the warp-specialised apply
+  int fx_cap[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // ... of the staged fixed-point apply per shape
   // work vectors (length N)
   double *r = nullptr, *z = nullptr, *t = nullptr, *d = nullptr;
   // Navier-Stokes Newton blocks W_t,dc per stage (2D): CSR-ordered on the
@@ -247,6 +252,13 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
                               double scale, int transpose);  // colour -1: all patches to d_Y
 cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale);
 int kron_max_slots();
+bool fixed_fits(Ctx& C, Level& L);
+int fixed_shapes();  // launch shapes of the fixed-point apply (Level::kron_shape):
+                     // 0..3 warp per patch, 4.. TMA-staged
+bool fixed_shape_fits(Ctx& C, Level& L, int shape);
+cudaError_t launch_patch_to_fixed(Ctx& C, Level& L);
+cudaError_t launch_vanka_kron_fx(Ctx& C, Level& L, int colour, const double* r, double* out,
+                                 double scale, int transpose);
 bool kron_staged_fits(Ctx& C, Level& L, int shape);
 bool kron_ws_fits(Ctx& C, Level& L);
 cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,

@@ -829,6 +829,8 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   }
   P.nmax = L.kron_nmax;
   if (P.count <= 0) return cudaSuccess;
+  if (L.apply_kernel == 8 || L.apply_kernel == 9)
+    return launch_vanka_kron_fx(C, L, colour, r, out, scale, transpose);
   const int prec = C.opt.patch_precision;
   if (L.apply_kernel == 7) {
     WsShape wsh;

@@ -40,7 +40,8 @@ class Options(ct.Structure):
                 ("restart", ct.c_int), ("maxit", ct.c_int), ("patch_precision", ct.c_int),
                 ("wind", ct.POINTER(ct.c_double)), ("cuda_stream", ct.c_void_p),
                 ("timeout_spins", ct.c_int64), ("apply_variant", ct.c_int),
-                ("patch_form", ct.c_int), ("cheb_auto", ct.c_int), ("patch_lu_tc", ct.c_int)]
+                ("patch_form", ct.c_int), ("cheb_auto", ct.c_int), ("patch_lu_tc", ct.c_int),
+                ("patch_fixed", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -58,7 +59,8 @@ class LevelInfo(ct.Structure):
                                           "apply_kernel")] + [("apply_ms", ct.c_double * 2),
                                                               ("dim", ct.c_int64),
                                                               ("single_launch", ct.c_int64),
-                                                              ("cheb", ct.c_double * 2)]
+                                                              ("cheb", ct.c_double * 2),
+                                                              ("apply_shape", ct.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("apply_ms", "cheb")}
@@ -104,6 +106,7 @@ _SIGS = {
     "irkmg_update": (ct.c_int, [_P, ct.c_double, ct.c_double]),
     "irkmg_set_wind": (ct.c_int, [_P, _P]),
     "irkmg_level_info_get": (ct.c_int, [_P, ct.c_int, ct.POINTER(LevelInfo)]),
+    "irkmg_level_set_apply": (ct.c_int, [_P, ct.c_int, ct.c_int, ct.c_int]),
     "irkmg_p2_coords": (ct.c_int, [_P, ct.c_int, _P]),
     "irkmg_free_nodes": (ct.c_int, [_P, ct.c_int, _P]),
     "irkmg_patch_map": (ct.c_int, [_P, ct.c_int, _P, _P]),
@@ -267,11 +270,15 @@ class Context:
         self.handle = handle
         self.s = s
         self._keep = keep
+        self.refresh()
+
+    def refresh(self):
+        """Re-read the per-level information (after irkmg_level_set_apply)."""
         self.levels = []
         k = 0
         while True:
             info = LevelInfo()
-            if lib().irkmg_level_info_get(handle, k, ct.byref(info)) != IRKMG_OK:
+            if lib().irkmg_level_info_get(self.handle, k, ct.byref(info)) != IRKMG_OK:
                 break
             self.levels.append(info.as_dict())
             k += 1
@@ -371,6 +378,11 @@ def irkmg_apply(ctx, x, y, level=-1, transpose=False):
     level %= ctx.nlevels
     n = ctx.N(level)
     _check(lib().irkmg_apply(ctx.handle, level, _dptr(x, n, "x"), _dptr(y, n, "y"), int(transpose)))
+
+
+def irkmg_level_set_apply(ctx, level, shape, single_launch):
+    _check(lib().irkmg_level_set_apply(ctx.handle, int(level), int(shape), int(single_launch)))
+    ctx.refresh()
 
 
 def irkmg_vanka_correction(ctx, r, c, level=-1, transpose=False):
