@@ -65,7 +65,8 @@ KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.c
                "k_vanka_apply_kron_staged": "k_patch_kron.cu",
                "k_vanka_apply_kron_big": "k_patch_kron.cu",
                "k_vanka_apply_kron_ws": "k_patch_kron.cu",
-               "k_vanka_apply_kron_fx": "k_patch_fixed.cu"}
+               "k_vanka_apply_kron_fx": "k_patch_fixed.cu",
+               "k_vanka_apply_kron_fx_staged": "k_patch_fixed.cu"}
 
 
 def kernel_source_hash(kernel="k_vanka_apply_kron"):
@@ -617,7 +618,7 @@ def run_ours(args, wl, rank, world, local_rank):
                  3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
                  5: "k_vanka_apply_kron_staged",
                  6: "k_vanka_apply_kron_big", 7: "k_vanka_apply_kron_ws",
-                 8: "k_vanka_apply_kron_fx"}[ctx.finest["apply_kernel"]]
+                 8: "k_vanka_apply_kron_fx", 9: "k_vanka_apply_kron_fx_staged"}[ctx.finest["apply_kernel"]]
         h = kernel_source_hash(kname)
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None
@@ -648,6 +649,10 @@ def run_ours(args, wl, rank, world, local_rank):
             "config": {**base_config(wl),
                        "patch_precision": prec, "patch_form": args.patch_form,
                        "patch_fixed": fixed,
+                       "patch_arith": ("FP64 data; patch mat-vecs as exact integer dot products of "
+                                       "57-bit fixed-point matrix rows and 58-bit fixed-point "
+                                       "sources, rounded once to FP64" if fixed else
+                                       "FP64 FMAs" if prec == 64 else "FP32 patch entries"),
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
                              % (ctx.finest["factor_bytes"] / 1e9),
@@ -686,7 +691,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32-patch and batched forms reported beside the headline")
     ap.add_argument("--batch", type=int, default=64, help="systems in the batched form")
-    ap.add_argument("--patch-fixed", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--patch-fixed", type=int, default=1, choices=[0, 1],
                     help="decoupled FP64 patches: 1 = exact fixed-point mat-vecs "
                          "(irkmg_options.patch_fixed)")
     ap.add_argument("--patch-form", type=int, default=1, choices=[0, 1, 2, 3],

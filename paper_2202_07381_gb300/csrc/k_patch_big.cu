@@ -703,8 +703,8 @@ __global__ void __launch_bounds__(kBigThreads) k_vanka_apply_big(BigParams P, co
       T v0[kBatch], v1[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
-        v0[u] = __ldcs(x0 + (int64_t)(j + u) * np);
-        if (has1) v1[u] = __ldcs(x1 + (int64_t)(j + u) * np);
+        v0[u] = __ldg(x0 + (int64_t)(j + u) * np);
+        if (has1) v1[u] = __ldg(x1 + (int64_t)(j + u) * np);
       }
 #pragma unroll
       for (int u = 0; u < kBatch; u += 2) {
@@ -717,8 +717,8 @@ __global__ void __launch_bounds__(kBigThreads) k_vanka_apply_big(BigParams P, co
       }
     }
     for (; j < np; ++j) {
-      a0 = fma(__ldcs(x0 + (int64_t)j * np), y[j], a0);
-      if (has1) a1 = fma(__ldcs(x1 + (int64_t)j * np), y[j], a1);
+      a0 = fma(__ldg(x0 + (int64_t)j * np), y[j], a0);
+      if (has1) a1 = fma(__ldg(x1 + (int64_t)j * np), y[j], a1);
     }
   }
   if (i0 < np) P.out[g[i0]] += P.scale * (double)(a0 + b0);

@@ -306,7 +306,7 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
           const int2* p = mp[k] + j0 * cstep;
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            q[u][k] = __ldcs(p);
+            q[u][k] = __ldg(p);
             p += cstep;
           }
         }
@@ -314,7 +314,7 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-          for (int k = 0; k < RC; ++k) q[u][k] = __ldcs(mp[k] + min(j0 + u, n - 1) * cstep);
+          for (int k = 0; k < RC; ++k) q[u][k] = __ldg(mp[k] + min(j0 + u, n - 1) * cstep);
       }
     };
     auto mac = [&](const int2 (&q)[U][RC], int b) {
