@@ -537,7 +537,7 @@ int tune_apply(Ctx& C) {
           if (!fixed_shape_fits(C, L, shape)) continue;
           L.single = single != 0;
           L.kron_shape = shape;
-          L.apply_kernel = shape < 4 ? 8 : 9;
+          L.apply_kernel = fixed_shape_kernel(shape);
           float best = 1e30f;
           for (int rep = 0; rep < 3 && rc == IRKMG_OK; ++rep) {
             cudaEventRecord(a, C.stream);
@@ -557,7 +557,7 @@ int tune_apply(Ctx& C) {
         }
       L.single = pick_single;
       L.kron_shape = pick_shape;
-      L.apply_kernel = pick_shape < 4 ? 8 : 9;
+      L.apply_kernel = fixed_shape_kernel(pick_shape);
       L.apply_ms[1] = 0.f;
       L.apply_ms[2] = best_all;
       continue;
@@ -1747,7 +1747,7 @@ int irkmg_level_set_apply(irkmg_ctx* C, int level, int shape, int single_launch)
   if ((L.apply_kernel == 5 && !kron_staged_fits(*C, L, shape)) || (L.fixed && !fixed_shape_fits(*C, L, shape)))
     return fail(IRKMG_EINVAL, "launch shape does not fit in shared memory");
   L.kron_shape = shape;
-  if (L.fixed) L.apply_kernel = shape < 4 ? 8 : 9;
+  if (L.fixed) L.apply_kernel = fixed_shape_kernel(shape);
   L.single = single_launch != 0;
   drop_graphs(*C);  // captured coarse levels hold the previous launches
   return IRKMG_OK;

@@ -255,6 +255,7 @@ int kron_max_slots();
 bool fixed_fits(Ctx& C, Level& L);
 int fixed_shapes();  // launch shapes of the fixed-point apply (Level::kron_shape):
                      // 0..3 warp per patch, 4.. TMA-staged
+int fixed_shape_kernel(int shape);  // 8: warp per patch, 9: TMA-staged
 bool fixed_shape_fits(Ctx& C, Level& L, int shape);
 cudaError_t launch_patch_to_fixed(Ctx& C, Level& L);
 cudaError_t launch_vanka_kron_fx(Ctx& C, Level& L, int colour, const double* r, double* out,

@@ -693,6 +693,8 @@ cudaError_t launch_fx(const FxApply& P, const int2* fac, int shape, unsigned gri
 
 int fixed_shapes() { return kFxShapes + kFxStagedShapes; }
 
+int fixed_shape_kernel(int shape) { return shape < kFxShapes ? 8 : 9; }
+
 bool fixed_shape_fits(Ctx& C, Level& L, int shape) {
   if (shape < 0 || shape >= kFxShapes + kFxStagedShapes) return false;
   if (shape < kFxShapes) return true;
