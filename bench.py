@@ -352,12 +352,13 @@ def irkmg_rel_diff(torch, a, b):
     return (a - b).norm() / b.norm()
 
 
-def run_batched(args, dev, stream, patch_form=1):
+def run_batched(args, dev, stream, patch_form=1, patch_fixed=1):
     """64 independent Oseen stage systems (lid-driven cavity, seeded smooth
     wind with max |w| = 1 at the P2 nodes, Re ~ U[100, 1000], dt log-uniform in
     [1e-3, 1e-1], meshes from {32, 64, 128, 256}^2 over an 8 x 8 coarsest mesh,
-    Radau IIA(2), FP64 patches in the given form): solved one after another
-    with irkmg_solve, then together with irkmg_batch_solve."""
+    Radau IIA(2), FP64 patches in the given form, by default decoupled with
+    fixed-point mat-vecs): solved one after another with irkmg_solve, then
+    together with irkmg_batch_solve."""
     import torch
     from paper_2202_07381_gb300 import irkmg
     specs = synth.oseen_batch(0, args.batch)
@@ -369,6 +370,7 @@ def run_batched(args, dev, stream, patch_form=1):
         o.nlevels = int(round(np.log2(sp["n"] / 8))) + 1
         o.maxit = 600
         o.patch_form = patch_form
+        o.patch_fixed = patch_fixed if patch_form != 0 else 0
         ctx = irkmg.irkmg_setup(*synth.square_mesh(8), A, b, c, sp["dt"], sp["nu"], o,
                                 stream=stream.cuda_stream)
         xy = irkmg.irkmg_p2_coords(ctx)
@@ -407,7 +409,7 @@ def run_batched(args, dev, stream, patch_form=1):
                         "meshes from {32,64,128,256}^2, Re ~ U[100,1000], dt in [1e-3,1e-1]",
             "systems": len(specs), "dofs_total": dofs, "all_converged": ok,
             "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
-            "patch_form": patch_form,
+            "patch_form": patch_form, "patch_fixed": patch_fixed if patch_form != 0 else 0,
             "s_per_solve_batched": t_bat / len(specs), "iters_min_mean_max":
             [min(its), float(np.mean(its)), max(its)], "max_rel_diff_vs_sequential": diff,
             "setup_s": setup_s}
