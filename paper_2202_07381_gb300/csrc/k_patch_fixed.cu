@@ -1,10 +1,10 @@
 // Exact fixed-point apply of the decoupled FP64 patch inverses (the Vanka
 // patch solves of Section 4.2 in the Kronecker-decoupled form).
 //
-// GB300 retires 2 FP64 FMAs per clock per SM; 32 × 32 → 64-bit integer
-// multiply-adds with a 64-bit addend (mad.wide.s32) run at about 20 per clock
-// per SM.  Four of them per matrix entry make the decoupled mat-vecs bound by
-// HBM instead of by the FP64 pipe.  Each row i of a stored inverse block M
+// GB300 retires 2 FP64 FMAs per clock per SM and an order of magnitude more
+// 32 × 32 → 64-bit integer multiply-adds with a 64-bit addend (mad.wide.s32),
+// so four of those per matrix entry leave the decoupled mat-vecs bound by HBM
+// instead of by the FP64 pipe.  Each row i of a stored inverse block M
 // (column-major, n ≤ 63) is kept as 57-bit fixed point with its own power of
 // two,
 //     M_ij = q_ij 2^(E_i − 57),   |q_ij| ≤ 2^57,   q_ij = a1 2^29 + a0,
@@ -23,6 +23,10 @@
 // The transposed apply (adjoint) sums down a column, across rows with
 // different E_j; there the source entries are pre-scaled by the exact powers
 // of two 2^(E_j − max_j E_j) before their conversion.
+//
+// Two kernels: warp per patch (k_vanka_apply_kron_fx; entries streamed into
+// registers in column batches) and a TMA-staged persistent kernel
+// (k_vanka_apply_kron_fx_staged); the set-up autotuner picks per level.
 #include <climits>
 
 #include "irkmg_internal.h"
@@ -298,6 +302,8 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
       for (int q = 0; q < 4; ++q) acc[k][q] = 0;
     }
     int2 qa[U][RC], qb[U][RC];
+    // default-cached loads: rows 32..38 of a matrix are read by a later pass
+    // of this warp, and an evict-first hint drops their lines from L2 first
     auto load = [&](int2 (&q)[U][RC], int b) {
       const int j0 = b * U;
       if (j0 + U <= n) {

@@ -256,3 +256,23 @@ def test_fixed_option_rejected_values_and_fp32():
         assert all(lv["apply_kernel"] not in (8, 9) for lv in ctx.levels[1:])
     finally:
         ctx.close()
+
+
+def test_fixed_update_reconverts_the_patches():
+    """irkmg_update (new dt) refactors the decoupled patches and converts
+    them to fixed point again: the correction matches the oracle built at
+    the new step size."""
+    irkmg = need_gpu()
+    fam, s, n0, nl = "radau_iia", 3, 2, 4
+    ctx = _context(irkmg, fam, s, 1 / 64, n0, nl, variant=4)
+    try:
+        for dt in (1 / 16, 1 / 256):
+            irkmg.irkmg_update(ctx, dt, 1.0)
+            assert ctx.levels[nl - 1]["apply_kernel"] in (8, 9)
+            L = _oracle(fam, s, dt, n0, nl).finest
+            r = synth.random_vector(816, L.N)
+            c = dev(np.zeros(L.N))
+            irkmg.irkmg_vanka_correction(ctx, dev(r), c)
+            assert rel(host(c), L.vanka.correction(r)) < 1e-11
+    finally:
+        ctx.close()
