@@ -155,10 +155,16 @@ __device__ __forceinline__ double fx_round(const int64_t* a, int e) {
                                           (m & 0xfffffffffffffull)));
 }
 
-__device__ __forceinline__ double warp_max(double v) {
+// Bit pattern of the largest |x_i| over a warp's entries (i = lane, lane + 32,
+// ... < n): non-negative doubles order like their bit patterns, so integer
+// maxima suffice; a NaN or an infinity gives a pattern >= 0x7ff0000000000000.
+__device__ __forceinline__ uint64_t warp_absmax_bits(const double* x, int n, int lane) {
+  unsigned long long m = 0;
+  for (int i = lane; i < n; i += 32)
+    m = max(m, (unsigned long long)__double_as_longlong(x[i]) & 0x7fffffffffffffffull);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
 }
 
 __device__ __forceinline__ int warp_max_int(int v) {
@@ -256,17 +262,9 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
   __syncwarp();
   // each source to 58-bit integers with one exponent, split into two limbs
   for (int c = 0; c < P.nsrc; ++c) {
-    double mx = 0.0;
-    bool finite = true;
-    for (int i = lane; i < n; i += 32) {
-      const double a = s_x[c * n + i];
-      finite = finite && isfinite(a);
-      mx = fmax(mx, fabs(a));
-    }
-    mx = warp_max(mx);
-    finite = __all_sync(0xffffffffu, finite);
-    int F = 0;
-    if (mx > 0.0) F = fx_exponent(mx);
+    const uint64_t mb = warp_absmax_bits(s_x + c * n, n, lane);
+    const bool finite = mb < 0x7ff0000000000000ull;
+    const int F = finite && mb != 0 ? fx_exponent(__longlong_as_double((long long)mb)) : 0;
     for (int i = lane; i < ls; i += 32) {
       const int64_t v = finite && i < n ? fx_scale_round(s_x[c * n + i], 58 - F) : 0;
       const int32_t v0 = (int32_t)((int64_t)((uint64_t)v << 35) >> 35);
@@ -535,16 +533,9 @@ __global__ void __launch_bounds__(kFxStagedThreads, 1)
     __syncthreads();
     if (warp < P.nsrc) {  // source `warp` to 58-bit integers, two limbs
       const int c = warp;
-      double mx = 0.0;
-      bool finite = true;
-      for (int i = lane; i < n; i += 32) {
-        const double a = s_x[c * n + i];
-        finite = finite && isfinite(a);
-        mx = fmax(mx, fabs(a));
-      }
-      mx = warp_max(mx);
-      finite = __all_sync(0xffffffffu, finite);
-      const int F = mx > 0.0 ? fx_exponent(mx) : 0;
+      const uint64_t mb = warp_absmax_bits(s_x + c * n, n, lane);
+      const bool finite = mb < 0x7ff0000000000000ull;
+      const int F = finite && mb != 0 ? fx_exponent(__longlong_as_double((long long)mb)) : 0;
       for (int i = lane; i < n; i += 32) {
         const int64_t v = finite ? fx_scale_round(s_x[c * n + i], 58 - F) : 0;
         const int32_t v0 = (int32_t)((int64_t)((uint64_t)v << 35) >> 35);
