@@ -58,6 +58,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 NCU_TRAFFIC = {
     ("k_vanka_apply", "c01e3c9fe148"): 0.97,
     ("k_vanka_apply_kron", "15072119f8f1"): 1.02,
+    ("k_vanka_apply_kron_fx", "731c3058e683"): 1.09,
 }
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
                "k_vanka_apply_lu": "k_patch_big.cu", "k_vanka_apply_kron": "k_patch_kron.cu",
