@@ -58,21 +58,24 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 NCU_TRAFFIC = {
     ("k_vanka_apply", "c01e3c9fe148"): 0.97,
     ("k_vanka_apply_kron", "15072119f8f1"): 1.02,
-    ("k_vanka_apply_kron_fx", "731c3058e683"): 1.09,
+    ("k_vanka_apply_kron_fx", "37f8eee9d889"): 1.09,
 }
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
                "k_vanka_apply_lu": "k_patch_big.cu", "k_vanka_apply_kron": "k_patch_kron.cu",
                "k_vanka_apply_kron_staged": "k_patch_kron.cu",
                "k_vanka_apply_kron_big": "k_patch_kron.cu",
                "k_vanka_apply_kron_ws": "k_patch_kron.cu",
-               "k_vanka_apply_kron_fx": "k_patch_fixed.cu",
-               "k_vanka_apply_kron_fx_staged": "k_patch_fixed.cu"}
+               "k_vanka_apply_kron_fx": ("k_patch_fixed.cu", "fx_math.h"),
+               "k_vanka_apply_kron_fx_staged": ("k_patch_fixed.cu", "fx_math.h")}
 
 
 def kernel_source_hash(kernel="k_vanka_apply_kron"):
-    path = os.path.join(ROOT, "paper_2202_07381_gb300", "csrc", KERNEL_FILE[kernel])
-    with open(path, "rb") as fh:
-        return hashlib.sha1(fh.read()).hexdigest()[:12]
+    files = KERNEL_FILE[kernel]
+    h = hashlib.sha1()
+    for f in (files,) if isinstance(files, str) else files:
+        with open(os.path.join(ROOT, "paper_2202_07381_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
 
 
 def peaks():

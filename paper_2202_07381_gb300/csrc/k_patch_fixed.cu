@@ -29,6 +29,7 @@
 // (k_vanka_apply_kron_fx_staged); the set-up autotuner picks per level.
 #include <climits>
 
+#include "fx_math.h"
 #include "irkmg_internal.h"
 #include "tma.cuh"
 
@@ -79,80 +80,6 @@ __device__ __forceinline__ int64_t mad_wide(int32_t a, int32_t b, int64_t c) {
   int64_t d;
   asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
   return d;
-}
-
-// round(x · 2^k) to the nearest integer, ties to even, for |x · 2^k| ≤ 2^62,
-// from the bits of x (|x| = m 2^e with a 53-bit integer m): a shift of m,
-// with round-half-even on the bits shifted out.  No FP64 instruction.
-__device__ __forceinline__ int64_t fx_scale_round(double x, int k) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const int ef = (int)((b >> 52) & 0x7ff);
-  uint64_t m = b & 0xfffffffffffffull;
-  int e = -1074;
-  if (ef != 0) {
-    m |= 1ull << 52;
-    e = ef - 1075;
-  }
-  const int sh = e + k;
-  uint64_t v;
-  if (sh >= 0) {
-    v = m << sh;
-  } else if (sh <= -64) {
-    v = 0;  // m < 2^53: below one half
-  } else {
-    const int r = -sh;
-    const uint64_t q = m >> r, rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
-    v = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-  }
-  return (b >> 63) ? -(int64_t)v : (int64_t)v;
-}
-
-// F with |y| < 2^F ≤ 2|y| for y > 0 (the exponent frexp returns), from the bits.
-__device__ __forceinline__ int fx_exponent(double y) {
-  const uint64_t b = (uint64_t)__double_as_longlong(y);
-  const int ef = (int)((b >> 52) & 0x7ff);
-  if (ef != 0) return ef - 1022;
-  return -1010 - __clzll((long long)(b & 0xfffffffffffffull));  // subnormal
-}
-
-// The double nearest to t · 2^e (ties to even) for the exact sum
-// t = a[0] 2^58 + (a[1] + a[2]) 2^29 + a[3]: the top 64 bits of |t| (the rest
-// folded into a sticky bit), rounded to 53 bits and packed with the exponent
-// by integer operations; results outside the normal range go through the
-// library's ldexp.
-__device__ __forceinline__ double fx_round(const int64_t* a, int e) {
-  const __int128 t = (__int128)a[0] * ((__int128)1 << 58) +
-                     ((__int128)a[1] + (__int128)a[2]) * ((__int128)1 << 29) + (__int128)a[3];
-  if (t == 0) return 0.0;
-  const bool neg = t < 0;
-  const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)t : (unsigned __int128)t;
-  const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
-  uint64_t w;  // |t| ~ w 2^x, top bit of w at 63
-  int x;
-  if (hi == 0) {
-    const int lz = __clzll((long long)lo);
-    w = lo << lz;
-    x = -lz;
-  } else {
-    const int sh = 64 - __clzll((long long)hi);  // 1 .. 57, since |t| < 2^121
-    w = (uint64_t)(u >> sh) | (uint64_t)((lo << (64 - sh)) != 0);
-    x = sh;
-  }
-  uint64_t m = w >> 11;
-  const uint64_t rem = w & 0x7ff;
-  if (rem > 0x400 || (rem == 0x400 && (m & 1))) ++m;
-  int X = x + e + 11;  // |t 2^e| rounds to m 2^X, m in [2^52, 2^53]
-  if (m >> 53) {
-    m >>= 1;
-    ++X;
-  }
-  const int be = X + 52 + 1023;
-  if (be <= 0 || be >= 2047) {
-    const double d = ldexp((double)m, X);
-    return neg ? -d : d;
-  }
-  return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)be << 52) |
-                                          (m & 0xfffffffffffffull)));
 }
 
 // Bit pattern of the largest |x_i| over a warp's entries (i = lane, lane + 32,
@@ -207,8 +134,8 @@ __global__ void k_patch_to_fixed(int nm, int nmax, int64_t npatch, const int32_t
     for (int j = 0; j < n; ++j) {
       const double a = X[(int64_t)j * n + i];
       const int64_t q = finite ? fx_scale_round(a, 57 - E) : 0;
-      const int32_t a0 = (int32_t)((int64_t)((uint64_t)q << 35) >> 35);  // low 29 bits, signed
-      const int32_t a1 = (int32_t)((q - a0) >> 29);
+      int32_t a1, a0;
+      fx_split29(q, &a1, &a0);
       Q[(int64_t)j * n + i] = make_int2(a0, a1);
     }
   }
@@ -264,13 +191,11 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
   for (int c = 0; c < P.nsrc; ++c) {
     const uint64_t mb = warp_absmax_bits(s_x + c * n, n, lane);
     const bool finite = mb < 0x7ff0000000000000ull;
-    const int F = finite && mb != 0 ? fx_exponent(__longlong_as_double((long long)mb)) : 0;
+    const int F = finite && mb != 0 ? fx_exponent(fx_from_bits(mb)) : 0;
     for (int i = lane; i < ls; i += 32) {
       const int64_t v = finite && i < n ? fx_scale_round(s_x[c * n + i], 58 - F) : 0;
-      const int32_t v0 = (int32_t)((int64_t)((uint64_t)v << 35) >> 35);
       Limbs L;
-      L.v1 = (int32_t)((v - v0) >> 29);
-      L.v0 = v0;
+      fx_split29(v, &L.v1, &L.v0);
       s_lim[c * ls + i] = L;
     }
     if (lane == 0) s_F[c] = finite ? F : INT_MIN;
@@ -535,13 +460,11 @@ __global__ void __launch_bounds__(kFxStagedThreads, 1)
       const int c = warp;
       const uint64_t mb = warp_absmax_bits(s_x + c * n, n, lane);
       const bool finite = mb < 0x7ff0000000000000ull;
-      const int F = finite && mb != 0 ? fx_exponent(__longlong_as_double((long long)mb)) : 0;
+      const int F = finite && mb != 0 ? fx_exponent(fx_from_bits(mb)) : 0;
       for (int i = lane; i < n; i += 32) {
         const int64_t v = finite ? fx_scale_round(s_x[c * n + i], 58 - F) : 0;
-        const int32_t v0 = (int32_t)((int64_t)((uint64_t)v << 35) >> 35);
         Limbs L;
-        L.v1 = (int32_t)((v - v0) >> 29);
-        L.v0 = v0;
+        fx_split29(v, &L.v1, &L.v0);
         s_lim[c * n + i] = L;
       }
       if (lane == 0) s_F[c] = finite ? F : INT_MIN;
