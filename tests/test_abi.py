@@ -76,7 +76,8 @@ def test_defaults_and_strerror(irkmg):
     assert irkmg.irkmg_strerror(99) == "unknown status"
 
 
-@pytest.mark.parametrize("bad", ["tableau", "dt", "levels", "precision", "smoother", "dim"])
+@pytest.mark.parametrize("bad", ["tableau", "dt", "levels", "precision", "smoother", "dim",
+                                 "fixed"])
 def test_setup_rejects_bad_arguments_before_touching_the_gpu(irkmg, bad):
     """Validation failures are reported as EINVAL/ENOTIMPL with a message and a
     NULL context; they happen before any CUDA call, so this runs on the CPU."""
@@ -92,6 +93,9 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(irkmg, bad):
         o.nlevels = 1
     elif bad == "precision":
         o.patch_precision = 16
+    elif bad == "fixed":
+        o.patch_form = 1
+        o.patch_fixed = 2
     elif bad == "smoother":
         o.smoother = 1
         o.cheb_lo, o.cheb_hi = 8.0, 2.0
@@ -212,3 +216,35 @@ def test_hessenberg_eigenvalues_special_cases(irkmg):
     H = np.array([[1.0, 1.0], [1e-12, 1.0]])
     ev = irkmg.irkmg_hessenberg_eigvals(H)
     np.testing.assert_allclose(np.sort(ev.real), np.sort(np.linalg.eigvals(H).real), atol=1e-9)
+
+
+def test_binding_structs_match_the_header_layout(irkmg, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the same struct from include/irkmg.h (a field
+    added on one side only would shift every later field)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = [(irkmg.Mesh, "irkmg_mesh"), (irkmg.Tableau, "irkmg_tableau"),
+             (irkmg.Options, "irkmg_options"), (irkmg.Stats, "irkmg_stats"),
+             (irkmg.LevelInfo, "irkmg_level_info"), (irkmg.NSStats, "irkmg_ns_stats"),
+             (irkmg.Trace, "irkmg_trace")]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "irkmg.h"', "int main(void) {"]
+    expect = []
+    for cls, cname in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expect.append(ct.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {name}));')
+            expect.append(getattr(cls, name).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == expect
