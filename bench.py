@@ -599,6 +599,10 @@ def run_ours(args, wl, rank, world, local_rank):
 
     assert base_config(wl)["N"] == N and base_config(wl)["patches_finest"] == ctx.finest["nv"]
     forms = {}
+    shapes_ms = None
+    if rank == 0 and fixed and not args.small:
+        # after the timed region: one finest-level correction per launch shape
+        shapes_ms = shape_sweep(irkmg, torch, ctx, dev, stream)
     if rank == 0 and not args.small and prec == 64 and not args.no_forms:
         for name, fp, pf, fx in (("dense_fp64", 64, 0, 0), ("dense_fp32", 32, 0, 0),
                                  ("kron_fp64", 64, 1, 0), ("kron_fp64_fixed", 64, 1, 1),
@@ -659,6 +663,7 @@ def run_ours(args, wl, rank, world, local_rank):
                                        "sources, rounded once to FP64" if fixed else
                                        "FP64 FMAs" if prec == 64 else "FP32 patch entries"),
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
+                       "apply_shape_per_level": [lv["apply_shape"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
                              % (ctx.finest["factor_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -671,6 +676,7 @@ def run_ours(args, wl, rank, world, local_rank):
                               "launches": trace["op_launches"],
                               "avg_launch_ms": trace["op_ms"] / max(trace["op_launches"], 1)},
             "gpu_launches": trace["launches"],
+            "finest_correction_ms_per_shape": shapes_ms,
             "forms": forms,
             "clocks": clk.summary(),
             "e2e": {"value": replica_value(e2e_s * 1e3, args.steps, world), "unit": UNIT,
