@@ -1,5 +1,6 @@
-"""The minimal use shown to library users (one decoupled-patch stage solve and
-time step on a 128x128 mesh) runs and converges."""
+"""The minimal use shown to library users (one decoupled-patch stage solve with
+fixed-point patch mat-vecs and one time step on a 128x128 mesh) runs and
+converges."""
 import pytest
 
 from tests.gpu_util import need_gpu
@@ -15,6 +16,7 @@ def test_minimal_stage_solve_and_step():
     opt = irkmg.irkmg_default_options()
     opt.nlevels = 5
     opt.patch_form = 1
+    opt.patch_fixed = 1
     ctx = irkmg.irkmg_setup(*synth.square_mesh(8), A, b, c, 1 / 64, 1.0, opt)
     fin = ctx.finest
     dev = lambda n: torch.zeros(n, dtype=torch.float64, device="cuda")
