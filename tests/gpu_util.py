@@ -28,7 +28,18 @@ def host(t):
 
 
 def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    """Error of a against the reference b, as the larger of two measures so
+    that an assertion rel(a, b) < tol checks both: the relative l2 error
+    ||a - b|| / ||b||, and entry by entry max_i |a_i - b_i| / (|b_i| + ||b||_inf)
+    (a few wrong entries of a long vector hide in the l2 norm, not here)."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    d = np.abs(a - b)
+    l2 = np.linalg.norm(d) / max(np.linalg.norm(b), 1e-300)
+    if b.size == 0:
+        return l2
+    ent = np.max(d / np.maximum(np.abs(b) + np.max(np.abs(b)), 1e-300))
+    return max(l2, float(ent))
 
 
 @functools.lru_cache(maxsize=None)

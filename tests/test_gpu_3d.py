@@ -114,21 +114,29 @@ def test_3d_solve_and_fp32_form(pair3):
     F = dev(np.zeros(L.N))
     irkmg.irkmg_stage_rhs(ctx, dev(un), dev(pn), dev(f.ravel()), F)
     assert rel(host(F), F_ref) < 1e-12
+    # at the benchmark tolerance 1e-10: same iteration count as the oracle +-2
     k = dev(np.zeros(L.N))
     st = irkmg.irkmg_solve(ctx, dev(F_ref), k)
     assert st["status"] == 0
-    x_ref, its_ref, _ = fgmres.fgmres(L.J, F_ref, H.vcycle, rtol=1e-10, project=H.project_pressure,
-                                      maxit=400)
-    assert rel(H.project_pressure(host(k)), H.project_pressure(x_ref)) < 1e-6
+    _, its_ref, _ = fgmres.fgmres(L.J, F_ref, H.vcycle, rtol=1e-10, project=H.project_pressure,
+                                  maxit=400)
     assert abs(st["iters"] - its_ref) <= 2
-    # FP32 patch factors and applies inside the FP64 FGMRES
-    n0, nl = int(round(m.nv ** (1 / 3))) - 1, len(H.levels)
-    c32 = _ctx(irkmg, 2, nl, H.s, H.dt, precision=32)
-    k32 = dev(np.zeros(L.N))
-    st32 = irkmg.irkmg_solve(c32, dev(F_ref), k32)
-    assert st32["status"] == 0 and st32["rfinal"] <= 1e-10 * np.linalg.norm(F_ref)
-    assert rel(H.project_pressure(host(k32)), H.project_pressure(host(k))) < 1e-6
-    c32.close()
+    # solved to 1e-13 on both sides, the solutions agree to 1e-8: FP64 patches
+    # and FP32 patch factors and applies inside the FP64 FGMRES, both against
+    # the oracle
+    x_ref, _, _ = fgmres.fgmres(L.J, F_ref, H.vcycle, rtol=1e-13, project=H.project_pressure,
+                                maxit=800)
+    ref = H.project_pressure(x_ref)
+    nl = len(H.levels)
+    for prec in (64, 32):
+        c = _ctx(irkmg, 2, nl, H.s, H.dt, precision=prec, rtol=1e-13, maxit=800)
+        try:
+            kk = dev(np.zeros(L.N))
+            stp = irkmg.irkmg_solve(c, dev(F_ref), kk)
+            assert stp["status"] == 0 and stp["rfinal"] <= 1e-13 * np.linalg.norm(F_ref), (prec, stp)
+            assert rel(H.project_pressure(host(kk)), ref) < 1e-8, prec
+        finally:
+            c.close()
 
 
 def test_3d_unsupported_forms_say_so(pair3):

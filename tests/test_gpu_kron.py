@@ -3,9 +3,10 @@ the oracle's dense patch inverses.
 
 The decoupled form applies A_v⁻¹ = (T ⊗ I) (I ⊗ M̃ + Δt D ⊗ K̃)⁻¹ (T⁻¹ ⊗ I),
 exact in exact arithmetic (the Kronecker form of the stage system, Section 3).
-Its rounding differs from a dense LU by about cond(T) · κ(blocks) · eps, a few
-times the dense form's, so the Vanka and V-cycle bars are 1e-11 (dense: 1e-12);
-the FGMRES solution keeps the 1e-8 bar."""
+Its rounding differs from a dense LU by about cond(T) · κ(blocks) · eps; on
+the 2D cases below the measured errors stay below 3e-14, so the 2D Vanka and
+V-cycle bars are the dense form's 1e-12 (3D patches, whose blocks are
+factored by the blocked LU, keep 1e-11); the FGMRES solution keeps 1e-8."""
 import functools
 
 import numpy as np
@@ -63,16 +64,16 @@ def test_decoupled_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
             r = synth.random_vector(500 + l, L.N)
             c = dev(np.zeros(L.N))
             irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l)
-            assert rel(host(c), L.vanka.correction(r)) < 1e-11
+            assert rel(host(c), L.vanka.correction(r)) < 1e-12
             irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l, transpose=True)
             ref_t = np.zeros(L.N)
             for idx, f in zip(L.vanka.dofs, L.vanka.lu):
                 ref_t[idx] += sla.lu_solve(f, r[idx], trans=1)
-            assert rel(host(c), ref_t) < 1e-11
+            assert rel(host(c), ref_t) < 1e-12
         r = synth.random_vector(599, H.finest.N)
         z = dev(np.zeros(H.finest.N))
         irkmg.irkmg_vcycle(ctx, dev(r), z)
-        assert rel(host(z), H.vcycle(r)) < 1e-11
+        assert rel(host(z), H.vcycle(r)) < 1e-12
     finally:
         ctx.close()
 
@@ -152,10 +153,10 @@ def test_decoupled_oseen_matches_oracle():
         r = synth.random_vector(808, L.N)
         c = dev(np.zeros(L.N))
         irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=nl - 1)
-        assert rel(host(c), L.vanka.correction(r)) < 1e-11
+        assert rel(host(c), L.vanka.correction(r)) < 1e-12
         z = dev(np.zeros(L.N))
         irkmg.irkmg_vcycle(ctx, dev(r), z)
-        assert rel(host(z), H.vcycle(r)) < 1e-11
+        assert rel(host(z), H.vcycle(r)) < 1e-12
     finally:
         ctx.close()
 

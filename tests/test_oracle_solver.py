@@ -51,12 +51,19 @@ def test_richardson_omega_half_is_not_contractive():
 
 
 @pytest.mark.slow
-def test_iterations_flat_under_refinement():
-    A, b, c = tableau.radau_iia(2)
+@pytest.mark.parametrize("s,dt", [(2, 1 / 8), (3, 1 / 64)])
+def test_iterations_flat_under_refinement(s, dt):
+    """FGMRES iterations for 4x4 ... 32x32 finest meshes (2 .. 5 levels from
+    2x2) stay within 2 of the middle of their range (max - min <= 4), and one
+    refinement adds at most 2 (Section 5.1, Table 1: nearly constant counts;
+    the paper's own fixed-dt Radau IIA rows grow by 5 to 8 over two
+    refinements, so this bar is stricter than the paper's behaviour)."""
+    A, b, c = tableau.radau_iia(s)
     its = []
     for nl in (2, 3, 4, 5):
-        H = mg.Hierarchy(*synth.square_mesh(2), nl, A, 1 / 8)
+        H = mg.Hierarchy(*synth.square_mesh(2), nl, A, dt)
         F, _, _ = problem.mms_rhs(H, c)
         _, k, _ = fgmres.fgmres(H.finest.J, F, H.vcycle, rtol=1e-10, project=H.project_pressure)
         its.append(k)
     assert max(its) - min(its) <= 4, its
+    assert all(b_ - a_ <= 2 for a_, b_ in zip(its, its[1:])), its
