@@ -92,8 +92,10 @@ FX_HD void fx_split29(int64_t q, int32_t* hi, int32_t* lo) {
 // The double nearest to t · 2^e (ties to even) for the exact sum
 // t = a[0] 2^58 + (a[1] + a[2]) 2^29 + a[3], |t| < 2^127: the top 64 bits of
 // |t| (the rest folded into a sticky bit), rounded to 53 bits and packed with
-// the exponent by integer operations; results outside the normal range go
-// through the library's ldexp.
+// the exponent by integer operations.  A result below the normal range is
+// rounded once, from the same 64 bits and sticky bit, to a multiple of
+// 2^−1074 (the subnormal spacing); an overflow goes through the library's
+// ldexp (an exact m 2^X, or infinity).
 FX_HD double fx_round(const int64_t* a, int e) {
   const __int128 t = (__int128)a[0] * ((__int128)1 << 58) +
                      ((__int128)a[1] + (__int128)a[2]) * ((__int128)1 << 29) + (__int128)a[3];
@@ -121,7 +123,21 @@ FX_HD double fx_round(const int64_t* a, int e) {
     ++X;
   }
   const int be = X + 52 + 1023;
-  if (be <= 0 || be >= 2047) {
+  if (be <= 0) {
+    // |t 2^e| = w 2^(x+e) rounds to k 2^−1074: shift w right by sh >= 11
+    const int sh = -(x + e + 1074);
+    uint64_t k;
+    if (sh >= 65) {
+      k = 0;  // below a quarter of the spacing
+    } else if (sh == 64) {
+      k = w > (1ull << 63) ? 1 : 0;  // w 2^−64 in [1/2, 1): an exact half goes to 0 (even)
+    } else {
+      const uint64_t q = w >> sh, rem = w & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+      k = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+    }
+    return fx_from_bits(((uint64_t)neg << 63) | k);  // k = 2^52 packs the least normal
+  }
+  if (be >= 2047) {
     const double d = ldexp((double)m, X);
     return neg ? -d : d;
   }

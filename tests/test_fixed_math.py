@@ -119,3 +119,47 @@ def test_round_is_the_nearest_double(driver):
         t = a[0] * 2 ** 58 + (a[1] + a[2]) * 2 ** 29 + a[3]
         ref = nearest_double(Fraction(t) * Fraction(2) ** e)
         assert float.fromhex(g) == ref, (a, e, g, ref)
+
+
+def nearest_double_any(fr):
+    """The double nearest to a Fraction, ties to even, subnormals included:
+    below 2^-1022 the grid is the multiples of 2^-1074."""
+    if fr == 0:
+        return 0.0
+    neg, a = fr < 0, abs(fr)
+    if a >= Fraction(2) ** -1022:
+        return nearest_double(fr)
+    d = math.ldexp(rne(a / Fraction(2) ** -1074), -1074)
+    return -d if neg else d
+
+
+def test_round_below_the_normal_range_rounds_once(driver):
+    """Results below 2^-1022 must be rounded once, straight to the subnormal
+    spacing: rounding first to 53 bits and then again to the subnormal
+    precision gets the halfway cases wrong (double rounding)."""
+    rng = random.Random(15)
+    cases = []
+    for _ in range(6000):
+        a = [rng.randint(-2 ** 62, 2 ** 62) for _ in range(4)]
+        for i in range(rng.randint(0, 3)):
+            a[rng.randrange(4)] = 0
+        t = a[0] * 2 ** 58 + (a[1] + a[2]) * 2 ** 29 + a[3]
+        if t == 0:
+            continue
+        # put |t 2^e| between 2^-1140 and 2^-1020
+        e = rng.randint(-1140, -1020) - (abs(t).bit_length() - 1)
+        cases.append((a, e))
+    # double-rounding traps: t 2^e = (2k + 1) 2^-1075 + a tiny excess that a
+    # first rounding to 53 bits drops (for k >= 2^52 / 2^11 ...) or keeps
+    for k in (1, 3, 2 ** 40 + 1, 2 ** 51 - 1, 2 ** 52 - 1):
+        for excess in (1, -1, 0):
+            t = ((2 * k + 1) << 10) + excess          # (2k+1) 2^10 (+-1), e = -1085
+            a0, rest = divmod(t, 2 ** 58)
+            cases.append(([a0, 0, 0, rest], -1085))
+            cases.append(([-a0, 0, 0, -rest], -1085))   # the negative of it
+    got = run(driver, "r", [" ".join(map(str, a)) + f" {e}" for a, e in cases])
+    assert len(got) == len(cases)
+    for (a, e), g in zip(cases, got):
+        t = a[0] * 2 ** 58 + (a[1] + a[2]) * 2 ** 29 + a[3]
+        ref = nearest_double_any(Fraction(t) * Fraction(2) ** e)
+        assert float.fromhex(g) == ref, (a, e, g, ref)
