@@ -23,16 +23,20 @@ step; set-up time is reported separately as setup_s.
 sample of the same workload.
 """
 import os
+import sys
 
-os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-os.environ.setdefault("OMP_NUM_THREADS", "1")
+# the oracle (reference arm, CPU baseline) gets every host core for its BLAS;
+# the GPU arm's own process keeps one BLAS thread (its oracle timing runs in a
+# fresh subprocess)
+_BLAS_THREADS = str(os.cpu_count() or 1) if "reference" in sys.argv else "1"
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, _BLAS_THREADS)
 
 import argparse  # noqa: E402
 import hashlib  # noqa: E402
 import json  # noqa: E402
 import statistics  # noqa: E402
 import subprocess  # noqa: E402
-import sys  # noqa: E402
 import time  # noqa: E402
 
 import numpy as np  # noqa: E402
@@ -45,9 +49,10 @@ import synth  # noqa: E402
 METRIC = "IRK stage solve time to 1e-10 resid; Vanka apply+SpMV HBM GB/s vs peak"
 UNIT = "s/solve"
 FALLBACK_HBM = 6800.0
-# FP64 ALU peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz
-# (nominal 1.25 TFLOP/s; the project's FMA probe measured 1.251).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 ALU peak of GB300 from the unit count and the maximum clock: 152 SMs x
+# 2 FP64 FMA per clock x 2 flop x 2070 MHz.  The run measures it as well
+# (irkmg_probe_peak, measure_alu_peaks) and reports against the measurement.
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM traffic of the finest-level Vanka kernel from an ncu capture, as the
 # ratio (dram__bytes_read + dram__bytes_write) / algorithmic bytes of the
@@ -76,6 +81,19 @@ def kernel_source_hash(kernel="k_vanka_apply_kron"):
         with open(os.path.join(ROOT, "paper_2202_07381_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def measure_alu_peaks(irkmg, stream):
+    """FP64 and FP32 FMA rates (TFLOP/s) and the 32 x 32 -> 64-bit integer
+    multiply-add rate (T/s) of this GPU, each from one timed launch of
+    irkmg_probe_peak (about 10-20 ms each)."""
+    h = stream.cuda_stream
+    return {"fp64_tflops": irkmg.irkmg_probe_peak(0, 4000, h) / 1e12,
+            "fp32_tflops": irkmg.irkmg_probe_peak(1, 200000, h) / 1e12,
+            "mad_wide_s32_tops": irkmg.irkmg_probe_peak(2, 100000, h) / 1e12,
+            "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
+            "how": "irkmg_probe_peak: one launch of 8 CTAs x 256 threads per SM, 8 independent "
+                   "multiply-add chains per thread, CUDA events on the launch stream"}
 
 
 def peaks():
@@ -160,23 +178,93 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # reference arm: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, n_sample):
-    """Time the oracle's FGMRES + V-cycle solve of the same problem on an
-    n_sample x n_sample mesh; returns (seconds per solve at the sample size,
-    seconds scaled to the workload by the DoF ratio, description)."""
+class _TimedOp:
+    """A matrix whose products `@` add their wall time to acc[key] (timing of
+    the oracle's phases; the product itself is the matrix's own)."""
+
+    def __init__(self, A, acc, key):
+        self.A, self.acc, self.key = A, acc, key
+
+    def __matmul__(self, x):
+        t = time.perf_counter()
+        y = self.A @ x
+        self.acc[self.key] += time.perf_counter() - t
+        return y
+
+    @property
+    def T(self):
+        return _TimedOp(self.A.T, self.acc, self.key)
+
+    def __getattr__(self, name):
+        return getattr(self.A, name)
+
+
+def _timed_call(fn, acc, key):
+    def wrapped(*a, **k):
+        t = time.perf_counter()
+        y = fn(*a, **k)
+        acc[key] += time.perf_counter() - t
+        return y
+    return wrapped
+
+
+def oracle_run(wl, n_sample, solves=1):
+    """The oracle's set-up and FGMRES + V-cycle solve of the workload's problem
+    on an n_sample x n_sample finest mesh (same tableau, dt, nu, smoother,
+    coarsest mesh and tolerance), timed by phase: the stage operator products,
+    the Vanka corrections, the transfers, the coarsest solves, and the rest of
+    FGMRES (Gram-Schmidt, Givens, vector updates).  The phases are timed by
+    wrapping the oracle's own objects; its arithmetic is untouched."""
     from oracle import fgmres, mg, problem, tableau
     A, b, c = tableau.radau_iia(wl["s"])
     levels = int(round(np.log2(n_sample / wl["n0"]))) + 1
+    w0, c0 = time.perf_counter(), time.process_time()
     H = mg.Hierarchy(*synth.square_mesh(wl["n0"]), levels, A, wl["dt"], nu=wl["nu"])
+    setup_s = time.perf_counter() - w0
     F, _, _ = problem.mms_rhs(H, c)
-    t0 = time.perf_counter()
-    _, its, _ = fgmres.fgmres(H.finest.J, F, H.vcycle, rtol=1e-10, project=H.project_pressure)
-    dt = time.perf_counter() - t0
-    n_full = wl["s"] * (2 * (2 * wl["n"] - 1) ** 2 + (wl["n"] + 1) ** 2)
-    scaled = dt * n_full / H.finest.N
-    desc = (f"oracle solve at {n_sample}x{n_sample} ({levels} levels, N={H.finest.N}, {its} FGMRES "
-            f"iterations, {dt:.2f} s, 1 thread), scaled by N ratio {n_full}/{H.finest.N}")
-    return dt, scaled, desc
+    acc = {"stage_operator": 0.0, "vanka": 0.0, "transfers": 0.0, "coarse": 0.0}
+    for l, L in enumerate(H.levels):
+        L.J = _TimedOp(L.J, acc, "stage_operator")
+        if l > 0:
+            L.P = _TimedOp(L.P, acc, "transfers")
+            L.vanka.correction = _timed_call(L.vanka.correction, acc, "vanka")
+    H.coarse_solve = _timed_call(H.coarse_solve, acc, "coarse")
+    times, its = [], None
+    for _ in range(solves):
+        t0 = time.perf_counter()
+        _, its, _ = fgmres.fgmres(H.finest.J, F, H.vcycle, rtol=1e-10, project=H.project_pressure)
+        times.append(time.perf_counter() - t0)
+    wall, cpu = time.perf_counter() - w0, time.process_time() - c0
+    solve = float(np.mean(times))
+    phases = {k: v / solves for k, v in acc.items()}
+    phases["fgmres_rest"] = solve - sum(phases.values())
+    return {"n": n_sample, "levels": levels, "N": H.finest.N, "iters": its, "setup_s": setup_s,
+            "solve_s": solve, "solves": solves, "phases_s": phases,
+            "cpu_time_over_wall": cpu / wall, "blas_threads": int(os.environ["OPENBLAS_NUM_THREADS"])}
+
+
+def oracle_fit(runs, n_full):
+    """t_solve = a N^alpha through the two largest measured sizes, evaluated at
+    the workload's N: an extrapolation, labelled as such."""
+    r1, r2 = sorted(runs, key=lambda r: r["N"])[-2:]
+    alpha = float(np.log(r2["solve_s"] / r1["solve_s"]) / np.log(r2["N"] / r1["N"]))
+    return {"law": "t_solve = a * N^alpha through the two largest measured sizes",
+            "alpha": alpha, "N": n_full,
+            "extrapolated_s_per_solve": r2["solve_s"] * (n_full / r2["N"]) ** alpha}
+
+
+def oracle_baseline_subprocess(args, sizes=(32, 64)):
+    """The oracle's per-phase timings at the given sizes, run in a fresh
+    process whose BLAS may use every host core (this process keeps one)."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--oracle-sizes",
+           ",".join(map(str, sizes)), "--n", str(args.n)]
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(os.cpu_count() or 1)
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, env=env)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def max_over_ranks(x, device):
@@ -205,23 +293,38 @@ def base_config(wl):
 
 
 def run_reference(args, wl, rank):
+    """The oracle on the host cores.  Each step is one FGMRES solve of the
+    workload's problem on a bounded sample mesh (64 x 64, 32 x 32 for long
+    runs), after one set-up; the line reports the measured time of that size
+    and names it in config.  --oracle-sizes: per-phase timings at several
+    sizes plus the fitted extrapolation (the GPU arm's cpu_baseline)."""
     if rank != 0:
         return
-    n_sample = 8 if args.small else 64
-    vals, desc = [], ""
-    for _ in range(max(1, args.warmup)):
-        oracle_sample(wl, n_sample)
-        if not args.small:
-            break
-    for _ in range(args.steps):
-        _, scaled, desc = oracle_sample(wl, n_sample)
-        vals.append(scaled)
-    v = float(np.mean(vals))
+    n_full = base_config(wl)["N"]
+    if args.oracle_sizes:
+        runs = [oracle_run(wl, int(n)) for n in args.oracle_sizes.split(",")]
+        print(json.dumps({"runs": runs, "fit": oracle_fit(runs, n_full) if len(runs) > 1 else None,
+                          "cores_available": os.cpu_count()}), flush=True)
+        return
+    n_sample = 8 if args.small else (64 if args.steps + min(args.warmup, 1) <= 30 else 32)
+    a2 = argparse.Namespace(**vars(args))
+    a2.n = n_sample
+    swl = workload(a2)
+    run = oracle_run(swl, n_sample, solves=args.steps + min(args.warmup, 1))
+    v = run["solve_s"]
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": base_config(wl),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "data": "synthetic", "config": base_config(swl),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"oracle FGMRES + V-cycle solve at {n_sample}x{n_sample} "
+                                       f"({run['levels']} levels, N={run['N']}, {run['iters']} "
+                                       f"iterations), mean of {run['solves']} solves after one "
+                                       f"set-up ({run['setup_s']:.1f} s); BLAS threads "
+                                       f"{run['blas_threads']}, CPU time / wall "
+                                       f"{run['cpu_time_over_wall']:.2f}",
+                             "phases_s": run["phases_s"]},
+            "measured_size": {"n": n_sample, "N": run["N"], "iters": run["iters"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -313,7 +416,7 @@ def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form, 
                                "bytes_per_launch": tr["vanka_bytes"] / nvl,
                                "flops_per_launch": tr["vanka_flops"] / nvl,
                                "hbm_gbs": gbs, "hbm_frac": gbs / hbm, "tflops": tf,
-                               "fp64_frac": (tf / FP64_PEAK_TFLOPS
+                               "fp64_frac": (tf / FP64_NOMINAL_TFLOPS
                                              if precision == 64 and not patch_fixed else None),
                                "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
     if patch_fixed:
@@ -334,8 +437,10 @@ def shape_sweep(irkmg, torch, ctx, dev, stream, reps=10):
     for shape in range(16):
         try:
             irkmg.irkmg_level_set_apply(ctx, fin, shape, 1)
-        except irkmg.IrkmgError:
-            break
+        except irkmg.IrkmgError as e:
+            if "does not fit" in str(e):
+                continue    # a later shape may still fit
+            break           # no such launch shape: the list is exhausted
         for _ in range(2):
             irkmg.irkmg_vanka_correction(ctx, r, c)
         torch.cuda.synchronize()
@@ -348,6 +453,26 @@ def shape_sweep(irkmg, torch, ctx, dev, stream, reps=10):
         res[f"kernel{ctx.finest['apply_kernel']}_shape{shape}"] = e0.elapsed_time(e1) / reps
     irkmg.irkmg_level_set_apply(ctx, fin, *keep)
     return res
+
+
+def mesh_sweep(irkmg, torch, wl, args, dev, stream, prec, fixed, sizes=(32, 64, 128, 256)):
+    """FGMRES iterations of the same stage solve (same tableau, dt, smoother,
+    patch form and tolerance) on coarser finest meshes from the same 8 x 8
+    coarsest mesh: the mesh-independence figure of Section 5.1, Table 1."""
+    out = {}
+    for n in sizes:
+        w = dict(wl, n=n, levels=int(round(np.log2(n / wl["n0"]))) + 1)
+        ctx, _, c = make_context(irkmg, w, prec, stream.cuda_stream, 0, args.patch_form, fixed)
+        u0, p0, f = initial_data(irkmg, ctx, w, c)
+        T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+        F = torch.zeros(ctx.N(), dtype=torch.float64, device=dev)
+        irkmg.irkmg_stage_rhs(ctx, T(u0), T(p0), T(f), F)
+        k = torch.zeros_like(F)
+        st = irkmg.irkmg_solve(ctx, F, k)
+        out[n] = {"iters": st["iters"], "levels": w["levels"], "N": ctx.N(),
+                  "rel_residual": st["rfinal"] / st["r0"], "status": st["status"]}
+        ctx.close()
+    return out
 
 
 def irkmg_rel_diff(torch, a, b):
@@ -395,6 +520,19 @@ def run_batched(args, dev, stream, patch_form=1, patch_fixed=1):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     batch = irkmg.Batch(ctxs)
+    persistent = batch.persistent
+    t_graph = None
+    if persistent:   # the same batch with one V-cycle graph per system
+        batch.persistent = False
+        ks = [torch.zeros_like(F) for F in Fs]
+        batch.solve(Fs, ks)          # captures the graphs
+        ks = [torch.zeros_like(F) for F in Fs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch.solve(Fs, ks)
+        torch.cuda.synchronize()
+        t_graph = time.perf_counter() - t0
+        batch.persistent = True
     ks = [torch.zeros_like(F) for F in Fs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -412,6 +550,7 @@ def run_batched(args, dev, stream, patch_form=1, patch_fixed=1):
                         "meshes from {32,64,128,256}^2, Re ~ U[100,1000], dt in [1e-3,1e-1]",
             "systems": len(specs), "dofs_total": dofs, "all_converged": ok,
             "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
+            "persistent_launch": persistent, "batched_graphs_s": t_graph,
             "patch_form": patch_form, "patch_fixed": patch_fixed if patch_form != 0 else 0,
             "s_per_solve_batched": t_bat / len(specs), "iters_min_mean_max":
             [min(its), float(np.mean(its)), max(its)], "max_rel_diff_vs_sequential": diff,
@@ -463,6 +602,63 @@ def run_ns(args, dev, stream, n=128, re=1000.0, dt=0.01, steps=2):
                         f"dt={dt:g}, Newton + Eisenstat-Walker, FP64 dense patches",
             "N": L["N"], "setup_s": setup_s, "steps": out,
             "s_per_step": float(np.mean([x["s"] for x in out]))}
+
+
+def run_adjoint(args, dev, stream, n=128, s=2, dt=1 / 32, nsteps=8, every=2):
+    """Gradient of J = 1/2 ||u(T) - u_target||_M^2 (u_target: the manufactured
+    velocity) with respect to a per-cell P0 forcing control (seeded N(0,1)) and
+    nu through nsteps implicit Radau IIA(s) steps of dt on n x n, checkpoints
+    every `every` steps (irkmg_step / irkmg_adjoint_step behind
+    torch.autograd): wall time of forward + backward, and the agreement of the
+    directional derivatives with central differences of the forward model."""
+    import torch
+    from paper_2202_07381_gb300 import irkmg
+    from paper_2202_07381_gb300.adjoint import TrackingProblem, tracking_objective
+    A, b, c = irkmg.irkmg_radau_iia(s)
+    o = irkmg.irkmg_default_options()
+    o.nlevels = int(round(np.log2(n / 8))) + 1
+    o.patch_form = args.patch_form
+    o.patch_fixed = args.patch_fixed if args.patch_form != 0 else 0
+    o.rtol, o.atol, o.maxit = 1e-12, 1e-15, 400
+    t0 = time.perf_counter()
+    ctx = irkmg.irkmg_setup(*synth.square_mesh(8), A, b, c, dt, 1.0, o, stream=stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    xy = irkmg.irkmg_p2_coords(ctx)
+    free = irkmg.irkmg_free_nodes(ctx)
+    nv = ctx.finest["nv"]
+    ux, uy = synth.mms_velocity(xy[free, 0], xy[free, 1])
+    u0 = np.concatenate([ux, uy])
+    p0 = synth.mms_pressure(xy[:nv, 0], xy[:nv, 1])
+    fx, fy = synth.mms_forcing(xy[:, 0], xy[:, 1], nu=1.0)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    prob = TrackingProblem(ctx, dt, T(u0), T(p0 - p0.mean()),
+                           T(np.concatenate([np.concatenate([fx, fy])] * s)), T(u0), nsteps, every)
+    theta = T(synth.normal(7, 2 * ctx.finest["nc"]))
+    times = []
+    for rep in range(2):                       # the first pass is a warm-up
+        th = theta.clone().requires_grad_(True)
+        nu = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J = tracking_objective(th, nu, prob)
+        J.backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t1)
+    d = T(synth.normal(11, theta.numel()))
+    with torch.no_grad():                      # J is quadratic in theta: unit step
+        fd = (prob.objective(theta + d, 1.0) - prob.objective(theta - d, 1.0)) / 2.0
+    ad = float((th.grad * d).sum())
+    hn = 1e-6
+    fdn = (prob.objective(theta, 1.0 + hn) - prob.objective(theta, 1.0 - hn)) / (2 * hn)
+    its = [st_["iters"] for st_ in prob.stats]
+    ctx.close()
+    return {"workload": f"adjoint: Radau IIA({s}) {n}x{n}, {nsteps} steps dt={dt:g}, checkpoints "
+                        f"every {every}, gradient of 1/2||u(T)-u_target||_M^2 w.r.t. a P0 forcing "
+                        "field (N(0,1)) and nu",
+            "forward_backward_s": times[-1], "setup_s": setup_s, "objective": float(J),
+            "fd_rel_err_theta": abs(fd - ad) / abs(fd), "fd_rel_err_nu": abs(fdn - nu.grad.item()) / abs(fdn),
+            "rtol": 1e-12, "fgmres_iters_min_max": [min(its), max(its)],
+            "patch_form": args.patch_form, "patch_fixed": o.patch_fixed}
 
 
 def run_3d(args, dev, stream, patch_form=1):
@@ -544,7 +740,8 @@ def run_ours(args, wl, rank, world, local_rank):
     torch.cuda.synchronize()
     stats.clear()
     barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
-    irkmg.irkmg_trace_enable(ctx, True)
+    # tracing off in the timed region: the library only counts its launches
+    irkmg.irkmg_trace_enable(ctx, False)
     with ClockSampler(local_rank) as clk:
         barrier()
         torch.cuda.synchronize()
@@ -561,8 +758,7 @@ def run_ours(args, wl, rank, world, local_rank):
         barrier()
         time.sleep(0.25)
     ms = e0.elapsed_time(e1)
-    trace = irkmg.irkmg_trace_read(ctx)
-    irkmg.irkmg_trace_enable(ctx, False)
+    launches = irkmg.irkmg_trace_read(ctx)["launches"]
     if world > 1:
         ms = max_over_ranks(ms, dev)
     iters = [s_["iters"] for s_ in stats]
@@ -598,8 +794,27 @@ def run_ours(args, wl, rank, world, local_rank):
         e2e_s = max_over_ranks(e2e_s, dev)
 
     assert base_config(wl)["N"] == N and base_config(wl)["patches_finest"] == ctx.finest["nv"]
+    # one traced step after the timed regions: CUDA events around every
+    # finest-level Vanka, operator, transfer and Gram-Schmidt launch
+    irkmg.irkmg_trace_enable(ctx, True)
+    stats_keep = list(stats)
+    step()
+    trace = irkmg.irkmg_trace_read(ctx)
+    irkmg.irkmg_trace_enable(ctx, False)
+    stats[:] = stats_keep
     forms = {}
     shapes_ms = None
+    mesh = None
+    if rank == 0 and not args.small and wl.get("dim", 2) == 2 and not args.no_mesh_sweep:
+        sw = mesh_sweep(irkmg, torch, wl, args, dev, stream, prec, fixed,
+                        sizes=tuple(n for n in (32, 64, 128, 256) if n < wl["n"]))
+        sw[wl["n"]] = {"iters": iters[-1], "levels": wl["levels"], "N": N,
+                       "rel_residual": resid[-1], "status": stats[-1]["status"]}
+        its = [v["iters"] for v in sw.values()]
+        mesh = {"what": "FGMRES iterations to 1e-10 per finest mesh n x n, same solver, "
+                        "tableau, dt and coarsest mesh (8 x 8)",
+                "per_n": {str(n): v for n, v in sw.items()},
+                "iters": its, "max_minus_min": max(its) - min(its)}
     if rank == 0 and fixed and not args.small:
         # after the timed region: one finest-level correction per launch shape
         shapes_ms = shape_sweep(irkmg, torch, ctx, dev, stream)
@@ -613,15 +828,22 @@ def run_ours(args, wl, rank, world, local_rank):
             forms[name]["speedup_vs_headline"] = (ms / args.steps) / forms[name]["ms_per_step"]
         forms["batched"] = run_batched(args, dev, stream)
         forms["ns_newton"] = run_ns(args, dev, stream)
+        forms["adjoint"] = run_adjoint(args, dev, stream)
         forms["3d"] = run_3d(args, dev, stream, 1)
         forms["3d_dense"] = run_3d(args, dev, stream, 0)
         forms["3d"]["speedup_vs_dense"] = forms["3d_dense"]["ms_per_step"] / forms["3d"]["ms_per_step"]
     result = None
     if rank == 0:
         hbm, hbm_kind = peaks()
+        alu = measure_alu_peaks(irkmg, stream)
+        fp64_peak = alu["fp64_tflops"]
         van_gbs = trace["vanka_bytes"] / (trace["vanka_ms"] * 1e-3) / 1e9 if trace["vanka_ms"] else None
         op_gbs = trace["op_bytes"] / (trace["op_ms"] * 1e-3) / 1e9 if trace["op_ms"] else None
         op_tf = trace["op_flops"] / (trace["op_ms"] * 1e-3) / 1e12 if trace["op_ms"] else None
+        xfer_gbs = (trace["xfer_bytes"] / (trace["xfer_ms"] * 1e-3) / 1e9
+                    if trace["xfer_ms"] else None)
+        arn_gbs = (trace["arnoldi_bytes"] / (trace["arnoldi_ms"] * 1e-3) / 1e9
+                   if trace["arnoldi_ms"] else None)
         nvl = max(trace["vanka_launches"], 1)
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
                  3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
@@ -642,9 +864,9 @@ def run_ours(args, wl, rank, world, local_rank):
         if prec == 64 and not fixed:
             # FP64 on GB300 runs at 1/62 of FP32: a dense FP64 mat-vec (2 flop per
             # 8-byte entry) is bound by the FP64 pipe, not by HBM
-            roofline = {"bound": "alu", "achieved": van_tf, "peak": FP64_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": van_tf / FP64_PEAK_TFLOPS if van_tf else None,
-                        "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz", **common}
+            roofline = {"bound": "alu", "achieved": van_tf, "peak": fp64_peak,
+                        "unit": "TFLOP/s", "frac": van_tf / fp64_peak if van_tf else None,
+                        "peak_source": "FP64 FMA rate measured by irkmg_probe_peak", **common}
         else:
             roofline = {"bound": "hbm", "achieved": van_gbs, "peak": hbm, "unit": "GB/s",
                         "frac": van_gbs / hbm if van_gbs else None,
@@ -669,14 +891,33 @@ def run_ours(args, wl, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iters_per_solve": iters, "rel_residual": max(resid), "setup_s": setup_s,
             "roofline": roofline,
+            "alu_peaks": alu,
             "roofline_spmv": {"bound": "alu", "kernel": "k_residual_sell (finest level)",
-                              "achieved": op_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": op_tf / FP64_PEAK_TFLOPS if op_tf else None,
+                              "achieved": op_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": op_tf / fp64_peak if op_tf else None,
+                              "peak_source": "FP64 FMA rate measured by irkmg_probe_peak",
                               "hbm_gbs": op_gbs, "hbm_frac": op_gbs / hbm if op_gbs else None,
                               "launches": trace["op_launches"],
                               "avg_launch_ms": trace["op_ms"] / max(trace["op_launches"], 1)},
-            "gpu_launches": trace["launches"],
+            "roofline_transfers": {"bound": "hbm", "kernel": "k_transfer (finest level)",
+                                   "achieved": xfer_gbs, "peak": hbm, "unit": "GB/s",
+                                   "frac": xfer_gbs / hbm if xfer_gbs else None,
+                                   "launches": trace["xfer_launches"],
+                                   "bytes_per_launch": trace["xfer_bytes"] / max(trace["xfer_launches"], 1),
+                                   "avg_launch_ms": trace["xfer_ms"] / max(trace["xfer_launches"], 1),
+                                   "bytes": "vector bytes only (weights closed-form)"},
+            "roofline_arnoldi": {"bound": "hbm",
+                                 "kernel": "k_multidot_part + k_multidot_final + k_multiaxpy "
+                                           "(classical Gram-Schmidt twice, finest level)",
+                                 "achieved": arn_gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": arn_gbs / hbm if arn_gbs else None,
+                                 "steps": trace["arnoldi_steps"],
+                                 "avg_step_ms": trace["arnoldi_ms"] / max(trace["arnoldi_steps"], 1),
+                                 "bytes_per_step": trace["arnoldi_bytes"] / max(trace["arnoldi_steps"], 1)},
+            "traced_step": "figures from one separate traced step after the timed region",
+            "gpu_launches": launches,
             "finest_correction_ms_per_shape": shapes_ms,
+            "mesh_independence": mesh,
             "forms": forms,
             "clocks": clk.summary(),
             "e2e": {"value": replica_value(e2e_s * 1e3, args.steps, world), "unit": UNIT,
@@ -702,6 +943,12 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32-patch and batched forms reported beside the headline")
     ap.add_argument("--batch", type=int, default=64, help="systems in the batched form")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run only the batched Oseen form (64 systems by default) and print it")
+    ap.add_argument("--oracle-sizes", default="",
+                    help="with --impl reference: comma-separated sample sizes, per-phase timings")
+    ap.add_argument("--no-mesh-sweep", action="store_true",
+                    help="skip the FGMRES iteration counts on the coarser meshes")
     ap.add_argument("--patch-fixed", type=int, default=1, choices=[0, 1],
                     help="decoupled FP64 patches: 1 = exact fixed-point mat-vecs "
                          "(irkmg_options.patch_fixed)")
@@ -717,6 +964,12 @@ def main():
     if args.impl == "reference":
         run_reference(args, wl, rank)
         return
+    if args.only_batched:
+        import torch
+        torch.cuda.set_device(local_rank)
+        dev = torch.device("cuda", local_rank)
+        print(json.dumps(run_batched(args, dev, torch.cuda.current_stream(dev))), flush=True)
+        return
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)
@@ -724,10 +977,19 @@ def main():
     res = run_ours(args, wl, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline and wl.get("dim", 2) == 2:
-            n_sample = 8 if args.small else min(64, wl["n"])
-            _, scaled, desc = oracle_sample(wl, n_sample)
-            res["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": desc}
+            sizes = (8,) if args.small else (32, 64)
+            ob = oracle_baseline_subprocess(args, sizes)
+            if ob is not None:
+                big = ob["runs"][-1]
+                res["cpu_baseline"] = {
+                    "value": big["solve_s"], "unit": UNIT, "cores": ob["cores_available"],
+                    "kind": "oracle",
+                    "sample": f"oracle FGMRES + V-cycle solve of the same problem at "
+                              f"{big['n']}x{big['n']} ({big['levels']} levels, N={big['N']}, "
+                              f"{big['iters']} iterations), measured on {ob['cores_available']} "
+                              f"host cores (BLAS threads {big['blas_threads']}, CPU time / wall "
+                              f"{big['cpu_time_over_wall']:.2f}); value is that size's time",
+                    "runs": ob["runs"], "fit_to_workload": ob["fit"]}
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch

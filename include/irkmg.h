@@ -97,9 +97,11 @@ typedef struct {
   const double *wind;      /* host, finest-level Oseen wind at every P2 node,
                               np2·2 doubles (x, y per node), or NULL for Stokes     */
   void *cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream  */
-  int64_t timeout_spins;   /* bound on polls of one device-side wait (0 = 2^26; each
-                              wait also gives up after 2 s); an expired wait makes
-                              FGMRES return IRKMG_ETIMEOUT                          */
+  int64_t timeout_spins;   /* bound on polls of one device-side wait (0 = 2^26; the
+                              first poll returns at once, later ones may suspend
+                              the thread briefly; each wait also gives up after
+                              2 s); an expired wait makes FGMRES return
+                              IRKMG_ETIMEOUT                                        */
   int apply_variant;       /* Vanka apply kernel per level (dense or decoupled form
                               alike): 0 = autotuned at set-up (every candidate
                               timed once per level, the fastest kept); 1 = TMA-
@@ -122,7 +124,10 @@ typedef struct {
                               (the Kronecker form of Section 3), stored as s n×n
                               matrices (2: complex form X, Y) or s + pairs of them
                               (3: X + Y, X, Y, three real mat-vecs per pair);
-                              1 picks 3 for FP64 patches and 2 for FP32.  Exact in
+                              1 picks 2 for FP32 patches and for 2D FP64 patches
+                              with patch_fixed = 1 (their applies are bound by
+                              memory traffic), 3 otherwise (fewest FP64
+                              multiply-adds).  Exact in
                               exact arithmetic.  Blocks up to 160 DoFs are
                               inverted in shared memory, larger ones (3D, up to
                               512) by the blocked LU; with decoupling, 3D works
@@ -181,7 +186,7 @@ typedef struct {
   int64_t apply_shape;     /* launch shape of the apply kernel: 0..1 for kernel 5
                               (staged, three- or two-stage ring); 0..3 for kernel 8
                               (columns per load batch × resident CTAs per SM:
-                              8×3, 4×4, 6×3, 8×4) and 4..6 for kernel 9 (stages ×
+                              8×3, 4×4, 6×3, 8×4), 4..6 for kernel 9 (stages ×
                               CTAs per SM: 4×1, 3×1, 2×2); 0 otherwise             */
 } irkmg_level_info;
 
@@ -249,6 +254,16 @@ int irkmg_level_info_get(const irkmg_ctx *ctx, int level, irkmg_level_info *info
  * with dense patches. */
 int irkmg_level_set_apply(irkmg_ctx *ctx, int level, int shape, int single_launch);
 
+/* Replace the bound on the polls of one device-side wait (irkmg_options.
+ * timeout_spins; 0 = 2^26, and each wait also gives up after 2 s) for the
+ * calls that follow.  A wait that expires records IRKMG_ETIMEOUT, its CTA
+ * waits (with its own bound) for the copies it still has in flight and
+ * leaves; FGMRES returns IRKMG_ETIMEOUT after the Arnoldi step that saw it and
+ * the context stays usable.  Failure detection of the staged kernels
+ * (Section 4.2's patch solves streamed by bulk copies); IRKMG_EINVAL if
+ * timeout_spins < 0. */
+int irkmg_set_timeout(irkmg_ctx *ctx, int64_t timeout_spins);
+
 /* Host copies of set-up data of level l, for inspection and tests.
  * irkmg_p2_coords: np2·2 doubles.  irkmg_free_nodes: nf int64 P2-node ids.
  * irkmg_patch_map: ptr[npatch+1] and nodes[ptr[npatch]] (free-node ids,
@@ -286,9 +301,11 @@ int irkmg_smooth(irkmg_ctx *ctx, int level, const double *d_F, double *d_x, int 
  * 2 × 524,288 doubles (8 MB, held by every GPU that loads the library until
  * the process exits), so the level must have N <= 524,288 (e.g. 128×128 with
  * s = 3); larger levels are rejected with IRKMG_EINVAL and no work is done.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the array: calls that overlap on the GPU (other
+ * Each call made outside stream capture looks up the array's device address
+ * with the calling device current (so a device context that was torn down and
+ * re-created is followed); a call made during capture reuses the address the
+ * last uncaptured call on that device found, so make the first call on a
+ * device before any stream capture (otherwise IRKMG_EINVAL).  Every call shares the array: calls that overlap on the GPU (other
  * streams, other contexts, other threads) race and must be serialised by the
  * caller.  The array keeps the last call's contents; every value a call reads
  * from it is written (or cleared) first by that same call. */
@@ -345,15 +362,35 @@ int irkmg_stage_rhs_full(irkmg_ctx *ctx, const double *d_un_all, const double *d
  * it gives every context its own non-blocking stream (restored by
  * irkmg_batch_destroy; contexts stay owned by the caller and must outlive the
  * batch).  irkmg_batch_solve runs FGMRES on all systems in lock step: each
- * Arnoldi step of every unconverged system is issued on its stream (its
- * V-cycle as one CUDA graph, captured on first use), then all are synchronised
- * once and the small Hessenberg updates run on the host.  Results equal those
- * of irkmg_solve on each system.  d_F[i], d_k[i] live on the device of
- * system i's context; stats (may be NULL) has nsys entries. */
+ * Arnoldi step of every unconverged system is issued on its stream, then all
+ * are synchronised once and the small Hessenberg updates run on the host.
+ *
+ * When every system is 2D with the same stage count, Chebyshev smoothing of
+ * 1..8 steps and fixed-point decoupled patches on its finest level
+ * (patch_form != 0, patch_fixed = 1), and there are at most 128 systems, the
+ * finest-level relaxation of all unconverged systems runs as ONE persistent
+ * cooperative launch per smoothing stage (operator rows, patch solves and
+ * per-DoF sums of every system, separated by bounded grid-wide barriers that
+ * report IRKMG_ETIMEOUT through the solve, with the bound of the first
+ * system's timeout_spins); the coarse corrections run on the systems' own
+ * streams.  The batch then relaxes those finest levels by one launch over all
+ * patches plus the per-DoF sum, also in irkmg_solve on those contexts until
+ * irkmg_batch_destroy restores their mode.  Otherwise each system's V-cycle
+ * is one CUDA graph on its stream, captured on first use.  Either way the
+ * results equal those of irkmg_solve on each system (bit for bit in the same
+ * relaxation mode).  d_F[i], d_k[i] live on the device of system i's context;
+ * stats (may be NULL) has nsys entries. */
 typedef struct irkmg_batch irkmg_batch;
 int irkmg_batch_create(int nsys, irkmg_ctx *const *ctxs, irkmg_batch **out);
 int irkmg_batch_solve(irkmg_batch *batch, const double *const *d_F, double *const *d_k,
                       irkmg_stats *stats);
+/* 1 if the batch relaxes its finest levels in one persistent launch, else 0. */
+int irkmg_batch_persistent(const irkmg_batch *batch);
+/* Switch a qualifying batch between the persistent launch (on = 1, the
+ * default) and one V-cycle graph per system (on = 0); the finest levels stay
+ * in the one-launch relaxation mode either way, so the results do not change.
+ * IRKMG_ENOTIMPL for on = 1 on a batch that does not qualify. */
+int irkmg_batch_set_persistent(irkmg_batch *batch, int on);
 void irkmg_batch_destroy(irkmg_batch *batch);
 
 /* ---- Navier–Stokes: Newton on the stage equations (Section 3.2) ---------
@@ -423,9 +460,10 @@ int irkmg_tracking(irkmg_ctx *ctx, const double *d_u, const double *d_utarget, d
 /* ---- tracing ---------------------------------------------------------------- */
 
 /* Kernel accounting since the last irkmg_trace_enable.  `launches` counts every
- * kernel the library issued.  With tracing on, each finest-level Vanka colour
- * launch and each finest-level stage-operator launch is bracketed by CUDA events
- * on the context stream; *_ms is their summed device time and *_bytes their
+ * kernel the library issued (with tracing on or off).  With tracing on, each
+ * finest-level Vanka colour launch, each finest-level stage-operator launch,
+ * each finest-level transfer and each Gram–Schmidt step of FGMRES is bracketed
+ * by CUDA events on the context stream; *_ms is their summed device time and *_bytes their
  * algorithmic bytes: per Vanka sweep, sum over patches of n_p^2·w + 4·n_p plus
  * 24·N for reading r and updating the target (split over the colour launches
  * in proportion to their inverse bytes); per operator application,
@@ -443,6 +481,20 @@ typedef struct {
                               per timed operator launch                              */
   int64_t reduce_launches; /* timed per-DoF sums of the one-launch relaxation      */
   double reduce_ms, reduce_bytes;
+  int64_t xfer_launches;   /* timed finest-level transfers (Section 4.1): restriction
+                              to the next level (8·(N_f + N_c) bytes: the fine vector
+                              read, the coarse one written) and prolongation added
+                              into the fine vector (8·(N_c + 2 N_f) bytes); the
+                              interpolation weights are closed-form per refinement
+                              pattern and not counted                              */
+  double xfer_ms, xfer_bytes;
+  int64_t arnoldi_steps;   /* timed classical Gram–Schmidt steps (twice) of FGMRES
+                              (Section 4) after the j-th preconditioned product:
+                              per pass the j + 1 basis vectors and w are read by
+                              the dot products and again by the update, which
+                              also writes w, then ||w||²:
+                              8N·(2(j + 2) + 2(j + 3) + 1) bytes                    */
+  double arnoldi_ms, arnoldi_bytes;
 } irkmg_trace;
 
 /* Reset the counters; on = 1 also starts event timing.  Never fails on a valid ctx. */

@@ -736,6 +736,7 @@ int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_i
 }
 
 int coarse_graph(Ctx& C, int tr);
+int coarse_correction(Ctx& C, int l, const double* b, double* z, int tr);
 
 int vcycle_level(Ctx& C, int l, const double* b, double* z, int tr) {
   if (l == 0) {
@@ -743,12 +744,28 @@ int vcycle_level(Ctx& C, int l, const double* b, double* z, int tr) {
     C.launches++;
     return IRKMG_OK;
   }
+  int rc;
+  if ((rc = smooth(C, C.L[l], b, z, C.opt.nu_pre, true, tr))) return rc;
+  if ((rc = coarse_correction(C, l, b, z, tr))) return rc;
+  return smooth(C, C.L[l], b, z, C.opt.nu_post, false, tr);
+}
+
+// z += (I_s ⊗ P) V-cycle_{l-1}((I_s ⊗ P)ᵀ (b - J z)) on level l >= 1: the
+// residual, its restriction, the coarse levels (one graph launch below the
+// finest level), the prolongation added into z.
+int coarse_correction(Ctx& C, int l, const double* b, double* z, int tr) {
   Level& L = C.L[l];
   Level& Lc = C.L[l - 1];
   int rc;
-  if ((rc = smooth(C, L, b, z, C.opt.nu_pre, true, tr))) return rc;
   { int rc_ = op(C, L, b, z, L.t, tr); if (rc_) return rc_; }
+  const bool timed = C.trace_on && l == (int)C.L.size() - 1;
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  if (timed) {  // restriction reads the fine vector and writes the coarse one
+    if ((rc = trace_pair(C, 3, 8.0 * (double)(L.N + Lc.N), &ta, &tb))) return rc;
+    CK(cudaEventRecord(ta, C.stream));
+  }
   CK(launch_restrict(C, L, L.t, Lc.r));
+  if (timed) CK(cudaEventRecord(tb, C.stream));
   if (l == (int)C.L.size() - 1 && l >= 2 && !C.capturing) {
     // everything below the finest level: one graph launch
     if ((rc = coarse_graph(C, tr))) return rc;
@@ -761,9 +778,14 @@ int vcycle_level(Ctx& C, int l, const double* b, double* z, int tr) {
   } else if ((rc = vcycle_level(C, l - 1, Lc.r, Lc.z, tr))) {
     return rc;
   }
+  if (timed) {  // prolongation reads the coarse vector and updates the fine one
+    if ((rc = trace_pair(C, 3, 8.0 * (double)(Lc.N + 2 * L.N), &ta, &tb))) return rc;
+    CK(cudaEventRecord(ta, C.stream));
+  }
   CK(launch_prolong(C, L, Lc.z, z, 1));
+  if (timed) CK(cudaEventRecord(tb, C.stream));
   C.launches += 2;
-  return smooth(C, L, b, z, C.opt.nu_post, false, tr);
+  return IRKMG_OK;
 }
 
 // --- FGMRES (Section 4) -----------------------------------------------------
@@ -812,11 +834,21 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
       C.launches++;
       if ((rc = op(C, L, nullptr, zj, w, tr))) return rc;
       // classical Gram–Schmidt, twice
+      cudaEvent_t ga = nullptr, gb = nullptr;
+      if (C.trace_on) {
+        // per pass: the j + 1 basis vectors and w read by the dot products,
+        // read again with w read and written by the update; then ||w||²
+        const double k1 = (double)(j + 1), nb = 8.0 * (double)n;
+        if ((rc = trace_pair(C, 4, 2.0 * (nb * (k1 + 1.0) + nb * (k1 + 2.0)) + nb, &ga, &gb)))
+          return rc;
+        CK(cudaEventRecord(ga, C.stream));
+      }
       CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd, C.stream));
       CK(launch_multiaxpy(w, V, n, j + 1, hd, -1.0, n, C.stream));
       CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd + 64, C.stream));
       CK(launch_multiaxpy(w, V, n, j + 1, hd + 64, -1.0, n, C.stream));
       CK(launch_multidot(w, 0, 1, w, n, C.d_part, hd + 128, C.stream));
+      if (C.trace_on) CK(cudaEventRecord(gb, C.stream));
       C.launches += 10;
       CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 129, cudaMemcpyDeviceToHost, C.stream));
       CK(cudaMemcpyAsync(C.h_err, C.d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, C.stream));
@@ -941,9 +973,15 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
   if (opt->patch_form != 0) {
     KronSplit K;
     if (kron_split(C->s, C->A, &K) != IRKMG_OK) return fail(IRKMG_ENOTIMPL, "Butcher matrix split");
+    // patch_form 1: the complex layout (s·n² entries) where the apply is
+    // bound by memory traffic (FP32 entries, and 2D FP64 entries applied in
+    // fixed point), the three-product layout (fewest FP64 multiply-adds)
+    // where the FP64 pipe bounds it
+    const bool traffic_bound =
+        opt->patch_precision == 32 || (opt->patch_fixed == 1 && mesh->dim == 2);
     const int layout = opt->patch_form == 2 ? 1
                        : opt->patch_form == 3 ? 2
-                                              : (opt->patch_precision == 64 ? 2 : 1);
+                                              : (traffic_bound ? 1 : 2);
     if ((rc = kron_plan(K, layout, &C->kplan))) return fail(rc, "decoupled patch plan");
     C->kron = true;
   }
@@ -1045,23 +1083,31 @@ bool level_ok(const irkmg_ctx* ctx, int level) {
 // --- relaxation without device allocation -----------------------------------
 // Work vectors for irkmg_smooth_noalloc: [0, kNoallocMaxN) holds the residual,
 // [kNoallocMaxN, 2 kNoallocMaxN) the Chebyshev direction.  Host code cannot
-// use the symbol as an address; the device address is looked up once per
-// device and cached.
+// use the symbol as an address: the device address is looked up with the
+// device current.  A call outside stream capture looks it up again (the
+// module, and so the array, moves if the device's context was torn down and
+// re-created); a call during capture, when no lookup that might load a module
+// is wanted, uses the address the last uncaptured call on that device found.
 constexpr int64_t kNoallocMaxN = 1 << 19;
 constexpr int kNoallocMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoallocMaxN];
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kNoallocMaxDevices] = {};
 
-int noalloc_scratch(double** out) {
+int noalloc_scratch(cudaStream_t st, double** out) {
   int dev = -1;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoallocMaxDevices) return fail(IRKMG_EINVAL, "device index out of range");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_noalloc_ptr[dev] = (double*)p;
+  } else if (!g_noalloc_ptr[dev]) {
+    return fail(IRKMG_EINVAL, "the first no-allocation call on a device must come before any "
+                              "stream capture");
   }
   *out = g_noalloc_ptr[dev];
   return IRKMG_OK;
@@ -1437,8 +1483,56 @@ int issue_norm(Ctx& C, const double* v, int slot) {
   return IRKMG_OK;
 }
 
-int batch_fgmres(std::vector<FState>& S) {
+// What a batch owns besides its contexts: one stream per system; with a
+// persistent plan, the batch stream and events ordering the persistent
+// launches against the systems' streams, and the relaxation mode each finest
+// level had before the batch pinned it to one launch.
+struct BatchLink {
+  BatchPlan* plan = nullptr;
+  bool on = false;  // relax through the plan (else per-system V-cycle graphs)
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> ready;
+};
+
+// One V-cycle per active system (b_i -> z_i) with the finest-level smoothing
+// of all of them in two persistent launches (before and after the coarse
+// corrections, which run on the systems' own streams).
+int batch_vcycles(BatchLink& K, std::vector<FState>& S, const std::vector<int>& act,
+                  const std::vector<const double*>& b, const std::vector<double*>& z) {
+  auto join = [&]() -> int {  // every active system's stream -> the batch stream
+    for (int i : act) {
+      CK(cudaEventRecord(K.ready[i], S[i].C->stream));
+      CK(cudaStreamWaitEvent(K.stream, K.ready[i], 0));
+    }
+    return IRKMG_OK;
+  };
+  auto fork = [&]() -> int {  // the batch stream -> every active system's stream
+    CK(cudaEventRecord(K.done, K.stream));
+    for (int i : act) CK(cudaStreamWaitEvent(S[i].C->stream, K.done, 0));
+    return IRKMG_OK;
+  };
+  Ctx& C0 = *S[act[0]].C;
   int rc;
+  if ((rc = join())) return rc;
+  CK(batch_plan_smooth(K.plan, act, b, z, C0.opt.nu_pre, true, C0.opt.timeout_spins, C0.d_err,
+                       K.stream));
+  C0.launches++;
+  if ((rc = fork())) return rc;
+  for (size_t k = 0; k < act.size(); ++k) {
+    Ctx& C = *S[act[k]].C;
+    if ((rc = coarse_correction(C, (int)C.L.size() - 1, b[k], z[k], 0))) return rc;
+  }
+  if ((rc = join())) return rc;
+  CK(batch_plan_smooth(K.plan, act, b, z, C0.opt.nu_post, false, C0.opt.timeout_spins, C0.d_err,
+                       K.stream));
+  C0.launches++;
+  return fork();
+}
+
+int batch_fgmres(std::vector<FState>& S, BatchLink* K) {
+  int rc;
+  if (K && K->plan && (rc = batch_plan_refresh(K->plan, K->stream))) return fail(rc, "batch plan");
   for (FState& f : S) {  // initial residuals and norms
     Ctx& C = *f.C;
     const int64_t n = C.L.back().N;
@@ -1449,7 +1543,7 @@ int batch_fgmres(std::vector<FState>& S) {
     f.g.assign(f.m + 1, 0.0);
     f.y.assign(f.m, 0.0);
     f.t0 = now();
-    if ((rc = capture_vcycle(C))) return rc;
+    if (!(K && K->plan) && (rc = capture_vcycle(C))) return rc;
     if ((rc = issue_norm(C, f.F, 192))) return rc;
     if ((rc = op(C, C.L.back(), f.F, f.x, C.d_V, 0))) return rc;
     if ((rc = issue_norm(C, C.d_V, 193))) return rc;
@@ -1465,14 +1559,19 @@ int batch_fgmres(std::vector<FState>& S) {
     f.finishing = false;
     f.j = -1;  // a new cycle starts
   }
+  std::vector<int> act;
+  std::vector<const double*> vb;
+  std::vector<double*> vz;
   for (;;) {
     bool any = false;
-    for (FState& f : S) {  // issue one Arnoldi step per active system
+    act.clear();
+    vb.clear();
+    vz.clear();
+    for (size_t i = 0; i < S.size(); ++i) {  // new cycles start; the V-cycles' inputs
+      FState& f = S[i];
       if (f.done) continue;
-      any = true;
       Ctx& C = *f.C;
-      Level& L = C.L.back();
-      const int64_t n = L.N;
+      const int64_t n = C.L.back().N;
       if (f.j < 0) {
         CK(launch_axpby(C.d_V, C.d_V, 1.0 / f.beta, 0.0, n, C.stream));
         C.launches++;
@@ -1480,11 +1579,24 @@ int batch_fgmres(std::vector<FState>& S) {
         f.g[0] = f.beta;
         f.j = 0;
       }
+      act.push_back((int)i);
+      vb.push_back(C.d_V + (int64_t)f.j * n);
+      vz.push_back(C.d_Z + (int64_t)f.j * n);
+    }
+    if (K && K->plan && !act.empty() && (rc = batch_vcycles(*K, S, act, vb, vz))) return rc;
+    for (FState& f : S) {  // issue the rest of one Arnoldi step per active system
+      if (f.done) continue;
+      any = true;
+      Ctx& C = *f.C;
+      Level& L = C.L.back();
+      const int64_t n = L.N;
       double* vj = C.d_V + (int64_t)f.j * n;
       double* zj = C.d_Z + (int64_t)f.j * n;
-      CK(cudaMemcpyAsync(C.d_gin, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.stream));
-      CK(cudaGraphLaunch(C.vgraph, C.stream));
-      CK(cudaMemcpyAsync(zj, C.d_gout, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.stream));
+      if (!(K && K->plan)) {  // the whole V-cycle as one graph on the system's stream
+        CK(cudaMemcpyAsync(C.d_gin, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.stream));
+        CK(cudaGraphLaunch(C.vgraph, C.stream));
+        CK(cudaMemcpyAsync(zj, C.d_gout, sizeof(double) * n, cudaMemcpyDeviceToDevice, C.stream));
+      }
       CK(launch_pressure_mean_remove(C, L, zj));
       if ((rc = op(C, L, nullptr, zj, C.d_w, 0))) return rc;
       CK(launch_multidot(C.d_V, n, f.j + 1, C.d_w, n, C.d_part, C.d_h, C.stream));
@@ -1733,7 +1845,7 @@ int irkmg_level_info_get(const irkmg_ctx* C, int level, irkmg_level_info* info) 
   info->cheb[0] = level > 0 ? L.cheb_lo : 0.0;
   info->cheb[1] = level > 0 ? L.cheb_hi : 0.0;
   info->apply_shape =
-      level > 0 && (L.apply_kernel == 5 || L.apply_kernel == 8 || L.apply_kernel == 9) ? L.kron_shape : 0;
+      level > 0 && (L.apply_kernel == 5 || L.apply_kernel >= 8) ? L.kron_shape : 0;
   return IRKMG_OK;
 }
 
@@ -1750,6 +1862,14 @@ int irkmg_level_set_apply(irkmg_ctx* C, int level, int shape, int single_launch)
   if (L.fixed) L.apply_kernel = fixed_shape_kernel(shape);
   L.single = single_launch != 0;
   drop_graphs(*C);  // captured coarse levels hold the previous launches
+  return IRKMG_OK;
+}
+
+int irkmg_set_timeout(irkmg_ctx* C, int64_t timeout_spins) {
+  if (!C) return fail(IRKMG_EINVAL, "null ctx");
+  if (timeout_spins < 0) return fail(IRKMG_EINVAL, "timeout_spins >= 0");
+  C->opt.timeout_spins = timeout_spins;
+  drop_graphs(*C);  // captured coarse levels hold the previous bound
   return IRKMG_OK;
 }
 
@@ -1818,7 +1938,7 @@ int irkmg_smooth_noalloc(irkmg_ctx* C, int level, const double* F, double* x, in
                                   " unknowns; the static work array holds at most " +
                                   std::to_string(kNoallocMaxN));
   double* scratch = nullptr;
-  int rc = noalloc_scratch(&scratch);
+  int rc = noalloc_scratch(C->stream, &scratch);
   if (rc) return rc;
   return smooth_in(*C, L, F, x, nsteps, transpose ? 1 : 0, scratch, scratch + kNoallocMaxN);
 }
@@ -1986,6 +2106,8 @@ int irkmg_stage_rhs_full(irkmg_ctx* C, const double* un_all, const double* pn, c
 struct irkmg_batch {
   std::vector<irkmg_ctx*> sys;
   std::vector<cudaStream_t> own, saved;
+  BatchLink link;
+  std::vector<char> saved_single;  // finest levels' relaxation mode before the batch
 };
 
 int irkmg_batch_create(int nsys, irkmg_ctx* const* ctxs, irkmg_batch** out) {
@@ -2010,6 +2132,33 @@ int irkmg_batch_create(int nsys, irkmg_ctx* const* ctxs, irkmg_batch** out) {
     B->saved.push_back(ctxs[i]->stream);
     ctxs[i]->stream = st;
   }
+  // the finest levels relax in one persistent launch for the whole batch when
+  // the systems allow it (else each V-cycle is a graph on its system's stream)
+  std::vector<Ctx*> sys(B->sys.begin(), B->sys.end());
+  if (batch_plan_unsupported(sys).empty()) {
+    BatchLink& K = B->link;
+    int rc = batch_plan_create(sys, &K.plan);
+    cudaError_t e = rc == IRKMG_OK ? cudaStreamCreateWithFlags(&K.stream, cudaStreamNonBlocking)
+                                   : cudaSuccess;
+    if (rc == IRKMG_OK && e == cudaSuccess)
+      e = cudaEventCreateWithFlags(&K.done, cudaEventDisableTiming);
+    for (int i = 0; rc == IRKMG_OK && e == cudaSuccess && i < nsys; ++i) {
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      K.ready.push_back(ev);
+    }
+    if (rc != IRKMG_OK || e != cudaSuccess) {
+      irkmg_batch_destroy(B);
+      return fail(rc != IRKMG_OK ? rc : IRKMG_ECUDA, "batched relaxation plan");
+    }
+    for (Ctx* C : sys) {  // the persistent smoother's relaxation mode
+      Level& L = C->L.back();
+      B->saved_single.push_back(L.single ? 1 : 0);
+      L.single = true;
+      drop_graphs(*C);
+    }
+    K.on = true;
+  }
   *out = B;
   return IRKMG_OK;
 }
@@ -2024,16 +2173,37 @@ int irkmg_batch_solve(irkmg_batch* B, const double* const* F, double* const* k, 
     S[i].x = k[i];
     S[i].st = st ? &st[i] : nullptr;
   }
-  return batch_fgmres(S);
+  return batch_fgmres(S, B->link.on ? &B->link : nullptr);
+}
+
+int irkmg_batch_persistent(const irkmg_batch* B) { return B && B->link.on ? 1 : 0; }
+
+int irkmg_batch_set_persistent(irkmg_batch* B, int on) {
+  if (!B || (on != 0 && on != 1)) return fail(IRKMG_EINVAL, "bad arguments");
+  if (on && !B->link.plan)
+    return fail(IRKMG_ENOTIMPL, "the batch's systems cannot relax in one persistent launch");
+  B->link.on = on != 0;
+  return IRKMG_OK;
 }
 
 void irkmg_batch_destroy(irkmg_batch* B) {
   if (!B) return;
+  BatchLink& K = B->link;
+  if (K.stream) cudaStreamSynchronize(K.stream);
   for (size_t i = 0; i < B->own.size(); ++i) {
     cudaStreamSynchronize(B->own[i]);
     if (i < B->sys.size()) B->sys[i]->stream = B->saved[i];
     cudaStreamDestroy(B->own[i]);
   }
+  for (size_t i = 0; i < B->saved_single.size() && i < B->sys.size(); ++i) {
+    B->sys[i]->L.back().single = B->saved_single[i] != 0;
+    drop_graphs(*B->sys[i]);
+  }
+  for (cudaEvent_t ev : K.ready)
+    if (ev) cudaEventDestroy(ev);
+  if (K.done) cudaEventDestroy(K.done);
+  if (K.stream) cudaStreamDestroy(K.stream);
+  batch_plan_destroy(K.plan);
   delete B;
 }
 
@@ -2065,6 +2235,14 @@ int irkmg_trace_read(irkmg_ctx* C, irkmg_trace* out) {
       out->reduce_launches++;
       out->reduce_ms += ms;
       out->reduce_bytes += C->ev_bytes[k];
+    } else if (C->ev_class[k] == 3) {
+      out->xfer_launches++;
+      out->xfer_ms += ms;
+      out->xfer_bytes += C->ev_bytes[k];
+    } else if (C->ev_class[k] == 4) {
+      out->arnoldi_steps++;
+      out->arnoldi_ms += ms;
+      out->arnoldi_bytes += C->ev_bytes[k];
     } else {
       out->op_launches++;
       out->op_ms += ms;

@@ -307,6 +307,19 @@ cudaError_t launch_patch_factor_kron_big(Ctx& C, Level& L, void* work, int64_t w
 int64_t kron_big_workspace(int pmax, int nmax, int prec);
 int kron_big_max_n();
 
+// Batched relaxation of the finest levels of many systems in one persistent
+// launch (k_batch.cu).  batch_plan_unsupported gives why a set of systems
+// cannot use it ("" when it can).
+struct BatchPlan;
+std::string batch_plan_unsupported(const std::vector<Ctx*>& sys);
+int batch_plan_create(const std::vector<Ctx*>& sys, BatchPlan** out);
+void batch_plan_destroy(BatchPlan* P);
+int batch_plan_refresh(BatchPlan* P, cudaStream_t st);
+cudaError_t batch_plan_smooth(BatchPlan* P, const std::vector<int>& active,
+                              const std::vector<const double*>& b, const std::vector<double*>& x,
+                              int nsteps, bool zero_init, int64_t spins, int* err,
+                              cudaStream_t st);
+
 constexpr int kMultidotBlocks = 304;
 constexpr int kMaxSmallNp = 160;  // patches up to this size: explicit inverse in shared memory
 constexpr int kMaxBigNp = 512;    // patches up to this size: blocked LU in the patch block  // 2 x 152 SMs; fixed for a deterministic sum order

@@ -777,9 +777,10 @@ __global__ void __launch_bounds__(kStagedThreads) k_vanka_apply_staged(StagedPar
     }
     __syncthreads();
     if (s_abort) {
-      // wait (bounded) for every copy this CTA still has in flight, then leave
+      // wait (bounded) for every copy this CTA still has in flight (patches
+      // k .. k + stages - 1 are issued), then leave
       for (int64_t j = k; j < nmine && j < k + S.stages; ++j)
-        mbar_wait_bounded(&bar[j % S.stages], (uint32_t)((j / S.stages) & 1), S.spins);
+        mbar_drain(&bar[j % S.stages], (uint32_t)((j / S.stages) & 1));
       return;
     }
     const unsigned char* stage = dyn + (size_t)st * S.stage_bytes;

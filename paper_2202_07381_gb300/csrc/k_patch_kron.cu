@@ -357,15 +357,16 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
     }
   };
   // in flight after the prologue: copies 0 .. min(nmine, stages) - 1
-  auto drain = [&](int64_t from) {
-    for (int64_t j = from; j < nmine && j < from + S.stages; ++j)
-      mbar_wait_bounded(&bar[j % S.stages], (uint32_t)((j / S.stages) & 1), S.spins);
+  // copies issued and perhaps in flight: patches from .. upto - 1
+  auto drain = [&](int64_t from, int64_t upto) {
+    for (int64_t j = from; j < nmine && j < upto; ++j)
+      mbar_drain(&bar[j % S.stages], (uint32_t)((j / S.stages) & 1));
   };
   __syncthreads();  // s_n of the first stages
   if (nmine > 0 && wait_stage(0)) gather(0);
   __syncthreads();
   if (s_abort) {
-    drain(0);
+    drain(0, S.stages);
     return;
   }
 
@@ -417,8 +418,8 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
     }
     fence_proxy_async();
     __syncthreads();  // stage st and the work arrays fully consumed
-    if (s_abort) {
-      drain(k + 1);
+    if (s_abort) {  // patches up to k + stages - 1 were issued
+      drain(k + 1, k + S.stages);
       return;
     }
     if (tid == 0 && k + S.stages < nmine) {
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
       }
       if (s_abort)  // copies still in flight complete before the CTA leaves
         for (int64_t k = issued > S ? issued - S : 0; k < issued; ++k)
-          mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), W.spins);
+          mbar_drain(&full[k % S], (uint32_t)((k / S) & 1));
     }
     return;
   }
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
   int32_t* s_g = reinterpret_cast<int32_t*>(s_src + (P.ns > P.nt ? P.ns : P.nt) * nmax);
   for (int64_t k = c; k < nmine; k += kWsConsumers) {
     const int st = (int)(k % S);
-    if (s_abort) return;
+    if (__any_sync(0xffffffffu, s_abort != 0)) return;  // the whole warp leaves together
     // Patches of one stage go to different consumers, so a consumer may reach
     // stage st before the fill for patch k - S has completed; a parity wait
     // would then match the older phase.  Waiting until the producer has
@@ -542,7 +543,8 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
         if ((it & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
       }
     }
-    if (!started || !mbar_wait_bounded(&full[st], (uint32_t)((k / S) & 1), W.spins)) {
+    const bool ok = started && mbar_wait_bounded(&full[st], (uint32_t)((k / S) & 1), W.spins);
+    if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the whole warp leaves together
       if (lane == 0) {
         s_abort = 1;
         atomicCAS(&W.err[0], 0, IRKMG_ETIMEOUT);
@@ -829,7 +831,7 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   }
   P.nmax = L.kron_nmax;
   if (P.count <= 0) return cudaSuccess;
-  if (L.apply_kernel == 8 || L.apply_kernel == 9)
+  if (L.fixed)  // kernels 8, 9 and 10: the stored blocks are fixed point
     return launch_vanka_kron_fx(C, L, colour, r, out, scale, transpose);
   const int prec = C.opt.patch_precision;
   if (L.apply_kernel == 7) {
@@ -912,7 +914,7 @@ __global__ void k_vanka_reduce(int s, int64_t m, int64_t Q, const int32_t* __res
   const double* yt = y + t * Q;
   double a = 0.0;
   for (int32_t e = cptr[d]; e < cptr[d + 1]; ++e) a += yt[cidx[e]];
-  out[id] += scale * a;
+  out[id] = __fma_rn(scale, a, out[id]);  // one rounding, as the batched smoother
 }
 
 cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale) {

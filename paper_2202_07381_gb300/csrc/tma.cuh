@@ -55,16 +55,40 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait on a stage barrier: at most `spins` polls and at most 2 s of
-// wall time; false if either bound expired.
+// Non-blocking test of a phase (mbarrier.test_wait returns at once, where
+// try_wait may suspend the thread for a while first).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a stage barrier: at most `spins` polls, the first one
+// non-blocking and the others (try_wait) allowed a short hardware-chosen
+// suspension, and at most 2 s of wall time; false if either bound expired.
+// spins = 1 is a single non-blocking poll.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t spins) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (int64_t k = 0; k < spins; ++k) {
+  for (int64_t k = 1; k < spins; ++k) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((k & 255) == 255 && global_ns() - t0 > 2000000000ull) return false;
   }
   return false;
+}
+
+// Wait for a copy this CTA issued before the CTA leaves after an expired wait.
+// It has its own bound (2^26 polls and the 2 s wall-clock limit), not the
+// caller's timeout, which may be tiny: a CTA must not exit while a bulk copy
+// is still landing in its shared memory.
+constexpr int64_t kDrainSpins = (int64_t)1 << 26;
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  mbar_wait_bounded(bar, parity, kDrainSpins);
 }
 
 }  // namespace irkmg

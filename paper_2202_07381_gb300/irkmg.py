@@ -82,7 +82,10 @@ class Trace(ct.Structure):
                 ("vanka_bytes", ct.c_double), ("op_launches", ct.c_int64), ("op_ms", ct.c_double),
                 ("op_bytes", ct.c_double), ("vanka_flops", ct.c_double), ("op_flops", ct.c_double),
                 ("reduce_launches", ct.c_int64), ("reduce_ms", ct.c_double),
-                ("reduce_bytes", ct.c_double)]
+                ("reduce_bytes", ct.c_double), ("xfer_launches", ct.c_int64),
+                ("xfer_ms", ct.c_double), ("xfer_bytes", ct.c_double),
+                ("arnoldi_steps", ct.c_int64), ("arnoldi_ms", ct.c_double),
+                ("arnoldi_bytes", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,6 +110,8 @@ _SIGS = {
     "irkmg_set_wind": (ct.c_int, [_P, _P]),
     "irkmg_level_info_get": (ct.c_int, [_P, ct.c_int, ct.POINTER(LevelInfo)]),
     "irkmg_level_set_apply": (ct.c_int, [_P, ct.c_int, ct.c_int, ct.c_int]),
+    "irkmg_set_timeout": (ct.c_int, [_P, ct.c_int64]),
+    "irkmg_probe_peak": (ct.c_int, [ct.c_int, ct.c_int64, _P, ct.POINTER(ct.c_double)]),
     "irkmg_p2_coords": (ct.c_int, [_P, ct.c_int, _P]),
     "irkmg_free_nodes": (ct.c_int, [_P, ct.c_int, _P]),
     "irkmg_patch_map": (ct.c_int, [_P, ct.c_int, _P, _P]),
@@ -127,6 +132,8 @@ _SIGS = {
     "irkmg_batch_create": (ct.c_int, [ct.c_int, ct.POINTER(_P), ct.POINTER(_P)]),
     "irkmg_batch_solve": (ct.c_int, [_P, ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(Stats)]),
     "irkmg_batch_destroy": (None, [_P]),
+    "irkmg_batch_persistent": (ct.c_int, [_P]),
+    "irkmg_batch_set_persistent": (ct.c_int, [_P, ct.c_int]),
     "irkmg_forcing_load": (ct.c_int, [_P, _P, _P]),
     "irkmg_step": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(Stats)]),
     "irkmg_adjoint_step": (ct.c_int, [_P, _P, _P, _P, _P, _P, ct.POINTER(ct.c_double),
@@ -385,6 +392,20 @@ def irkmg_level_set_apply(ctx, level, shape, single_launch):
     ctx.refresh()
 
 
+def irkmg_probe_peak(kind, iters, stream=None):
+    """Measured arithmetic rate of the current device (include/irkmg_probe.h):
+    kind 0 FP64 FMA flop/s, 1 FP32 FMA flop/s, 2 mad.wide.s32 per second."""
+    out = ct.c_double()
+    rc = lib().irkmg_probe_peak(int(kind), int(iters), stream, ct.byref(out))
+    if rc != 0:
+        raise IrkmgError(IRKMG_ECUDA, f"irkmg_probe_peak returned {rc}")
+    return out.value
+
+
+def irkmg_set_timeout(ctx, timeout_spins):
+    _check(lib().irkmg_set_timeout(ctx.handle, int(timeout_spins)))
+
+
 def irkmg_vanka_correction(ctx, r, c, level=-1, transpose=False):
     level %= ctx.nlevels
     n = ctx.N(level)
@@ -489,6 +510,15 @@ class Batch:
         if not (rc == IRKMG_ENOCONV and not raise_on_noconv):
             _check(rc)
         return [x.as_dict() for x in st]
+
+    @property
+    def persistent(self):
+        """True if the finest levels relax in one persistent launch."""
+        return bool(lib().irkmg_batch_persistent(self.handle))
+
+    @persistent.setter
+    def persistent(self, on):
+        _check(lib().irkmg_batch_set_persistent(self.handle, int(bool(on))))
 
     def close(self):
         if self.handle:

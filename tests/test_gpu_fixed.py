@@ -8,7 +8,8 @@ dot products against sources scaled to 58-bit integers, rounded once to FP64.
 The conversions cost at most 2^-57 of a row's largest entry and 2^-58 of a
 source's largest entry, below the FP64 rounding of the same mat-vec, so the
 bars are those of the FP64 decoupled form: Vanka corrections and V-cycles at
-1e-11, FGMRES solutions at 1e-8 with the oracle's iteration count +-1."""
+1e-12 (measured: below 3e-14), FGMRES solutions at 1e-8 with the oracle's
+iteration count +-1."""
 import functools
 
 import numpy as np
@@ -44,7 +45,7 @@ def _context(irkmg, fam, s, dt, n0, nl, form=1, fixed=1, variant=0, nu=1.0, wind
 @pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
 @pytest.mark.parametrize("fam,s,dt", CASES)
 def test_fixed_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
-    """Every level uses the fixed-point kernel (apply_kernel 8); one
+    """Every level uses a fixed-point kernel (apply_kernel 8 or 9); one
     correction per level with J and with Jᵀ patches, and one V-cycle."""
     irkmg = need_gpu()
     n0, nl = 2, 4
@@ -59,48 +60,52 @@ def test_fixed_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
             r = synth.random_vector(700 + l, L.N)
             c = dev(np.zeros(L.N))
             irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l)
-            assert rel(host(c), L.vanka.correction(r)) < 1e-11
+            assert rel(host(c), L.vanka.correction(r)) < 1e-12
             irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l, transpose=True)
             ref_t = np.zeros(L.N)
             for idx, f in zip(L.vanka.dofs, L.vanka.lu):
                 ref_t[idx] += sla.lu_solve(f, r[idx], trans=1)
-            assert rel(host(c), ref_t) < 1e-11
+            assert rel(host(c), ref_t) < 1e-12
         r = synth.random_vector(799, H.finest.N)
         z = dev(np.zeros(H.finest.N))
         irkmg.irkmg_vcycle(ctx, dev(r), z)
-        assert rel(host(z), H.vcycle(r)) < 1e-11
+        assert rel(host(z), H.vcycle(r)) < 1e-12
     finally:
         ctx.close()
 
 
+FIXED_SHAPE_KERNEL = [8] * 4 + [9] * 3
+
+
+@pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
 @pytest.mark.parametrize("single", [0, 1], ids=["per_colour", "one_launch"])
-def test_every_fixed_launch_shape_matches_oracle(single):
+def test_every_fixed_launch_shape_matches_oracle(single, form):
     """Each launch shape of the fixed-point kernels (warp per patch: columns
     per load batch x resident CTAs; TMA-staged: stages x CTAs), pinned on
     every level: corrections with J and Jᵀ patches against the oracle."""
     irkmg = need_gpu()
     fam, s, dt, n0, nl = "radau_iia", 3, 1 / 64, 2, 4
     H = _oracle(fam, s, dt, n0, nl)
-    ctx = _context(irkmg, fam, s, dt, n0, nl)
+    ctx = _context(irkmg, fam, s, dt, n0, nl, form=form)
     try:
-        for shape in range(7):
+        for shape in range(len(FIXED_SHAPE_KERNEL)):
             for l in range(1, nl):
                 irkmg.irkmg_level_set_apply(ctx, l, shape, single)
                 info = ctx.levels[l]
                 assert (info["apply_kernel"], info["apply_shape"], info["single_launch"]) == \
-                    (8 if shape < 4 else 9, shape, single)
+                    (FIXED_SHAPE_KERNEL[shape], shape, single)
                 L = H.levels[l]
                 r = synth.random_vector(900 + 10 * shape + l, L.N)
                 c = dev(np.zeros(L.N))
                 irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l)
-                assert rel(host(c), L.vanka.correction(r)) < 1e-11
+                assert rel(host(c), L.vanka.correction(r)) < 1e-12
                 irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l, transpose=True)
                 ref_t = np.zeros(L.N)
                 for idx, f in zip(L.vanka.dofs, L.vanka.lu):
                     ref_t[idx] += sla.lu_solve(f, r[idx], trans=1)
-                assert rel(host(c), ref_t) < 1e-11
+                assert rel(host(c), ref_t) < 1e-12
         with pytest.raises(irkmg.IrkmgError):
-            irkmg.irkmg_level_set_apply(ctx, 1, 7, single)
+            irkmg.irkmg_level_set_apply(ctx, 1, len(FIXED_SHAPE_KERNEL), single)
     finally:
         ctx.close()
 
@@ -230,10 +235,10 @@ def test_fixed_oseen_matches_oracle():
         r = synth.random_vector(815, L.N)
         c = dev(np.zeros(L.N))
         irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=nl - 1)
-        assert rel(host(c), L.vanka.correction(r)) < 1e-11
+        assert rel(host(c), L.vanka.correction(r)) < 1e-12
         z = dev(np.zeros(L.N))
         irkmg.irkmg_vcycle(ctx, dev(r), z)
-        assert rel(host(z), H.vcycle(r)) < 1e-11
+        assert rel(host(z), H.vcycle(r)) < 1e-12
     finally:
         ctx.close()
 
@@ -273,6 +278,6 @@ def test_fixed_update_reconverts_the_patches():
             r = synth.random_vector(816, L.N)
             c = dev(np.zeros(L.N))
             irkmg.irkmg_vanka_correction(ctx, dev(r), c)
-            assert rel(host(c), L.vanka.correction(r)) < 1e-11
+            assert rel(host(c), L.vanka.correction(r)) < 1e-12
     finally:
         ctx.close()
