@@ -332,12 +332,14 @@ def run_reference(args, wl, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def make_context(irkmg, wl, precision, stream, apply_variant=0, patch_form=0, patch_fixed=0):
+def make_context(irkmg, wl, precision, stream, apply_variant=0, patch_form=0, patch_fixed=0,
+                 op_fixed=0):
     A, b, c = irkmg.irkmg_radau_iia(wl["s"])
     o = irkmg.irkmg_default_options()
     o.apply_variant = apply_variant
     o.patch_form = patch_form
     o.patch_fixed = patch_fixed
+    o.op_fixed = op_fixed if wl.get("dim", 2) == 2 else 0
     if "cheb" in wl:
         o.cheb_lo, o.cheb_hi = wl["cheb"]
     o.nlevels = wl["levels"]
@@ -368,13 +370,14 @@ def initial_data(irkmg, ctx, wl, c):
     return u0, p0, f
 
 
-def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form, patch_fixed=0):
+def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form, patch_fixed=0,
+             op_fixed=0):
     """Another form on the same workload (FP32 patches and/or decoupled patch
     solves): time per solve, iterations, the difference of its solution from
     the plain FP64 form's, and the finest-level Vanka roofline from the live
     trace (FP64 patches: FP64-pipe bound; FP32 patches: HBM bound)."""
     ctx, setup_s, c = make_context(irkmg, wl, precision, stream.cuda_stream, 0, patch_form,
-                                   patch_fixed)
+                                   patch_fixed, op_fixed)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -404,7 +407,7 @@ def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form, 
     out = {"ms_per_step": ms, "iters": stats[-1]["iters"],
            "rel_residual": stats[-1]["rfinal"] / stats[-1]["r0"], "setup_s": setup_s,
            "rel_diff_vs_fp64_solution": diff, "patch_precision": precision,
-           "patch_form": patch_form, "patch_fixed": patch_fixed,
+           "patch_form": patch_form, "patch_fixed": patch_fixed, "op_fixed": op_fixed,
            "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
            "factor_bytes_finest": ctx.finest["factor_bytes"]}
     if tr["vanka_ms"]:
@@ -715,8 +718,9 @@ def run_ours(args, wl, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     prec = 32 if (args.form == "fp32" or wl.get("dim", 2) == 3) else 64
     fixed = args.patch_fixed if prec == 64 and args.patch_form != 0 else 0
+    opfx = args.op_fixed if wl.get("dim", 2) == 2 else 0
     ctx, setup_s, c = make_context(irkmg, wl, prec, stream.cuda_stream, args.apply,
-                                   args.patch_form, fixed)
+                                   args.patch_form, fixed, opfx)
     u0, p0, f = initial_data(irkmg, ctx, wl, c)
     T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
     u, p, fd = T(u0), T(p0), T(f)
@@ -819,12 +823,13 @@ def run_ours(args, wl, rank, world, local_rank):
         # after the timed region: one finest-level correction per launch shape
         shapes_ms = shape_sweep(irkmg, torch, ctx, dev, stream)
     if rank == 0 and not args.small and prec == 64 and not args.no_forms:
-        for name, fp, pf, fx in (("dense_fp64", 64, 0, 0), ("dense_fp32", 32, 0, 0),
-                                 ("kron_fp64", 64, 1, 0), ("kron_fp64_fixed", 64, 1, 1),
-                                 ("kron_fp32", 32, 1, 0)):
-            if pf == args.patch_form and fp == prec and fx == fixed:
+        for name, fp, pf, fx, ox in (("dense_fp64", 64, 0, 0, 0), ("dense_fp32", 32, 0, 0, 0),
+                                     ("kron_fp64", 64, 1, 0, 0), ("kron_fp64_fixed", 64, 1, 1, 0),
+                                     ("kron_fp64_fixed_op_fixed", 64, 1, 1, 1),
+                                     ("kron_fp32", 32, 1, 0, 0)):
+            if pf == args.patch_form and fp == prec and fx == fixed and ox == opfx:
                 continue
-            forms[name] = run_form(irkmg, torch, wl, args, dev, stream, k, fp, pf, fx)
+            forms[name] = run_form(irkmg, torch, wl, args, dev, stream, k, fp, pf, fx, ox)
             forms[name]["speedup_vs_headline"] = (ms / args.steps) / forms[name]["ms_per_step"]
         forms["batched"] = run_batched(args, dev, stream)
         forms["ns_newton"] = run_ns(args, dev, stream)
@@ -884,6 +889,12 @@ def run_ours(args, wl, rank, world, local_rank):
                                        "57-bit fixed-point matrix rows and 58-bit fixed-point "
                                        "sources, rounded once to FP64" if fixed else
                                        "FP64 FMAs" if prec == 64 else "FP32 patch entries"),
+                       "op_fixed": opfx,
+                       "op_arith": ("FP64 data; stage operator as exact integer dot products of "
+                                    "57-bit fixed-point rows and 58-bit fixed-point iterates "
+                                    "(stage mixing applied exactly to the iterate, rounded once), "
+                                    "each sum rounded once to FP64, at most three sums added in "
+                                    "FP64" if opfx else "FP64 FMAs"),
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
                        "apply_shape_per_level": [lv["apply_shape"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"
@@ -892,13 +903,22 @@ def run_ours(args, wl, rank, world, local_rank):
             "iters_per_solve": iters, "rel_residual": max(resid), "setup_s": setup_s,
             "roofline": roofline,
             "alu_peaks": alu,
-            "roofline_spmv": {"bound": "alu", "kernel": "k_residual_sell (finest level)",
-                              "achieved": op_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                              "frac": op_tf / fp64_peak if op_tf else None,
-                              "peak_source": "FP64 FMA rate measured by irkmg_probe_peak",
-                              "hbm_gbs": op_gbs, "hbm_frac": op_gbs / hbm if op_gbs else None,
-                              "launches": trace["op_launches"],
-                              "avg_launch_ms": trace["op_ms"] / max(trace["op_launches"], 1)},
+            "roofline_spmv": ({"bound": "hbm",
+                               "kernel": "k_block_absmax + k_op_convert + k_residual_fx "
+                                         "(finest level, one application)",
+                               "achieved": op_gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": op_gbs / hbm if op_gbs else None,
+                               "peak_source": f"{hbm_kind} hbm_gbs",
+                               "bytes": "operator rows, indices and vectors of the FP64 form "
+                                        "(survey formula); the conversion passes are extra"}
+                              if opfx else
+                              {"bound": "alu", "kernel": "k_residual_sell (finest level)",
+                               "achieved": op_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                               "frac": op_tf / fp64_peak if op_tf else None,
+                               "peak_source": "FP64 FMA rate measured by irkmg_probe_peak",
+                               "hbm_gbs": op_gbs, "hbm_frac": op_gbs / hbm if op_gbs else None})
+                              | {"launches": trace["op_launches"], "tflops": op_tf,
+                                 "avg_launch_ms": trace["op_ms"] / max(trace["op_launches"], 1)},
             "roofline_transfers": {"bound": "hbm", "kernel": "k_transfer (finest level)",
                                    "achieved": xfer_gbs, "peak": hbm, "unit": "GB/s",
                                    "frac": xfer_gbs / hbm if xfer_gbs else None,
@@ -954,6 +974,9 @@ def main():
                          "(irkmg_options.patch_fixed)")
     ap.add_argument("--patch-form", type=int, default=1, choices=[0, 1, 2, 3],
                     help="0 dense patch systems; 1..3 Kronecker-decoupled (irkmg_options.patch_form)")
+    ap.add_argument("--op-fixed", type=int, default=0, choices=[0, 1],
+                    help="2D: exact fixed-point stage operator (irkmg_options.op_fixed); "
+                         "measured slower than the FP64 operator on GB300, so off by default")
     ap.add_argument("--apply", type=int, default=0, choices=[0, 1, 2],
                     help="Vanka apply kernel: 0 autotuned per level, 1 TMA-staged, 2 warp-per-patch")
     args = ap.parse_args()

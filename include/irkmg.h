@@ -150,6 +150,16 @@ typedef struct {
                               sources scaled to 58-bit integers, rounded once to
                               FP64; 0 = FP64 entries and FP64 FMAs.  Levels that do
                               not qualify keep FP64 entries                        */
+  int op_fixed;            /* 2D levels, s ≤ 3: 1 = the stage operator J x (and
+                              the residual F − J x) from 57-bit fixed-point copies
+                              of its rows (one power of two per row) and the
+                              iterate as 58-bit integers with one power of two per
+                              velocity / pressure group, the stage mixing dt·A
+                              applied exactly to the iterate (rounded once to 58
+                              bits), every product sum exact and rounded once to
+                              FP64, at most three sums added in FP64 per output;
+                              0 = FP64 FMAs.  The transposed operator and the
+                              Newton blocks of Navier–Stokes stay FP64            */
 } irkmg_options;
 
 typedef struct {

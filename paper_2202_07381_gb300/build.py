@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libirkmg.so")
 SOURCES = ["host_mesh.cpp", "host_assemble.cpp", "k_patch.cu", "k_linalg.cu", "k_coarse.cu",
            "k_adjoint.cu", "k_patch_big.cu", "k_patch_kron.cu", "k_patch_fixed.cu", "k_ns.cu", "host_kron.cpp", "host_eig.cpp",
-           "k_batch.cu", "api.cu", "probe_peak.cu"]
+           "k_batch.cu", "k_op_fixed.cu", "api.cu", "probe_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

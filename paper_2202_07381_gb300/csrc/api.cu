@@ -943,6 +943,7 @@ int validate(const irkmg_mesh* mesh, const irkmg_tableau* tab, double dt, double
     return fail(IRKMG_EINVAL, "patch_form is 0, 1, 2 or 3");
   if (o->patch_lu_tc != 0 && o->patch_lu_tc != 1) return fail(IRKMG_EINVAL, "patch_lu_tc is 0 or 1");
   if (o->patch_fixed != 0 && o->patch_fixed != 1) return fail(IRKMG_EINVAL, "patch_fixed is 0 or 1");
+  if (o->op_fixed != 0 && o->op_fixed != 1) return fail(IRKMG_EINVAL, "op_fixed is 0 or 1");
   if (o->patch_form != 0) {
     KronSplit K;
     if (kron_split(tab->s, tab->A, &K) != IRKMG_OK)
@@ -1019,6 +1020,24 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
     if ((rc = upload_sell(*C, L.sbt, L.hops.bt, L.dim))) return rc;
     if (l == nl - 1 && (rc = upload_csr(*C, L.mall, L.hops.mall, 2))) return rc;
     if (l == nl - 1 && (rc = upload_csr(*C, L.btall, L.hops.btall, L.dim))) return rc;
+    if (op_fixed_fits(*C, L)) {  // fixed-point copies of the operator rows
+      FxOpLevel& X = L.fxop;
+      if ((rc = dalloc(*C, &X.qM, L.svel.stored))) return rc;
+      if ((rc = dalloc(*C, &X.qK, L.svel.stored))) return rc;
+      if ((rc = dalloc(*C, &X.qB[0], L.sb.stored))) return rc;
+      if ((rc = dalloc(*C, &X.qB[1], L.sb.stored))) return rc;
+      if ((rc = dalloc(*C, &X.qT[0], L.sbt.stored))) return rc;
+      if ((rc = dalloc(*C, &X.qT[1], L.sbt.stored))) return rc;
+      if ((rc = dalloc(*C, &X.eM, L.nf))) return rc;
+      if ((rc = dalloc(*C, &X.eK, L.nf))) return rc;
+      if ((rc = dalloc(*C, &X.eB[0], L.nf))) return rc;
+      if ((rc = dalloc(*C, &X.eB[1], L.nf))) return rc;
+      if ((rc = dalloc(*C, &X.eT, L.nv))) return rc;
+      if ((rc = dalloc(*C, &X.xl, L.N))) return rc;
+      if ((rc = dalloc(*C, &X.bmax, 6))) return rc;
+      CK(launch_op_fixed_convert(*C, L));
+      L.fxop_on = true;
+    }
     if ((rc = dalloc(*C, &L.r, L.N))) return rc;
     if ((rc = dalloc(*C, &L.z, L.N))) return rc;
     if ((rc = dalloc(*C, &L.t, L.N))) return rc;
@@ -1804,6 +1823,7 @@ int irkmg_update(irkmg_ctx* C, double dt, double nu) {
     if ((rc = refresh_sell_values(*C, L.svel, L.hops.vel, 3))) return rc;
     if ((rc = refresh_sell_values(*C, L.sb, L.hops.b, L.dim))) return rc;
     if ((rc = refresh_sell_values(*C, L.sbt, L.hops.bt, L.dim))) return rc;
+    if (L.fxop_on) CK(launch_op_fixed_convert(*C, L));
     if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.mall, L.hops.mall, 2))) return rc;
     if (l + 1 == C->L.size() && (rc = refresh_csr_values(*C, L.btall, L.hops.btall, L.dim)))
       return rc;

@@ -122,6 +122,17 @@ struct DevSELL {
   int64_t stored = 0;
 };
 
+// Fixed-point copies of a level's SELL operator for the exact stage operator
+// (k_op_fixed.cu): 57-bit rows as (low, high) int32 limbs with one row
+// exponent per matrix (Bᵀ: both components under one), and the work arrays
+// of one application (x as 58-bit limbs; the block maxima of x).
+struct FxOpLevel {
+  int2 *qM = nullptr, *qK = nullptr, *qB[2] = {nullptr, nullptr}, *qT[2] = {nullptr, nullptr};
+  int16_t *eM = nullptr, *eK = nullptr, *eB[2] = {nullptr, nullptr}, *eT = nullptr;
+  int2* xl = nullptr;
+  unsigned long long* bmax = nullptr;
+};
+
 struct Level {
   HostMesh mesh;
   int dim = 2;
@@ -129,6 +140,8 @@ struct Level {
   HostOps hops;
   DevCSR vel, b, bt, mall, btall;
   DevSELL svel, sb, sbt;  // SELL copies of vel, b and bt for the stage operator
+  bool fxop_on = false;   // the exact fixed-point stage operator (op_fixed)
+  FxOpLevel fxop;
   // transfer from level-1 into this level (l > 0)
   DevCSR pu, put, pp, ppt;
   // topology for patch construction
@@ -267,6 +280,9 @@ cudaError_t launch_vanka(Ctx& C, Level& L, int colour, const double* r, double* 
 bool vanka_staged_fits(Ctx& C, Level& L);
 cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, double* r,
                             int transpose);
+bool op_fixed_fits(Ctx& C, Level& L);
+cudaError_t launch_op_fixed_convert(Ctx& C, Level& L);
+cudaError_t launch_residual_fx(Ctx& C, Level& L, const double* F, const double* x, double* r);
 cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coarse);
 cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine, int add);
 cudaError_t launch_axpby(double* y, const double* x, double a, double b, int64_t n,

@@ -69,6 +69,8 @@ OpParams op_params(Ctx& C, Level& L, int transpose) {
 
 cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, double* r,
                             int transpose) {
+  if (L.fxop_on && !transpose && !(C.ns && C.ns_active))
+    return launch_residual_fx(C, L, F, x, r);  // exact fixed point (k_op_fixed.cu)
   OpParams P = op_params(C, L, transpose);
   const int64_t rows = P.nf_pad + L.nv;
   const unsigned grid = (unsigned)((rows + 255) / 256);

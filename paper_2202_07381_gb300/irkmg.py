@@ -41,7 +41,7 @@ class Options(ct.Structure):
                 ("wind", ct.POINTER(ct.c_double)), ("cuda_stream", ct.c_void_p),
                 ("timeout_spins", ct.c_int64), ("apply_variant", ct.c_int),
                 ("patch_form", ct.c_int), ("cheb_auto", ct.c_int), ("patch_lu_tc", ct.c_int),
-                ("patch_fixed", ct.c_int)]
+                ("patch_fixed", ct.c_int), ("op_fixed", ct.c_int)]
 
 
 class Stats(ct.Structure):
