@@ -70,8 +70,9 @@ KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.c
                "k_vanka_apply_kron_staged": "k_patch_kron.cu",
                "k_vanka_apply_kron_big": "k_patch_kron.cu",
                "k_vanka_apply_kron_ws": "k_patch_kron.cu",
-               "k_vanka_apply_kron_fx": ("k_patch_fixed.cu", "fx_math.h"),
-               "k_vanka_apply_kron_fx_staged": ("k_patch_fixed.cu", "fx_math.h")}
+               "k_vanka_apply_kron_fx": ("k_patch_fixed.cu", "fx_patch.cuh", "fx_math.h"),
+               "k_vanka_apply_kron_fx_staged": ("k_patch_fixed.cu", "fx_patch.cuh", "fx_math.h"),
+               "k_vanka_apply_kron_fx_pair": ("k_patch_fixed.cu", "fx_patch.cuh", "fx_math.h")}
 
 
 def kernel_source_hash(kernel="k_vanka_apply_kron"):
@@ -854,7 +855,8 @@ def run_ours(args, wl, rank, world, local_rank):
                  3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
                  5: "k_vanka_apply_kron_staged",
                  6: "k_vanka_apply_kron_big", 7: "k_vanka_apply_kron_ws",
-                 8: "k_vanka_apply_kron_fx", 9: "k_vanka_apply_kron_fx_staged"}[ctx.finest["apply_kernel"]]
+                 8: "k_vanka_apply_kron_fx", 9: "k_vanka_apply_kron_fx_staged",
+                 10: "k_vanka_apply_kron_fx_pair"}[ctx.finest["apply_kernel"]]
         h = kernel_source_hash(kname)
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None

@@ -184,7 +184,8 @@ typedef struct {
                               6 CTA-per-patch (blocks above 160 DoFs, factored by
                               the blocked LU; 3D), 7 warp-specialised TMA
                               pipeline; patch_fixed: 8 warp-per-patch, 9 TMA-
-                              staged exact fixed-point mat-vecs                    */
+                              staged exact fixed-point mat-vecs, 10 warp-per-
+                              patch with X and Y rows paired (complex layout)     */
   double apply_ms[2];      /* autotuner: one sweep with the fastest staged (or, for
                               decoupled levels, CTA-per-patch) candidate / the
                               fastest warp-per-patch candidate (0 if untimed)      */
@@ -197,7 +198,10 @@ typedef struct {
                               (staged, three- or two-stage ring); 0..3 for kernel 8
                               (columns per load batch × resident CTAs per SM:
                               8×3, 4×4, 6×3, 8×4), 4..6 for kernel 9 (stages ×
-                              CTAs per SM: 4×1, 3×1, 2×2); 0 otherwise             */
+                              CTAs per SM: 4×1, 3×1, 2×2), 7..8 for kernel 10
+                              (columns per load batch 8, 2; 4 CTAs per SM; the
+                              transposed apply of such a level runs kernel 8
+                              with shape 3); 0 otherwise                           */
 } irkmg_level_info;
 
 /* ---- set-up -------------------------------------------------------------- */

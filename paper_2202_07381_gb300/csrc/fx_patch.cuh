@@ -21,6 +21,14 @@ struct __align__(8) Limbs {
   int32_t v1, v0;
 };
 
+// The complex layout's pair structure, for the paired apply: matrices X and Y
+// of the complex pair each read by two tasks (sources w1, w2), and at most
+// one real block (matrix m0, source w0, task t0; m0 < 0 when absent).
+struct FxPair {
+  int mX, mY, w1, w2, tX1, tX2, tY1, tY2;
+  int m0, w0, t0;
+};
+
 struct FxApply {
   int s, nsrc, nt, nm;  // nsrc: source vectors built (ns, or nt for the transpose)
   int64_t m;
@@ -38,6 +46,7 @@ struct FxApply {
   double* ybuf;  // one-launch mode (see KronApply)
   const int64_t* qoff;
   int64_t Q;
+  FxPair pair;
 };
 
 // Shared memory of one warp: limbs (nsrc·(nmax + kFxPad) × 8 B), residuals
@@ -51,10 +60,13 @@ __host__ __device__ inline size_t fx_warp_bytes(int s, int nsrc, int nt, int nma
   return (b + 15) & ~(size_t)15;
 }
 
+// c + a·b with the 32 × 32 → 64-bit product (a widening multiply-add).  Plain
+// C++ rather than inline PTX: the compiler then updates the accumulators in
+// place instead of moving them around each asm statement (measured: about
+// one extra integer instruction per product with the asm form).  The callers'
+// bounds keep every sum below 2^63.
 __device__ __forceinline__ int64_t mad_wide(int32_t a, int32_t b, int64_t c) {
-  int64_t d;
-  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-  return d;
+  return c + (int64_t)a * (int64_t)b;
 }
 
 // Bit pattern of the largest |x_i| over a warp's entries (i = lane, lane + 32,
@@ -232,10 +244,237 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Paired apply of one interior patch (n = kFxN2) in the complex layout: a
+// lane owns one row of X or Y and both of that matrix's tasks, so each loaded
+// entry meets the limbs of w1 and w2 (one 16-byte shared-memory read) and
+// feeds eight products; the rows of the real block m0 run in the same passes
+// against (w0, 0).  Rows of X and Y first, then those of m0: with a real
+// block, passes 0..2 hold 96 of the 117 rows (14 of pass 2's lanes on Y) and
+// pass 3 the last 21 rows of m0 on the single-source path.  Per task and row
+// the exact sum and its one rounding are those of fx_patch, so the results
+// are bitwise the same.
+// ---------------------------------------------------------------------------
+constexpr int kFxPairLS = kFxN2 + kFxPad;  // limb entries per source (zero tail)
+
+struct __align__(16) FxPairSmem {
+  int4 pa[kFxPairLS];  // (v1, v0) of w1, then of w2
+  int4 pb[kFxPairLS];  // (v1, v0) of w0, then zeros
+  double r[3 * kFxN2];
+  double x[kKronMaxTasks * kFxN2];  // sources, then task results
+  int g[kFxN2 + 1];
+  int F[kKronMaxSrc];
+};
+
+// The largest |x_i| over a source's entries as its exponent F (|x_i| < 2^F)
+// and whether every entry is finite: the top words' maximum by one warp
+// reduction when it is a normal number, else the 64-bit maximum.
+__device__ __forceinline__ void fx_source_exponent(const double* x, int n, int lane, bool* finite,
+                                                   int* F) {
+  uint32_t hw = 0;
+  for (int i = lane; i < n; i += 32)
+    hw = max(hw, (uint32_t)((uint64_t)__double_as_longlong(x[i]) >> 32) & 0x7fffffffu);
+  const uint32_t m = __reduce_max_sync(0xffffffffu, hw);
+  if (m >= 0x00100000u) {  // exponent field of the maximum nonzero: the field alone gives F
+    *finite = m < 0x7ff00000u;
+    *F = (int)(m >> 20) - 1022;
+  } else {
+    const uint64_t mb = warp_absmax_bits(x, n, lane);
+    *finite = true;
+    *F = mb != 0 ? fx_exponent(fx_from_bits(mb)) : 0;
+  }
+}
+
+template <int U, bool REAL>
+__device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __restrict__ fac,
+                                              unsigned char* base, int lane, int64_t pi) {
+  constexpr int N = kFxN2, NN = N * N, LS = kFxPairLS;
+  constexpr int nb = (N + U - 1) / U;
+  // stages, sources and tasks follow from the pair structure
+  constexpr int S = REAL ? 3 : 2, NSRC = S, NT = REAL ? 5 : 4;
+  FxPairSmem& sm = *reinterpret_cast<FxPairSmem*>(base);
+  const FxPair& Q = P.pair;
+  const int2* X = fac + P.fac_off[pi];
+  // pass 0's first column batch (rows 0..31 of X) before the gathers
+  int2 qa[U];
+  {
+    const int2* mp0 = X + (int64_t)Q.mX * NN + lane;
+#pragma unroll
+    for (int u = 0; u < U; ++u) qa[u] = __ldg(mp0 + u * N);
+  }
+  const int32_t* gidx = reinterpret_cast<const int32_t*>(
+      reinterpret_cast<const unsigned char*>(X) + (((int64_t)P.nm * NN * 8 + 15) & ~(int64_t)15));
+  for (int i = lane; i < N; i += 32) sm.g[i] = gidx[i];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < (S * N + 31) / 32; ++k) {
+    const int idx = lane + 32 * k;
+    if (idx < S * N) {
+      const int t = idx / N, i = idx - t * N;
+      sm.r[idx] = P.r[t * P.m + sm.g[i]];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < (NSRC * N + 31) / 32; ++k) {
+    const int idx = lane + 32 * k;
+    if (idx < NSRC * N) {
+      const int c = idx / N, i = idx - c * N;
+      double a = 0.0;
+#pragma unroll
+      for (int t = 0; t < S; ++t) a += P.G[c * 3 + t] * sm.r[t * N + i];
+      sm.x[idx] = a;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < NSRC; ++c) {
+    bool finite;
+    int F;
+    fx_source_exponent(sm.x + c * N, N, lane, &finite, &F);
+    int32_t* dst = c == Q.w1 ? &sm.pa[0].x : c == Q.w2 ? &sm.pa[0].z : &sm.pb[0].x;
+#pragma unroll
+    for (int k = 0; k < (LS + 31) / 32; ++k) {
+      const int i = lane + 32 * k;
+      if (i < LS) {
+        const int64_t v = finite && i < N ? fx_scale_round(sm.x[c * N + i], 58 - F) : 0;
+        int32_t v1, v0;
+        fx_split29(v, &v1, &v0);
+        dst[4 * i] = v1;
+        dst[4 * i + 1] = v0;
+        if (REAL && c == Q.w0) {
+          sm.pb[i].z = 0;
+          sm.pb[i].w = 0;
+        }
+      }
+    }
+    if (lane == 0) sm.F[c] = finite ? F : INT_MIN;
+  }
+  __syncwarp();
+  const int16_t* fe = P.fexp + pi * P.nm * P.nmax;
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  // passes 0..2: rows of X (slots 0..38), Y (39..77), m0 (78..116, with a real block)
+#pragma unroll 1
+  for (int k0 = 0; k0 < 3; ++k0) {
+    const int sl = 32 * k0 + lane;
+    const int kind = sl < N ? 0 : sl < 2 * N ? 1 : 2;  // X, Y, m0 (or idle)
+    const bool ok = kind < 2 || (REAL && sl < 3 * N);
+    const int row = ok ? sl - kind * N : 0;
+    const int mat = kind == 0 ? Q.mX : kind == 1 ? Q.mY : (REAL ? Q.m0 : Q.mX);
+    const int2* mp = X + (int64_t)mat * NN + row;
+    const int4* lp = REAL && kind == 2 ? sm.pb : sm.pa;  // idle lanes: bounded limbs
+    int64_t A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
+    int2 qb[U];
+    if (k0 > 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) qa[u] = __ldg(mp + u * N);
+    }
+    auto mac2 = [&](const int2 (&q)[U], int b) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int4 L = lp[b * U + u];
+        A[0] = mad_wide(q[u].y, L.x, A[0]);
+        A[1] = mad_wide(q[u].y, L.y, A[1]);
+        A[2] = mad_wide(q[u].x, L.x, A[2]);
+        A[3] = mad_wide(q[u].x, L.y, A[3]);
+        B[0] = mad_wide(q[u].y, L.z, B[0]);
+        B[1] = mad_wide(q[u].y, L.w, B[1]);
+        B[2] = mad_wide(q[u].x, L.z, B[2]);
+        B[3] = mad_wide(q[u].x, L.w, B[3]);
+      }
+    };
+#pragma unroll
+    for (int b = 0; b < nb; b += 2) {
+      if (b + 1 < nb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) qb[u] = __ldg(mp + min((b + 1) * U + u, N - 1) * N);
+      }
+      mac2(qa, b);
+      if (b + 1 < nb) {
+        if (b + 2 < nb) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) qa[u] = __ldg(mp + min((b + 2) * U + u, N - 1) * N);
+        }
+        mac2(qb, b + 1);
+      }
+    }
+    if (ok) {
+      const int ex = fe[mat * P.nmax + row];
+      const int sA = kind == 2 ? Q.w0 : Q.w1;
+      const int tA = kind == 0 ? Q.tX1 : kind == 1 ? Q.tY1 : Q.t0;
+      const int FA = sm.F[sA];
+      sm.x[tA * N + row] = FA == INT_MIN ? qnan : fx_round(A, ex + FA - 115);
+      if (kind < 2) {
+        const int FB = sm.F[Q.w2];
+        sm.x[(kind == 0 ? Q.tX2 : Q.tY2) * N + row] = FB == INT_MIN ? qnan : fx_round(B, ex + FB - 115);
+      }
+    }
+  }
+  if (REAL) {  // pass 3: rows 18..38 of m0 against w0 alone
+    const int row = 96 + lane - 2 * N;
+    const bool ok = row < N;
+    const int2* mp = X + (int64_t)Q.m0 * NN + (ok ? row : 0);
+    int64_t A[4] = {0, 0, 0, 0};
+    int2 qb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) qa[u] = __ldg(mp + u * N);
+    auto mac1 = [&](const int2 (&q)[U], int b) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int4 L = sm.pb[b * U + u];
+        A[0] = mad_wide(q[u].y, L.x, A[0]);
+        A[1] = mad_wide(q[u].y, L.y, A[1]);
+        A[2] = mad_wide(q[u].x, L.x, A[2]);
+        A[3] = mad_wide(q[u].x, L.y, A[3]);
+      }
+    };
+#pragma unroll
+    for (int b = 0; b < nb; b += 2) {
+      if (b + 1 < nb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) qb[u] = __ldg(mp + min((b + 1) * U + u, N - 1) * N);
+      }
+      mac1(qa, b);
+      if (b + 1 < nb) {
+        if (b + 2 < nb) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) qa[u] = __ldg(mp + min((b + 2) * U + u, N - 1) * N);
+        }
+        mac1(qb, b + 1);
+      }
+    }
+    if (ok) {
+      const int ex = fe[Q.m0 * P.nmax + row];
+      const int F0 = sm.F[Q.w0];
+      sm.x[Q.t0 * N + row] = F0 == INT_MIN ? qnan : fx_round(A, ex + F0 - 115);
+    }
+  }
+  __syncwarp();
+  const int64_t qo = P.ybuf ? P.qoff[pi] : 0;
+#pragma unroll
+  for (int k = 0; k < (S * N + 31) / 32; ++k) {
+    const int idx = lane + 32 * k;
+    if (idx < S * N) {
+      const int t = idx / N, i = idx - t * N;
+      double x = 0.0;
+#pragma unroll
+      for (int tau = 0; tau < NT; ++tau) x += P.H[t * kKronMaxTasks + tau] * sm.x[tau * N + i];
+      if (P.ybuf)
+        P.ybuf[t * P.Q + qo + i] = x;
+      else
+        P.out[t * P.m + sm.g[i]] += P.scale * x;
+    }
+  }
+}
+
 // The apply parameters of level L: colour >= 0, that colour's patches added
 // into out (scaled); colour < 0, every patch into the context's result buffer
 // (the one-launch relaxation).  k_patch_fixed.cu.
 FxApply fx_params(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                   int transpose);
+// The pair structure of the context's plan; false unless it is the complex
+// layout with one complex pair and at most one real block.  k_patch_fixed.cu.
+bool fx_pair_plan(const KronPlan& K, FxPair* out);
 
 }  // namespace irkmg

@@ -27,6 +27,7 @@
 // Two kernels: warp per patch (k_vanka_apply_kron_fx; entries streamed into
 // registers in column batches) and a TMA-staged persistent kernel
 // (k_vanka_apply_kron_fx_staged); the set-up autotuner picks per level.
+#include <algorithm>
 #include <climits>
 
 #include "fx_math.h"
@@ -93,6 +94,31 @@ __global__ void __launch_bounds__(kFxWarps * 32, MB) k_vanka_apply_kron_fx(FxApp
     fx_patch<kFxN2, RC, U, TR>(P, fac, base, lane, pi, n);
   else
     fx_patch<0, RC, U, TR>(P, fac, base, lane, pi, n);
+}
+
+// Boundary stars (n < kFxN2) of the paired kernel, out of line so that their
+// registers do not count against the interior path's.
+__device__ __noinline__ void fx_patch_boundary(const FxApply& P, const int2* __restrict__ fac,
+                                               unsigned char* base, int lane, int64_t pi, int n) {
+  fx_patch<0, 1, 8, false>(P, fac, base, lane, pi, n);
+}
+
+// The paired kernel (complex layout, non-transposed): interior patches by
+// fx_patch_pair, the others by fx_patch.
+template <int U, int MB, bool REAL>
+__global__ void __launch_bounds__(kFxWarps * 32, MB) k_vanka_apply_kron_fx_pair(
+    FxApply P, const int2* __restrict__ fac, uint32_t warp_bytes) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kFxWarps + warp;
+  if (w >= P.count) return;
+  unsigned char* base = dyn + (size_t)warp * warp_bytes;
+  const int64_t pi = P.first + w;
+  const int n = P.np[pi];
+  if (n == kFxN2)
+    fx_patch_pair<U, REAL>(P, fac, base, lane, pi);
+  else
+    fx_patch_boundary(P, fac, base, lane, pi, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,6 +396,36 @@ cudaError_t launch_fx_t(const FxApply& P, const int2* fac, unsigned grid, size_t
   return cudaGetLastError();
 }
 
+// Paired kernel shapes (kernel 10): columns per load batch, resident CTAs.
+constexpr int kFxPairShapes = 2;
+constexpr int kFxPairU[kFxPairShapes] = {8, 2};
+
+size_t fx_pair_warp_bytes(const FxApply& P) {
+  const size_t g = fx_warp_bytes(P.s, P.nsrc > P.nt ? P.nsrc : P.nt, P.nt, P.nmax);
+  return g > sizeof(FxPairSmem) ? g : sizeof(FxPairSmem);
+}
+
+template <int U, bool REAL>
+cudaError_t launch_fx_pair_t(const FxApply& P, const int2* fac, cudaStream_t st) {
+  auto kern = k_vanka_apply_kron_fx_pair<U, 4, REAL>;
+  const size_t wb = fx_pair_warp_bytes(P);
+  const size_t smem = (size_t)kFxWarps * wb;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((P.count + kFxWarps - 1) / kFxWarps);
+  kern<<<grid, kFxWarps * 32, smem, st>>>(P, fac, (uint32_t)wb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fx_pair(const FxApply& P, const int2* fac, int shape, cudaStream_t st) {
+  const bool real = P.pair.m0 >= 0;
+  if (shape == 0) return real ? launch_fx_pair_t<kFxPairU[0], true>(P, fac, st)
+                              : launch_fx_pair_t<kFxPairU[0], false>(P, fac, st);
+  if (shape == 1) return real ? launch_fx_pair_t<kFxPairU[1], true>(P, fac, st)
+                              : launch_fx_pair_t<kFxPairU[1], false>(P, fac, st);
+  return cudaErrorInvalidConfiguration;
+}
+
 // Launch shapes the set-up autotuner chooses from: slots per pass RC,
 // columns per load batch U, resident CTAs per SM asked of the compiler MB.
 constexpr int kFxShapes = 4;
@@ -395,13 +451,62 @@ cudaError_t launch_fx(const FxApply& P, const int2* fac, int shape, unsigned gri
 
 }  // namespace
 
-int fixed_shapes() { return kFxShapes + kFxStagedShapes; }
+int fixed_shapes() { return kFxShapes + kFxStagedShapes + kFxPairShapes; }
 
-int fixed_shape_kernel(int shape) { return shape < kFxShapes ? 8 : 9; }
+int fixed_shape_kernel(int shape) {
+  return shape < kFxShapes ? 8 : shape < kFxShapes + kFxStagedShapes ? 9 : 10;
+}
+
+bool fx_pair_plan(const KronPlan& K, FxPair* out) {
+  if (K.layout != 1) return false;
+  FxPair Q{};
+  Q.mX = Q.m0 = -1;
+  int npair = 0, nreal = 0;
+  for (int b = 0; b < K.nblk; ++b) {
+    if (K.blk_kind[b] == 1) {
+      ++npair;
+      Q.mX = K.blk_mat[b];
+      Q.mY = Q.mX + 1;
+    } else if (K.blk_kind[b] == 0) {
+      ++nreal;
+      Q.m0 = K.blk_mat[b];
+    } else {
+      return false;
+    }
+  }
+  if (npair != 1 || nreal > 1) return false;
+  int tx[2], ty[2], nx = 0, ny = 0, n0 = 0;
+  for (int t = 0; t < K.nt; ++t) {
+    if (K.task_mat[t] == Q.mX && nx < 2) tx[nx++] = t;
+    else if (K.task_mat[t] == Q.mY && ny < 2) ty[ny++] = t;
+    else if (K.task_mat[t] == Q.m0 && n0 < 1) Q.t0 = t, ++n0;
+    else return false;
+  }
+  if (nx != 2 || ny != 2 || n0 != nreal) return false;
+  Q.w1 = K.task_src[tx[0]];
+  Q.w2 = K.task_src[tx[1]];
+  if (Q.w1 == Q.w2 || K.task_src[ty[0]] != Q.w1 || K.task_src[ty[1]] != Q.w2) return false;
+  Q.tX1 = tx[0];
+  Q.tX2 = tx[1];
+  Q.tY1 = ty[0];
+  Q.tY2 = ty[1];
+  Q.w0 = nreal ? K.task_src[Q.t0] : -1;
+  if (nreal && (Q.w0 == Q.w1 || Q.w0 == Q.w2)) return false;
+  if (K.ns != 2 + nreal || K.s > 3) return false;
+  *out = Q;
+  return true;
+}
 
 bool fixed_shape_fits(Ctx& C, Level& L, int shape) {
-  if (shape < 0 || shape >= kFxShapes + kFxStagedShapes) return false;
+  if (shape < 0 || shape >= fixed_shapes()) return false;
   if (shape < kFxShapes) return true;
+  if (shape >= kFxShapes + kFxStagedShapes) {  // paired: complex pair, interior stars of 39
+    FxPair Q;
+    return L.kron_nmax == kFxN2 && fx_pair_plan(C.kplan, &Q) &&
+           (size_t)kFxWarps * std::max(fx_warp_bytes(C.s, std::max(C.kplan.ns, C.kplan.nt),
+                                                     C.kplan.nt, L.kron_nmax),
+                                       sizeof(FxPairSmem)) <= 227 * 1024;
+  }
   FxStagedShape shp;
   return fx_staged_config(C.kplan, C.s, L.kron_nmax, shape - kFxShapes, &shp);
 }
@@ -453,6 +558,8 @@ FxApply fx_params(Ctx& C, Level& L, int colour, const double* r, double* out, do
     P.count = L.colour_start[colour + 1] - P.first;
   }
   P.nmax = L.kron_nmax;
+  P.pair.m0 = -1;
+  if (!transpose) fx_pair_plan(K, &P.pair);
   return P;
 }
 
@@ -461,7 +568,10 @@ cudaError_t launch_vanka_kron_fx(Ctx& C, Level& L, int colour, const double* r, 
   const KronPlan& K = C.kplan;
   const FxApply P = fx_params(C, L, colour, r, out, scale, transpose);
   if (P.count <= 0) return cudaSuccess;
-  if (L.kron_shape >= kFxShapes) {  // TMA-staged kernel
+  if (L.kron_shape >= kFxShapes + kFxStagedShapes && !transpose)  // paired kernel
+    return launch_fx_pair(P, (const int2*)L.d_fac, L.kron_shape - kFxShapes - kFxStagedShapes,
+                          C.stream);
+  if (L.kron_shape >= kFxShapes && L.kron_shape < kFxShapes + kFxStagedShapes) {  // TMA-staged
     FxStagedShape shp;
     if (!fx_staged_config(K, C.s, L.kron_nmax, L.kron_shape - kFxShapes, &shp))
       return cudaErrorInvalidConfiguration;
@@ -480,8 +590,10 @@ cudaError_t launch_vanka_kron_fx(Ctx& C, Level& L, int colour, const double* r, 
   const size_t smem = (size_t)kFxWarps * fx_warp_bytes(P.s, K.ns > K.nt ? K.ns : K.nt, P.nt, P.nmax);
   const unsigned grid = (unsigned)((P.count + kFxWarps - 1) / kFxWarps);
   const int2* f = (const int2*)L.d_fac;
-  return transpose ? launch_fx<true>(P, f, L.kron_shape, grid, smem, C.stream)
-                   : launch_fx<false>(P, f, L.kron_shape, grid, smem, C.stream);
+  // the transposed apply of a level tuned to the paired kernel: shape 3
+  const int shape = L.kron_shape < kFxShapes ? L.kron_shape : 3;
+  return transpose ? launch_fx<true>(P, f, shape, grid, smem, C.stream)
+                   : launch_fx<false>(P, f, shape, grid, smem, C.stream);
 }
 
 }  // namespace irkmg

@@ -45,7 +45,7 @@ def _context(irkmg, fam, s, dt, n0, nl, form=1, fixed=1, variant=0, nu=1.0, wind
 @pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
 @pytest.mark.parametrize("fam,s,dt", CASES)
 def test_fixed_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
-    """Every level uses a fixed-point kernel (apply_kernel 8 or 9); one
+    """Every level uses a fixed-point kernel (apply_kernel 8, 9 or 10); one
     correction per level with J and with Jᵀ patches, and one V-cycle."""
     irkmg = need_gpu()
     n0, nl = 2, 4
@@ -54,7 +54,7 @@ def test_fixed_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
     try:
         for l in range(1, nl):
             info = ctx.levels[l]
-            assert info["apply_kernel"] in (8, 9)
+            assert info["apply_kernel"] in (8, 9, 10)
             assert info["single_launch"] == (1 if variant == 4 else 0)
             L = H.levels[l]
             r = synth.random_vector(700 + l, L.N)
@@ -74,21 +74,29 @@ def test_fixed_vanka_and_vcycle_match_oracle(fam, s, dt, form, variant):
         ctx.close()
 
 
-FIXED_SHAPE_KERNEL = [8] * 4 + [9] * 3
+FIXED_SHAPE_KERNEL = [8] * 4 + [9] * 3 + [10] * 2
 
 
 @pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
 @pytest.mark.parametrize("single", [0, 1], ids=["per_colour", "one_launch"])
-def test_every_fixed_launch_shape_matches_oracle(single, form):
+@pytest.mark.parametrize("s,dt", [(3, 1 / 64), (2, 1 / 8)], ids=["s3", "s2"])
+def test_every_fixed_launch_shape_matches_oracle(s, dt, single, form):
     """Each launch shape of the fixed-point kernels (warp per patch: columns
-    per load batch x resident CTAs; TMA-staged: stages x CTAs), pinned on
-    every level: corrections with J and Jᵀ patches against the oracle."""
+    per load batch x resident CTAs; TMA-staged: stages x CTAs; paired rows of
+    the complex layout: columns per load batch), pinned on every level:
+    corrections with J and Jᵀ patches against the oracle.  The paired kernel
+    exists for the complex layout only (s = 3: one real block and one complex
+    pair; s = 2: the pair alone)."""
     irkmg = need_gpu()
-    fam, s, dt, n0, nl = "radau_iia", 3, 1 / 64, 2, 4
+    fam, n0, nl = "radau_iia", 2, 4
     H = _oracle(fam, s, dt, n0, nl)
     ctx = _context(irkmg, fam, s, dt, n0, nl, form=form)
     try:
         for shape in range(len(FIXED_SHAPE_KERNEL)):
+            if FIXED_SHAPE_KERNEL[shape] == 10 and form != 2:
+                with pytest.raises(irkmg.IrkmgError):
+                    irkmg.irkmg_level_set_apply(ctx, 1, shape, single)
+                continue
             for l in range(1, nl):
                 irkmg.irkmg_level_set_apply(ctx, l, shape, single)
                 info = ctx.levels[l]
@@ -124,7 +132,7 @@ def test_fixed_error_not_above_fp64_error():
     for fixed in (0, 1):
         ctx = _context(irkmg, fam, s, dt, n0, nl, form=3, fixed=fixed, variant=4)
         try:
-            assert ctx.levels[nl - 1]["apply_kernel"] in ((8, 9) if fixed else (4,))
+            assert ctx.levels[nl - 1]["apply_kernel"] in ((8, 9, 10) if fixed else (4,))
             c = dev(np.zeros(L.N))
             irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=nl - 1)
             errs[fixed] = np.max(np.abs(host(c) - ref)) / np.max(np.abs(ref))
@@ -187,7 +195,7 @@ def test_fixed_solve_matches_oracle(fam, s, dt):
     x_ref, its, _ = fgmres.fgmres(H.finest.J, F, H.vcycle, rtol=1e-10, project=H.project_pressure)
     ctx = _context(irkmg, fam, s, dt, n0, nl)
     try:
-        assert all(lv["apply_kernel"] in (8, 9) for lv in ctx.levels[1:])
+        assert all(lv["apply_kernel"] in (8, 9, 10) for lv in ctx.levels[1:])
         k = dev(np.zeros(H.finest.N))
         st = irkmg.irkmg_solve(ctx, dev(F), k)
         assert st["status"] == 0
