@@ -21,14 +21,6 @@ struct __align__(8) Limbs {
   int32_t v1, v0;
 };
 
-// The complex layout's pair structure, for the paired apply: matrices X and Y
-// of the complex pair each read by two tasks (sources w1, w2), and at most
-// one real block (matrix m0, source w0, task t0; m0 < 0 when absent).
-struct FxPair {
-  int mX, mY, w1, w2, tX1, tX2, tY1, tY2;
-  int m0, w0, t0;
-};
-
 struct FxApply {
   int s, nsrc, nt, nm;  // nsrc: source vectors built (ns, or nt for the transpose)
   int64_t m;
@@ -46,7 +38,6 @@ struct FxApply {
   double* ybuf;  // one-launch mode (see KronApply)
   const int64_t* qoff;
   int64_t Q;
-  FxPair pair;
 };
 
 // Shared memory of one warp: limbs (nsrc·(nmax + kFxPad) × 8 B), residuals
@@ -246,15 +237,18 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
 
 
 // ---------------------------------------------------------------------------
-// Paired apply of one interior patch (n = kFxN2) in the complex layout: a
+// Paired apply of one interior patch (n = kFxN2) in the complex layout, whose
+// plan (host_kron.cpp) puts the complex pair first: matrices X = 0, Y = 1
+// (tasks 0, 1 = X·w1, X·w2 and 2, 3 = Y·w1, Y·w2, sources w1 = 0, w2 = 1),
+// then, for s = 3, the real block (matrix 2, task 4 = M2·w0, source 2).  A
 // lane owns one row of X or Y and both of that matrix's tasks, so each loaded
 // entry meets the limbs of w1 and w2 (one 16-byte shared-memory read) and
-// feeds eight products; the rows of the real block m0 run in the same passes
-// against (w0, 0).  Rows of X and Y first, then those of m0: with a real
-// block, passes 0..2 hold 96 of the 117 rows (14 of pass 2's lanes on Y) and
-// pass 3 the last 21 rows of m0 on the single-source path.  Per task and row
-// the exact sum and its one rounding are those of fx_patch, so the results
-// are bitwise the same.
+// feeds eight products; the rows of the real block run in the same passes
+// against (w0, 0).  Rows of X and Y first, then those of the real block: with
+// one, passes 0..2 hold 96 of the 117 rows (14 of pass 2's lanes on Y) and
+// pass 3 the last 21 on the single-source path.  Per task and row the exact
+// sum and its one rounding are those of fx_patch, so the results are
+// bitwise the same.
 // ---------------------------------------------------------------------------
 constexpr int kFxPairLS = kFxN2 + kFxPad;  // limb entries per source (zero tail)
 
@@ -294,12 +288,11 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
   // stages, sources and tasks follow from the pair structure
   constexpr int S = REAL ? 3 : 2, NSRC = S, NT = REAL ? 5 : 4;
   FxPairSmem& sm = *reinterpret_cast<FxPairSmem*>(base);
-  const FxPair& Q = P.pair;
   const int2* X = fac + P.fac_off[pi];
   // pass 0's first column batch (rows 0..31 of X) before the gathers
   int2 qa[U];
   {
-    const int2* mp0 = X + (int64_t)Q.mX * NN + lane;
+    const int2* mp0 = X + lane;  // matrix X = 0
 #pragma unroll
     for (int u = 0; u < U; ++u) qa[u] = __ldg(mp0 + u * N);
   }
@@ -333,7 +326,7 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
     bool finite;
     int F;
     fx_source_exponent(sm.x + c * N, N, lane, &finite, &F);
-    int32_t* dst = c == Q.w1 ? &sm.pa[0].x : c == Q.w2 ? &sm.pa[0].z : &sm.pb[0].x;
+    int32_t* dst = c == 0 ? &sm.pa[0].x : c == 1 ? &sm.pa[0].z : &sm.pb[0].x;
 #pragma unroll
     for (int k = 0; k < (LS + 31) / 32; ++k) {
       const int i = lane + 32 * k;
@@ -343,7 +336,7 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
         fx_split29(v, &v1, &v0);
         dst[4 * i] = v1;
         dst[4 * i + 1] = v0;
-        if (REAL && c == Q.w0) {
+        if (REAL && c == 2) {
           sm.pb[i].z = 0;
           sm.pb[i].w = 0;
         }
@@ -358,10 +351,10 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
 #pragma unroll 1
   for (int k0 = 0; k0 < 3; ++k0) {
     const int sl = 32 * k0 + lane;
-    const int kind = sl < N ? 0 : sl < 2 * N ? 1 : 2;  // X, Y, m0 (or idle)
+    const int kind = sl < N ? 0 : sl < 2 * N ? 1 : 2;  // X, Y, real block (or idle)
     const bool ok = kind < 2 || (REAL && sl < 3 * N);
     const int row = ok ? sl - kind * N : 0;
-    const int mat = kind == 0 ? Q.mX : kind == 1 ? Q.mY : (REAL ? Q.m0 : Q.mX);
+    const int mat = ok ? kind : 0;  // matrix index = kind
     const int2* mp = X + (int64_t)mat * NN + row;
     const int4* lp = REAL && kind == 2 ? sm.pb : sm.pa;  // idle lanes: bounded limbs
     int64_t A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
@@ -401,20 +394,18 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
     }
     if (ok) {
       const int ex = fe[mat * P.nmax + row];
-      const int sA = kind == 2 ? Q.w0 : Q.w1;
-      const int tA = kind == 0 ? Q.tX1 : kind == 1 ? Q.tY1 : Q.t0;
-      const int FA = sm.F[sA];
-      sm.x[tA * N + row] = FA == INT_MIN ? qnan : fx_round(A, ex + FA - 115);
+      const int FA = sm.F[kind == 2 ? 2 : 0];  // w0 or w1
+      sm.x[2 * kind * N + row] = FA == INT_MIN ? qnan : fx_round(A, ex + FA - 115);  // task 2·kind
       if (kind < 2) {
-        const int FB = sm.F[Q.w2];
-        sm.x[(kind == 0 ? Q.tX2 : Q.tY2) * N + row] = FB == INT_MIN ? qnan : fx_round(B, ex + FB - 115);
+        const int FB = sm.F[1];  // w2
+        sm.x[(2 * kind + 1) * N + row] = FB == INT_MIN ? qnan : fx_round(B, ex + FB - 115);
       }
     }
   }
   if (REAL) {  // pass 3: rows 18..38 of m0 against w0 alone
     const int row = 96 + lane - 2 * N;
     const bool ok = row < N;
-    const int2* mp = X + (int64_t)Q.m0 * NN + (ok ? row : 0);
+    const int2* mp = X + 2 * NN + (ok ? row : 0);
     int64_t A[4] = {0, 0, 0, 0};
     int2 qb[U];
 #pragma unroll
@@ -445,9 +436,9 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
       }
     }
     if (ok) {
-      const int ex = fe[Q.m0 * P.nmax + row];
-      const int F0 = sm.F[Q.w0];
-      sm.x[Q.t0 * N + row] = F0 == INT_MIN ? qnan : fx_round(A, ex + F0 - 115);
+      const int ex = fe[2 * P.nmax + row];
+      const int F0 = sm.F[2];
+      sm.x[4 * N + row] = F0 == INT_MIN ? qnan : fx_round(A, ex + F0 - 115);
     }
   }
   __syncwarp();
@@ -473,8 +464,8 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
 // (the one-launch relaxation).  k_patch_fixed.cu.
 FxApply fx_params(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                   int transpose);
-// The pair structure of the context's plan; false unless it is the complex
-// layout with one complex pair and at most one real block.  k_patch_fixed.cu.
-bool fx_pair_plan(const KronPlan& K, FxPair* out);
+// Whether the plan has the paired apply's structure (see fx_patch_pair):
+// *real = 1 with the real block of s = 3.  k_patch_fixed.cu.
+bool fx_pair_plan(const KronPlan& K, bool* real);
 
 }  // namespace irkmg

@@ -259,7 +259,15 @@ int kron_plan(const KronSplit& K, int layout, KronPlan* out) {
   P.layout = layout;
   const int s = K.s;
   double C[3][kKronMaxTasks] = {};  // y_k = Σ_τ C[k][τ] acc_τ
-  for (int b = 0; b < K.nblk; ++b) {
+  // layout 1 takes the complex pair first (matrices X, Y = 0, 1, sources
+  // w1, w2 = 0, 1, tasks 0..3), then a real block (matrix, source 2, task 4):
+  // the order the paired fixed-point apply is written for
+  int border[3], nb = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int b = 0; b < K.nblk; ++b)
+      if (layout == 2 ? pass == 0 : (pass == 0) == (K.blk_size[b] == 2)) border[nb++] = b;
+  for (int bi = 0; bi < K.nblk; ++bi) {
+    const int b = border[bi];
     const int c0 = K.col0[b];
     auto add_src = [&](double f0, int k0, double f1, int k1) {
       for (int t = 0; t < s; ++t)

@@ -417,8 +417,10 @@ cudaError_t launch_fx_pair_t(const FxApply& P, const int2* fac, cudaStream_t st)
   return cudaGetLastError();
 }
 
-cudaError_t launch_fx_pair(const FxApply& P, const int2* fac, int shape, cudaStream_t st) {
-  const bool real = P.pair.m0 >= 0;
+cudaError_t launch_fx_pair(const FxApply& P, const KronPlan& K, const int2* fac, int shape,
+                           cudaStream_t st) {
+  bool real = false;
+  if (!fx_pair_plan(K, &real)) return cudaErrorInvalidConfiguration;
   if (shape == 0) return real ? launch_fx_pair_t<kFxPairU[0], true>(P, fac, st)
                               : launch_fx_pair_t<kFxPairU[0], false>(P, fac, st);
   if (shape == 1) return real ? launch_fx_pair_t<kFxPairU[1], true>(P, fac, st)
@@ -457,43 +459,19 @@ int fixed_shape_kernel(int shape) {
   return shape < kFxShapes ? 8 : shape < kFxShapes + kFxStagedShapes ? 9 : 10;
 }
 
-bool fx_pair_plan(const KronPlan& K, FxPair* out) {
-  if (K.layout != 1) return false;
-  FxPair Q{};
-  Q.mX = Q.m0 = -1;
-  int npair = 0, nreal = 0;
-  for (int b = 0; b < K.nblk; ++b) {
-    if (K.blk_kind[b] == 1) {
-      ++npair;
-      Q.mX = K.blk_mat[b];
-      Q.mY = Q.mX + 1;
-    } else if (K.blk_kind[b] == 0) {
-      ++nreal;
-      Q.m0 = K.blk_mat[b];
-    } else {
-      return false;
-    }
-  }
-  if (npair != 1 || nreal > 1) return false;
-  int tx[2], ty[2], nx = 0, ny = 0, n0 = 0;
-  for (int t = 0; t < K.nt; ++t) {
-    if (K.task_mat[t] == Q.mX && nx < 2) tx[nx++] = t;
-    else if (K.task_mat[t] == Q.mY && ny < 2) ty[ny++] = t;
-    else if (K.task_mat[t] == Q.m0 && n0 < 1) Q.t0 = t, ++n0;
-    else return false;
-  }
-  if (nx != 2 || ny != 2 || n0 != nreal) return false;
-  Q.w1 = K.task_src[tx[0]];
-  Q.w2 = K.task_src[tx[1]];
-  if (Q.w1 == Q.w2 || K.task_src[ty[0]] != Q.w1 || K.task_src[ty[1]] != Q.w2) return false;
-  Q.tX1 = tx[0];
-  Q.tX2 = tx[1];
-  Q.tY1 = ty[0];
-  Q.tY2 = ty[1];
-  Q.w0 = nreal ? K.task_src[Q.t0] : -1;
-  if (nreal && (Q.w0 == Q.w1 || Q.w0 == Q.w2)) return false;
-  if (K.ns != 2 + nreal || K.s > 3) return false;
-  *out = Q;
+bool fx_pair_plan(const KronPlan& K, bool* real) {
+  // complex layout, the pair first: X, Y = 0, 1 with tasks (0, w1) (0, w2)
+  // (1, w1) (1, w2), w1, w2 = 0, 1; then at most one real block (2, 2)
+  if (K.layout != 1 || K.nblk < 1 || K.nblk > 2 || K.blk_kind[0] != 1 || K.blk_mat[0] != 0)
+    return false;
+  const bool r = K.nblk == 2;
+  if (r && (K.blk_kind[1] != 0 || K.blk_mat[1] != 2)) return false;
+  const int tm[5] = {0, 0, 1, 1, 2}, ts[5] = {0, 1, 0, 1, 2};
+  if (K.nt != (r ? 5 : 4) || K.ns != (r ? 3 : 2) || K.nm != (r ? 3 : 2) || K.s != (r ? 3 : 2))
+    return false;
+  for (int t = 0; t < K.nt; ++t)
+    if (K.task_mat[t] != tm[t] || K.task_src[t] != ts[t]) return false;
+  *real = r;
   return true;
 }
 
@@ -501,8 +479,8 @@ bool fixed_shape_fits(Ctx& C, Level& L, int shape) {
   if (shape < 0 || shape >= fixed_shapes()) return false;
   if (shape < kFxShapes) return true;
   if (shape >= kFxShapes + kFxStagedShapes) {  // paired: complex pair, interior stars of 39
-    FxPair Q;
-    return L.kron_nmax == kFxN2 && fx_pair_plan(C.kplan, &Q) &&
+    bool real;
+    return L.kron_nmax == kFxN2 && fx_pair_plan(C.kplan, &real) &&
            (size_t)kFxWarps * std::max(fx_warp_bytes(C.s, std::max(C.kplan.ns, C.kplan.nt),
                                                      C.kplan.nt, L.kron_nmax),
                                        sizeof(FxPairSmem)) <= 227 * 1024;
@@ -558,8 +536,6 @@ FxApply fx_params(Ctx& C, Level& L, int colour, const double* r, double* out, do
     P.count = L.colour_start[colour + 1] - P.first;
   }
   P.nmax = L.kron_nmax;
-  P.pair.m0 = -1;
-  if (!transpose) fx_pair_plan(K, &P.pair);
   return P;
 }
 
@@ -569,7 +545,7 @@ cudaError_t launch_vanka_kron_fx(Ctx& C, Level& L, int colour, const double* r, 
   const FxApply P = fx_params(C, L, colour, r, out, scale, transpose);
   if (P.count <= 0) return cudaSuccess;
   if (L.kron_shape >= kFxShapes + kFxStagedShapes && !transpose)  // paired kernel
-    return launch_fx_pair(P, (const int2*)L.d_fac, L.kron_shape - kFxShapes - kFxStagedShapes,
+    return launch_fx_pair(P, K, (const int2*)L.d_fac, L.kron_shape - kFxShapes - kFxStagedShapes,
                           C.stream);
   if (L.kron_shape >= kFxShapes && L.kron_shape < kFxShapes + kFxStagedShapes) {  // TMA-staged
     FxStagedShape shp;
