@@ -280,7 +280,8 @@ __device__ __forceinline__ void fx_source_exponent(const double* x, int n, int l
   }
 }
 
-template <int U, bool REAL>
+// RL2: the residual is read through L2 only (written earlier in the launch).
+template <int U, bool REAL, bool RL2 = false>
 __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __restrict__ fac,
                                               unsigned char* base, int lane, int64_t pi) {
   constexpr int N = kFxN2, NN = N * N, LS = kFxPairLS;
@@ -305,7 +306,7 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
     const int idx = lane + 32 * k;
     if (idx < S * N) {
       const int t = idx / N, i = idx - t * N;
-      sm.r[idx] = P.r[t * P.m + sm.g[i]];
+      sm.r[idx] = RL2 ? __ldcg(P.r + t * P.m + sm.g[i]) : P.r[t * P.m + sm.g[i]];
     }
   }
   __syncwarp();

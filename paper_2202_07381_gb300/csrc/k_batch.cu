@@ -67,6 +67,7 @@ struct BatchLaunch {
   int64_t spins;
   int* err;
   uint32_t warp_bytes;
+  int pair;  // every system in the complex layout's pair structure: paired rows
 };
 
 __device__ __forceinline__ int find_unit(const int64_t* pref, int n, int64_t u) {
@@ -128,6 +129,16 @@ __device__ __forceinline__ void stage_params(T* dst, const T* src, int* s_have, 
   if (threadIdx.x == 0) *s_have = k;  // read by the next call only after a barrier
 }
 
+// Patches outside the paired path (boundary stars; other layouts), out of
+// line so that their registers do not count against the paired path's.
+__device__ __noinline__ void batch_patch_generic(const FxApply& P, const int2* __restrict__ fac,
+                                                 unsigned char* base, int lane, int64_t pi, int np) {
+  if (np == kFxN2)
+    fx_patch<kFxN2, 1, 4, false, true>(P, fac, base, lane, pi, np);
+  else
+    fx_patch<0, 1, 4, false, true>(P, fac, base, lane, pi, np);
+}
+
 template <int S>
 __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_smooth(BatchLaunch R,
                                                                   const BatchSys* __restrict__ sys) {
@@ -170,10 +181,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_smooth(BatchLaunch R
       const int64_t pi = (u - R.patch_pref[i]) * kFxWarps + warp;
       if (pi < B.npatch) {
         const int np = s_fx.np[pi];
-        if (np == kFxN2)
-          fx_patch<kFxN2, 1, 4, false, true>(s_fx, B.fac, base, lane, pi, np);
+        if (S >= 2 && R.pair && np == kFxN2)  // complex layout: paired rows
+          fx_patch_pair<8, S == 3, true>(s_fx, B.fac, base, lane, pi);
         else
-          fx_patch<0, 1, 4, false, true>(s_fx, B.fac, base, lane, pi, np);
+          batch_patch_generic(s_fx, B.fac, base, lane, pi, np);
       }
     }
     if (!grid_sync(R.bar, R.spins, R.err, &s_fail)) return;
@@ -238,6 +249,7 @@ struct BatchPlan {
   size_t dyn = 0;
   uint32_t warp_bytes = 0;
   int ctas = 0;
+  int pair = 0;
 };
 
 // Why a batch cannot relax in one persistent launch ("" when it can): every
@@ -266,11 +278,15 @@ int batch_plan_create(const std::vector<Ctx*>& sys, BatchPlan** out) {
   P->sys = sys;
   P->s = sys[0]->s;
   size_t wb = 0;
+  P->pair = 1;
   for (Ctx* C : sys) {
     const Level& L = C->L.back();
     wb = std::max(wb, fx_warp_bytes(C->s, std::max(C->kplan.ns, C->kplan.nt), C->kplan.nt,
                                     L.kron_nmax));
+    bool real = false;
+    if (!fx_pair_plan(C->kplan, &real) || real != (P->s == 3)) P->pair = 0;
   }
+  if (P->pair) wb = std::max(wb, sizeof(FxPairSmem));
   P->warp_bytes = (uint32_t)wb;
   P->dyn = (size_t)kFxWarps * wb;
   int rc = P->s == 3 ? max_ctas<3>(P->dyn, &P->ctas)
@@ -361,6 +377,7 @@ cudaError_t batch_plan_smooth(BatchPlan* P, const std::vector<int>& active,
   R.spins = spins > 0 ? spins : (int64_t)1 << 26;
   R.err = err;
   R.warp_bytes = P->warp_bytes;
+  R.pair = P->pair;
   cudaError_t e = cudaMemsetAsync(P->d_bar, 0, sizeof(unsigned) * 2, st);
   if (e != cudaSuccess) return e;
   const int64_t most = std::max(R.patch_pref[R.n], std::max(R.op_pref[R.n], R.dof_pref[R.n]));
