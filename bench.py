@@ -59,11 +59,12 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # captured launch, keyed by kernel and by the hash of the kernel's source file
 # at capture time; reported as ratio x algorithmic bytes per launch, null once
 # the source has changed.  Captures: profiles/vanka_apply_128x128.md,
-# profiles/vanka_apply_kron_fp64_256x256.md.
+# profiles/vanka_apply_kron_fp64_256x256.md,
+# profiles/vanka_apply_kron_fx_pair_128x128.md.
 NCU_TRAFFIC = {
     ("k_vanka_apply", "c01e3c9fe148"): 0.97,
     ("k_vanka_apply_kron", "15072119f8f1"): 1.02,
-    ("k_vanka_apply_kron_fx", "37f8eee9d889"): 1.09,
+    ("k_vanka_apply_kron_fx_pair", "6850cc0d8407"): 1.096,
 }
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
                "k_vanka_apply_lu": "k_patch_big.cu", "k_vanka_apply_kron": "k_patch_kron.cu",
