@@ -62,8 +62,8 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # profiles/vanka_apply_kron_fp64_256x256.md,
 # profiles/vanka_apply_kron_fx_pair_128x128.md.
 NCU_TRAFFIC = {
-    ("k_vanka_apply", "c01e3c9fe148"): 0.97,
-    ("k_vanka_apply_kron", "15072119f8f1"): 1.02,
+    ("k_vanka_apply", "8f81809572f0"): 0.97,
+    ("k_vanka_apply_kron", "60c2ce575b6a"): 1.02,
     ("k_vanka_apply_kron_fx_pair", "6850cc0d8407"): 1.096,
 }
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
