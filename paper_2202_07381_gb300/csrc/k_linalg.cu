@@ -103,37 +103,67 @@ struct XferParams {
   const double* pw;
 };
 
-__global__ void k_transfer(XferParams P, const double* __restrict__ in, double* __restrict__ out,
-                           int add) {
+// One output row per thread: S stages × D velocity components (or S pressure
+// values) of that row, accumulated in registers in the CSR's entry order.
+template <int S, int D>
+__global__ void __launch_bounds__(256) k_transfer(XferParams P, const double* __restrict__ in,
+                                                  double* __restrict__ out, int add) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row < P.nf_out) {
-    double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int32_t p = P.uptr[row]; p < P.uptr[row + 1]; ++p) {
+    double acc[S][D];
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[t][c] = 0.0;
+    const int32_t p1 = P.uptr[row + 1];
+    for (int32_t p = P.uptr[row]; p < p1; ++p) {
       const int32_t j = P.ucol[p];
       const double w = P.uw[p];
-      for (int t = 0; t < P.s; ++t)
-        for (int c = 0; c < P.dim; ++c)
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
           acc[t][c] = fma(w, in[t * P.m_in + c * P.nf_in + j], acc[t][c]);
     }
-    for (int t = 0; t < P.s; ++t)
-      for (int c = 0; c < P.dim; ++c) {
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
         const int64_t g = t * P.m_out + c * P.nf_out + row;
         out[g] = add ? out[g] + acc[t][c] : acc[t][c];
       }
   } else if (row < P.nf_out + P.nv_out) {
     const int64_t v = row - P.nf_out;
-    double acc[3] = {0, 0, 0};
-    for (int32_t p = P.pptr[v]; p < P.pptr[v + 1]; ++p) {
+    double acc[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) acc[t] = 0.0;
+    const int32_t p1 = P.pptr[v + 1];
+    for (int32_t p = P.pptr[v]; p < p1; ++p) {
       const int32_t j = P.pcol[p];
       const double w = P.pw[p];
-      for (int t = 0; t < P.s; ++t)
-        acc[t] = fma(w, in[t * P.m_in + P.dim * P.nf_in + j], acc[t]);
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[t] = fma(w, in[t * P.m_in + D * P.nf_in + j], acc[t]);
     }
-    for (int t = 0; t < P.s; ++t) {
-      const int64_t g = t * P.m_out + P.dim * P.nf_out + v;
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int64_t g = t * P.m_out + D * P.nf_out + v;
       out[g] = add ? out[g] + acc[t] : acc[t];
     }
   }
+}
+
+cudaError_t launch_transfer(const XferParams& P, const double* in, double* out, int add,
+                            cudaStream_t st) {
+  const int64_t rows = P.nf_out + P.nv_out;
+  const unsigned grid = (unsigned)((rows + 255) / 256);
+#define XFER_CASE(S_, D_)                                                   \
+  if (P.s == S_ && P.dim == D_) {                                         \
+    k_transfer<S_, D_><<<grid, 256, 0, st>>>(P, in, out, add);            \
+    return cudaGetLastError();                                            \
+  }
+  XFER_CASE(1, 2) XFER_CASE(2, 2) XFER_CASE(3, 2) XFER_CASE(1, 3) XFER_CASE(2, 3) XFER_CASE(3, 3)
+#undef XFER_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coarse) {
@@ -152,9 +182,7 @@ cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coars
   P.pptr = Lf.ppt.ptr;
   P.pcol = Lf.ppt.col;
   P.pw = Lf.ppt.v[0];
-  const int64_t rows = Lc.nf + Lc.nv;
-  k_transfer<<<(unsigned)((rows + 255) / 256), 256, 0, C.stream>>>(P, fine, coarse, 0);
-  return cudaGetLastError();
+  return launch_transfer(P, fine, coarse, 0, C.stream);
 }
 
 cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine, int add) {
@@ -173,9 +201,7 @@ cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine
   P.pptr = Lf.pp.ptr;
   P.pcol = Lf.pp.col;
   P.pw = Lf.pp.v[0];
-  const int64_t rows = Lf.nf + Lf.nv;
-  k_transfer<<<(unsigned)((rows + 255) / 256), 256, 0, C.stream>>>(P, coarse, fine, add);
-  return cudaGetLastError();
+  return launch_transfer(P, coarse, fine, add, C.stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -284,26 +310,52 @@ cudaError_t launch_multiaxpy(double* w, const double* V, int64_t ldv, int k, con
   return cudaGetLastError();
 }
 
-// Per-stage pressure mean removal: block t sums stage t's pressure block in a
-// fixed order, then subtracts the mean.
-__global__ void __launch_bounds__(1024) k_pressure_mean(double* x, int64_t m, int64_t off,
-                                                        int64_t nv) {
-  __shared__ double red[1024];
-  double* p = x + blockIdx.x * m + off;
+// Per-stage pressure mean removal in two launches: kMeanBlocks blocks per
+// stage sum fixed contiguous chunks (a fixed tree per block), then every
+// block adds the partial sums of its stage in block order and subtracts the
+// mean from its chunk.  The same order on every call: reproducible bitwise.
+constexpr int kMeanBlocks = 152;
+
+__global__ void __launch_bounds__(256) k_pressure_part(const double* __restrict__ x, int64_t m,
+                                                       int64_t off, int64_t nv,
+                                                       double* __restrict__ part) {
+  __shared__ double red[256];
+  const int t = blockIdx.y;
+  const double* p = x + t * m + off;
+  const int64_t chunk = (nv + kMeanBlocks - 1) / kMeanBlocks;
+  const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(nv, b0 + chunk);
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) s += p[i];
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += p[i];
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = 512; o > 0; o >>= 1) {
+  for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < (unsigned)o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  const double mean = red[0] / (double)nv;
-  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) p[i] -= mean;
+  if (threadIdx.x == 0) part[t * kMeanBlocks + blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_pressure_sub(double* __restrict__ x, int64_t m,
+                                                      int64_t off, int64_t nv,
+                                                      const double* __restrict__ part) {
+  __shared__ double mean;
+  const int t = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < kMeanBlocks; ++b) s += part[t * kMeanBlocks + b];
+    mean = s / (double)nv;
+  }
+  __syncthreads();
+  double* p = x + t * m + off;
+  const int64_t chunk = (nv + kMeanBlocks - 1) / kMeanBlocks;
+  const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(nv, b0 + chunk);
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) p[i] -= mean;
 }
 
 cudaError_t launch_pressure_mean_remove(Ctx& C, Level& L, double* x) {
-  k_pressure_mean<<<C.s, 1024, 0, C.stream>>>(x, L.m, L.dim * L.nf, L.nv);
+  const dim3 grid(kMeanBlocks, (unsigned)C.s);
+  k_pressure_part<<<grid, 256, 0, C.stream>>>(x, L.m, L.dim * L.nf, L.nv, C.d_part);
+  k_pressure_sub<<<grid, 256, 0, C.stream>>>(x, L.m, L.dim * L.nf, L.nv, C.d_part);
   return cudaGetLastError();
 }
 

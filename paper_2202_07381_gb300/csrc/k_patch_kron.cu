@@ -905,22 +905,49 @@ namespace irkmg {
 // Deterministic gather of the one-launch patch results: for every stage t and
 // spatial DoF d, out[t·m + d] += scale · Σ_e ybuf[t·Q + e] over the entries e
 // of d (one per patch containing d, in the colour-ordered patch order).
-__global__ void k_vanka_reduce(int s, int64_t m, int64_t Q, const int32_t* __restrict__ cptr,
-                               const int32_t* __restrict__ cidx, const double* __restrict__ y,
-                               double scale, double* __restrict__ out) {
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= s * m) return;
-  const int64_t t = id / m, d = id - t * m;
-  const double* yt = y + t * Q;
-  double a = 0.0;
-  for (int32_t e = cptr[d]; e < cptr[d + 1]; ++e) a += yt[cidx[e]];
-  out[id] = __fma_rn(scale, a, out[id]);  // one rounding, as the batched smoother
+// One spatial DoF per thread, all S stages: the contribution indices of a
+// DoF are loaded eight at a time and their S·8 results issued together; each
+// stage's sum still runs over the contributions in order (bitwise the sum of
+// the batched smoother) and is added to out with one rounding.
+template <int S>
+__global__ void __launch_bounds__(256) k_vanka_reduce(int64_t m, int64_t Q,
+                                                      const int32_t* __restrict__ cptr,
+                                                      const int32_t* __restrict__ cidx,
+                                                      const double* __restrict__ y, double scale,
+                                                      double* __restrict__ out) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= m) return;
+  const int32_t e0 = cptr[d], e1 = cptr[d + 1];
+  double a[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) a[t] = 0.0;
+  for (int32_t e = e0; e < e1; e += 8) {
+    int32_t c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c[k] = e + k < e1 ? cidx[e + k] : -1;
+    double v[8][S];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int t = 0; t < S; ++t) v[k][t] = c[k] >= 0 ? y[t * Q + c[k]] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (c[k] >= 0)
+#pragma unroll
+        for (int t = 0; t < S; ++t) a[t] += v[k][t];
+  }
+#pragma unroll
+  for (int t = 0; t < S; ++t) out[t * m + d] = __fma_rn(scale, a[t], out[t * m + d]);
 }
 
 cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale) {
-  const int64_t thr = (int64_t)C.s * L.m;
-  k_vanka_reduce<<<(unsigned)((thr + 255) / 256), 256, 0, C.stream>>>(C.s, L.m, L.Q, L.d_cptr,
-                                                                     L.d_cidx, C.d_Y, scale, out);
+  const unsigned grid = (unsigned)((L.m + 255) / 256);
+  switch (C.s) {
+    case 1: k_vanka_reduce<1><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx, C.d_Y, scale, out); break;
+    case 2: k_vanka_reduce<2><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx, C.d_Y, scale, out); break;
+    case 3: k_vanka_reduce<3><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx, C.d_Y, scale, out); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
