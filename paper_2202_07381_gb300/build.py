@@ -48,7 +48,7 @@ def build(verbose=False, ptxas_info=False):
             if err.strip():
                 print(err)
     objs = [o for o, _ in results]
-    cmd = [_nvcc(), "-shared", *ARCH, "-o", LIB, *objs, "-cudart", "static"]
+    cmd = [_nvcc(), "-shared", *ARCH, "-o", LIB, *objs, "-cudart", "static", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <memory>
+#include <thread>
 
 #include "irkmg_internal.h"
 
@@ -121,16 +123,73 @@ inline int64_t slot(const HostCSR& A, int64_t row, int32_t col) {
   return (it != e && *it == col) ? (it - A.col.begin()) : -1;
 }
 
+// f(lo, hi) over contiguous ranges of [0, n), one per host thread (serially
+// below min_n); every index is handled by exactly one call, so no result
+// depends on the thread count.
+template <typename F>
+void parallel_ranges(int64_t n, F f, int64_t min_n = 2048) {
+  const unsigned T = host_threads();
+  if (T == 1 || n < min_n) {
+    f((int64_t)0, n);
+    return;
+  }
+  const int64_t chunk = (n + T - 1) / T;
+  std::vector<std::thread> th;
+  for (unsigned k = 1; k < T; ++k) {
+    const int64_t lo = k * chunk, hi = std::min(n, lo + chunk);
+    if (lo < hi) th.emplace_back(f, lo, hi);
+  }
+  f((int64_t)0, std::min(n, chunk));
+  for (auto& t : th) t.join();
+}
+
+// Element matrices of cell c: Me, Ke (nn x nn, row-major) and Be (d x nn x kv).
+void cell_matrices(const HostMesh& m, const QuadRule& q, double nu, const double* wind, int64_t c,
+                   double* Me, double* Ke, double* Be) {
+  const int d = m.dim, kv = m.nvc(), nn = m.nn(), nq = (int)q.w.size();
+  double gl[4][3];
+  const double vol = cell_geometry(m, c, gl);
+  int32_t node[10];
+  for (int a = 0; a < nn; ++a)
+    node[a] = a < kv ? m.cells[kv * c + a] : (int32_t)(m.nv + m.cell_edges[m.nle() * c + a - kv]);
+  for (int a = 0; a < nn * nn; ++a) Me[a] = Ke[a] = 0.0;
+  for (int a = 0; a < d * nn * kv; ++a) Be[a] = 0.0;
+  for (int iq = 0; iq < nq; ++iq) {
+    double phi[10], g[10][3];
+    p2_eval(d, q.lam[iq].data(), gl, phi, g);
+    const double wk = q.w[iq] * vol;
+    double wv[3] = {0.0, 0.0, 0.0};
+    if (wind && d == 2)
+      for (int a = 0; a < nn; ++a)
+        for (int k = 0; k < d; ++k) wv[k] += wind[d * node[a] + k] * phi[a];
+    for (int a = 0; a < nn; ++a) {
+      for (int b = 0; b < nn; ++b) {
+        Me[a * nn + b] += wk * phi[a] * phi[b];
+        double gg = 0.0, conv = 0.0;
+        for (int k = 0; k < d; ++k) {
+          gg += g[a][k] * g[b][k];
+          conv += wv[k] * g[b][k];
+        }
+        Ke[a * nn + b] += wk * (nu * gg + (wind && d == 2 ? conv * phi[a] : 0.0));
+      }
+      for (int p = 0; p < kv; ++p)
+        for (int k = 0; k < d; ++k) Be[(k * nn + a) * kv + p] -= wk * q.lam[iq][p] * g[a][k];
+    }
+  }
+}
+
 }  // namespace
 
+// Every part is computed per row (or per cell) in parallel host threads.  A
+// stored entry is the sum of its cells' element entries taken in ascending
+// cell order, so the operators do not depend on the thread count.
 void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& ops) {
   const int d = m.dim, kv = m.nvc(), nn = m.nn();
   const QuadRule q = d == 2 ? radon7() : duffy_tet();
-  const int nq = (int)q.w.size();
   auto cell_node = [&](int64_t c, int a) -> int32_t {
     return a < kv ? m.cells[kv * c + a] : (int32_t)(m.nv + m.cell_edges[m.nle() * c + a - kv]);
   };
-  // node -> cells, then sparsity patterns by union over cells
+  // node -> cells in ascending order
   std::vector<int32_t> nc_ptr(m.np2 + 1, 0), nc_idx(nn * m.nc);
   for (int64_t c = 0; c < m.nc; ++c)
     for (int a = 0; a < nn; ++a) nc_ptr[cell_node(c, a) + 1]++;
@@ -140,6 +199,16 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
     for (int64_t c = 0; c < m.nc; ++c)
       for (int a = 0; a < nn; ++a) nc_idx[fill[cell_node(c, a)]++] = (int32_t)c;
   }
+  // element matrices of every cell
+  // (uninitialised: cell_matrices writes every entry, first touch in parallel)
+  const int64_t sM = (int64_t)nn * nn, sB = (int64_t)d * nn * kv;
+  std::unique_ptr<double[]> Mall(new double[sM * m.nc]), Kall(new double[sM * m.nc]),
+      Ball(new double[sB * m.nc]);
+  parallel_ranges(m.nc, [&](int64_t lo, int64_t hi) {
+    for (int64_t c = lo; c < hi; ++c)
+      cell_matrices(m, q, nu, wind, c, &Mall[sM * c], &Kall[sM * c], &Ball[sB * c]);
+  });
+  // sparsity patterns by union over each row's cells, per thread range, then joined
   HostCSR& V = ops.vel;
   HostCSR& MA = ops.mall;
   HostCSR& B = ops.b;
@@ -150,124 +219,158 @@ void assemble_level(const HostMesh& m, double nu, const double* wind, HostOps& o
   V.ncols = m.nf;
   MA.ncols = m.np2;
   B.ncols = m.nv;
-  V.ptr.assign(1, 0);
-  MA.ptr.assign(1, 0);
-  B.ptr.assign(1, 0);
-  std::vector<int32_t> nodes, verts;
-  for (int64_t i = 0; i < m.nf; ++i) {
-    int32_t n = m.free_to_p2[i];
-    nodes.clear();
-    verts.clear();
-    for (int32_t p = nc_ptr[n]; p < nc_ptr[n + 1]; ++p) {
-      int64_t c = nc_idx[p];
-      for (int a = 0; a < nn; ++a) nodes.push_back(cell_node(c, a));
-      for (int a = 0; a < kv; ++a) verts.push_back(m.cells[kv * c + a]);
-    }
-    std::sort(nodes.begin(), nodes.end());
-    nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
-    std::sort(verts.begin(), verts.end());
-    verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
-    for (int32_t x : nodes) {
-      MA.col.push_back(x);
-      if (m.p2_to_free[x] >= 0) V.col.push_back(m.p2_to_free[x]);
-    }
-    for (int32_t x : verts) B.col.push_back(x);
-    V.ptr.push_back((int32_t)V.col.size());
-    MA.ptr.push_back((int32_t)MA.col.size());
-    B.ptr.push_back((int32_t)B.col.size());
+  {
+    struct Part {
+      std::vector<int32_t> vc, mc, bc, vn, mn, bn;  // columns, then per-row counts
+    };
+    const unsigned T = host_threads();
+    const int64_t chunk = (m.nf + T - 1) / T;
+    std::vector<Part> part(T);
+    parallel_ranges((int64_t)T, [&](int64_t k0, int64_t k1) {
+      std::vector<int32_t> nodes, verts;
+      for (int64_t k = k0; k < k1; ++k) {
+        Part& P = part[k];
+        for (int64_t i = k * chunk; i < std::min<int64_t>(m.nf, (k + 1) * chunk); ++i) {
+          const int32_t n = m.free_to_p2[i];
+          nodes.clear();
+          verts.clear();
+          for (int32_t p = nc_ptr[n]; p < nc_ptr[n + 1]; ++p) {
+            const int64_t c = nc_idx[p];
+            for (int a = 0; a < nn; ++a) nodes.push_back(cell_node(c, a));
+            for (int a = 0; a < kv; ++a) verts.push_back(m.cells[kv * c + a]);
+          }
+          std::sort(nodes.begin(), nodes.end());
+          nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+          std::sort(verts.begin(), verts.end());
+          verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+          int32_t nvc = 0;
+          for (int32_t x : nodes) {
+            P.mc.push_back(x);
+            if (m.p2_to_free[x] >= 0) {
+              P.vc.push_back(m.p2_to_free[x]);
+              ++nvc;
+            }
+          }
+          for (int32_t x : verts) P.bc.push_back(x);
+          P.vn.push_back(nvc);
+          P.mn.push_back((int32_t)nodes.size());
+          P.bn.push_back((int32_t)verts.size());
+        }
+      }
+    }, 1);
+    auto join = [&](HostCSR& A, std::vector<int32_t> Part::*cols, std::vector<int32_t> Part::*cnt) {
+      A.ptr.assign(1, 0);
+      for (const Part& P : part) {
+        for (int32_t k : P.*cnt) A.ptr.push_back(A.ptr.back() + k);
+        A.col.insert(A.col.end(), (P.*cols).begin(), (P.*cols).end());
+      }
+    };
+    join(V, &Part::vc, &Part::vn);
+    join(MA, &Part::mc, &Part::mn);
+    join(B, &Part::bc, &Part::bn);
   }
   V.v[0].assign(V.col.size(), 0.0);
   V.v[1].assign(V.col.size(), 0.0);
   MA.v[0].assign(MA.col.size(), 0.0);
   MA.v[1].assign(MA.col.size(), 0.0);
   for (int c = 0; c < d; ++c) B.v[c].assign(B.col.size(), 0.0);
-  // B with every P2 row (Dirichlet rows too), for the lifted right-hand side
-  std::vector<std::vector<std::pair<int32_t, std::array<double, 3>>>> bfull(m.np2);
-
-  double Me[10][10], Ke[10][10], Be[3][10][4];
-  for (int64_t c = 0; c < m.nc; ++c) {
-    double gl[4][3];
-    const double vol = cell_geometry(m, c, gl);
-    const int32_t* t = &m.cells[kv * c];
-    int32_t node[10];
-    for (int a = 0; a < nn; ++a) node[a] = cell_node(c, a);
-    for (int a = 0; a < nn; ++a)
-      for (int b = 0; b < nn; ++b) Me[a][b] = Ke[a][b] = 0.0;
-    for (int k = 0; k < d; ++k)
-      for (int a = 0; a < nn; ++a)
-        for (int p = 0; p < kv; ++p) Be[k][a][p] = 0.0;
-    for (int iq = 0; iq < nq; ++iq) {
-      double phi[10], g[10][3];
-      p2_eval(d, q.lam[iq].data(), gl, phi, g);
-      const double wk = q.w[iq] * vol;
-      double wv[3] = {0.0, 0.0, 0.0};
-      if (wind && d == 2)
-        for (int a = 0; a < nn; ++a)
-          for (int k = 0; k < d; ++k) wv[k] += wind[d * node[a] + k] * phi[a];
-      for (int a = 0; a < nn; ++a) {
+  // values: each free row takes row a of its cells' element matrices
+  parallel_ranges(m.nf, [&](int64_t lo, int64_t hi) {
+    for (int64_t row = lo; row < hi; ++row) {
+      const int32_t n = m.free_to_p2[row];
+      for (int32_t p = nc_ptr[n]; p < nc_ptr[n + 1]; ++p) {
+        const int64_t c = nc_idx[p];
+        int32_t node[10];
+        int a = 0;
+        for (int k = 0; k < nn; ++k) {
+          node[k] = cell_node(c, k);
+          if (node[k] == n) a = k;
+        }
+        const double* Me = &Mall[sM * c + a * nn];
+        const double* Ke = &Kall[sM * c + a * nn];
+        const double* Be = &Ball[sB * c];
         for (int b = 0; b < nn; ++b) {
-          Me[a][b] += wk * phi[a] * phi[b];
-          double gg = 0.0, conv = 0.0;
-          for (int k = 0; k < d; ++k) {
-            gg += g[a][k] * g[b][k];
-            conv += wv[k] * g[b][k];
+          const int64_t sa = slot(MA, row, node[b]);
+          MA.v[0][sa] += Me[b];
+          MA.v[1][sa] += Ke[b];
+          const int32_t cf = m.p2_to_free[node[b]];
+          if (cf >= 0) {
+            const int64_t sv = slot(V, row, cf);
+            V.v[0][sv] += Me[b];
+            V.v[1][sv] += Ke[b];
           }
-          Ke[a][b] += wk * (nu * gg + (wind && d == 2 ? conv * phi[a] : 0.0));
         }
-        for (int p = 0; p < kv; ++p)
-          for (int k = 0; k < d; ++k) Be[k][a][p] -= wk * q.lam[iq][p] * g[a][k];
-      }
-    }
-    for (int a = 0; a < nn; ++a)
-      for (int p = 0; p < kv; ++p)
-        bfull[node[a]].push_back({t[p], {Be[0][a][p], Be[1][a][p], d == 3 ? Be[2][a][p] : 0.0}});
-    for (int a = 0; a < nn; ++a) {
-      const int32_t row = m.p2_to_free[node[a]];
-      if (row < 0) continue;
-      for (int b = 0; b < nn; ++b) {
-        int64_t sa = slot(MA, row, node[b]);
-        MA.v[0][sa] += Me[a][b];
-        MA.v[1][sa] += Ke[a][b];
-        const int32_t cf = m.p2_to_free[node[b]];
-        if (cf >= 0) {
-          int64_t sv = slot(V, row, cf);
-          V.v[0][sv] += Me[a][b];
-          V.v[1][sv] += Ke[a][b];
+        const int32_t* t = &m.cells[kv * c];
+        for (int pp = 0; pp < kv; ++pp) {
+          const int64_t sb = slot(B, row, t[pp]);
+          for (int k = 0; k < d; ++k) B.v[k][sb] += Be[(k * nn + a) * kv + pp];
         }
       }
-      for (int p = 0; p < kv; ++p) {
-        int64_t sb = slot(B, row, t[p]);
-        for (int k = 0; k < d; ++k) B.v[k][sb] += Be[k][a][p];
-      }
     }
-  }
+  });
   // transpose of the velocity operator (same pattern, which is symmetric)
   V.v[2].resize(V.col.size());
-  for (int64_t i = 0; i < m.nf; ++i)
-    for (int32_t p = V.ptr[i]; p < V.ptr[i + 1]; ++p) {
-      int64_t st = slot(V, V.col[p], (int32_t)i);
-      V.v[2][p] = V.v[1][st];
-    }
+  parallel_ranges(m.nf, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      for (int32_t p = V.ptr[i]; p < V.ptr[i + 1]; ++p) {
+        const int64_t st = slot(V, V.col[p], (int32_t)i);
+        V.v[2][p] = V.v[1][st];
+      }
+  });
   ops.bt = transpose_csr(B, d);
-  // Bᵀ over every velocity column: vertex rows, P2-node columns, summed per pair
+  // Bᵀ over every velocity column: vertex rows, P2-node columns.  Per P2
+  // node, its cells' entries in cell order, summed per vertex in that order.
   HostCSR Bf;
   Bf.nrows = m.np2;
   Bf.ncols = m.nv;
-  Bf.ptr.assign(1, 0);
-  for (int64_t n = 0; n < m.np2; ++n) {
-    auto& e = bfull[n];
-    std::stable_sort(e.begin(), e.end(),
-                     [](const auto& a, const auto& b) { return a.first < b.first; });
-    for (size_t k = 0; k < e.size();) {
-      size_t j = k;
-      double sum[3] = {0.0, 0.0, 0.0};
-      for (; j < e.size() && e[j].first == e[k].first; ++j)
-        for (int c = 0; c < 3; ++c) sum[c] += e[j].second[c];
-      Bf.col.push_back(e[k].first);
-      for (int c = 0; c < d; ++c) Bf.v[c].push_back(sum[c]);
-      k = j;
+  {
+    struct Part {
+      std::vector<int32_t> cnt, col;
+      std::vector<double> v[3];
+    };
+    const unsigned T = host_threads();
+    const int64_t chunk = (m.np2 + T - 1) / T;
+    std::vector<Part> part(T);
+    parallel_ranges((int64_t)T, [&](int64_t k0, int64_t k1) {
+      std::vector<std::pair<int32_t, std::array<double, 3>>> e;
+      for (int64_t k = k0; k < k1; ++k) {
+        Part& P = part[k];
+        for (int64_t n = k * chunk; n < std::min<int64_t>(m.np2, (k + 1) * chunk); ++n) {
+          e.clear();
+          for (int32_t p = nc_ptr[n]; p < nc_ptr[n + 1]; ++p) {
+            const int64_t c = nc_idx[p];
+            int a = 0;
+            for (int kk = 0; kk < nn; ++kk)
+              if (cell_node(c, kk) == n) a = kk;
+            const double* Be = &Ball[sB * c];
+            const int32_t* t = &m.cells[kv * c];
+            for (int pp = 0; pp < kv; ++pp)
+              e.push_back({t[pp], {Be[(0 * nn + a) * kv + pp], Be[(1 * nn + a) * kv + pp],
+                                   d == 3 ? Be[(2 * nn + a) * kv + pp] : 0.0}});
+          }
+          std::stable_sort(e.begin(), e.end(),
+                           [](const auto& x, const auto& y) { return x.first < y.first; });
+          int32_t cnt = 0;
+          for (size_t i = 0; i < e.size();) {
+            size_t j = i;
+            double sum[3] = {0.0, 0.0, 0.0};
+            for (; j < e.size() && e[j].first == e[i].first; ++j)
+              for (int c = 0; c < 3; ++c) sum[c] += e[j].second[c];
+            P.col.push_back(e[i].first);
+            for (int c = 0; c < d; ++c) P.v[c].push_back(sum[c]);
+            ++cnt;
+            i = j;
+          }
+          P.cnt.push_back(cnt);
+        }
+      }
+    }, 1);
+    Bf.ptr.assign(1, 0);
+    for (const Part& P : part) {
+      for (int32_t k : P.cnt) Bf.ptr.push_back(Bf.ptr.back() + k);
+      Bf.col.insert(Bf.col.end(), P.col.begin(), P.col.end());
+      for (int c = 0; c < d; ++c) Bf.v[c].insert(Bf.v[c].end(), P.v[c].begin(), P.v[c].end());
     }
-    Bf.ptr.push_back((int32_t)Bf.col.size());
   }
   ops.btall = transpose_csr(Bf, d);
 }

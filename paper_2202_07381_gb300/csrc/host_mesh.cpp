@@ -9,6 +9,8 @@
 #include <cmath>
 #include <numeric>
 
+#include <thread>
+
 #include "irkmg_internal.h"
 
 namespace irkmg {
@@ -300,23 +302,55 @@ void build_prolongation(const HostMesh& c, const HostMesh& f, HostCSR& Pu, HostC
   }
 }
 
+unsigned host_threads() {
+  const unsigned T = std::thread::hardware_concurrency();
+  return std::max(1u, std::min(T, 64u));
+}
+
+// Counting-sort transpose; with many rows, T threads take contiguous row
+// ranges, count their columns, and write their entries at offsets that
+// follow the ranges in order, so every column of the result lists its rows
+// in ascending order whatever T is.
 HostCSR transpose_csr(const HostCSR& A, int nvals) {
   HostCSR T;
   T.nrows = A.ncols;
   T.ncols = A.nrows;
-  T.ptr.assign(T.nrows + 1, 0);
-  for (int32_t j : A.col) T.ptr[j + 1]++;
-  for (int64_t i = 0; i < T.nrows; ++i) T.ptr[i + 1] += T.ptr[i];
   T.col.resize(A.col.size());
   for (int k = 0; k < nvals; ++k) T.v[k].resize(A.col.size());
-  std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
-  for (int64_t i = 0; i < A.nrows; ++i)  // ascending rows -> sorted columns of T
-    for (int32_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-      int32_t j = A.col[p];
-      int32_t q = fill[j]++;
-      T.col[q] = (int32_t)i;
-      for (int k = 0; k < nvals; ++k) T.v[k][q] = A.v[k][p];
+  const unsigned nt = A.nrows >= 65536 ? host_threads() : 1u;
+  const int64_t chunk = (A.nrows + nt - 1) / nt;
+  std::vector<std::vector<int32_t>> cnt(nt);
+  auto run = [&](auto&& f) {
+    std::vector<std::thread> th;
+    for (unsigned k = 1; k < nt; ++k) th.emplace_back(f, k);
+    f(0u);
+    for (auto& t : th) t.join();
+  };
+  run([&](unsigned k) {
+    std::vector<int32_t>& c = cnt[k];
+    c.assign(T.nrows, 0);
+    for (int64_t i = k * chunk; i < std::min<int64_t>(A.nrows, (k + 1) * chunk); ++i)
+      for (int32_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) c[A.col[p]]++;
+  });
+  T.ptr.assign(T.nrows + 1, 0);
+  for (int64_t j = 0; j < T.nrows; ++j) {  // column j: range k's rows start after range k-1's
+    int32_t o = T.ptr[j];
+    for (unsigned k = 0; k < nt; ++k) {
+      const int32_t c = cnt[k][j];
+      cnt[k][j] = o;
+      o += c;
     }
+    T.ptr[j + 1] = o;
+  }
+  run([&](unsigned k) {
+    std::vector<int32_t>& fill = cnt[k];
+    for (int64_t i = k * chunk; i < std::min<int64_t>(A.nrows, (k + 1) * chunk); ++i)
+      for (int32_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+        const int32_t q = fill[A.col[p]]++;
+        T.col[q] = (int32_t)i;
+        for (int v = 0; v < nvals; ++v) T.v[v][q] = A.v[v][p];
+      }
+  });
   return T;
 }
 
