@@ -153,6 +153,12 @@ struct BigLuShared {
   double red_v[kBigThreads];
   int red_i[kBigThreads];
   int piv[kPanel];
+  double inv[kPanel];      // 1 / pivot of each panel column (scaling deferred to the panel's end)
+  float invf[kPanel];      // the same for FP32 patches
+  float red_f[kBigThreads / 32];
+  int perm[kMaxBigNp];     // net row permutation of a panel's interchanges
+  int chg[2 * kPanel];     // rows it moves
+  int nchg;
   int32_t nodes[96];
   double thr;
   uint64_t mbar;
@@ -247,31 +253,56 @@ __device__ void big_lu(const BigParams& P, int32_t v, T* A, int np, int32_t* piv
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
-      double best = -1.0;
+      // pivot: the largest |entry| of column j at or below row j, the lowest
+      // row among equals (a selection, so the reduction order does not
+      // matter): per thread, per warp by shuffles, then over the warps
+      // compared in the patch's precision: the FP64 pipe is scarce, and
+      // widening a float to double is exact, so the order is the same
+      T best = (T)-1;
       int bi = j;
       for (int r = j + tid; r < prow; r += kBigThreads) {
-        const double a = fabs((double)Pn[j * prow + r]);
+        const T a = fabs(Pn[j * prow + r]);
         if (a > best) {
           best = a;
           bi = r;
         }
       }
-      S.red_v[tid] = best;
-      S.red_i[tid] = bi;
-      __syncthreads();
-      for (int o = kBigThreads / 2; o > 0; o >>= 1) {
-        if (tid < o) {
-          const double a = S.red_v[tid + o];
-          const int ia = S.red_i[tid + o];
-          if (a > S.red_v[tid] || (a == S.red_v[tid] && ia < S.red_i[tid])) {
-            S.red_v[tid] = a;
-            S.red_i[tid] = ia;
-          }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T a = __shfl_xor_sync(0xffffffffu, best, o);
+        const int ia = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (a > best || (a == best && ia < bi)) {
+          best = a;
+          bi = ia;
         }
-        __syncthreads();
       }
-      const int p = S.red_i[0];
-      const double pabs = S.red_v[0];
+      if (lane == 0) {
+        if constexpr (sizeof(T) == 4)
+          S.red_f[warp] = best;
+        else
+          S.red_v[warp] = best;
+        S.red_i[warp] = bi;
+      }
+      __syncthreads();
+      T pbest;
+      if constexpr (sizeof(T) == 4)
+        pbest = S.red_f[0];
+      else
+        pbest = S.red_v[0];
+      int p = S.red_i[0];
+      for (int x = 1; x < kBigThreads / 32; ++x) {
+        T a;
+        if constexpr (sizeof(T) == 4)
+          a = S.red_f[x];
+        else
+          a = S.red_v[x];
+        const int ia = S.red_i[x];
+        if (a > pbest || (a == pbest && ia < p)) {
+          pbest = a;
+          p = ia;
+        }
+      }
+      const double pabs = (double)pbest;
       if (tid == 0) {
         S.piv[j] = p;
         piv[k0 + j] = k0 + p;
@@ -284,32 +315,64 @@ __device__ void big_lu(const BigParams& P, int32_t v, T* A, int np, int32_t* piv
           Pn[l * prow + p] = x;
         }
       __syncthreads();
+      // rank-1 update of the panel's trailing columns with the multipliers
+      // l_r = a_rj / a_jj; column j itself is scaled at the panel's end (later
+      // steps only swap its rows, which commutes with the scaling)
       const T pv = Pn[j * prow + j];
-      const T inv = pabs > 0.0 ? (T)1 / pv : (T)0;
-      for (int r = j + 1 + tid; r < prow; r += kBigThreads) Pn[j * prow + r] *= inv;
-      __syncthreads();
-      const int rows = prow - j - 1, cols = kb - j - 1;
-      for (int idx = tid; idx < rows * cols; idx += kBigThreads) {
-        const int l = j + 1 + idx / rows, r = j + 1 + idx % rows;
-        Pn[l * prow + r] -= Pn[j * prow + r] * Pn[l * prow + j];
+      const T inv = pbest > (T)0 ? (T)1 / pv : (T)0;
+      if (tid == 0) {
+        if constexpr (sizeof(T) == 4)
+          S.invf[j] = inv;
+        else
+          S.inv[j] = inv;
+      }
+      for (int r = j + 1 + tid; r < prow; r += kBigThreads) {
+        const T lr = Pn[j * prow + r] * inv;
+        for (int l = j + 1; l < kb; ++l) Pn[l * prow + r] -= lr * Pn[l * prow + j];
       }
       __syncthreads();
     }
     for (int idx = tid; idx < prow * kb; idx += kBigThreads) {
       const int l = idx / prow, r = idx - l * prow;
+      if (r > l) {
+        if constexpr (sizeof(T) == 4)
+          Pn[l * prow + r] *= S.invf[l];
+        else
+          Pn[l * prow + r] *= S.inv[l];
+      }
+    }
+    // net permutation of the panel's row interchanges (thread 0), and the
+    // rows it moves
+    if (tid == 0) {
+      for (int r = 0; r < prow; ++r) S.perm[r] = r;
+      for (int j = 0; j < kb; ++j) {
+        const int p = S.piv[j], x = S.perm[j];
+        S.perm[j] = S.perm[p];
+        S.perm[p] = x;
+      }
+      int c = 0;
+      for (int r = 0; r < prow; ++r)
+        if (S.perm[r] != r) S.chg[c++] = r;
+      S.nchg = c;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < prow * kb; idx += kBigThreads) {
+      const int l = idx / prow, r = idx - l * prow;
       A[(int64_t)(k0 + l) * np + k0 + r] = Pn[l * prow + r];
     }
-    // row interchanges of this panel, applied (in order) to every other column
-    for (int c = tid; c < np; c += kBigThreads) {
-      if (c >= k0 && c < k0 + kb) continue;
-      T* col = A + (int64_t)c * np + k0;
-      for (int j = 0; j < kb; ++j) {
-        const int p = S.piv[j];
-        if (p != j) {
-          const T x = col[j];
-          col[j] = col[p];
-          col[p] = x;
-        }
+    // the interchanges applied to every other column: one warp per column,
+    // all moved rows read, then written (row r takes old row perm[r])
+    {
+      const int nchg = S.nchg;
+      for (int c = warp; c < np; c += kBigThreads / 32) {
+        if (c >= k0 && c < k0 + kb) continue;
+        T* col = A + (int64_t)c * np + k0;
+        T x0 = (T)0, x1 = (T)0;
+        if (lane < nchg) x0 = col[S.perm[S.chg[lane]]];
+        if (lane + 32 < nchg) x1 = col[S.perm[S.chg[lane + 32]]];
+        __syncwarp();
+        if (lane < nchg) col[S.chg[lane]] = x0;
+        if (lane + 32 < nchg) col[S.chg[lane + 32]] = x1;
       }
     }
     __syncthreads();

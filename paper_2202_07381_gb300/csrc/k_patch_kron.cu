@@ -186,8 +186,9 @@ __global__ void __launch_bounds__(kKronBigThreads)
   __syncthreads();
   // units (matrix b, row i): every stored entry is loaded once and feeds the
   // one or two tasks that read its matrix; thread t takes units t and t + 256
-  // together, eight columns of each loaded before their multiply-adds
-  constexpr int kBatch = 8;
+  // together, a batch of columns of each (16 FP32 or 8 FP64 entries) loaded
+  // before their multiply-adds
+  constexpr int kBatch = sizeof(T) == 4 ? 16 : 8;
   const int nunit = P.nm * n;
   for (int u0 = tid; u0 < nunit; u0 += 2 * kKronBigThreads) {
     const int u1 = u0 + kKronBigThreads;
