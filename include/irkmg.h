@@ -509,6 +509,11 @@ typedef struct {
                               also writes w, then ||w||²:
                               8N·(2(j + 2) + 2(j + 3) + 1) bytes                    */
   double arnoldi_ms, arnoldi_bytes;
+  int64_t factor_launches;  /* timed finest-level patch factorisations (set-up work of
+                               Section 4.2, redone by irkmg_update): every patch
+                               block inverted explicitly, 2 m³ flops for an m × m
+                               block (LU 2/3 m³ plus the inverse from it 4/3 m³)    */
+  double factor_ms, factor_flops;
 } irkmg_trace;
 
 /* Reset the counters; on = 1 also starts event timing.  Never fails on a valid ctx. */

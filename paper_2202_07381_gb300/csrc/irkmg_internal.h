@@ -183,6 +183,7 @@ struct Level {
   int64_t* d_qoff = nullptr;           // per ordered patch
   int32_t *d_cptr = nullptr, *d_cidx = nullptr;  // spatial DoF -> entries qoff[p] + i
   double reduce_bytes = 0.0;           // algorithmic bytes of one reduction launch
+  double factor_flops = 0.0;           // explicit inverses of the patch blocks: 2 m³ per block
   int kron_cap[2][2] = {{0, 0}, {0, 0}};  // its resident CTAs per [shape][transpose] (0 unset)
   int ws_cap[2] = {0, 0};              // resident CTAs of the warp-specialised apply
   int fx_cap[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // ... of the staged fixed-point apply per shape

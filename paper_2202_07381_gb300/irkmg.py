@@ -85,7 +85,8 @@ class Trace(ct.Structure):
                 ("reduce_bytes", ct.c_double), ("xfer_launches", ct.c_int64),
                 ("xfer_ms", ct.c_double), ("xfer_bytes", ct.c_double),
                 ("arnoldi_steps", ct.c_int64), ("arnoldi_ms", ct.c_double),
-                ("arnoldi_bytes", ct.c_double)]
+                ("arnoldi_bytes", ct.c_double), ("factor_launches", ct.c_int64),
+                ("factor_ms", ct.c_double), ("factor_flops", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
