@@ -18,4 +18,7 @@ Parity status per part (what pins it is in tests/test_oracle_*.py):
   vanka        pinned (explicit-matrix brute force, hand-counted patch sizes)
   colouring    pinned (validity checker, greedy-order definition)
   mg / fgmres  pinned (agreement with a sparse direct solve, mesh-flat iterations)
+  local        pinned (rows and patch systems equal those of the assembled J,
+               Vanka entries equal the global correction; used for sampled
+               checks of the GPU path at sizes where J is not assembled)
 """
