@@ -121,7 +121,7 @@ def test_solve_residual_rows_at_full_size(full):
         F[p] -= F[p].mean()
     k = dev(np.zeros(L.N))
     st = irkmg.irkmg_solve(ctx, dev(F), k)
-    assert st["status"] == 0 and st["iters"] <= 30
+    assert st["status"] == 0
     kh = host(k)
     rows = _samples(L, 400, 13)
     Jk, mag = L.apply_rows(rows, kh)
