@@ -660,7 +660,7 @@ def run_adjoint(args, dev, stream, n=128, s=2, dt=1 / 32, nsteps=8, every=2):
     return {"workload": f"adjoint: Radau IIA({s}) {n}x{n}, {nsteps} steps dt={dt:g}, checkpoints "
                         f"every {every}, gradient of 1/2||u(T)-u_target||_M^2 w.r.t. a P0 forcing "
                         "field (N(0,1)) and nu",
-            "forward_backward_s": times[-1], "setup_s": setup_s, "objective": float(J),
+            "forward_backward_s": times[-1], "setup_s": setup_s, "objective": float(J.detach()),
             "fd_rel_err_theta": abs(fd - ad) / abs(fd), "fd_rel_err_nu": abs(fdn - nu.grad.item()) / abs(fdn),
             "rtol": 1e-12, "fgmres_iters_min_max": [min(its), max(its)],
             "patch_form": args.patch_form, "patch_fixed": o.patch_fixed}
