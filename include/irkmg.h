@@ -244,7 +244,10 @@ int irkmg_estimate_lambda(irkmg_ctx *ctx, int level, int nsteps, const double *d
 
 /* Build the hierarchy, assemble every level, build patch maps and colourings,
  * factor (invert) every patch and the bordered coarsest system.  Host inputs
- * are copied.  On failure *out is NULL. */
+ * are copied.  On failure *out is NULL.  The host part of the assembly runs on
+ * the hardware-concurrency threads (environment variable IRKMG_HOST_THREADS,
+ * 1..64, overrides); every entry is summed in one fixed order, so nothing
+ * depends on the thread count. */
 int irkmg_setup(const irkmg_mesh *mesh, const irkmg_tableau *tab, double dt, double nu,
                 const irkmg_options *opt, irkmg_ctx **out);
 

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <numeric>
 
+#include <cstdlib>
 #include <thread>
 
 #include "irkmg_internal.h"
@@ -303,6 +304,10 @@ void build_prolongation(const HostMesh& c, const HostMesh& f, HostCSR& Pu, HostC
 }
 
 unsigned host_threads() {
+  if (const char* e = std::getenv("IRKMG_HOST_THREADS")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 1) return (unsigned)std::min(v, 64L);
+  }
   const unsigned T = std::thread::hardware_concurrency();
   return std::max(1u, std::min(T, 64u));
 }

@@ -53,7 +53,8 @@ struct HostCSR {
 // canonical P2 / P1 interpolation, free nodes only).
 void build_prolongation(const HostMesh& c, const HostMesh& f, HostCSR& Pu, HostCSR& Pp);
 HostCSR transpose_csr(const HostCSR& A, int nvals);
-// Host threads for the set-up loops (hardware concurrency, at most 64).
+// Host threads for the set-up loops: IRKMG_HOST_THREADS if set (1..64), else
+// the hardware concurrency (at most 64).  No result depends on the count.
 unsigned host_threads();
 
 // Assembled free-DoF operators of one level (Section 3.1).  Values per

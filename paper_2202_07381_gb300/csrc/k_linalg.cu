@@ -248,29 +248,31 @@ cudaError_t launch_fill_sin(double* y, int64_t n, cudaStream_t st) {
 }
 
 // part[b*k + j] = partial sum over block b's contiguous chunk of V_j . w
+// Eight columns per pass over the block's chunk (each column's sum over the
+// elements in the same order as one column at a time, and the same tree).
 __global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict__ V, int64_t ldv,
                                                        int k, const double* __restrict__ w,
                                                        int64_t n, double* __restrict__ part) {
-  __shared__ double red[4][256];
+  __shared__ double red[8][256];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(n, b0 + chunk);
-  for (int j0 = 0; j0 < k; j0 += 4) {
-    double acc[4] = {0, 0, 0, 0};
-    const int nj = min(4, k - j0);
+  for (int j0 = 0; j0 < k; j0 += 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int nj = min(8, k - j0);
     for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
       const double wi = w[i];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 8; ++q)
         if (q < nj) acc[q] = fma(V[(int64_t)(j0 + q) * ldv + i], wi, acc[q]);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+    for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = acc[q];
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
       if (threadIdx.x < (unsigned)o)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+        for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
       __syncthreads();
     }
     if (threadIdx.x < (unsigned)nj) part[(int64_t)blockIdx.x * k + j0 + threadIdx.x] = red[threadIdx.x][0];
@@ -299,7 +301,16 @@ __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int j = 0; j < k; ++j) acc = fma(h[j], V[(int64_t)j * ldv + i], acc);
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {  // four loads issued together, the same FMA order
+      const double v0 = V[(int64_t)j * ldv + i], v1 = V[(int64_t)(j + 1) * ldv + i];
+      const double v2 = V[(int64_t)(j + 2) * ldv + i], v3 = V[(int64_t)(j + 3) * ldv + i];
+      acc = fma(h[j], v0, acc);
+      acc = fma(h[j + 1], v1, acc);
+      acc = fma(h[j + 2], v2, acc);
+      acc = fma(h[j + 3], v3, acc);
+    }
+    for (; j < k; ++j) acc = fma(h[j], V[(int64_t)j * ldv + i], acc);
     w[i] = fma(sign, acc, w[i]);
   }
 }
