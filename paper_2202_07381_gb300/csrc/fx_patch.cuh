@@ -465,8 +465,6 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
 // (the one-launch relaxation).  k_patch_fixed.cu.
 FxApply fx_params(Ctx& C, Level& L, int colour, const double* r, double* out, double scale,
                   int transpose);
-// Whether the plan has the paired apply's structure (see fx_patch_pair):
-// *real = 1 with the real block of s = 3.  k_patch_fixed.cu.
-bool fx_pair_plan(const KronPlan& K, bool* real);
+
 
 }  // namespace irkmg

@@ -102,6 +102,11 @@ int kron_split(int s, const double* A, KronSplit* out);
 // Eigenvalues of the n x n upper Hessenberg H (row-major), wr + i wi.
 int hessenberg_eigvals(int n, const double* H, double* wr, double* wi);
 int kron_plan(const KronSplit& K, int layout, KronPlan* out);
+// Whether the plan is the complex layout in the order the paired applies are
+// written for (the pair first: X, Y = 0, 1, tasks X·w1, X·w2, Y·w1, Y·w2 on
+// sources 0, 1; then, for s = 3, the real block 2 with task 4 on source 2);
+// *real = 1 with the real block.  k_patch_fixed.cu.
+bool fx_pair_plan(const KronPlan& K, bool* real);
 
 // ---------------------------------------------------------------------------
 // Device data.

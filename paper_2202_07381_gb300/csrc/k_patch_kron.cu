@@ -56,22 +56,17 @@ __host__ __device__ inline size_t kron_warp_bytes(int s, int ns, int nt, int nma
   return (b + 15) & ~(size_t)15;
 }
 
+// One patch by one warp (lanes over (task, row) slots, R slots per lane).
 template <typename T, int R, bool TR>
-__global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply P,
-                                                                      const T* __restrict__ fac) {
-  extern __shared__ __align__(128) unsigned char dyn[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kKronWarps + warp;
-  if (w >= P.count) return;
+__device__ __forceinline__ void kron_patch(const KronApply& P, const T* __restrict__ fac,
+                                           unsigned char* base, int lane, int64_t pi) {
   const int nmax = P.nmax;
-  unsigned char* base = dyn + (size_t)warp * kron_warp_bytes(P.s, P.ns, P.nt, nmax, sizeof(T));
   double* s_r = reinterpret_cast<double*>(base);
   double* s_acc = s_r + P.s * nmax;
   T* s_src = reinterpret_cast<T*>(s_acc + P.nt * nmax);
   const int nsrc = TR ? P.nt : P.ns;
   int32_t* s_g = reinterpret_cast<int32_t*>(s_src + (P.ns > P.nt ? P.ns : P.nt) * nmax);
 
-  const int64_t pi = P.first + w;
   const int n = P.np[pi];
   const int64_t nn = (int64_t)n * n;
   const T* X = fac + P.fac_off[pi];
@@ -135,6 +130,193 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply 
       P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
     else
       P.out[t * P.m + s_g[i]] += P.scale * x;
+  }
+}
+
+template <typename T, int R, bool TR>
+__global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply P,
+                                                                      const T* __restrict__ fac) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kKronWarps + warp;
+  if (w >= P.count) return;
+  unsigned char* base = dyn + (size_t)warp * kron_warp_bytes(P.s, P.ns, P.nt, P.nmax, sizeof(T));
+  kron_patch<T, R, TR>(P, fac, base, lane, P.first + w);
+}
+
+// ---------------------------------------------------------------------------
+// Paired FP32 rows for the complex layout (pair first: X = 0, Y = 1 with
+// tasks 0..3 on sources w1, w2 = 0, 1; the real block 2 with task 4 on
+// source 2, for s = 3).  Interior patches (n = kFxN2 = 39): a lane owns a
+// row of X or Y and both of its tasks, so every entry is loaded once and
+// meets (w1[j], w2[j]) in one 8-byte shared-memory read; rows of the real
+// block take (w0[j], 0).  Every (task, row) sum runs over the columns in the
+// same order as kron_patch, so the results are bitwise those of kernel 4.
+// Other patches go through kron_patch.
+// ---------------------------------------------------------------------------
+constexpr int kPairN = 39;
+
+struct __align__(16) KronPairSmem {
+  double r[3 * kPairN];
+  double acc[kKronMaxTasks * kPairN];
+  float2 pa[kPairN];  // (w1, w2)
+  float2 pb[kPairN];  // (w0, 0)
+  int g[kPairN + 1];
+};
+
+__device__ __noinline__ void kron_patch_f32_generic(const KronApply& P, const float* __restrict__ fac,
+                                                    unsigned char* base, int lane, int64_t pi) {
+  kron_patch<float, kKronMaxSlots, false>(P, fac, base, lane, pi);
+}
+
+template <bool REAL>
+__global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron_pair32(
+    KronApply P, const float* __restrict__ fac, uint32_t warp_bytes) {
+  constexpr int N = kPairN, NN = N * N, U = 8, nb = (N + U - 1) / U;
+  constexpr int S = REAL ? 3 : 2, NSRC = S, NT = REAL ? 5 : 4;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kKronWarps + warp;
+  if (w >= P.count) return;
+  unsigned char* base = dyn + (size_t)warp * warp_bytes;
+  const int64_t pi = P.first + w;
+  if (P.np[pi] != N) {
+    kron_patch_f32_generic(P, fac, base, lane, pi);
+    return;
+  }
+  KronPairSmem& sm = *reinterpret_cast<KronPairSmem*>(base);
+  const float* X = fac + P.fac_off[pi];
+  float qa[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) qa[u] = __ldg(X + lane + u * N);  // pass 0: rows 0..31 of X
+  const int32_t* gidx = reinterpret_cast<const int32_t*>(
+      reinterpret_cast<const unsigned char*>(X) + (((int64_t)P.nm * NN * 4 + 15) & ~(int64_t)15));
+  for (int i = lane; i < N; i += 32) sm.g[i] = gidx[i];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < (S * N + 31) / 32; ++k) {
+    const int idx = lane + 32 * k;
+    if (idx < S * N) {
+      const int t = idx / N, i = idx - t * N;
+      sm.r[idx] = P.r[t * P.m + sm.g[i]];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < (NSRC * N + 31) / 32; ++k) {
+    const int idx = lane + 32 * k;
+    if (idx < NSRC * N) {
+      const int c = idx / N, i = idx - c * N;
+      double a = 0.0;
+#pragma unroll
+      for (int t = 0; t < S; ++t) a += P.G[c * 3 + t] * sm.r[t * N + i];
+      const float f = (float)a;
+      if (c == 0)
+        sm.pa[i].x = f;
+      else if (c == 1)
+        sm.pa[i].y = f;
+      else {
+        sm.pb[i].x = f;
+        sm.pb[i].y = 0.f;
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int k0 = 0; k0 < 3; ++k0) {  // rows of X, Y, then the real block (or idle)
+    const int sl = 32 * k0 + lane;
+    const int kind = sl < N ? 0 : sl < 2 * N ? 1 : 2;
+    const bool ok = kind < 2 || (REAL && sl < 3 * N);
+    const int row = ok ? sl - kind * N : 0;
+    const int mat = ok ? kind : 0;
+    const float* mp = X + mat * NN + row;
+    const float2* lp = REAL && kind == 2 ? sm.pb : sm.pa;
+    float A = 0.f, B = 0.f;
+    float qb[U];
+    if (k0 > 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) qa[u] = __ldg(mp + u * N);
+    }
+#pragma unroll
+    for (int b = 0; b < nb; b += 2) {
+      if (b + 1 < nb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if ((b + 1) * U + u < N) qb[u] = __ldg(mp + ((b + 1) * U + u) * N);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (b * U + u < N) {
+          const float2 L = lp[b * U + u];
+          A = fmaf(qa[u], L.x, A);
+          B = fmaf(qa[u], L.y, B);
+        }
+      if (b + 1 < nb) {
+        if (b + 2 < nb) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if ((b + 2) * U + u < N) qa[u] = __ldg(mp + ((b + 2) * U + u) * N);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if ((b + 1) * U + u < N) {
+            const float2 L = lp[(b + 1) * U + u];
+            A = fmaf(qb[u], L.x, A);
+            B = fmaf(qb[u], L.y, B);
+          }
+      }
+    }
+    if (ok) {
+      sm.acc[2 * kind * N + row] = (double)A;  // task 0, 2 or 4
+      if (kind < 2) sm.acc[(2 * kind + 1) * N + row] = (double)B;
+    }
+  }
+  if (REAL) {  // rows 18..38 of the real block against w0 alone
+    const int row = 96 + lane - 2 * N;
+    const bool ok = row < N;
+    const float* mp = X + 2 * NN + (ok ? row : 0);
+    float A = 0.f;
+    float qb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) qa[u] = __ldg(mp + u * N);
+#pragma unroll
+    for (int b = 0; b < nb; b += 2) {
+      if (b + 1 < nb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if ((b + 1) * U + u < N) qb[u] = __ldg(mp + ((b + 1) * U + u) * N);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (b * U + u < N) A = fmaf(qa[u], sm.pb[b * U + u].x, A);
+      if (b + 1 < nb) {
+        if (b + 2 < nb) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if ((b + 2) * U + u < N) qa[u] = __ldg(mp + ((b + 2) * U + u) * N);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if ((b + 1) * U + u < N) A = fmaf(qb[u], sm.pb[(b + 1) * U + u].x, A);
+      }
+    }
+    if (ok) sm.acc[4 * N + row] = (double)A;
+  }
+  __syncwarp();
+  const int64_t qo = P.ybuf ? P.qoff[pi] : 0;
+#pragma unroll
+  for (int k = 0; k < (S * N + 31) / 32; ++k) {
+    const int idx = lane + 32 * k;
+    if (idx < S * N) {
+      const int t = idx / N, i = idx - t * N;
+      double x = 0.0;
+#pragma unroll
+      for (int tau = 0; tau < NT; ++tau) x += P.H[t * kKronMaxTasks + tau] * sm.acc[tau * N + i];
+      if (P.ybuf)
+        P.ybuf[t * P.Q + qo + i] = x;
+      else
+        P.out[t * P.m + sm.g[i]] += P.scale * x;
+    }
   }
 }
 
@@ -895,6 +1077,15 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
                      : launch_kron_t<double, false>(P, f, R, grid, smem, C.stream);
   }
   const float* f = (const float*)L.d_fac;
+  bool real = false;
+  if (!transpose && L.kron_nmax == kPairN && fx_pair_plan(K, &real)) {  // paired FP32 rows
+    const size_t wb = std::max(kron_warp_bytes(P.s, P.ns, P.nt, P.nmax, 4), sizeof(KronPairSmem));
+    const size_t sm2 = (size_t)kKronWarps * wb;
+    auto kern = real ? k_vanka_apply_kron_pair32<true> : k_vanka_apply_kron_pair32<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    kern<<<grid, kKronWarps * 32, sm2, C.stream>>>(P, f, (uint32_t)wb);
+    return cudaGetLastError();
+  }
   return transpose ? launch_kron_t<float, true>(P, f, R, grid, smem, C.stream)
                    : launch_kron_t<float, false>(P, f, R, grid, smem, C.stream);
 }
