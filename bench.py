@@ -426,8 +426,33 @@ def run_form(irkmg, torch, wl, args, dev, stream, k_ref, precision, patch_form, 
                                "hbm_peak_source": f"{hbm_kind} hbm_gbs"}
     if patch_fixed:
         out["finest_correction_ms_per_shape"] = shape_sweep(irkmg, torch, ctx, dev, stream)
+    # 2D patches are inverted in FP64 (Gauss-Jordan in shared memory) whatever
+    # precision they are stored in
+    out["factor"] = factor_roofline(irkmg, ctx, wl, stream, 64)
     ctx.close()
     return out
+
+
+def factor_roofline(irkmg, ctx, wl, stream, prec):
+    """Set-up work, after the timed regions: the finest level's patch
+    factorisation (explicit inverses, 2 m^3 flops per m x m block), timed by
+    the library's events while irkmg_update redoes the set-up for the same dt
+    and nu; FLOP/s against the measured FMA rate of the precision the
+    factorisation computes in (prec)."""
+    irkmg.irkmg_trace_enable(ctx, True)
+    irkmg.irkmg_update(ctx, wl["dt"], wl["nu"])
+    ftr = irkmg.irkmg_trace_read(ctx)
+    irkmg.irkmg_trace_enable(ctx, False)
+    if not (ftr["factor_launches"] and ftr["factor_ms"] > 0):
+        return None
+    alu = measure_alu_peaks(irkmg, stream)
+    pk = alu["fp64_tflops"] if prec == 64 else alu["fp32_tflops"]
+    tf = ftr["factor_flops"] / (ftr["factor_ms"] * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "patch factorisation (finest level, set-up)",
+            "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk,
+            "peak_source": "FP%d FMA rate measured by irkmg_probe_peak" % prec,
+            "ms": ftr["factor_ms"], "flops": ftr["factor_flops"],
+            "flops_counted": "2 m^3 per m x m block inverted (LU 2/3 m^3 + inverse 4/3 m^3)"}
 
 
 def shape_sweep(irkmg, torch, ctx, dev, stream, reps=10):
@@ -707,6 +732,7 @@ def run_3d(args, dev, stream, patch_form=1):
            "vanka_lu_finest": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                "frac": gbs / hbm if gbs else None,
                                "avg_launch_ms": tr["vanka_ms"] / max(tr["vanka_launches"], 1)}}
+    out["factor"] = factor_roofline(irkmg, ctx, wl, stream, 32)
     ctx.close()
     return out
 
@@ -808,25 +834,9 @@ def run_ours(args, wl, rank, world, local_rank):
     trace = irkmg.irkmg_trace_read(ctx)
     irkmg.irkmg_trace_enable(ctx, False)
     stats[:] = stats_keep
-    factor = None
-    if rank == 0 and not args.small:
-        # set-up work, after the timed regions: the finest level's patch
-        # factorisation (explicit inverses, 2 m^3 flops per m x m block), timed
-        # by the library's events while irkmg_update redoes the set-up for the
-        # same dt and nu
-        irkmg.irkmg_trace_enable(ctx, True)
-        irkmg.irkmg_update(ctx, wl["dt"], wl["nu"])
-        ftr = irkmg.irkmg_trace_read(ctx)
-        irkmg.irkmg_trace_enable(ctx, False)
-        if ftr["factor_launches"] and ftr["factor_ms"] > 0:
-            alu = measure_alu_peaks(irkmg, stream)
-            pk = alu["fp64_tflops"] if prec == 64 else alu["fp32_tflops"]
-            tf = ftr["factor_flops"] / (ftr["factor_ms"] * 1e-3) / 1e12
-            factor = {"bound": "alu", "kernel": "patch factorisation (finest level, set-up)",
-                      "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk,
-                      "peak_source": "FP%d FMA rate measured by irkmg_probe_peak" % prec,
-                      "ms": ftr["factor_ms"], "flops": ftr["factor_flops"],
-                      "flops_counted": "2 m^3 per m x m block inverted (LU 2/3 m^3 + inverse 4/3 m^3)"}
+    # 2D patches are inverted in FP64; the 3D blocked LU computes in FP32
+    factor = (factor_roofline(irkmg, ctx, wl, stream, 64 if wl.get("dim", 2) == 2 else 32)
+              if rank == 0 and not args.small else None)
     forms = {}
     shapes_ms = None
     mesh = None
