@@ -46,10 +46,27 @@ struct KronApply {
   // tasks reading each stored matrix (at most two: the complex layout applies
   // X and Y to both sources of a pair), -1 if unused
   int mat_task[kKronMaxTasks][2];
+  // G and H rounded to FP32, for the FP32-accumulating paired apply
+  float Gf[kKronMaxSrc * 3], Hf[3 * kKronMaxTasks];
 };
 
+// The stage mixing around the patch solves (sources from the gathered
+// residual by the rows of T⁻¹, results back by T) runs in the patch
+// precision: FP64 for FP64 patches, FP32 for FP32 patches (the FP32 form
+// accumulates in FP32 throughout the patch apply, and GB300's FP64 pipe is
+// 1/62 of its FP32 rate).
+template <typename T>
+__device__ __forceinline__ T mix_g(const KronApply& P, int k) {
+  if constexpr (sizeof(T) == 4) return P.Gf[k]; else return P.G[k];
+}
+template <typename T>
+__device__ __forceinline__ T mix_h(const KronApply& P, int k) {
+  if constexpr (sizeof(T) == 4) return P.Hf[k]; else return P.H[k];
+}
+
 // Shared memory of one warp: residuals (s·nmax doubles), task results
-// (nt·nmax doubles), sources (max(ns, nt)·nmax of T), indices (nmax int32).
+// (nt·nmax doubles), sources (max(ns, nt)·nmax of T), indices (nmax int32);
+// FP32 patches keep the residuals and results as floats in the same slots.
 __host__ __device__ inline size_t kron_warp_bytes(int s, int ns, int nt, int nmax, int tsize) {
   const int nsrc = ns > nt ? ns : nt;
   size_t b = (size_t)(s + nt) * nmax * 8 + (size_t)nsrc * nmax * tsize + (size_t)nmax * 4;
@@ -73,19 +90,21 @@ __device__ __forceinline__ void kron_patch(const KronApply& P, const T* __restri
   const int32_t* gidx = reinterpret_cast<const int32_t*>(
       reinterpret_cast<const unsigned char*>(X) +
       (((int64_t)P.nm * nn * (int64_t)sizeof(T) + 15) & ~(int64_t)15));
+  T* s_rm = reinterpret_cast<T*>(s_r);
+  T* s_accm = reinterpret_cast<T*>(s_acc);
   for (int i = lane; i < n; i += 32) s_g[i] = gidx[i];
   __syncwarp();
   for (int idx = lane; idx < P.s * n; idx += 32) {
     const int t = idx / n, i = idx - t * n;
-    s_r[idx] = P.r[t * P.m + s_g[i]];
+    s_rm[idx] = (T)P.r[t * P.m + s_g[i]];
   }
   __syncwarp();
   for (int idx = lane; idx < nsrc * n; idx += 32) {
     const int c = idx / n, i = idx - c * n;
-    double a = 0.0;
+    T a = (T)0;
     for (int t = 0; t < P.s; ++t)
-      a += (TR ? P.H[t * kKronMaxTasks + c] : P.G[c * 3 + t]) * s_r[t * n + i];
-    s_src[idx] = (T)a;
+      a = fma(TR ? mix_h<T>(P, t * kKronMaxTasks + c) : mix_g<T>(P, c * 3 + t), s_rm[t * n + i], a);
+    s_src[idx] = a;
   }
   __syncwarp();
 
@@ -117,19 +136,19 @@ __device__ __forceinline__ void kron_patch(const KronApply& P, const T* __restri
   }
 #pragma unroll
   for (int k = 0; k < R; ++k)
-    if (ok[k]) s_acc[lane + 32 * k] = (double)acc[k];
+    if (ok[k]) s_accm[lane + 32 * k] = acc[k];
   __syncwarp();
   for (int idx = lane; idx < P.s * n; idx += 32) {
     const int t = idx / n, i = idx - t * n;
-    double x = 0.0;
+    T x = (T)0;
     for (int tau = 0; tau < P.nt; ++tau) {
-      const double h = TR ? P.G[P.task_src[tau] * 3 + t] : P.H[t * kKronMaxTasks + tau];
-      x += h * s_acc[tau * n + i];
+      const T h = TR ? mix_g<T>(P, P.task_src[tau] * 3 + t) : mix_h<T>(P, t * kKronMaxTasks + tau);
+      x = fma(h, s_accm[tau * n + i], x);
     }
     if (P.ybuf)
-      P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
+      P.ybuf[t * P.Q + P.qoff[pi] + i] = (double)x;
     else
-      P.out[t * P.m + s_g[i]] += P.scale * x;
+      P.out[t * P.m + s_g[i]] += P.scale * (double)x;
   }
 }
 
@@ -155,10 +174,11 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply 
 // Other patches go through kron_patch.
 // ---------------------------------------------------------------------------
 constexpr int kPairN = 39;
+constexpr int kPair32U = 8;  // columns per load batch (two batches in flight)
 
 struct __align__(16) KronPairSmem {
-  double r[3 * kPairN];
-  double acc[kKronMaxTasks * kPairN];
+  float r[3 * kPairN];
+  float acc[kKronMaxTasks * kPairN];
   float2 pa[kPairN];  // (w1, w2)
   float2 pb[kPairN];  // (w0, 0)
   int g[kPairN + 1];
@@ -166,13 +186,16 @@ struct __align__(16) KronPairSmem {
 
 __device__ __noinline__ void kron_patch_f32_generic(const KronApply& P, const float* __restrict__ fac,
                                                     unsigned char* base, int lane, int64_t pi) {
-  kron_patch<float, kKronMaxSlots, false>(P, fac, base, lane, pi);
+  // nt·n ≤ 5·39 slots: seven per lane (kKronMaxSlots would raise the whole
+  // kernel's register count, and so cut its resident warps, for the few
+  // boundary patches that come here)
+  kron_patch<float, (kKronMaxTasks * kPairN + 31) / 32, false>(P, fac, base, lane, pi);
 }
 
 template <bool REAL>
-__global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron_pair32(
+__global__ void __launch_bounds__(kKronWarps * 32, 4) k_vanka_apply_kron_pair32(
     KronApply P, const float* __restrict__ fac, uint32_t warp_bytes) {
-  constexpr int N = kPairN, NN = N * N, U = 8, nb = (N + U - 1) / U;
+  constexpr int N = kPairN, NN = N * N, U = kPair32U, nb = (N + U - 1) / U;
   constexpr int S = REAL ? 3 : 2, NSRC = S, NT = REAL ? 5 : 4;
   extern __shared__ __align__(128) unsigned char dyn[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -198,7 +221,7 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron_pair32(
     const int idx = lane + 32 * k;
     if (idx < S * N) {
       const int t = idx / N, i = idx - t * N;
-      sm.r[idx] = P.r[t * P.m + sm.g[i]];
+      sm.r[idx] = (float)P.r[t * P.m + sm.g[i]];
     }
   }
   __syncwarp();
@@ -207,10 +230,9 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron_pair32(
     const int idx = lane + 32 * k;
     if (idx < NSRC * N) {
       const int c = idx / N, i = idx - c * N;
-      double a = 0.0;
+      float f = 0.f;
 #pragma unroll
-      for (int t = 0; t < S; ++t) a += P.G[c * 3 + t] * sm.r[t * N + i];
-      const float f = (float)a;
+      for (int t = 0; t < S; ++t) f = fmaf(P.Gf[c * 3 + t], sm.r[t * N + i], f);
       if (c == 0)
         sm.pa[i].x = f;
       else if (c == 1)
@@ -267,8 +289,8 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron_pair32(
       }
     }
     if (ok) {
-      sm.acc[2 * kind * N + row] = (double)A;  // task 0, 2 or 4
-      if (kind < 2) sm.acc[(2 * kind + 1) * N + row] = (double)B;
+      sm.acc[2 * kind * N + row] = A;  // task 0, 2 or 4
+      if (kind < 2) sm.acc[(2 * kind + 1) * N + row] = B;
     }
   }
   if (REAL) {  // rows 18..38 of the real block against w0 alone
@@ -300,7 +322,7 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron_pair32(
           if ((b + 1) * U + u < N) A = fmaf(qb[u], sm.pb[(b + 1) * U + u].x, A);
       }
     }
-    if (ok) sm.acc[4 * N + row] = (double)A;
+    if (ok) sm.acc[4 * N + row] = A;
   }
   __syncwarp();
   const int64_t qo = P.ybuf ? P.qoff[pi] : 0;
@@ -309,13 +331,13 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron_pair32(
     const int idx = lane + 32 * k;
     if (idx < S * N) {
       const int t = idx / N, i = idx - t * N;
-      double x = 0.0;
+      float x = 0.f;
 #pragma unroll
-      for (int tau = 0; tau < NT; ++tau) x += P.H[t * kKronMaxTasks + tau] * sm.acc[tau * N + i];
+      for (int tau = 0; tau < NT; ++tau) x = fmaf(P.Hf[t * kKronMaxTasks + tau], sm.acc[tau * N + i], x);
       if (P.ybuf)
-        P.ybuf[t * P.Q + qo + i] = x;
+        P.ybuf[t * P.Q + qo + i] = (double)x;
       else
-        P.out[t * P.m + sm.g[i]] += P.scale * x;
+        P.out[t * P.m + sm.g[i]] += P.scale * (double)x;
     }
   }
 }
@@ -352,18 +374,20 @@ __global__ void __launch_bounds__(kKronBigThreads)
   const int32_t* gidx = reinterpret_cast<const int32_t*>(
       reinterpret_cast<const unsigned char*>(X) +
       (((int64_t)P.nm * nn * (int64_t)sizeof(T) + 15) & ~(int64_t)15));
+  T* s_rm = reinterpret_cast<T*>(s_r);
+  T* s_accm = reinterpret_cast<T*>(s_acc);
   for (int i = tid; i < n; i += kKronBigThreads) s_g[i] = gidx[i];
   __syncthreads();
   for (int idx = tid; idx < P.s * n; idx += kKronBigThreads) {
     const int t = idx / n, i = idx - t * n;
-    s_r[idx] = P.r[t * P.m + s_g[i]];
+    s_rm[idx] = (T)P.r[t * P.m + s_g[i]];
   }
   __syncthreads();
   for (int idx = tid; idx < P.ns * n; idx += kKronBigThreads) {
     const int c = idx / n, i = idx - c * n;
-    double a = 0.0;
-    for (int t = 0; t < P.s; ++t) a += P.G[c * 3 + t] * s_r[t * n + i];
-    s_src[idx] = (T)a;
+    T a = (T)0;
+    for (int t = 0; t < P.s; ++t) a = fma(mix_g<T>(P, c * 3 + t), s_rm[t * n + i], a);
+    s_src[idx] = a;
   }
   __syncthreads();
   // units (matrix b, row i): every stored entry is loaded once and feeds the
@@ -414,22 +438,22 @@ __global__ void __launch_bounds__(kKronBigThreads)
         a11 = fma(w1, s11[j], a11);
       }
     }
-    s_acc[t00 * n + i0] = (double)a00;
-    if (t01 >= 0) s_acc[t01 * n + i0] = (double)a01;
+    s_accm[t00 * n + i0] = a00;
+    if (t01 >= 0) s_accm[t01 * n + i0] = a01;
     if (has1) {
-      s_acc[t10 * n + i1] = (double)a10;
-      if (t11 >= 0) s_acc[t11 * n + i1] = (double)a11;
+      s_accm[t10 * n + i1] = a10;
+      if (t11 >= 0) s_accm[t11 * n + i1] = a11;
     }
   }
   __syncthreads();
   for (int idx = tid; idx < P.s * n; idx += kKronBigThreads) {
     const int t = idx / n, i = idx - t * n;
-    double x = 0.0;
-    for (int tau = 0; tau < P.nt; ++tau) x += P.H[t * kKronMaxTasks + tau] * s_acc[tau * n + i];
+    T x = (T)0;
+    for (int tau = 0; tau < P.nt; ++tau) x = fma(mix_h<T>(P, t * kKronMaxTasks + tau), s_accm[tau * n + i], x);
     if (P.ybuf)
-      P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
+      P.ybuf[t * P.Q + P.qoff[pi] + i] = (double)x;
     else
-      P.out[t * P.m + s_g[i]] += P.scale * x;
+      P.out[t * P.m + s_g[i]] += P.scale * (double)x;
   }
 }
 
@@ -469,6 +493,8 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
   const int nmax = P.nmax;
   double* s_r = reinterpret_cast<double*>(dyn + S.work_off);  // s · nmax
   double* s_acc = s_r + P.s * nmax;                           // nt · nmax
+  T* s_rm = reinterpret_cast<T*>(s_r);
+  T* s_accm = reinterpret_cast<T*>(s_acc);
   T* s_src = reinterpret_cast<T*>(s_acc + P.nt * nmax);        // max(ns, nt) · nmax
   const int nsrc = TR ? P.nt : P.ns;
   const int64_t nmine = (P.count > blockIdx.x) ? (P.count - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -560,15 +586,15 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
     const int64_t nn = (int64_t)n * n;
     const int64_t gk = gix, qk = qo;
     const double ok_ = ov;
-    if (gk >= 0) s_r[tid] = rv;
+    if (gk >= 0) s_rm[tid] = (T)rv;
     __syncthreads();
     if (k + 1 < nmine && wait_stage(k + 1)) gather(k + 1);
     for (int idx = tid; idx < nsrc * n; idx += kKronStagedThreads) {
       const int c = idx / n, i = idx - c * n;
-      double a = 0.0;
+      T a = (T)0;
       for (int t = 0; t < P.s; ++t)
-        a += (TR ? P.H[t * kKronMaxTasks + c] : P.G[c * 3 + t]) * s_r[t * n + i];
-      s_src[idx] = (T)a;
+        a = fma(TR ? mix_h<T>(P, t * kKronMaxTasks + c) : mix_g<T>(P, c * 3 + t), s_rm[t * n + i], a);
+      s_src[idx] = a;
     }
     __syncthreads();
     for (int tau = tid; tau < P.nt * n; tau += kKronStagedThreads) {
@@ -584,20 +610,20 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
         a1 = fma(M[(j + 1) * step], src[j + 1], a1);
       }
       if (j < n) a0 = fma(M[j * step], src[j], a0);
-      s_acc[tau] = (double)(a0 + a1);
+      s_accm[tau] = a0 + a1;
     }
     __syncthreads();
     if (gk >= 0) {
       const int t = tid / n, i = tid - t * n;
-      double x = 0.0;
+      T x = (T)0;
       for (int tau = 0; tau < P.nt; ++tau) {
-        const double h = TR ? P.G[P.task_src[tau] * 3 + t] : P.H[t * kKronMaxTasks + tau];
-        x += h * s_acc[tau * n + i];
+        const T h = TR ? mix_g<T>(P, P.task_src[tau] * 3 + t) : mix_h<T>(P, t * kKronMaxTasks + tau);
+        x = fma(h, s_accm[tau * n + i], x);
       }
       if (P.ybuf)
-        P.ybuf[t * P.Q + qk + i] = x;
+        P.ybuf[t * P.Q + qk + i] = (double)x;
       else
-        P.out[gk] = ok_ + P.scale * x;
+        P.out[gk] = ok_ + P.scale * (double)x;
     }
     fence_proxy_async();
     __syncthreads();  // stage st and the work arrays fully consumed
@@ -704,6 +730,8 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
   unsigned char* wb = dyn + W.work_off + (size_t)c * W.warp_bytes;
   double* s_r = reinterpret_cast<double*>(wb);
   double* s_acc = s_r + P.s * nmax;
+  T* s_rm = reinterpret_cast<T*>(s_r);
+  T* s_accm = reinterpret_cast<T*>(s_acc);
   T* s_src = reinterpret_cast<T*>(s_acc + P.nt * nmax);
   const int nsrc = TR ? P.nt : P.ns;
   int32_t* s_g = reinterpret_cast<int32_t*>(s_src + (P.ns > P.nt ? P.ns : P.nt) * nmax);
@@ -744,15 +772,15 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
     __syncwarp();
     for (int idx = lane; idx < P.s * n; idx += 32) {
       const int t = idx / n, i = idx - t * n;
-      s_r[idx] = P.r[t * P.m + s_g[i]];
+      s_rm[idx] = (T)P.r[t * P.m + s_g[i]];
     }
     __syncwarp();
     for (int idx = lane; idx < nsrc * n; idx += 32) {
       const int cc = idx / n, i = idx - cc * n;
-      double a = 0.0;
+      T a = (T)0;
       for (int t = 0; t < P.s; ++t)
-        a += (TR ? P.H[t * kKronMaxTasks + cc] : P.G[cc * 3 + t]) * s_r[t * n + i];
-      s_src[idx] = (T)a;
+        a = fma(TR ? mix_h<T>(P, t * kKronMaxTasks + cc) : mix_g<T>(P, cc * 3 + t), s_rm[t * n + i], a);
+      s_src[idx] = a;
     }
     __syncwarp();
     // units (matrix b, row i); transposed: row i of Mᵀ is column i of M
@@ -771,8 +799,8 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
         a0 = fma(m, q0[j], a0);
         a1 = fma(m, q1[j], a1);
       }
-      s_acc[t0 * n + i] = (double)a0;
-      if (t1 >= 0) s_acc[t1 * n + i] = (double)a1;
+      s_accm[t0 * n + i] = a0;
+      if (t1 >= 0) s_accm[t1 * n + i] = a1;
     }
     fence_proxy_async();  // the stage's reads before the producer's next copy into it
     __syncwarp();
@@ -780,15 +808,15 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
     for (int idx = lane; idx < P.s * n; idx += 32) {
       const int t = idx / n, i = idx - t * n;
-      double x = 0.0;
+      T x = (T)0;
       for (int tau = 0; tau < P.nt; ++tau) {
-        const double h = TR ? P.G[P.task_src[tau] * 3 + t] : P.H[t * kKronMaxTasks + tau];
-        x += h * s_acc[tau * n + i];
+        const T h = TR ? mix_g<T>(P, P.task_src[tau] * 3 + t) : mix_h<T>(P, t * kKronMaxTasks + tau);
+        x = fma(h, s_accm[tau * n + i], x);
       }
       if (P.ybuf)
-        P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
+        P.ybuf[t * P.Q + P.qoff[pi] + i] = (double)x;
       else
-        P.out[t * P.m + s_g[i]] += P.scale * x;
+        P.out[t * P.m + s_g[i]] += P.scale * (double)x;
     }
     __syncwarp();
   }
@@ -980,8 +1008,8 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
   P.nt = K.nt;
   P.nm = K.nm;
   P.m = L.m;
-  for (int i = 0; i < kKronMaxSrc * 3; ++i) P.G[i] = K.G[i];
-  for (int i = 0; i < 3 * kKronMaxTasks; ++i) P.H[i] = K.H[i];
+  for (int i = 0; i < kKronMaxSrc * 3; ++i) P.G[i] = K.G[i], P.Gf[i] = (float)K.G[i];
+  for (int i = 0; i < 3 * kKronMaxTasks; ++i) P.H[i] = K.H[i], P.Hf[i] = (float)K.H[i];
   for (int i = 0; i < kKronMaxTasks; ++i) {
     P.task_mat[i] = K.task_mat[i];
     P.task_src[i] = K.task_src[i];

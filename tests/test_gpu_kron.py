@@ -228,3 +228,39 @@ def test_3d_decoupled_fp32_solve():
     vel = np.concatenate([np.arange(t * m, t * m + m - nv) for t in range(2)])
     assert rel(sols[1][0][vel], sols[0][0][vel]) < 1e-6
     assert sols[1][1] <= sols[0][1] + 2
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6],
+                         ids=["tma_staged", "warp_per_patch", "tma_staged_one_launch",
+                              "warp_one_launch", "warp_specialised", "warp_specialised_one_launch"])
+@pytest.mark.parametrize("form", [2, 3], ids=["complex", "three_product"])
+def test_fp32_decoupled_vanka_every_kernel(form, variant):
+    """FP32 decoupled patches (F1: patch inverses stored in FP32, the stage
+    mixing T⁻¹ r and T y and the block mat-vecs in FP32) with every apply
+    kernel forced on every level, J and Jᵀ patches, against the oracle's FP64
+    dense patch solves, entry by entry.  Each output sums at most 5 FP32
+    block products of 39 terms mixed through T (entries O(1)): a few hundred
+    units of FP32 roundoff (u = 6e-8) relative to the largest entry bound it;
+    the bar is 1e-6 of max |ref| plus the entry itself.  The interior patches
+    (39 DoFs per stage) take the paired-row kernel under variants 2 and 4 with
+    the complex layout."""
+    irkmg = need_gpu()
+    fam, s, dt = "radau_iia", 3, 1 / 64
+    n0, nl = 2, 4
+    H = _oracle(fam, s, dt, n0, nl)
+    ctx = _context(irkmg, fam, s, dt, n0, nl, form, precision=32, variant=variant)
+    try:
+        for l in range(1, nl):
+            assert ctx.levels[l]["apply_kernel"] == {1: 5, 2: 4, 3: 5, 4: 4, 5: 7, 6: 7}[variant]
+            L = H.levels[l]
+            r = synth.random_vector(640 + l, L.N)
+            ref_t = np.zeros(L.N)
+            for idx, f in zip(L.vanka.dofs, L.vanka.lu):
+                ref_t[idx] += sla.lu_solve(f, r[idx], trans=1)
+            for tr, ref in ((False, L.vanka.correction(r)), (True, ref_t)):
+                c = dev(np.zeros(L.N))
+                irkmg.irkmg_vanka_correction(ctx, dev(r), c, level=l, transpose=tr)
+                err = np.abs(host(c) - ref) / (np.abs(ref) + np.abs(ref).max())
+                assert err.max() < 1e-6, (l, tr, err.max())
+    finally:
+        ctx.close()
