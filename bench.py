@@ -60,17 +60,20 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # at capture time; reported as ratio x algorithmic bytes per launch, null once
 # the source has changed.  Captures: profiles/vanka_apply_128x128.md,
 # profiles/vanka_apply_kron_fp64_256x256.md,
-# profiles/vanka_apply_kron_fx_pair_128x128.md.
+# profiles/vanka_apply_kron_fx_pair_128x128.md,
+# profiles/vanka_apply_kron_pair32_256x256.md.
 NCU_TRAFFIC = {
     ("k_vanka_apply", "8f81809572f0"): 0.97,
     ("k_vanka_apply_kron", "60c2ce575b6a"): 1.02,
     ("k_vanka_apply_kron_fx_pair", "6850cc0d8407"): 1.096,
+    ("k_vanka_apply_kron_pair32", "8f68162f379b"): 1.110,
 }
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
                "k_vanka_apply_lu": "k_patch_big.cu", "k_vanka_apply_kron": "k_patch_kron.cu",
                "k_vanka_apply_kron_staged": "k_patch_kron.cu",
                "k_vanka_apply_kron_big": "k_patch_kron.cu",
                "k_vanka_apply_kron_ws": "k_patch_kron.cu",
+               "k_vanka_apply_kron_pair32": "k_patch_kron.cu",
                "k_vanka_apply_kron_fx": ("k_patch_fixed.cu", "fx_patch.cuh", "fx_math.h"),
                "k_vanka_apply_kron_fx_staged": ("k_patch_fixed.cu", "fx_patch.cuh", "fx_math.h"),
                "k_vanka_apply_kron_fx_pair": ("k_patch_fixed.cu", "fx_patch.cuh", "fx_math.h")}
@@ -887,6 +890,10 @@ def run_ours(args, wl, rank, world, local_rank):
                  6: "k_vanka_apply_kron_big", 7: "k_vanka_apply_kron_ws",
                  8: "k_vanka_apply_kron_fx", 9: "k_vanka_apply_kron_fx_staged",
                  10: "k_vanka_apply_kron_fx_pair"}[ctx.finest["apply_kernel"]]
+        if kname == "k_vanka_apply_kron" and prec == 32 and wl.get("dim", 2) == 2:
+            # the warp kernel's FP32 complex-layout launch on 39-DoF patches
+            # runs its paired-row form
+            kname = "k_vanka_apply_kron_pair32"
         h = kernel_source_hash(kname)
         ratio = NCU_TRAFFIC.get((kname, h))
         traffic = ratio * trace["vanka_bytes"] / nvl if ratio is not None else None

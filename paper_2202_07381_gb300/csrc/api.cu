@@ -82,7 +82,9 @@ struct HostSELL {
   std::vector<double> v[3];
 };
 
-HostSELL to_sell(const HostCSR& A, int nvals) {
+// skip_pad: padded entries get column −1 (the transfers stop there) instead
+// of the row's last column with a zero value.
+HostSELL to_sell(const HostCSR& A, int nvals, bool skip_pad = false) {
   HostSELL S;
   const int64_t n = A.nrows, ns = (n + 31) / 32;
   S.ptr.assign(ns + 1, 0);
@@ -105,15 +107,15 @@ HostSELL to_sell(const HostCSR& A, int nvals) {
         S.col[dst] = A.col[A.ptr[r] + k];
         for (int q = 0; q < nvals; ++q) S.v[q][dst] = A.v[q][A.ptr[r] + k];
       } else {
-        S.col[dst] = pad;
+        S.col[dst] = skip_pad ? -1 : pad;
       }
     }
   }
   return S;
 }
 
-int upload_sell(Ctx& C, DevSELL& d, const HostCSR& h, int nvals) {
-  HostSELL S = to_sell(h, nvals);
+int upload_sell(Ctx& C, DevSELL& d, const HostCSR& h, int nvals, bool skip_pad = false) {
+  HostSELL S = to_sell(h, nvals, skip_pad);
   d.nrows = (int32_t)h.nrows;
   d.stored = (int64_t)S.col.size();
   int rc;
@@ -1066,10 +1068,10 @@ int setup_impl(irkmg_ctx* C, const irkmg_mesh* mesh, const irkmg_tableau* tab, d
     if (l > 0) {
       HostCSR Pu, Pp;
       build_prolongation(C->L[l - 1].mesh, L.mesh, Pu, Pp);
-      if ((rc = upload_csr(*C, L.pu, Pu, 1))) return rc;
-      if ((rc = upload_csr(*C, L.put, transpose_csr(Pu, 1), 1))) return rc;
-      if ((rc = upload_csr(*C, L.pp, Pp, 1))) return rc;
-      if ((rc = upload_csr(*C, L.ppt, transpose_csr(Pp, 1), 1))) return rc;
+      if ((rc = upload_sell(*C, L.pu, Pu, 1, true))) return rc;
+      if ((rc = upload_sell(*C, L.put, transpose_csr(Pu, 1), 1, true))) return rc;
+      if ((rc = upload_sell(*C, L.pp, Pp, 1, true))) return rc;
+      if ((rc = upload_sell(*C, L.ppt, transpose_csr(Pp, 1), 1, true))) return rc;
       if ((rc = build_patches(*C, L))) return rc;
       level_trace_bytes(*C, L);
     }

@@ -150,8 +150,9 @@ struct Level {
   DevSELL svel, sb, sbt;  // SELL copies of vel, b and bt for the stage operator
   bool fxop_on = false;   // the exact fixed-point stage operator (op_fixed)
   FxOpLevel fxop;
-  // transfer from level-1 into this level (l > 0)
-  DevCSR pu, put, pp, ppt;
+  // transfer from level-1 into this level (l > 0), SELL-32 with col −1 after
+  // the end of a row
+  DevSELL pu, put, pp, ppt;
   // topology for patch construction
   int32_t *d_cells = nullptr, *d_cell_edges = nullptr, *d_vc_ptr = nullptr, *d_vc_idx = nullptr;
   int32_t *d_vv_ptr = nullptr, *d_vv_idx = nullptr, *d_p2_to_free = nullptr;

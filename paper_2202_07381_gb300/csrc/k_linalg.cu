@@ -97,28 +97,36 @@ cudaError_t launch_residual(Ctx& C, Level& L, const double* F, const double* x, 
 struct XferParams {
   int s, dim;
   int64_t nf_out, nv_out, m_out, nf_in, m_in;
-  const int32_t *uptr, *ucol;
+  int64_t nf_pad;  // velocity rows rounded up to whole slices
+  const int64_t* uptr;
+  const int32_t* ucol;
   const double* uw;
-  const int32_t *pptr, *pcol;
+  const int64_t* pptr;
+  const int32_t* pcol;
   const double* pw;
 };
 
-// One output row per thread: S stages × D velocity components (or S pressure
-// values) of that row, accumulated in registers in the CSR's entry order.
+// One output row per thread on SELL-32 copies of the transfer matrices (a
+// warp is one slice, so index and weight reads are coalesced; a row ends at
+// its first column −1): S stages × D velocity components (or S pressure
+// values) of that row, accumulated in registers in the row's entry order.
 template <int S, int D>
 __global__ void __launch_bounds__(256) k_transfer(XferParams P, const double* __restrict__ in,
                                                   double* __restrict__ out, int add) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row < P.nf_out) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < P.nf_pad) {
+    const int64_t row = tid;
+    if (row >= P.nf_out) return;
     double acc[S][D];
 #pragma unroll
     for (int t = 0; t < S; ++t)
 #pragma unroll
       for (int c = 0; c < D; ++c) acc[t][c] = 0.0;
-    const int32_t p1 = P.uptr[row + 1];
-    for (int32_t p = P.uptr[row]; p < p1; ++p) {
-      const int32_t j = P.ucol[p];
-      const double w = P.uw[p];
+    const int64_t sl = row >> 5, e1 = P.uptr[sl + 1];
+    for (int64_t e = P.uptr[sl] + (row & 31); e < e1; e += 32) {
+      const int32_t j = P.ucol[e];
+      if (j < 0) break;
+      const double w = P.uw[e];
 #pragma unroll
       for (int t = 0; t < S; ++t)
 #pragma unroll
@@ -132,15 +140,16 @@ __global__ void __launch_bounds__(256) k_transfer(XferParams P, const double* __
         const int64_t g = t * P.m_out + c * P.nf_out + row;
         out[g] = add ? out[g] + acc[t][c] : acc[t][c];
       }
-  } else if (row < P.nf_out + P.nv_out) {
-    const int64_t v = row - P.nf_out;
+  } else if (tid < P.nf_pad + P.nv_out) {
+    const int64_t v = tid - P.nf_pad;
     double acc[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) acc[t] = 0.0;
-    const int32_t p1 = P.pptr[v + 1];
-    for (int32_t p = P.pptr[v]; p < p1; ++p) {
-      const int32_t j = P.pcol[p];
-      const double w = P.pw[p];
+    const int64_t sl = v >> 5, e1 = P.pptr[sl + 1];
+    for (int64_t e = P.pptr[sl] + (v & 31); e < e1; e += 32) {
+      const int32_t j = P.pcol[e];
+      if (j < 0) break;
+      const double w = P.pw[e];
 #pragma unroll
       for (int t = 0; t < S; ++t) acc[t] = fma(w, in[t * P.m_in + D * P.nf_in + j], acc[t]);
     }
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(256) k_transfer(XferParams P, const double* __
 
 cudaError_t launch_transfer(const XferParams& P, const double* in, double* out, int add,
                             cudaStream_t st) {
-  const int64_t rows = P.nf_out + P.nv_out;
+  const int64_t rows = P.nf_pad + P.nv_out;
   const unsigned grid = (unsigned)((rows + 255) / 256);
 #define XFER_CASE(S_, D_)                                                   \
   if (P.s == S_ && P.dim == D_) {                                         \
@@ -173,6 +182,7 @@ cudaError_t launch_restrict(Ctx& C, Level& Lf, const double* fine, double* coars
   P.dim = Lf.dim;
   P.nf_out = Lc.nf;
   P.nv_out = Lc.nv;
+  P.nf_pad = (P.nf_out + 31) / 32 * 32;
   P.m_out = Lc.m;
   P.nf_in = Lf.nf;
   P.m_in = Lf.m;
@@ -192,6 +202,7 @@ cudaError_t launch_prolong(Ctx& C, Level& Lf, const double* coarse, double* fine
   P.dim = Lf.dim;
   P.nf_out = Lf.nf;
   P.nv_out = Lf.nv;
+  P.nf_pad = (P.nf_out + 31) / 32 * 32;
   P.m_out = Lf.m;
   P.nf_in = Lc.nf;
   P.m_in = Lc.m;
