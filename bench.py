@@ -966,8 +966,9 @@ def run_ours(args, wl, rank, world, local_rank):
                                    "avg_launch_ms": trace["xfer_ms"] / max(trace["xfer_launches"], 1),
                                    "bytes": "vector bytes only (weights closed-form)"},
             "roofline_arnoldi": {"bound": "hbm",
-                                 "kernel": "k_multidot_part + k_multidot_final + k_multiaxpy "
-                                           "(classical Gram-Schmidt twice, finest level)",
+                                 "kernel": "k_multidot_part + k_multiaxpy_dot + k_multidot_final "
+                                           "(classical Gram-Schmidt twice, each update fused "
+                                           "with the next reduction, finest level)",
                                  "achieved": arn_gbs, "peak": hbm, "unit": "GB/s",
                                  "frac": arn_gbs / hbm if arn_gbs else None,
                                  "steps": trace["arnoldi_steps"],

@@ -489,7 +489,8 @@ int factor_all(Ctx& C) {
   return check_err(C, "factorisation");
 }
 
-int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr);
+int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr,
+              const ChebFuse* fuse = nullptr);
 
 // Choose the Vanka apply kernel of every level: the option forces one, or
 // (apply_variant 0) both are timed on one sweep of the level (after a warm-up
@@ -654,7 +655,10 @@ int tune_apply(Ctx& C) {
 }
 
 // --- smoothers and V-cycle -------------------------------------------------
-int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr) {
+// fuse (one-launch levels only, L.kron && L.single): the Chebyshev update
+// carried out by the per-DoF sum (ChebFuse).
+int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int tr,
+              const ChebFuse* fuse) {
   if (L.big && tr)
     return fail(IRKMG_ENOTIMPL, "transposed patch solves of LU-factored (3D) patches");
   const bool timed = C.trace_on && &L == &C.L.back();
@@ -677,15 +681,19 @@ int vanka_all(Ctx& C, Level& L, const double* r, double* out, double scale, int 
     C.launches++;
     if (timed) {
       CK(cudaEventRecord(b, C.stream));
-      int rc = trace_pair(C, 2, L.reduce_bytes, &c2, &d2, 0.0);
+      // fused: x read (added) and written, d not read when zeroed
+      const double xb = fuse ? 8.0 * (double)L.N * ((fuse->xadd ? 2.0 : 1.0) - (fuse->dzero ? 1.0 : 0.0))
+                             : 0.0;
+      int rc = trace_pair(C, 2, L.reduce_bytes + xb, &c2, &d2, 0.0);
       if (rc) return rc;
       CK(cudaEventRecord(c2, C.stream));
     }
-    CK(launch_vanka_reduce(C, L, out, scale));
+    CK(launch_vanka_reduce(C, L, out, scale, fuse));
     C.launches++;
     if (timed) CK(cudaEventRecord(d2, C.stream));
     return IRKMG_OK;
   }
+  if (fuse) return fail(IRKMG_EINVAL, "fused Chebyshev step on a per-colour level");
   for (int c = 0; c < L.ncolours; ++c) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (timed) {
@@ -736,6 +744,20 @@ int smooth(Ctx& C, Level& L, const double* b, double* x, int nsteps, bool zero_i
   if (!zero_init) {
     { int rc_ = op(C, L, b, x, L.t, tr); if (rc_) return rc_; }
     res = L.t;
+  }
+  if (L.kron && L.single) {
+    // one-launch levels: the per-DoF sum also scales d and updates x (the
+    // same roundings as the fill / axpby launches below)
+    ChebFuse f{0.0, true, !zero_init, x};
+    if ((rc = vanka_all(C, L, res, L.d, 1.0 / theta, tr, &f))) return rc;
+    for (int k = 1; k < nsteps; ++k) {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      { int rc_ = op(C, L, b, x, L.t, tr); if (rc_) return rc_; }
+      ChebFuse g{rho_new * rho, false, true, x};
+      if ((rc = vanka_all(C, L, L.t, L.d, 2.0 * rho_new / delta, tr, &g))) return rc;
+      rho = rho_new;
+    }
+    return IRKMG_OK;
   }
   CK(launch_fill(L.d, 0.0, L.N, C.stream));
   C.launches++;
@@ -859,20 +881,22 @@ int fgmres(Ctx& C, const double* F, double* x, irkmg_stats* st, int tr) {
       // classical Gram–Schmidt, twice
       cudaEvent_t ga = nullptr, gb = nullptr;
       if (C.trace_on) {
-        // per pass: the j + 1 basis vectors and w read by the dot products,
-        // read again with w read and written by the update; then ||w||²
+        // k = j + 1 basis vectors: the dot products read V and w; each update
+        // reads V and w and writes w, fused with the next dot products (or
+        // ||w||²) when k <= 16; otherwise every update and reduction reads
+        // its vectors again
         const double k1 = (double)(j + 1), nb = 8.0 * (double)n;
-        if ((rc = trace_pair(C, 4, 2.0 * (nb * (k1 + 1.0) + nb * (k1 + 2.0)) + nb, &ga, &gb)))
-          return rc;
+        const double bytes = j + 1 <= 16 ? nb * (3.0 * k1 + 5.0)
+                                         : 2.0 * (nb * (k1 + 1.0) + nb * (k1 + 2.0)) + nb;
+        if ((rc = trace_pair(C, 4, bytes, &ga, &gb))) return rc;
         CK(cudaEventRecord(ga, C.stream));
       }
       CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd, C.stream));
-      CK(launch_multiaxpy(w, V, n, j + 1, hd, -1.0, n, C.stream));
-      CK(launch_multidot(V, n, j + 1, w, n, C.d_part, hd + 64, C.stream));
-      CK(launch_multiaxpy(w, V, n, j + 1, hd + 64, -1.0, n, C.stream));
-      CK(launch_multidot(w, 0, 1, w, n, C.d_part, hd + 128, C.stream));
+      CK(launch_multiaxpy_dot(w, V, n, j + 1, hd, -1.0, n, C.d_part, hd + 64, false, C.stream));
+      CK(launch_multiaxpy_dot(w, V, n, j + 1, hd + 64, -1.0, n, C.d_part, hd + 128, true,
+                              C.stream));
       if (C.trace_on) CK(cudaEventRecord(gb, C.stream));
-      C.launches += 10;
+      C.launches += j + 1 <= 16 ? 6 : 10;
       CK(cudaMemcpyAsync(hh, hd, sizeof(double) * 129, cudaMemcpyDeviceToHost, C.stream));
       CK(cudaMemcpyAsync(C.h_err, C.d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, C.stream));
       CK(cudaStreamSynchronize(C.stream));
@@ -1642,11 +1666,11 @@ int batch_fgmres(std::vector<FState>& S, BatchLink* K) {
       CK(launch_pressure_mean_remove(C, L, zj));
       if ((rc = op(C, L, nullptr, zj, C.d_w, 0))) return rc;
       CK(launch_multidot(C.d_V, n, f.j + 1, C.d_w, n, C.d_part, C.d_h, C.stream));
-      CK(launch_multiaxpy(C.d_w, C.d_V, n, f.j + 1, C.d_h, -1.0, n, C.stream));
-      CK(launch_multidot(C.d_V, n, f.j + 1, C.d_w, n, C.d_part, C.d_h + 64, C.stream));
-      CK(launch_multiaxpy(C.d_w, C.d_V, n, f.j + 1, C.d_h + 64, -1.0, n, C.stream));
-      CK(launch_multidot(C.d_w, 0, 1, C.d_w, n, C.d_part, C.d_h + 128, C.stream));
-      C.launches += 11;
+      CK(launch_multiaxpy_dot(C.d_w, C.d_V, n, f.j + 1, C.d_h, -1.0, n, C.d_part, C.d_h + 64,
+                              false, C.stream));
+      CK(launch_multiaxpy_dot(C.d_w, C.d_V, n, f.j + 1, C.d_h + 64, -1.0, n, C.d_part,
+                              C.d_h + 128, true, C.stream));
+      C.launches += f.j + 1 <= 16 ? 7 : 11;
       CK(cudaMemcpyAsync(C.h_h, C.d_h, sizeof(double) * 129, cudaMemcpyDeviceToHost, C.stream));
       CK(cudaMemcpyAsync(C.h_err, C.d_err, sizeof(int) * 2, cudaMemcpyDeviceToHost, C.stream));
     }

@@ -273,7 +273,17 @@ cudaError_t launch_patch_invert_kron(Ctx& C, Level& L);
 cudaError_t launch_patch_gidx_kron(Ctx& C, Level& L);
 cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, double* out,
                               double scale, int transpose);  // colour -1: all patches to d_Y
-cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale);
+// A Chebyshev step fused into the per-DoF sum (one-launch relaxation): with
+// c the summed patch corrections, d ← (dzero ? 0 : c1·d) + scale·c and then
+// x ← d (xadd false) or x ← x + d, each operation rounded as the separate
+// axpby / sum / axpby launches round it.
+struct ChebFuse {
+  double c1;
+  bool dzero, xadd;
+  double* x;
+};
+cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale,
+                                const ChebFuse* f = nullptr);
 int kron_max_slots();
 bool fixed_fits(Ctx& C, Level& L);
 int fixed_shapes();  // launch shapes of the fixed-point apply (Level::kron_shape):
@@ -302,7 +312,12 @@ cudaError_t launch_fill_sin(double* y, int64_t n, cudaStream_t st);  // y_i = si
 cudaError_t launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                             double* part, double* out, cudaStream_t st);
 cudaError_t launch_multiaxpy(double* w, const double* V, int64_t ldv, int k, const double* h,
-                             double sign, int64_t n, cudaStream_t st);  // w += sign * V h
+                             double sign, int64_t n, cudaStream_t st);
+// w += sign·V h fused with the next reduction (Vᵀ w into out[0..k), or
+// ‖w‖² into out[0] when norm): bitwise launch_multiaxpy then launch_multidot.
+cudaError_t launch_multiaxpy_dot(double* w, const double* V, int64_t ldv, int k, const double* h,
+                                 double sign, int64_t n, double* part, double* out, bool norm,
+                                 cudaStream_t st);  // w += sign * V h
 cudaError_t launch_pressure_mean_remove(Ctx& C, Level& L, double* x);
 cudaError_t launch_stage_rhs(Ctx& C, const double* un, const double* pn, const double* f,
                              double* F);

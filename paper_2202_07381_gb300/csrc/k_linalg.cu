@@ -261,6 +261,10 @@ cudaError_t launch_fill_sin(double* y, int64_t n, cudaStream_t st) {
 // part[b*k + j] = partial sum over block b's contiguous chunk of V_j . w
 // Eight columns per pass over the block's chunk (each column's sum over the
 // elements in the same order as one column at a time, and the same tree).
+// Partial dot products of w with k columns of V over fixed contiguous chunks
+// (one chunk per block, a fixed tree per block), KMAX columns per pass over
+// the chunk (w is read once per pass).
+template <int KMAX>
 __global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict__ V, int64_t ldv,
                                                        int k, const double* __restrict__ w,
                                                        int64_t n, double* __restrict__ part) {
@@ -268,42 +272,64 @@ __global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict_
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(n, b0 + chunk);
-  for (int j0 = 0; j0 < k; j0 += 8) {
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int nj = min(8, k - j0);
+  for (int p0 = 0; p0 < k; p0 += KMAX) {
+    const int nj = min(KMAX, k - p0);
+    const double* Vp = V + (int64_t)p0 * ldv;
+    double acc[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) acc[q] = 0.0;
     for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
       const double wi = w[i];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < nj) acc[q] = fma(V[(int64_t)(j0 + q) * ldv + i], wi, acc[q]);
+      for (int q = 0; q < KMAX; ++q)
+        if (q < nj) acc[q] = fma(Vp[(int64_t)q * ldv + i], wi, acc[q]);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = acc[q];
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < (unsigned)o)
+    for (int j0 = 0; j0 < KMAX; j0 += 8) {
+      if (j0 < nj) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
-      __syncthreads();
+        for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = acc[j0 + q];
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+          if (threadIdx.x < (unsigned)o)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+          __syncthreads();
+        }
+        if (threadIdx.x < 8 && j0 + (int)threadIdx.x < nj)
+          part[(int64_t)blockIdx.x * k + p0 + j0 + threadIdx.x] = red[threadIdx.x][0];
+        __syncthreads();
+      }
     }
-    if (threadIdx.x < (unsigned)nj) part[(int64_t)blockIdx.x * k + j0 + threadIdx.x] = red[threadIdx.x][0];
-    __syncthreads();
   }
 }
 
-__global__ void k_multidot_final(const double* __restrict__ part, int nblocks, int k,
-                                 double* __restrict__ out) {
-  const int j = threadIdx.x;
-  if (j >= k) return;
+// The sums of the partials, column j in block j: a fixed tree over the blocks'
+// partials (strided per thread, then halved), the same order on every call.
+__global__ void __launch_bounds__(256) k_multidot_final(const double* __restrict__ part,
+                                                        int nblocks, int k,
+                                                        double* __restrict__ out) {
+  __shared__ double red[256];
+  const int j = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * k + j];
-  out[j] = s;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[(int64_t)b * k + j];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < (unsigned)o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = red[0];
 }
 
 cudaError_t launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                             double* part, double* out, cudaStream_t st) {
-  k_multidot_part<<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
-  k_multidot_final<<<1, 64, 0, st>>>(part, kMultidotBlocks, k, out);
+  if (k < 1 || k > 64) return cudaErrorInvalidValue;
+  if (k <= 8)
+    k_multidot_part<8><<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
+  else
+    k_multidot_part<16><<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
+  k_multidot_final<<<k, 256, 0, st>>>(part, kMultidotBlocks, k, out);
   return cudaGetLastError();
 }
 
@@ -329,6 +355,93 @@ __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V
 cudaError_t launch_multiaxpy(double* w, const double* V, int64_t ldv, int k, const double* h,
                              double sign, int64_t n, cudaStream_t st) {
   k_multiaxpy<<<grid_for(n), 256, 0, st>>>(w, V, ldv, k, h, sign, n);
+  return cudaGetLastError();
+}
+
+// One classical Gram–Schmidt update fused with the next reduction: w ←
+// w + sign·V h (k_multiaxpy's FMA order), then the partial dot products of
+// the updated w with the k columns of V (NORM: with itself) over
+// k_multidot_part's chunks, in its per-thread order and block tree.  The
+// results are bitwise those of k_multiaxpy followed by launch_multidot; V and
+// w are read once instead of twice.
+template <int KMAX, bool NORM>
+__global__ void __launch_bounds__(256, 2) k_multiaxpy_dot(double* __restrict__ w,
+                                                       const double* __restrict__ V, int64_t ldv,
+                                                       int k, const double* __restrict__ h,
+                                                       double sign, int64_t n,
+                                                       double* __restrict__ part) {
+  constexpr int ND = NORM ? 1 : KMAX;
+  __shared__ double red[8][256];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = min(n, b0 + chunk);
+  __shared__ double s_h[KMAX];
+  if (threadIdx.x < KMAX) s_h[threadIdx.x] = (int)threadIdx.x < k ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  double d[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) d[q] = 0.0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    double v[KMAX];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < k) v[q] = V[(int64_t)q * ldv + i];
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < k) acc = fma(s_h[q], v[q], acc);
+    const double wn = fma(sign, acc, w[i]);
+    w[i] = wn;
+    if (NORM) {
+      d[0] = fma(wn, wn, d[0]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < ND; ++q)
+        if (q < k) d[q] = fma(v[q], wn, d[q]);
+    }
+  }
+  const int kk = NORM ? 1 : k;
+#pragma unroll
+  for (int j0 = 0; j0 < ND; j0 += 8) {
+    if (j0 < kk) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = j0 + q < ND ? d[j0 + q] : 0.0;
+      __syncthreads();
+      for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+        __syncthreads();
+      }
+      if (threadIdx.x < 8 && j0 + (int)threadIdx.x < kk)
+        part[(int64_t)blockIdx.x * kk + j0 + threadIdx.x] = red[threadIdx.x][0];
+      __syncthreads();
+    }
+  }
+}
+
+cudaError_t launch_multiaxpy_dot(double* w, const double* V, int64_t ldv, int k, const double* h,
+                                 double sign, int64_t n, double* part, double* out, bool norm,
+                                 cudaStream_t st) {
+  if (k < 1 || k > 16) {  // more columns than registers: the two launches
+    cudaError_t e = launch_multiaxpy(w, V, ldv, k, h, sign, n, st);
+    if (e != cudaSuccess) return e;
+    return norm ? launch_multidot(w, 0, 1, w, n, part, out, st)
+                : launch_multidot(V, ldv, k, w, n, part, out, st);
+  }
+  const int kk = norm ? 1 : k;
+  if (norm) {
+    if (k <= 8)
+      k_multiaxpy_dot<8, true><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+    else
+      k_multiaxpy_dot<16, true><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+  } else {
+    if (k <= 8)
+      k_multiaxpy_dot<8, false><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+    else
+      k_multiaxpy_dot<16, false><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+  }
+  k_multidot_final<<<kk, 256, 0, st>>>(part, kMultidotBlocks, kk, out);
   return cudaGetLastError();
 }
 

@@ -1129,12 +1129,12 @@ namespace irkmg {
 // DoF are loaded eight at a time and their S·8 results issued together; each
 // stage's sum still runs over the contributions in order (bitwise the sum of
 // the batched smoother) and is added to out with one rounding.
-template <int S>
+template <int S, bool CHEB>
 __global__ void __launch_bounds__(256) k_vanka_reduce(int64_t m, int64_t Q,
                                                       const int32_t* __restrict__ cptr,
                                                       const int32_t* __restrict__ cidx,
                                                       const double* __restrict__ y, double scale,
-                                                      double* __restrict__ out) {
+                                                      double* __restrict__ out, ChebFuse F) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= m) return;
   const int32_t e0 = cptr[d], e1 = cptr[d + 1];
@@ -1157,17 +1157,37 @@ __global__ void __launch_bounds__(256) k_vanka_reduce(int64_t m, int64_t Q,
         for (int t = 0; t < S; ++t) a[t] += v[k][t];
   }
 #pragma unroll
-  for (int t = 0; t < S; ++t) out[t * m + d] = __fma_rn(scale, a[t], out[t * m + d]);
+  for (int t = 0; t < S; ++t) {
+    const int64_t g = t * m + d;
+    if (!CHEB) {
+      out[g] = __fma_rn(scale, a[t], out[g]);
+    } else {
+      const double d2 = __fma_rn(scale, a[t], F.dzero ? 0.0 : __dmul_rn(F.c1, out[g]));
+      out[g] = d2;
+      F.x[g] = F.xadd ? __dadd_rn(d2, F.x[g]) : d2;
+    }
+  }
 }
 
-cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale) {
+cudaError_t launch_vanka_reduce(Ctx& C, Level& L, double* out, double scale, const ChebFuse* f) {
   const unsigned grid = (unsigned)((L.m + 255) / 256);
+  const ChebFuse F = f ? *f : ChebFuse{1.0, false, false, nullptr};
+#define REDUCE_CASE(S_)                                                                     \
+  case S_:                                                                                  \
+    if (f)                                                                                  \
+      k_vanka_reduce<S_, true><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx,    \
+                                                           C.d_Y, scale, out, F);           \
+    else                                                                                    \
+      k_vanka_reduce<S_, false><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx,   \
+                                                            C.d_Y, scale, out, F);          \
+    break;
   switch (C.s) {
-    case 1: k_vanka_reduce<1><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx, C.d_Y, scale, out); break;
-    case 2: k_vanka_reduce<2><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx, C.d_Y, scale, out); break;
-    case 3: k_vanka_reduce<3><<<grid, 256, 0, C.stream>>>(L.m, L.Q, L.d_cptr, L.d_cidx, C.d_Y, scale, out); break;
+    REDUCE_CASE(1)
+    REDUCE_CASE(2)
+    REDUCE_CASE(3)
     default: return cudaErrorInvalidValue;
   }
+#undef REDUCE_CASE
   return cudaGetLastError();
 }
 
