@@ -883,6 +883,8 @@ def run_ours(args, wl, rank, world, local_rank):
                     if trace["xfer_ms"] else None)
         arn_gbs = (trace["arnoldi_bytes"] / (trace["arnoldi_ms"] * 1e-3) / 1e9
                    if trace["arnoldi_ms"] else None)
+        red_gbs = (trace["reduce_bytes"] / (trace["reduce_ms"] * 1e-3) / 1e9
+                   if trace["reduce_ms"] else None)
         nvl = max(trace["vanka_launches"], 1)
         kname = {1: "k_vanka_apply_staged", 2: "k_vanka_apply",
                  3: "k_vanka_apply_lu", 4: "k_vanka_apply_kron",
@@ -974,6 +976,17 @@ def run_ours(args, wl, rank, world, local_rank):
                                  "steps": trace["arnoldi_steps"],
                                  "avg_step_ms": trace["arnoldi_ms"] / max(trace["arnoldi_steps"], 1),
                                  "bytes_per_step": trace["arnoldi_bytes"] / max(trace["arnoldi_steps"], 1)},
+            "roofline_reduce": {"bound": "hbm",
+                                "kernel": "k_vanka_reduce (per-DoF sum of the one-launch patch "
+                                          "results with the Chebyshev update, finest level)",
+                                "achieved": red_gbs, "peak": hbm, "unit": "GB/s",
+                                "frac": red_gbs / hbm if red_gbs else None,
+                                "launches": trace["reduce_launches"],
+                                "bytes_per_launch": trace["reduce_bytes"] / max(trace["reduce_launches"], 1),
+                                "avg_launch_ms": trace["reduce_ms"] / max(trace["reduce_launches"], 1),
+                                "bytes": "s (8 Q + 16 m) + 4 Q + 4 m (results, contribution "
+                                         "indices and pointers, direction read and written) "
+                                         "+ the iterate read and written"},
             "roofline_factor": factor,
             "traced_step": "figures from one separate traced step after the timed region",
             "gpu_launches": launches,

@@ -373,16 +373,25 @@ int build_patches(Ctx& C, Level& L) {
   else
     CK(launch_patch_gidx(C, L));
   if (L.kron) {
-    // one-launch relaxation: offsets of the ordered patches' results and, per
-    // spatial DoF d, its entries qoff[p] + i in ordered-patch order
+    // one-launch relaxation: the results of the patch of vertex v at
+    // i·ystride + v (local row i), and, per spatial DoF d, its entries in
+    // ordered-patch (colour) order.  The per-DoF sum then reads the results
+    // of neighbouring vertices from adjacent addresses, and the launch takes
+    // the patches in vertex order, so that the writes of one 32-byte sector
+    // come from neighbouring warps at about the same time.
+    const int64_t ys = (L.nv + 31) / 32 * 32;
     std::vector<int64_t> qoff(L.nv);
-    int64_t Q = 0;
+    std::vector<int32_t> perm(L.nv);
+    int64_t Qent = 0, nloc = 0;
     for (int64_t p = 0; p < L.nv; ++p) {
-      qoff[p] = Q;
-      Q += npv[p];
+      qoff[p] = order[p];
+      perm[order[p]] = (int32_t)p;
+      Qent += npv[p];
+      nloc = std::max<int64_t>(nloc, npv[p]);
     }
+    const int64_t Q = nloc * ys;
     if (Q > INT32_MAX) return fail(IRKMG_ENOTIMPL, "patch results exceed 2^31 entries");
-    std::vector<int32_t> cptr(L.m + 1, 0), cidx(Q);
+    std::vector<int32_t> cptr(L.m + 1, 0), cidx(Qent);
     auto dof = [&](int32_t v, int64_t i) -> int64_t {
       const int32_t nb = L.h_patch_ptr[v], nl = L.h_patch_ptr[v + 1] - nb;
       if (i < (int64_t)L.dim * nl) {
@@ -396,13 +405,17 @@ int build_patches(Ctx& C, Level& L) {
     for (int64_t d = 0; d < L.m; ++d) cptr[d + 1] += cptr[d];
     std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
     for (int64_t p = 0; p < L.nv; ++p)
-      for (int64_t i = 0; i < npv[p]; ++i) cidx[fill[dof(order[p], i)]++] = (int32_t)(qoff[p] + i);
+      for (int64_t i = 0; i < npv[p]; ++i)
+        cidx[fill[dof(order[p], i)]++] = (int32_t)(i * ys + qoff[p]);
     if ((rc = upload(C, &L.d_qoff, qoff))) return rc;
+    if ((rc = upload(C, &L.d_perm, perm))) return rc;
     if ((rc = upload(C, &L.d_cptr, cptr))) return rc;
     if ((rc = upload(C, &L.d_cidx, cidx))) return rc;
     L.Q = Q;
+    L.Qent = Qent;
+    L.ystride = ys;
     // the reduction reads every result and its index once, and out per DoF
-    L.reduce_bytes = (double)C.s * (8.0 * Q + 16.0 * L.m) + 4.0 * Q + 4.0 * L.m;
+    L.reduce_bytes = (double)C.s * (8.0 * Qent + 16.0 * L.m) + 4.0 * Qent + 4.0 * L.m;
   }
   return IRKMG_OK;
 }

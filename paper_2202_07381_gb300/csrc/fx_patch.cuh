@@ -38,7 +38,14 @@ struct FxApply {
   double* ybuf;  // one-launch mode (see KronApply)
   const int64_t* qoff;
   int64_t Q;
+  int64_t ys;
+  const int32_t* perm;
 };
+
+// Ordered patch index of the k-th patch a launch takes.
+__device__ __forceinline__ int64_t fx_pi(const FxApply& P, int64_t k) {
+  return P.perm ? (int64_t)P.perm[P.first + k] : P.first + k;
+}
 
 // Shared memory of one warp: limbs (nsrc·(nmax + kFxPad) × 8 B), residuals
 // (s·nmax doubles), sources and then task results (max(nsrc, nt)·nmax
@@ -229,7 +236,7 @@ __device__ __forceinline__ void fx_patch(const FxApply& P, const int2* __restric
       x += h * s_x[tau * n + i];
     }
     if (P.ybuf)
-      P.ybuf[t * P.Q + P.qoff[pi] + i] = x;
+      P.ybuf[t * P.Q + P.qoff[pi] + i * P.ys] = x;
     else
       P.out[t * P.m + s_g[i]] += P.scale * x;
   }
@@ -453,7 +460,7 @@ __device__ __forceinline__ void fx_patch_pair(const FxApply& P, const int2* __re
 #pragma unroll
       for (int tau = 0; tau < NT; ++tau) x += P.H[t * kKronMaxTasks + tau] * sm.x[tau * N + i];
       if (P.ybuf)
-        P.ybuf[t * P.Q + qo + i] = x;
+        P.ybuf[t * P.Q + qo + i * P.ys] = x;
       else
         P.out[t * P.m + sm.g[i]] += P.scale * x;
     }

@@ -184,11 +184,18 @@ struct Level {
   int kron_shape = 0;                  // launch shape of the staged decoupled apply (0, 1)
   double cheb_lo = 2.0, cheb_hi = 8.0; // Chebyshev interval of this level's smoother
   // one-launch relaxation of a decoupled level: patch results to Ctx::d_Y at
-  // t·Q + qoff[p] + i, then the per-DoF sum over the contribution lists
+  // t·Q + qoff[p] + i·ystride, then the per-DoF sum over the contribution
+  // lists.  Row-major over (local row i, patch vertex v): qoff[p] = v and
+  // ystride = the vertex count rounded up to 32, so that consecutive
+  // vertices' results for one local row are adjacent; the launch takes the
+  // patches in vertex order (d_perm: ordered index of vertex v's patch).
   bool single = false;
-  int64_t Q = 0;                       // Σ n over the patches
-  int64_t* d_qoff = nullptr;           // per ordered patch
-  int32_t *d_cptr = nullptr, *d_cidx = nullptr;  // spatial DoF -> entries qoff[p] + i
+  int64_t Q = 0;                       // stage stride of d_Y: n_max · ystride
+  int64_t Qent = 0;                    // Σ n over the patches
+  int64_t ystride = 1;
+  int64_t* d_qoff = nullptr;           // per ordered patch: its vertex
+  int32_t* d_perm = nullptr;           // per vertex: ordered index of its patch
+  int32_t *d_cptr = nullptr, *d_cidx = nullptr;  // spatial DoF -> entries qoff[p] + i·ystride
   double reduce_bytes = 0.0;           // algorithmic bytes of one reduction launch
   double factor_flops = 0.0;           // explicit inverses of the patch blocks: 2 m³ per block
   int kron_cap[2][2] = {{0, 0}, {0, 0}};  // its resident CTAs per [shape][transpose] (0 unset)

@@ -178,8 +178,9 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_smooth(BatchLaunch R
       const int i = find_unit(R.patch_pref, n, u);
       const BatchSys& B = sys[R.sys[i]];
       stage_params(&s_fx, &B.fx, &s_have_fx, R.sys[i]);
-      const int64_t pi = (u - R.patch_pref[i]) * kFxWarps + warp;
-      if (pi < B.npatch) {
+      const int64_t k = (u - R.patch_pref[i]) * kFxWarps + warp;
+      if (k < B.npatch) {
+        const int64_t pi = fx_pi(s_fx, k);  // vertex order, as the one-launch apply
         const int np = s_fx.np[pi];
         if (S >= 2 && R.pair && np == kFxN2)  // complex layout: paired rows
           fx_patch_pair<8, S == 3, true>(s_fx, B.fac, base, lane, pi);

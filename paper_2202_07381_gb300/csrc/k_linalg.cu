@@ -259,44 +259,63 @@ cudaError_t launch_fill_sin(double* y, int64_t n, cudaStream_t st) {
 }
 
 // part[b*k + j] = partial sum over block b's contiguous chunk of V_j . w
-// Eight columns per pass over the block's chunk (each column's sum over the
-// elements in the same order as one column at a time, and the same tree).
 // Partial dot products of w with k columns of V over fixed contiguous chunks
 // (one chunk per block, a fixed tree per block), KMAX columns per pass over
-// the chunk (w is read once per pass).
-template <int KMAX>
-__global__ void __launch_bounds__(256) k_multidot_part(const double* __restrict__ V, int64_t ldv,
-                                                       int k, const double* __restrict__ w,
-                                                       int64_t n, double* __restrict__ part) {
+// the chunk (w is read once per pass).  Each thread's elements i, i + 256,
+// ... are taken U at a time: all their loads are issued before the
+// multiply-adds, which then run in ascending i, so every column's sum has the
+// order of one element at a time.
+template <int KMAX, int U>
+__global__ void __launch_bounds__(256, 2) k_multidot_part(const double* __restrict__ V, int64_t ldv,
+                                                          int k, const double* __restrict__ w,
+                                                          int64_t n, double* __restrict__ part) {
   __shared__ double red[8][256];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(n, b0 + chunk);
+  const int64_t st = blockDim.x;
   for (int p0 = 0; p0 < k; p0 += KMAX) {
     const int nj = min(KMAX, k - p0);
     const double* Vp = V + (int64_t)p0 * ldv;
     double acc[KMAX];
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) acc[q] = 0.0;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    int64_t i = b0 + threadIdx.x;
+    for (; i + (U - 1) * st < b1; i += U * st) {
+      double wv[U], vv[U][KMAX];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        wv[u] = w[i + u * st];
+#pragma unroll
+        for (int q = 0; q < KMAX; ++q)
+          if (q < nj) vv[u][q] = Vp[(int64_t)q * ldv + i + u * st];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < KMAX; ++q)
+          if (q < nj) acc[q] = fma(vv[u][q], wv[u], acc[q]);
+    }
+    for (; i < b1; i += st) {
       const double wi = w[i];
 #pragma unroll
       for (int q = 0; q < KMAX; ++q)
         if (q < nj) acc[q] = fma(Vp[(int64_t)q * ldv + i], wi, acc[q]);
     }
+    constexpr int QN = KMAX < 8 ? KMAX : 8;  // columns per block tree
 #pragma unroll
-    for (int j0 = 0; j0 < KMAX; j0 += 8) {
+    for (int j0 = 0; j0 < KMAX; j0 += QN) {
       if (j0 < nj) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = acc[j0 + q];
+        for (int q = 0; q < QN; ++q) red[q][threadIdx.x] = acc[j0 + q];
         __syncthreads();
         for (int o = 128; o > 0; o >>= 1) {
           if (threadIdx.x < (unsigned)o)
 #pragma unroll
-            for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+            for (int q = 0; q < QN; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
           __syncthreads();
         }
-        if (threadIdx.x < 8 && j0 + (int)threadIdx.x < nj)
+        if (threadIdx.x < QN && j0 + (int)threadIdx.x < nj)
           part[(int64_t)blockIdx.x * k + p0 + j0 + threadIdx.x] = red[threadIdx.x][0];
         __syncthreads();
       }
@@ -325,10 +344,12 @@ __global__ void __launch_bounds__(256) k_multidot_final(const double* __restrict
 cudaError_t launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t n,
                             double* part, double* out, cudaStream_t st) {
   if (k < 1 || k > 64) return cudaErrorInvalidValue;
-  if (k <= 8)
-    k_multidot_part<8><<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
+  if (k <= 4)
+    k_multidot_part<4, 4><<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
+  else if (k <= 8)
+    k_multidot_part<8, 2><<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
   else
-    k_multidot_part<16><<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
+    k_multidot_part<16, 1><<<kMultidotBlocks, 256, 0, st>>>(V, ldv, k, w, n, part);
   k_multidot_final<<<k, 256, 0, st>>>(part, kMultidotBlocks, k, out);
   return cudaGetLastError();
 }
@@ -364,7 +385,7 @@ cudaError_t launch_multiaxpy(double* w, const double* V, int64_t ldv, int k, con
 // k_multidot_part's chunks, in its per-thread order and block tree.  The
 // results are bitwise those of k_multiaxpy followed by launch_multidot; V and
 // w are read once instead of twice.
-template <int KMAX, bool NORM>
+template <int KMAX, int U, bool NORM>
 __global__ void __launch_bounds__(256, 2) k_multiaxpy_dot(double* __restrict__ w,
                                                        const double* __restrict__ V, int64_t ldv,
                                                        int k, const double* __restrict__ h,
@@ -381,7 +402,37 @@ __global__ void __launch_bounds__(256, 2) k_multiaxpy_dot(double* __restrict__ w
   double d[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) d[q] = 0.0;
-  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+  // U elements per thread at a time, loads first, then the updates
+  // and the partial sums in ascending i (the order of one at a time)
+  const int64_t st = blockDim.x;
+  int64_t i = b0 + threadIdx.x;
+  for (; i + (U - 1) * st < b1; i += U * st) {
+    double v[U][KMAX], wo[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      wo[u] = w[i + u * st];
+#pragma unroll
+      for (int q = 0; q < KMAX; ++q)
+        if (q < k) v[u][q] = V[(int64_t)q * ldv + i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < KMAX; ++q)
+        if (q < k) acc = fma(s_h[q], v[u][q], acc);
+      const double wn = fma(sign, acc, wo[u]);
+      w[i + u * st] = wn;
+      if (NORM) {
+        d[0] = fma(wn, wn, d[0]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < ND; ++q)
+          if (q < k) d[q] = fma(v[u][q], wn, d[q]);
+      }
+    }
+  }
+  for (; i < b1; i += st) {
     double v[KMAX];
 #pragma unroll
     for (int q = 0; q < KMAX; ++q)
@@ -401,19 +452,20 @@ __global__ void __launch_bounds__(256, 2) k_multiaxpy_dot(double* __restrict__ w
     }
   }
   const int kk = NORM ? 1 : k;
+  constexpr int QN = ND < 8 ? ND : 8;  // columns per block tree
 #pragma unroll
-  for (int j0 = 0; j0 < ND; j0 += 8) {
+  for (int j0 = 0; j0 < ND; j0 += QN) {
     if (j0 < kk) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = j0 + q < ND ? d[j0 + q] : 0.0;
+      for (int q = 0; q < QN; ++q) red[q][threadIdx.x] = d[j0 + q];
       __syncthreads();
       for (int o = 128; o > 0; o >>= 1) {
         if (threadIdx.x < (unsigned)o)
 #pragma unroll
-          for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+          for (int q = 0; q < QN; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
         __syncthreads();
       }
-      if (threadIdx.x < 8 && j0 + (int)threadIdx.x < kk)
+      if (threadIdx.x < QN && j0 + (int)threadIdx.x < kk)
         part[(int64_t)blockIdx.x * kk + j0 + threadIdx.x] = red[threadIdx.x][0];
       __syncthreads();
     }
@@ -430,16 +482,21 @@ cudaError_t launch_multiaxpy_dot(double* w, const double* V, int64_t ldv, int k,
                 : launch_multidot(V, ldv, k, w, n, part, out, st);
   }
   const int kk = norm ? 1 : k;
+  // fewer columns, more elements per thread in flight
   if (norm) {
-    if (k <= 8)
-      k_multiaxpy_dot<8, true><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+    if (k <= 4)
+      k_multiaxpy_dot<4, 4, true><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+    else if (k <= 8)
+      k_multiaxpy_dot<8, 2, true><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
     else
-      k_multiaxpy_dot<16, true><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+      k_multiaxpy_dot<16, 1, true><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
   } else {
-    if (k <= 8)
-      k_multiaxpy_dot<8, false><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+    if (k <= 4)
+      k_multiaxpy_dot<4, 4, false><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+    else if (k <= 8)
+      k_multiaxpy_dot<8, 2, false><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
     else
-      k_multiaxpy_dot<16, false><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
+      k_multiaxpy_dot<16, 1, false><<<kMultidotBlocks, 256, 0, st>>>(w, V, ldv, k, h, sign, n, part);
   }
   k_multidot_final<<<kk, 256, 0, st>>>(part, kMultidotBlocks, kk, out);
   return cudaGetLastError();

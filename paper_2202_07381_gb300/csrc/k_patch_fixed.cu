@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kFxWarps * 32, MB) k_vanka_apply_kron_fx(FxApp
   const int64_t w = (int64_t)blockIdx.x * kFxWarps + warp;
   if (w >= P.count) return;
   unsigned char* base = dyn + (size_t)warp * fx_warp_bytes(P.s, P.nsrc, P.nt, P.nmax);
-  const int64_t pi = P.first + w;
+  const int64_t pi = fx_pi(P, w);
   const int n = P.np[pi];
   if (n == kFxN2)
     fx_patch<kFxN2, RC, U, TR>(P, fac, base, lane, pi, n);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kFxWarps * 32, MB) k_vanka_apply_kron_fx_pair(
   const int64_t w = (int64_t)blockIdx.x * kFxWarps + warp;
   if (w >= P.count) return;
   unsigned char* base = dyn + (size_t)warp * warp_bytes;
-  const int64_t pi = P.first + w;
+  const int64_t pi = fx_pi(P, w);
   const int n = P.np[pi];
   if (n == kFxN2)
     fx_patch_pair<U, REAL>(P, fac, base, lane, pi);
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kFxStagedThreads, 1)
   int64_t ox = 0;
   auto meta = [&](int64_t k) {
     if (k < nmine) {
-      const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+      const int64_t pi = fx_pi(P, blockIdx.x + k * gridDim.x);
       nx = P.np[pi];
       ox = P.fac_off[pi];
     }
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kFxStagedThreads, 1)
       gix = t * P.m + G[i];
       rv = P.r[gix];
       if (P.ybuf)
-        qo = P.qoff[P.first + blockIdx.x + k * gridDim.x];
+        qo = P.qoff[fx_pi(P, blockIdx.x + k * gridDim.x)];
       else
         ov = P.out[gix];
     }
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kFxStagedThreads, 1)
   for (int64_t k = 0; k < nmine; ++k) {
     const int st = (int)(k % S.stages);
     const int n = s_n[st];
-    const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+    const int64_t pi = fx_pi(P, blockIdx.x + k * gridDim.x);
     const int2* X = reinterpret_cast<const int2*>(dyn + (size_t)st * S.stage_bytes);
     const int nn = n * n;
     const int16_t* fe = P.fexp + pi * P.nm * nmax;
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kFxStagedThreads, 1)
         x += h * s_x[tau * n + i];
       }
       if (P.ybuf)
-        P.ybuf[t * P.Q + qk + i] = x;
+        P.ybuf[t * P.Q + qk + i * P.ys] = x;
       else
         P.out[gk] = ok_ + P.scale * x;
     }
@@ -531,9 +531,16 @@ FxApply fx_params(Ctx& C, Level& L, int colour, const double* r, double* out, do
     P.ybuf = C.d_Y;
     P.qoff = L.d_qoff;
     P.Q = L.Q;
+    P.ys = L.ystride;
+    P.perm = L.d_perm;
   } else {
     P.first = L.colour_start[colour];
     P.count = L.colour_start[colour + 1] - P.first;
+    P.ybuf = nullptr;
+    P.qoff = nullptr;
+    P.Q = 0;
+    P.ys = 1;
+    P.perm = nullptr;
   }
   P.nmax = L.kron_nmax;
   return P;

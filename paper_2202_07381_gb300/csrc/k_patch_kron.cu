@@ -38,17 +38,25 @@ struct KronApply {
   double scale;
   int64_t first, count;  // ordered-patch range of this colour (or of all patches)
   int nmax;              // per-warp shared-memory stride
-  // one-launch mode: the patch results go to ybuf[t·Q + qoff[p] + i] instead
-  // of out, and k_vanka_reduce adds them up per DoF afterwards
+  // one-launch mode: the patch results go to ybuf[t·Q + qoff[p] + i·ys]
+  // instead of out, and k_vanka_reduce adds them up per DoF afterwards; the
+  // launch takes the ordered patches perm[0], perm[1], ... (vertex order)
   double* ybuf;
   const int64_t* qoff;
   int64_t Q;
+  int64_t ys;
+  const int32_t* perm;
   // tasks reading each stored matrix (at most two: the complex layout applies
   // X and Y to both sources of a pair), -1 if unused
   int mat_task[kKronMaxTasks][2];
   // G and H rounded to FP32, for the FP32-accumulating paired apply
   float Gf[kKronMaxSrc * 3], Hf[3 * kKronMaxTasks];
 };
+
+// Ordered patch index of the k-th patch a launch takes.
+__device__ __forceinline__ int64_t kron_pi(const KronApply& P, int64_t k) {
+  return P.perm ? (int64_t)P.perm[P.first + k] : P.first + k;
+}
 
 // The stage mixing around the patch solves (sources from the gathered
 // residual by the rows of T⁻¹, results back by T) runs in the patch
@@ -146,7 +154,7 @@ __device__ __forceinline__ void kron_patch(const KronApply& P, const T* __restri
       x = fma(h, s_accm[tau * n + i], x);
     }
     if (P.ybuf)
-      P.ybuf[t * P.Q + P.qoff[pi] + i] = (double)x;
+      P.ybuf[t * P.Q + P.qoff[pi] + i * P.ys] = (double)x;
     else
       P.out[t * P.m + s_g[i]] += P.scale * (double)x;
   }
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(kKronWarps * 32) k_vanka_apply_kron(KronApply 
   const int64_t w = (int64_t)blockIdx.x * kKronWarps + warp;
   if (w >= P.count) return;
   unsigned char* base = dyn + (size_t)warp * kron_warp_bytes(P.s, P.ns, P.nt, P.nmax, sizeof(T));
-  kron_patch<T, R, TR>(P, fac, base, lane, P.first + w);
+  kron_patch<T, R, TR>(P, fac, base, lane, kron_pi(P, w));
 }
 
 // ---------------------------------------------------------------------------
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(kKronWarps * 32, 4) k_vanka_apply_kron_pair32(
   const int64_t w = (int64_t)blockIdx.x * kKronWarps + warp;
   if (w >= P.count) return;
   unsigned char* base = dyn + (size_t)warp * warp_bytes;
-  const int64_t pi = P.first + w;
+  const int64_t pi = kron_pi(P, w);
   if (P.np[pi] != N) {
     kron_patch_f32_generic(P, fac, base, lane, pi);
     return;
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(kKronWarps * 32, 4) k_vanka_apply_kron_pair32(
 #pragma unroll
       for (int tau = 0; tau < NT; ++tau) x = fmaf(P.Hf[t * kKronMaxTasks + tau], sm.acc[tau * N + i], x);
       if (P.ybuf)
-        P.ybuf[t * P.Q + qo + i] = (double)x;
+        P.ybuf[t * P.Q + qo + i * P.ys] = (double)x;
       else
         P.out[t * P.m + sm.g[i]] += P.scale * (double)x;
     }
@@ -367,7 +375,7 @@ __global__ void __launch_bounds__(kKronBigThreads)
   const int64_t w = blockIdx.x;
   if (w >= P.count) return;
   const int tid = threadIdx.x;
-  const int64_t pi = P.first + w;
+  const int64_t pi = kron_pi(P, w);
   const int n = P.np[pi];
   const int64_t nn = (int64_t)n * n;
   const T* X = fac + P.fac_off[pi];
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(kKronBigThreads)
     T x = (T)0;
     for (int tau = 0; tau < P.nt; ++tau) x = fma(mix_h<T>(P, t * kKronMaxTasks + tau), s_accm[tau * n + i], x);
     if (P.ybuf)
-      P.ybuf[t * P.Q + P.qoff[pi] + i] = (double)x;
+      P.ybuf[t * P.Q + P.qoff[pi] + i * P.ys] = (double)x;
     else
       P.out[t * P.m + s_g[i]] += P.scale * (double)x;
   }
@@ -516,7 +524,7 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
   int64_t ox = 0;
   auto meta = [&](int64_t k) {
     if (k < nmine) {
-      const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+      const int64_t pi = kron_pi(P, blockIdx.x + k * gridDim.x);
       nx = P.np[pi];
       ox = P.fac_off[pi];
     }
@@ -560,7 +568,7 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
       gix = t * P.m + G[i];
       rv = P.r[gix];
       if (P.ybuf)
-        qo = P.qoff[P.first + blockIdx.x + k * gridDim.x];
+        qo = P.qoff[kron_pi(P, blockIdx.x + k * gridDim.x)];
       else
         ov = P.out[gix];
     }
@@ -621,7 +629,7 @@ __global__ void __launch_bounds__(kKronStagedThreads, 5)
         x = fma(h, s_accm[tau * n + i], x);
       }
       if (P.ybuf)
-        P.ybuf[t * P.Q + qk + i] = (double)x;
+        P.ybuf[t * P.Q + qk + i * P.ys] = (double)x;
       else
         P.out[gk] = ok_ + P.scale * (double)x;
     }
@@ -708,7 +716,7 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
           atomicCAS(&W.err[0], 0, IRKMG_ETIMEOUT);
         }
         if (s_abort) break;
-        const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+        const int64_t pi = kron_pi(P, blockIdx.x + k * gridDim.x);
         const int n = P.np[pi];
         const uint32_t bytes = (uint32_t)(mats_bytes(n) + (((int64_t)n * 4 + 15) & ~(int64_t)15));
         s_n[st] = n;
@@ -762,7 +770,7 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
       }
       return;
     }
-    const int64_t pi = P.first + blockIdx.x + k * gridDim.x;
+    const int64_t pi = kron_pi(P, blockIdx.x + k * gridDim.x);
     const int n = s_n[st];
     const int64_t nn = (int64_t)n * n;
     const T* X = reinterpret_cast<const T*>(dyn + (size_t)st * W.stage_bytes);
@@ -814,7 +822,7 @@ __global__ void __launch_bounds__(kWsThreads) k_vanka_apply_kron_ws(KronWs W, co
         x = fma(h, s_accm[tau * n + i], x);
       }
       if (P.ybuf)
-        P.ybuf[t * P.Q + P.qoff[pi] + i] = (double)x;
+        P.ybuf[t * P.Q + P.qoff[pi] + i * P.ys] = (double)x;
       else
         P.out[t * P.m + s_g[i]] += P.scale * (double)x;
     }
@@ -1033,12 +1041,16 @@ cudaError_t launch_vanka_kron(Ctx& C, Level& L, int colour, const double* r, dou
     P.ybuf = C.d_Y;
     P.qoff = L.d_qoff;
     P.Q = L.Q;
+    P.ys = L.ystride;
+    P.perm = L.d_perm;
   } else {
     P.first = L.colour_start[colour];
     P.count = L.colour_start[colour + 1] - P.first;
     P.ybuf = nullptr;
     P.qoff = nullptr;
     P.Q = 0;
+    P.ys = 1;
+    P.perm = nullptr;
   }
   P.nmax = L.kron_nmax;
   if (P.count <= 0) return cudaSuccess;
