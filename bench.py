@@ -66,6 +66,7 @@ NCU_TRAFFIC = {
     ("k_vanka_apply", "8f81809572f0"): 0.97,
     ("k_vanka_apply_kron", "60c2ce575b6a"): 1.02,
     ("k_vanka_apply_kron_fx_pair", "6850cc0d8407"): 1.096,
+    ("k_vanka_apply_kron_fx_pair", "4975a091f1c6"): 1.089,
     ("k_vanka_apply_kron_pair32", "8f68162f379b"): 1.110,
 }
 KERNEL_FILE = {"k_vanka_apply": "k_patch.cu", "k_vanka_apply_staged": "k_patch.cu",
@@ -932,10 +933,9 @@ def run_ours(args, wl, rank, world, local_rank):
                                        "FP64 FMAs" if prec == 64 else "FP32 patch entries"),
                        "op_fixed": opfx,
                        "op_arith": ("FP64 data; stage operator as exact integer dot products of "
-                                    "57-bit fixed-point rows and 58-bit fixed-point iterates "
-                                    "(stage mixing applied exactly to the iterate, rounded once), "
-                                    "each sum rounded once to FP64, at most three sums added in "
-                                    "FP64" if opfx else "FP64 FMAs"),
+                                    "57-bit fixed-point rows and 58-bit fixed-point iterates, "
+                                    "each sum rounded once to FP64, K x + B p added and the "
+                                    "stage mixing applied in FP64" if opfx else "FP64 FMAs"),
                        "apply_kernel_per_level": [lv["apply_kernel"] for lv in ctx.levels[1:]],
                        "apply_shape_per_level": [lv["apply_shape"] for lv in ctx.levels[1:]],
                        "l2": "no flush: inputs larger than L2 (finest patch inverses %.1f GB)"

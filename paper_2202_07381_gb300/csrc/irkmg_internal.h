@@ -185,10 +185,13 @@ struct Level {
   double cheb_lo = 2.0, cheb_hi = 8.0; // Chebyshev interval of this level's smoother
   // one-launch relaxation of a decoupled level: patch results to Ctx::d_Y at
   // t·Q + qoff[p] + i·ystride, then the per-DoF sum over the contribution
-  // lists.  Row-major over (local row i, patch vertex v): qoff[p] = v and
-  // ystride = the vertex count rounded up to 32, so that consecutive
-  // vertices' results for one local row are adjacent; the launch takes the
-  // patches in vertex order (d_perm: ordered index of vertex v's patch).
+  // lists.  Warp-per-patch levels: row-major over (local row i, patch vertex
+  // v), qoff[p] = v and ystride = the vertex count rounded up to 32, so that
+  // consecutive vertices' results for one local row are adjacent, and the
+  // launch takes the patches in vertex order (d_perm: ordered index of
+  // vertex v's patch).  Large-patch (3D) levels: each patch's results
+  // contiguous (qoff[p] = Σ n over the patches before it, ystride 1), the
+  // patches in colour order (d_perm null).
   bool single = false;
   int64_t Q = 0;                       // stage stride of d_Y: n_max · ystride
   int64_t Qent = 0;                    // Σ n over the patches

@@ -2,9 +2,9 @@
 3.1: J = I_s ⊗ [[M,0],[0,0]] + dt A ⊗ [[K,B],[Bᵀ,0]]) with the oracle.
 
 Operator rows are 57-bit fixed point with a power of two per row, the iterate
-58-bit integers with a power of two per velocity / pressure group, the stage
-mixing dt A applied exactly to the iterate and rounded once, each product sum
-exact and rounded once, at most three sums added per output.  The bar is that
+58-bit integers with a power of two per velocity / pressure group, each
+product sum (M x_t, K x_t, B p_t, Bᵀ u_t) exact and rounded once, K x_t + B p_t
+added and the stage mixing dt A applied in FP64.  The bar is that
 of the FP64 operator, 1e-13 relative (l2 and entry-wise), on every level; the
 fixed-point result is at least as close to the oracle as the FP64 one (up to
 a factor 2); scaling x by 2^±500 scales J x bit for bit; the FGMRES solution
