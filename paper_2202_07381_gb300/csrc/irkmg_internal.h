@@ -196,7 +196,7 @@ struct Level {
   int64_t Q = 0;                       // stage stride of d_Y: n_max · ystride
   int64_t Qent = 0;                    // Σ n over the patches
   int64_t ystride = 1;
-  int64_t* d_qoff = nullptr;           // per ordered patch: its vertex
+  int64_t* d_qoff = nullptr;           // per ordered patch: its vertex (large patches: Σ n before it)
   int32_t* d_perm = nullptr;           // per vertex: ordered index of its patch
   int32_t *d_cptr = nullptr, *d_cidx = nullptr;  // spatial DoF -> entries qoff[p] + i·ystride
   double reduce_bytes = 0.0;           // algorithmic bytes of one reduction launch
